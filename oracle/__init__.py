@@ -1,0 +1,13 @@
+"""FP64 CPU oracle for the MBE(3)-OSV-MP2 pair-solve path.
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
+The product path (``paper_2603_16575_gb300``) never does, and the two share
+no code.
+"""
+from .osv_mp2 import (  # noqa: F401
+    semicanonical_tii, osv_from_tii, build_osv, pair_basis, swap_blocks,
+    exchange_block, preconditioner, Fragment, FragmentResult, solve_fragment,
+    solve_fragment_dense, canonical_mp2_energy, dist2, mbe3_fragments,
+    OSVSystem, fragment_gradient, mbe3_energy_gradient,
+)
