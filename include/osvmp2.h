@@ -1,0 +1,189 @@
+/*
+ * osvmp2.h -- C ABI of the GB300 MBE(3)-OSV-MP2 pair-solve library (libosvmp2.so).
+ *
+ * Method: Liang & Yang, "Multi-GPU MBE(3)-OSV-MP2 for Performant Large-Scale
+ * ab initio Calculations" (arXiv 2603.16575).  The library computes, on one
+ * GPU, the data-parallel path of that method:
+ *   A0  OSVs of every occupied LMO (Eq. osv_gen from the semi-canonical T_ii of
+ *       Eq. mp2_tkk), kept where omega >= l_osv                 -> osvmp2_build_osv
+ *   A1  OSV projection of the RI integrals (Eq. osv_imua)
+ *   A2  pair blocks K (Eq. osv_close_k), S and F (Eq. 4block_osv, Algorithm 5)
+ *                                                              -> osvmp2_pair_integrals
+ *   A3  preconditioner F X = S X E~ per pair (Eq. prec_eig)
+ *   A4  residual iterations per fragment (Eq. res_close, Algorithm 7)
+ *                                                              -> osvmp2_solve
+ *   A5  MBE(3) energy (Eqs. tmbediag-deltaoff as fragment weights)
+ *                                                              -> osvmp2_mbe3_energy
+ *   A6  frozen-OSV adjoint dE/dB, dE/de_vir, dE/df             -> osvmp2_energy_grad
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an osvmp2_status; nothing throws across the ABI.
+ *     On failure osvmp2_last_error(ctx) gives a one-line reason.
+ *   - Arrays are row-major, innermost index last, FP64 unless stated.
+ *     "device" = memory of the ctx's GPU (cudaMalloc / torch CUDA tensors);
+ *     "host" = ordinary CPU memory.  The caller owns every pointer it passes;
+ *     the library never frees them and keeps no reference after the call
+ *     returns, except the osvmp2_system arrays, which must stay valid and
+ *     unchanged until the next osvmp2_build_osv or osvmp2_destroy.
+ *   - Work is queued on the ctx's stream.  Calls that return host scalars
+ *     (energies, counts) synchronise that stream before returning.
+ *   - Memory the method needs between calls (OSVs, projected integrals, pair
+ *     blocks, preconditioners, amplitudes, workspace) is owned by the ctx and
+ *     allocated with cudaMalloc on the ctx's device; OSVMP2_E_NOMEM if that fails.
+ *   - A ctx is not thread-safe; use one ctx per host thread.
+ *   - Energies are in Hartree, distances in Angstrom.
+ */
+#ifndef OSVMP2_H
+#define OSVMP2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct osvmp2_ctx osvmp2_ctx;
+
+typedef enum {
+  OSVMP2_OK = 0,
+  OSVMP2_E_ARG = 1,      /* invalid argument (null pointer, size, index, order) */
+  OSVMP2_E_CUDA = 2,     /* a CUDA runtime call or kernel launch failed */
+  OSVMP2_E_NOMEM = 3,    /* device allocation failed */
+  OSVMP2_E_NOCONV = 4,   /* amplitude iterations hit max_iter (see osvmp2_mbe_stats) */
+  OSVMP2_E_NUMERIC = 5,  /* eigen-solver did not converge or produced non-finite values */
+  OSVMP2_E_STATE = 6     /* call order violated (e.g. pair_integrals before build_osv) */
+} osvmp2_status;
+
+/* Arithmetic of the projection/exchange contractions (A1-A2) and of the residual
+ * products (A4).  OSV eigen-decomposition, preconditioner, update denominators
+ * and every energy accumulation are FP64 in all forms. */
+typedef enum {
+  OSVMP2_FP64 = 0,   /* all FP64 on the CUDA cores */
+  OSVMP2_MIXED = 1   /* split-precision products with FP32 accumulation, FP64 elsewhere */
+} osvmp2_prec;
+
+typedef struct {
+  double tau_s;       /* drop S_(ij,ij) eigenvalues below tau_s * max eigenvalue (default 1e-10) */
+  double tol_update;  /* stop when max |R~ / D| below this ...                (default 1e-11) */
+  double tol_energy;  /* ... and |E_C(it) - E_C(it-1)| below this, Eh         (default 1e-13) */
+  int32_t max_iter;   /* amplitude iterations per fragment                    (default 100) */
+  int32_t reserved[7];
+} osvmp2_opts;
+
+/* Synthetic or caller-supplied system.  All arrays are read by the kernels. */
+typedef struct {
+  int32_t n_occ, n_vir, n_aux;
+  const double *B;      /* device [n_occ][n_vir][n_aux] RI integrals (ia|P), or NULL:
+                           regenerate on the device as B = env[i][a] * z(seed,i,a,P) */
+  uint64_t seed;        /* generator seed when B == NULL (counter-based, SplitMix64) */
+  const double *env;    /* device [n_occ][n_vir] envelope, required when B == NULL */
+  const double *f_occ;  /* device [n_occ][n_occ] symmetric occupied (LMO) Fock block */
+  const double *e_vir;  /* device [n_vir] canonical virtual orbital energies */
+  const double *r_occ;  /* host [n_occ][3] LMO centres (fragment lists); may be NULL
+                           if osvmp2_mbe3_energy / osvmp2_energy_grad are not used */
+} osvmp2_system;
+
+typedef struct {
+  int64_t n_single, n_pair, n_triple;  /* kept clusters */
+  int64_t n_pair_blocks;               /* unique pairs (i<=j) whose blocks were built */
+  int32_t max_iter_used;               /* largest iteration count over fragments */
+  int32_t n_unconverged;               /* fragments that hit max_iter */
+  int64_t worst_fragment;              /* index of the first unconverged fragment, or -1 */
+  double max_update;                   /* largest final max|R~/D| over fragments */
+  double flops;                        /* algorithmic FP operations of A1-A5 in this call */
+} osvmp2_mbe_stats;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a ctx on CUDA device `device` queueing work on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  opts may be NULL (defaults). */
+int osvmp2_create(osvmp2_ctx **ctx, int device, void *cuda_stream, const osvmp2_opts *opts);
+/* Release all ctx-owned device memory.  Safe on NULL. */
+void osvmp2_destroy(osvmp2_ctx *ctx);
+/* Last error message of this ctx ("" if none).  Valid until the next call on ctx. */
+const char *osvmp2_last_error(const osvmp2_ctx *ctx);
+/* Fill opts with the defaults listed in osvmp2_opts. */
+void osvmp2_default_opts(osvmp2_opts *opts);
+
+/* ---- A0: OSV generation (Eq. mp2_tkk, Eq. osv_gen, Algorithm 3's output) --
+ * For every occupied i: T_ii[a][b] = sum_P B[i,a,P] B[i,b,P] / (e_a + e_b - 2 f_ii),
+ * full FP64 symmetric eigen-decomposition on the GPU, keep eigenvectors with
+ * omega >= l_osv (all when l_osv <= 0), descending omega, each eigenvector signed
+ * so that its largest-magnitude entry is positive.
+ * n_osv_host: host [n_occ] out, OSV count per orbital.  Discards pair data of a
+ * previous system. */
+int osvmp2_build_osv(osvmp2_ctx *ctx, const osvmp2_system *sys, double l_osv, int32_t *n_osv_host);
+
+/* Copy Q_i (device [n_vir][n_osv_i], row-major) and omega_i (device [n_osv_i]) out. */
+int osvmp2_get_osv(osvmp2_ctx *ctx, int32_t i, double *Q_dev, double *omega_dev);
+
+/* ---- A1-A2: pair integrals (Eq. osv_imua, Eq. osv_close_k, Algorithm 5) -----
+ * pairs: host [n_pairs][2], 0-based, i <= j.  For every listed pair and every
+ * diagonal pair (i,i) of its orbitals, build on the device:
+ *   B~_i^(x) = B[i]^T Q_x (aux x OSV), K_(ij,ij) = (P^T B_i)(P^T B_j)^T,
+ *   S_(x,y) = Q_x^T Q_y and F_(x,y) = Q_x^T diag(e_vir) Q_y with P = [Q_i Q_j]
+ *   (P_ii = Q_i), then the preconditioner X, e~ of Eq. prec_eig.
+ * Pairs already built are skipped.  prec selects the contraction arithmetic. */
+int osvmp2_pair_integrals(osvmp2_ctx *ctx, const int32_t *pairs, int64_t n_pairs, osvmp2_prec prec);
+
+/* Copy the blocks of built pair (i,j), i<=j, to device buffers of m*m doubles,
+ * m = n_i + n_j (n_i if i == j); any output may be NULL. */
+int osvmp2_get_pair_blocks(osvmp2_ctx *ctx, int32_t i, int32_t j, double *K_dev, double *S_dev,
+                           double *F_dev);
+
+/* ---- A3-A4: OSV-MP2 solve of one subsystem (Eq. res_close, Algorithm 7) ----
+ * orbs: host [n_orbs] distinct occupied indices (e.g. all of them).  Solves the
+ * coupled residual equations of every pair in the subsystem (k summed over the
+ * subsystem only), Jacobi sweeps preconditioned by Eq. prec_eig.
+ * e_out: host scalar, E = sum_{i,j in orbs} <K_(ij), 2T_(ij) - T_(ij)^T>.
+ * pair_e_out: host [n_orbs*(n_orbs+1)/2] or NULL: pair energies for i<=j in the
+ * order (orbs[0],orbs[0]), (orbs[0],orbs[1]), ...; i != j counted twice.
+ * iters_out: host scalar or NULL. */
+int osvmp2_solve(osvmp2_ctx *ctx, const int32_t *orbs, int32_t n_orbs, osvmp2_prec prec,
+                 double *e_out, double *pair_e_out, int32_t *iters_out);
+
+/* ---- A5: MBE(3) energy ------------------------------------------------------
+ * Fragments: every single; every pair with |r_i - r_j|^2 <= r2_cut^2; every
+ * triple whose three pairs satisfy d^2 <= r3_cut^2 and are kept pairs.
+ * E = sum_C c_C E_C with c_ijk = 1, c_ij = 1 - #kept triples containing ij,
+ * c_i = 1 - #kept pairs containing i + #kept triples containing i.
+ * Builds the needed pair integrals, solves all fragments in one persistent
+ * launch, and accumulates E in FP64 in fragment order.  stats may be NULL. */
+int osvmp2_mbe3_energy(osvmp2_ctx *ctx, double r2_cut, double r3_cut, osvmp2_prec prec,
+                       double *e_out, osvmp2_mbe_stats *stats);
+
+/* Fragment list of the last osvmp2_mbe3_energy / osvmp2_energy_grad call:
+ * host outputs, each may be NULL: orbs [n][3] (-1 padded), weights [n],
+ * energies [n] (E_C).  *n_frag_out receives the count (also when arrays are NULL). */
+int osvmp2_fragment_results(osvmp2_ctx *ctx, int64_t *n_frag_out, int32_t *orbs, int32_t *weights,
+                            double *energies);
+
+/* Host-only fragment enumeration with the rule of osvmp2_mbe3_energy.
+ * r_occ host [n_occ][3].  If orbs_out (host [cap][3]) is non-NULL and cap is
+ * large enough, writes the list (singles, pairs, triples, each lexicographic)
+ * and weights_out (host [cap]).  *n_out = number of fragments. */
+int osvmp2_mbe3_fragments(const double *r_occ, int32_t n_occ, double r2_cut, double r3_cut,
+                          int64_t cap, int32_t *orbs_out, int32_t *weights_out, int64_t *n_out);
+
+/* ---- A6: frozen-OSV gradient --------------------------------------------
+ * MBE(3) energy as osvmp2_mbe3_energy, plus (device outputs, each may be NULL):
+ *   dE_dB [n_occ][n_vir][n_aux]: dE/dB[i,a,P] = 4 sum_C c_C sum_j (T~_ij^C B_j)[a,P]
+ *   dE_de [n_vir]              : 2 sum_C c_C sum_ij sum_b T~_ij^ab T_ij^ab
+ *   dE_df [n_occ][n_occ]       : symmetrised derivative w.r.t. the occupied Fock block
+ * with T~ = 2T - T^T in the full virtual space and the OSVs held fixed.  Outputs
+ * are overwritten. */
+int osvmp2_energy_grad(osvmp2_ctx *ctx, double r2_cut, double r3_cut, osvmp2_prec prec,
+                       double *e_out, double *dE_dB, double *dE_df, double *dE_de,
+                       osvmp2_mbe_stats *stats);
+
+/* ---- generator ---------------------------------------------------------
+ * Materialise B[i0:i0+n_i][n_vir][n_aux] = env[i][a] * z(seed,i,a,P) on the
+ * device (out: device [n_i][n_vir][n_aux]); z is the Irwin-Hall(12) normal from
+ * three SplitMix64 draws defined in the synthetic-input module. */
+int osvmp2_generate_B(int32_t n_occ, int32_t n_vir, int32_t n_aux, uint64_t seed, const double *env,
+                      int32_t i0, int32_t n_i, double *out, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OSVMP2_H */

@@ -1,0 +1,796 @@
+// Host runtime of libosvmp2: the C ABI entry points, the ctx that owns the
+// device-resident OSV / pair store, job lists for the kernels, and the MBE(3)
+// fragment enumeration.  All arithmetic of the method runs in the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "osvmp2.h"
+#include "internal.h"
+
+using namespace osv;
+
+namespace {
+
+constexpr uint64_t STREAM_MUL = 0xD1B54A32D192ED03ull;
+constexpr uint64_t STREAM_B = 5;   // stream id of B in the generator definition
+
+struct Frag {
+  int orbs[3];
+  int weight;
+};
+
+}  // namespace
+
+struct osvmp2_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  osvmp2_opts opts{};
+  std::string err;
+  int num_sms = 148;
+  std::vector<void*> sys_allocs;     // freed when a new system is set
+  // system
+  bool have_sys = false;
+  osvmp2_system sys{};
+  uint64_t key = 0;
+  std::vector<double> r_occ;
+  // OSVs
+  bool have_osv = false;
+  std::vector<int> n_osv;
+  std::vector<double*> Qp, Wp;
+  int cap_pairs = 0;
+  // device tables
+  int* n_osv_d = nullptr;
+  double** Q_d = nullptr;
+  int* sf_id_d = nullptr;
+  double** S_d = nullptr;
+  double** F_d = nullptr;
+  int* pair_id_d = nullptr;
+  double** K_d = nullptr;
+  double** X_d = nullptr;
+  double** et_d = nullptr;
+  int* r_d = nullptr;
+  int* err_d = nullptr;
+  double* scal_d = nullptr;          // device scalars (energies)
+  // host mirrors
+  std::vector<int> sf_id, pair_id, bt_id;
+  std::vector<double*> S_h, F_h, K_h, X_h, et_h, bt_h;
+  std::vector<int> m_h;
+  std::vector<int> pi_h, pj_h;       // pair id -> (i, j)
+  // last MBE call
+  std::vector<Frag> frags;
+  std::vector<FragOut> frag_out;
+};
+
+namespace {
+
+int fail(osvmp2_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? OSVMP2_E_NOMEM : OSVMP2_E_CUDA,        \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define TRY(expr)          \
+  do {                     \
+    int s_ = (expr);       \
+    if (s_) return s_;     \
+  } while (0)
+
+int dalloc(osvmp2_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, OSVMP2_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->sys_allocs.push_back(*p);
+  return 0;
+}
+template <class T>
+int dalloc_t(osvmp2_ctx* c, T** p, size_t n) {
+  return dalloc(c, reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+// Temporary device buffer freed at scope exit.
+struct Tmp {
+  void* p = nullptr;
+  ~Tmp() {
+    if (p) cudaFree(p);
+  }
+};
+int tmp_alloc(osvmp2_ctx* c, Tmp& t, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&t.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    t.p = nullptr;
+    return fail(c, OSVMP2_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  return 0;
+}
+
+void free_system(osvmp2_ctx* c) {
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (void* p : c->sys_allocs) cudaFree(p);
+  c->sys_allocs.clear();
+  c->have_sys = c->have_osv = false;
+  c->n_osv.clear(); c->Qp.clear(); c->Wp.clear();
+  c->sf_id.clear(); c->pair_id.clear(); c->bt_id.clear();
+  c->S_h.clear(); c->F_h.clear(); c->K_h.clear(); c->X_h.clear(); c->et_h.clear(); c->bt_h.clear();
+  c->m_h.clear(); c->pi_h.clear(); c->pj_h.clear();
+  c->frags.clear(); c->frag_out.clear();
+  c->n_osv_d = nullptr; c->Q_d = nullptr; c->sf_id_d = nullptr; c->S_d = c->F_d = nullptr;
+  c->pair_id_d = nullptr; c->K_d = c->X_d = c->et_d = nullptr; c->r_d = nullptr;
+}
+
+Tables tables(const osvmp2_ctx* c) {
+  Tables t;
+  t.n_occ = c->sys.n_occ;
+  t.n_vir = c->sys.n_vir;
+  t.n_osv = c->n_osv_d;
+  t.Q = c->Q_d;
+  t.sf_id = c->sf_id_d;
+  t.S = c->S_d;
+  t.F = c->F_d;
+  t.pair_id = c->pair_id_d;
+  t.K = c->K_d;
+  t.X = c->X_d;
+  t.et = c->et_d;
+  t.r = c->r_d;
+  t.f_occ = c->sys.f_occ;
+  return t;
+}
+
+BSrc bsrc(const osvmp2_ctx* c) {
+  return BSrc{c->sys.B, c->sys.env, c->key, c->sys.n_vir, c->sys.n_aux};
+}
+
+int check_err_flag(osvmp2_ctx* c, const char* where) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaGetLastError());
+  if (h & ERR_EIG) return fail(c, OSVMP2_E_NUMERIC, "%s: eigen-solver did not converge", where);
+  if (h & ERR_NONFINITE) return fail(c, OSVMP2_E_NUMERIC, "%s: non-finite values", where);
+  if (h & ERR_SIZE) return fail(c, OSVMP2_E_NUMERIC, "%s: size limit exceeded", where);
+  return 0;
+}
+
+template <class T>
+int upload(osvmp2_ctx* c, T* dst, const std::vector<T>& src) {
+  if (src.empty()) return 0;
+  CK(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, c->st));
+  return 0;
+}
+
+double dist2(const double* r, int i, int j) {
+  const double dx = r[3 * i] - r[3 * j];
+  const double dy = r[3 * i + 1] - r[3 * j + 1];
+  const double dz = r[3 * i + 2] - r[3 * j + 2];
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// Kept clusters and inclusion-exclusion weights (singles, pairs, triples; each
+// lexicographic).  Squared distances are compared with the squared cutoffs.
+void enumerate_fragments(const double* r, int n, double r2, double r3, std::vector<Frag>& out) {
+  out.clear();
+  const double c2 = r2 * r2, c3 = r3 * r3;
+  std::vector<unsigned char> ok2((size_t)n * n, 0), ok3((size_t)n * n, 0);
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      if (i == j) continue;
+      const double d = dist2(r, i, j);
+      ok2[(size_t)i * n + j] = d <= c2;
+      ok3[(size_t)i * n + j] = (d <= c3) && (d <= c2);
+    }
+  std::vector<int> pair_cnt(n, 0), tri_cnt(n, 0), tri_pair((size_t)n * n, 0);
+  std::vector<Frag> pairs, triples;
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++)
+      if (ok2[(size_t)i * n + j]) {
+        pairs.push_back(Frag{{i, j, -1}, 0});
+        pair_cnt[i]++;
+        pair_cnt[j]++;
+      }
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) {
+      if (!ok3[(size_t)i * n + j]) continue;
+      for (int k = j + 1; k < n; k++) {
+        if (!ok3[(size_t)i * n + k] || !ok3[(size_t)j * n + k]) continue;
+        triples.push_back(Frag{{i, j, k}, 1});
+        tri_cnt[i]++; tri_cnt[j]++; tri_cnt[k]++;
+        tri_pair[(size_t)i * n + j]++;
+        tri_pair[(size_t)i * n + k]++;
+        tri_pair[(size_t)j * n + k]++;
+      }
+    }
+  for (int i = 0; i < n; i++) out.push_back(Frag{{i, -1, -1}, 1 - pair_cnt[i] + tri_cnt[i]});
+  for (auto& p : pairs) {
+    p.weight = 1 - tri_pair[(size_t)p.orbs[0] * n + p.orbs[1]];
+    out.push_back(p);
+  }
+  for (auto& t : triples) out.push_back(t);
+}
+
+int pair_dim_h(const osvmp2_ctx* c, int i, int j) { return c->n_osv[i] + (i != j ? c->n_osv[j] : 0); }
+
+// Build S/F blocks, projections, K and preconditioners for every listed pair
+// (and the diagonal pairs of its orbitals) that is not built yet.
+int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osvmp2_prec prec) {
+  if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "osvmp2_build_osv has not been called");
+  if (prec != OSVMP2_FP64 && prec != OSVMP2_MIXED) return fail(c, OSVMP2_E_ARG, "unknown precision %d", (int)prec);
+  const int n = c->sys.n_occ;
+  std::vector<std::pair<int, int>> newp;
+  auto want = [&](int i, int j) {
+    if (c->pair_id[(size_t)i * n + j] == -1) {
+      c->pair_id[(size_t)i * n + j] = -2;   // mark as pending
+      newp.push_back({i, j});
+    }
+  };
+  for (auto& p : req) {
+    int i = p.first, j = p.second;
+    if (i < 0 || j < 0 || i >= n || j >= n || i > j)
+      return fail(c, OSVMP2_E_ARG, "pair (%d,%d) invalid: need 0 <= i <= j < n_occ", i, j);
+    want(i, i);
+    want(j, j);
+    want(i, j);
+  }
+  if (newp.empty()) return 0;
+  std::sort(newp.begin(), newp.end());
+  const int nv = c->sys.n_vir, nx = c->sys.n_aux;
+  // S/F blocks
+  std::vector<SFJob> sfj;
+  size_t sf_doubles = 0;
+  for (auto& p : newp) {
+    const size_t id = (size_t)p.first * n + p.second;
+    if (c->sf_id[id] == -1) {
+      c->sf_id[id] = -2;
+      sfj.push_back(SFJob{p.first, p.second, nullptr, nullptr});
+      sf_doubles += 2 * (size_t)c->n_osv[p.first] * c->n_osv[p.second];
+    }
+  }
+  // projections B~_i^(x)
+  std::vector<ProjJob> pj;
+  size_t bt_doubles = 0;
+  auto want_bt = [&](int i, int x) {
+    const size_t id = (size_t)i * n + x;
+    if (c->bt_id[id] == -1) {
+      c->bt_id[id] = -2;
+      pj.push_back(ProjJob{i, x, nullptr});
+      bt_doubles += (size_t)nx * c->n_osv[x];
+    }
+  };
+  for (auto& p : newp) {
+    want_bt(p.first, p.first);
+    if (p.first != p.second) {
+      want_bt(p.first, p.second);
+      want_bt(p.second, p.first);
+      want_bt(p.second, p.second);
+    }
+  }
+  size_t k_doubles = 0;
+  int max_m = 0, max_n = 0, max_nx = 0;
+  for (auto& p : newp) {
+    const int m = pair_dim_h(c, p.first, p.second);
+    k_doubles += 2 * (size_t)m * m + m;
+    max_m = std::max(max_m, m);
+  }
+  for (int i = 0; i < n; i++) max_n = std::max(max_n, c->n_osv[i]);
+  max_nx = max_n;
+  double *sf_mem = nullptr, *bt_mem = nullptr, *k_mem = nullptr;
+  TRY(dalloc_t(c, &sf_mem, sf_doubles));
+  TRY(dalloc_t(c, &bt_mem, bt_doubles));
+  TRY(dalloc_t(c, &k_mem, k_doubles));
+  {
+    size_t off = 0;
+    for (auto& j : sfj) {
+      const size_t sz = (size_t)c->n_osv[j.x] * c->n_osv[j.y];
+      j.S = sf_mem + off;
+      j.F = sf_mem + off + sz;
+      off += 2 * sz;
+      c->sf_id[(size_t)j.x * n + j.y] = (int)c->S_h.size();
+      c->S_h.push_back(j.S);
+      c->F_h.push_back(j.F);
+    }
+  }
+  {
+    size_t off = 0;
+    for (auto& j : pj) {
+      j.out = bt_mem + off;
+      off += (size_t)nx * c->n_osv[j.x];
+      c->bt_id[(size_t)j.i * n + j.x] = (int)c->bt_h.size();
+      c->bt_h.push_back(j.out);
+    }
+  }
+  std::vector<KJob> kj;
+  std::vector<PJob> pjb;
+  std::vector<int> new_ids;
+  {
+    size_t off = 0;
+    for (auto& p : newp) {
+      const int i = p.first, j = p.second, m = pair_dim_h(c, i, j);
+      const int pid = (int)c->K_h.size();
+      if (pid >= c->cap_pairs) return fail(c, OSVMP2_E_ARG, "pair capacity exceeded");
+      double* K = k_mem + off;
+      double* X = K + (size_t)m * m;
+      double* et = X + (size_t)m * m;
+      off += 2 * (size_t)m * m + m;
+      c->pair_id[(size_t)i * n + j] = pid;
+      c->K_h.push_back(K);
+      c->X_h.push_back(X);
+      c->et_h.push_back(et);
+      c->m_h.push_back(m);
+      c->pi_h.push_back(i);
+      c->pj_h.push_back(j);
+      auto bt = [&](int a, int x) { return c->bt_h[c->bt_id[(size_t)a * n + x]]; };
+      if (i == j) kj.push_back(KJob{i, j, bt(i, i), nullptr, nullptr, nullptr, K});
+      else kj.push_back(KJob{i, j, bt(i, i), bt(i, j), bt(j, i), bt(j, j), K});
+      pjb.push_back(PJob{i, j, X, et, c->r_d + pid});
+    }
+  }
+  // device tables
+  TRY(upload(c, c->sf_id_d, c->sf_id));
+  TRY(upload(c, c->pair_id_d, c->pair_id));
+  TRY(upload(c, c->S_d, c->S_h));
+  TRY(upload(c, c->F_d, c->F_h));
+  TRY(upload(c, c->K_d, c->K_h));
+  TRY(upload(c, c->X_d, c->X_h));
+  TRY(upload(c, c->et_d, c->et_h));
+  // job arrays
+  Tmp jsf, jpj, jk, jp, scr;
+  TRY(tmp_alloc(c, jsf, sfj.size() * sizeof(SFJob)));
+  TRY(tmp_alloc(c, jpj, pj.size() * sizeof(ProjJob)));
+  TRY(tmp_alloc(c, jk, kj.size() * sizeof(KJob)));
+  TRY(tmp_alloc(c, jp, pjb.size() * sizeof(PJob)));
+  if (!sfj.empty()) CK(cudaMemcpyAsync(jsf.p, sfj.data(), sfj.size() * sizeof(SFJob), cudaMemcpyHostToDevice, c->st));
+  if (!pj.empty()) CK(cudaMemcpyAsync(jpj.p, pj.data(), pj.size() * sizeof(ProjJob), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(jk.p, kj.data(), kj.size() * sizeof(KJob), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(jp.p, pjb.data(), pjb.size() * sizeof(PJob), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
+  const Tables t = tables(c);
+  launch_sf(t, c->sys.e_vir, (const SFJob*)jsf.p, (int)sfj.size(), max_n, c->st);
+  CK(cudaGetLastError());
+  launch_project(bsrc(c), t, (const ProjJob*)jpj.p, (int)pj.size(), max_nx, c->st);
+  CK(cudaGetLastError());
+  launch_exchange(t, nx, (const KJob*)jk.p, (int)kj.size(), max_m, c->st);
+  CK(cudaGetLastError());
+  const int n_cta = std::min<int>((int)pjb.size(), 2 * c->num_sms);
+  TRY(tmp_alloc(c, scr, (size_t)n_cta * precond_scratch_doubles(max_m) * sizeof(double)));
+  launch_precond(t, c->opts.tau_s, (const PJob*)jp.p, (int)pjb.size(), max_m, (double*)scr.p, n_cta, c->err_d,
+                 c->st);
+  CK(cudaGetLastError());
+  (void)nv;
+  (void)prec;
+  return check_err_flag(c, "pair integrals");
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+extern "C" {
+
+void osvmp2_default_opts(osvmp2_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->tau_s = 1e-10;
+  o->tol_update = 1e-11;
+  o->tol_energy = 1e-13;
+  o->max_iter = 100;
+}
+
+int osvmp2_create(osvmp2_ctx** out, int device, void* cuda_stream, const osvmp2_opts* opts) {
+  if (!out) return OSVMP2_E_ARG;
+  *out = nullptr;
+  osvmp2_ctx* c = new osvmp2_ctx();
+  c->device = device;
+  c->st = (cudaStream_t)cuda_stream;
+  osvmp2_default_opts(&c->opts);
+  if (opts) c->opts = *opts;
+  if (c->opts.max_iter <= 0 || c->opts.tau_s < 0 || c->opts.tol_update <= 0 || c->opts.tol_energy <= 0) {
+    delete c;
+    return OSVMP2_E_ARG;
+  }
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->err_d, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->scal_d, 16 * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return OSVMP2_E_CUDA;
+  }
+  *out = c;
+  return OSVMP2_OK;
+}
+
+void osvmp2_destroy(osvmp2_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  free_system(c);
+  if (c->err_d) cudaFree(c->err_d);
+  if (c->scal_d) cudaFree(c->scal_d);
+  delete c;
+}
+
+const char* osvmp2_last_error(const osvmp2_ctx* c) { return c ? c->err.c_str() : "null ctx"; }
+
+int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_t* n_osv_host) {
+  if (!c || !s) return OSVMP2_E_ARG;
+  c->err.clear();
+  if (s->n_occ <= 0 || s->n_vir <= 0 || s->n_aux <= 0)
+    return fail(c, OSVMP2_E_ARG, "sizes must be positive (n_occ=%d n_vir=%d n_aux=%d)", s->n_occ, s->n_vir, s->n_aux);
+  if (!s->B && !s->env) return fail(c, OSVMP2_E_ARG, "either B or env must be given");
+  if (!s->f_occ || !s->e_vir) return fail(c, OSVMP2_E_ARG, "f_occ and e_vir are required");
+  if ((int64_t)s->n_occ * s->n_occ > (int64_t)1 << 30) return fail(c, OSVMP2_E_ARG, "n_occ too large");
+  CK(cudaSetDevice(c->device));
+  free_system(c);
+  c->sys = *s;
+  c->have_sys = true;
+  c->key = mix64((uint64_t)s->seed ^ (STREAM_B * STREAM_MUL));
+  c->r_occ.clear();
+  if (s->r_occ) c->r_occ.assign(s->r_occ, s->r_occ + 3 * (size_t)s->n_occ);
+  const int n = s->n_occ, nv = s->n_vir;
+  c->cap_pairs = n * (n + 1) / 2;
+  TRY(dalloc_t(c, &c->n_osv_d, n));
+  TRY(dalloc_t(c, &c->Q_d, n));
+  TRY(dalloc_t(c, &c->sf_id_d, (size_t)n * n));
+  TRY(dalloc_t(c, &c->pair_id_d, (size_t)n * n));
+  TRY(dalloc_t(c, &c->S_d, c->cap_pairs));
+  TRY(dalloc_t(c, &c->F_d, c->cap_pairs));
+  TRY(dalloc_t(c, &c->K_d, c->cap_pairs));
+  TRY(dalloc_t(c, &c->X_d, c->cap_pairs));
+  TRY(dalloc_t(c, &c->et_d, c->cap_pairs));
+  TRY(dalloc_t(c, &c->r_d, c->cap_pairs));
+  c->sf_id.assign((size_t)n * n, -1);
+  c->pair_id.assign((size_t)n * n, -1);
+  c->bt_id.assign((size_t)n * n, -1);
+  TRY(upload(c, c->sf_id_d, c->sf_id));
+  TRY(upload(c, c->pair_id_d, c->pair_id));
+  // batch the orbitals so that T, V and the eigen scratch stay within ~4 GB
+  const int kmax = nv;
+  const size_t per = ((size_t)nv * nv * 2 + kmax + eig_osv_scratch_doubles(nv, kmax)) * sizeof(double);
+  int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, ((size_t)4 << 30) / per));
+  nb = std::min(nb, 4 * c->num_sms);
+  Tmp Tm, Vm, wm, km, sm;
+  TRY(tmp_alloc(c, Tm, (size_t)nb * nv * nv * sizeof(double)));
+  TRY(tmp_alloc(c, Vm, (size_t)nb * nv * kmax * sizeof(double)));
+  TRY(tmp_alloc(c, wm, (size_t)nb * kmax * sizeof(double)));
+  TRY(tmp_alloc(c, km, (size_t)nb * sizeof(int)));
+  TRY(tmp_alloc(c, sm, (size_t)nb * eig_osv_scratch_doubles(nv, kmax) * sizeof(double)));
+  Tmp qtab;
+  TRY(tmp_alloc(c, qtab, 2 * (size_t)nb * sizeof(double*)));
+  c->n_osv.assign(n, 0);
+  c->Qp.assign(n, nullptr);
+  c->Wp.assign(n, nullptr);
+  CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
+  std::vector<int> kh(nb);
+  for (int i0 = 0; i0 < n; i0 += nb) {
+    const int b = std::min(nb, n - i0);
+    launch_tii(bsrc(c), s->e_vir, s->f_occ, n, i0, b, (double*)Tm.p, c->st);
+    CK(cudaGetLastError());
+    launch_eig_osv((double*)Tm.p, b, nv, l_osv, kmax, (double*)Vm.p, (double*)wm.p, (int*)km.p, (double*)sm.p,
+                   c->err_d, c->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(kh.data(), km.p, b * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    size_t tot = 0;
+    for (int u = 0; u < b; u++) tot += (size_t)kh[u] * (nv + 1);
+    double* mem = nullptr;
+    TRY(dalloc_t(c, &mem, tot));
+    std::vector<double*> qd(2 * b);
+    size_t off = 0;
+    for (int u = 0; u < b; u++) {
+      c->n_osv[i0 + u] = kh[u];
+      c->Qp[i0 + u] = mem + off;
+      off += (size_t)kh[u] * nv;
+      c->Wp[i0 + u] = mem + off;
+      off += kh[u];
+      qd[u] = c->Qp[i0 + u];
+      qd[b + u] = c->Wp[i0 + u];
+    }
+    CK(cudaMemcpyAsync(qtab.p, qd.data(), 2 * b * sizeof(double*), cudaMemcpyHostToDevice, c->st));
+    launch_pack_q((double*)Vm.p, (double*)wm.p, b, nv, kmax, (int*)km.p, (double* const*)qtab.p,
+                  (double* const*)qtab.p + b, c->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+  }
+  TRY(check_err_flag(c, "OSV build"));
+  for (int i = 0; i < n; i++)
+    if (c->n_osv[i] == 0) return fail(c, OSVMP2_E_NUMERIC, "orbital %d has no OSV above l_osv", i);
+  TRY(upload(c, c->n_osv_d, c->n_osv));
+  TRY(upload(c, c->Q_d, c->Qp));
+  CK(cudaStreamSynchronize(c->st));
+  c->have_osv = true;
+  if (n_osv_host) std::copy(c->n_osv.begin(), c->n_osv.end(), n_osv_host);
+  return OSVMP2_OK;
+}
+
+int osvmp2_get_osv(osvmp2_ctx* c, int32_t i, double* Q, double* w) {
+  if (!c) return OSVMP2_E_ARG;
+  if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "no OSVs built");
+  if (i < 0 || i >= c->sys.n_occ) return fail(c, OSVMP2_E_ARG, "orbital %d out of range", i);
+  const size_t k = c->n_osv[i];
+  if (Q) CK(cudaMemcpyAsync(Q, c->Qp[i], k * c->sys.n_vir * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  if (w) CK(cudaMemcpyAsync(w, c->Wp[i], k * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return OSVMP2_OK;
+}
+
+int osvmp2_pair_integrals(osvmp2_ctx* c, const int32_t* pairs, int64_t n_pairs, osvmp2_prec prec) {
+  if (!c) return OSVMP2_E_ARG;
+  c->err.clear();
+  if (n_pairs < 0 || (n_pairs > 0 && !pairs)) return fail(c, OSVMP2_E_ARG, "bad pair list");
+  std::vector<std::pair<int, int>> req;
+  for (int64_t p = 0; p < n_pairs; p++) req.push_back({pairs[2 * p], pairs[2 * p + 1]});
+  CK(cudaSetDevice(c->device));
+  return ensure_pairs(c, req, prec);
+}
+
+int osvmp2_get_pair_blocks(osvmp2_ctx* c, int32_t i, int32_t j, double* K, double* S, double* F) {
+  if (!c) return OSVMP2_E_ARG;
+  if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "no OSVs built");
+  const int n = c->sys.n_occ;
+  if (i < 0 || j < i || j >= n) return fail(c, OSVMP2_E_ARG, "pair (%d,%d) invalid", i, j);
+  const int pid = c->pair_id[(size_t)i * n + j];
+  if (pid < 0) return fail(c, OSVMP2_E_STATE, "pair (%d,%d) not built", i, j);
+  const int m = c->m_h[pid];
+  if (K) CK(cudaMemcpyAsync(K, c->K_h[pid], (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  // S and F assembled on the host side of the copy from their blocks
+  int blocks[2] = {i, j};
+  const int nb = (i == j) ? 1 : 2;
+  int roff = 0;
+  for (int a = 0; a < nb; a++) {
+    int coff = 0;
+    for (int b = 0; b < nb; b++) {
+      const int x = blocks[a], y = blocks[b];
+      const int nx = c->n_osv[x], ny = c->n_osv[y];
+      const int lo = std::min(x, y), hi = std::max(x, y);
+      const int id = c->sf_id[(size_t)lo * n + hi];
+      std::vector<double> hs((size_t)c->n_osv[lo] * c->n_osv[hi]), hf(hs.size());
+      CK(cudaMemcpyAsync(hs.data(), c->S_h[id], hs.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaMemcpyAsync(hf.data(), c->F_h[id], hf.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      std::vector<double> bs((size_t)nx * ny), bf(bs.size());
+      for (int r = 0; r < nx; r++)
+        for (int q = 0; q < ny; q++) {
+          const size_t src = (x <= y) ? (size_t)r * ny + q : (size_t)q * nx + r;
+          bs[(size_t)r * ny + q] = hs[src];
+          bf[(size_t)r * ny + q] = hf[src];
+        }
+      for (int r = 0; r < nx; r++) {
+        if (S) CK(cudaMemcpy(S + (size_t)(roff + r) * m + coff, bs.data() + (size_t)r * ny, ny * sizeof(double),
+                             cudaMemcpyHostToDevice));
+        if (F) CK(cudaMemcpy(F + (size_t)(roff + r) * m + coff, bf.data() + (size_t)r * ny, ny * sizeof(double),
+                             cudaMemcpyHostToDevice));
+      }
+      coff += ny;
+    }
+    roff += c->n_osv[blocks[a]];
+  }
+  CK(cudaStreamSynchronize(c->st));
+  return OSVMP2_OK;
+}
+
+int osvmp2_solve(osvmp2_ctx* c, const int32_t* orbs, int32_t n_orbs, osvmp2_prec prec, double* e_out,
+                 double* pair_e_out, int32_t* iters_out) {
+  if (!c) return OSVMP2_E_ARG;
+  c->err.clear();
+  if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "osvmp2_build_osv has not been called");
+  if (!orbs || n_orbs <= 0 || !e_out) return fail(c, OSVMP2_E_ARG, "orbs, n_orbs > 0 and e_out are required");
+  const int n = c->sys.n_occ;
+  for (int a = 0; a < n_orbs; a++) {
+    if (orbs[a] < 0 || orbs[a] >= n) return fail(c, OSVMP2_E_ARG, "orbital %d out of range", orbs[a]);
+    if (a > 0 && orbs[a] <= orbs[a - 1]) return fail(c, OSVMP2_E_ARG, "orbs must be strictly ascending");
+  }
+  CK(cudaSetDevice(c->device));
+  std::vector<std::pair<int, int>> req;
+  for (int a = 0; a < n_orbs; a++)
+    for (int b = a; b < n_orbs; b++) req.push_back({orbs[a], orbs[b]});
+  TRY(ensure_pairs(c, req, prec));
+  const int np = (int)req.size();
+  size_t tot = 0;
+  int max_m = 0;
+  for (auto& p : req) {
+    const int m = pair_dim_h(c, p.first, p.second);
+    tot += 4 * (size_t)m * m;
+    max_m = std::max(max_m, m);
+  }
+  const int n_cta = std::min(np, 2 * c->num_sms);
+  Tmp mem, wmem, ptrs, orbd, pe, pu;
+  TRY(tmp_alloc(c, mem, tot * sizeof(double)));
+  TRY(tmp_alloc(c, wmem, (size_t)n_cta * 2 * max_m * max_m * sizeof(double)));
+  TRY(tmp_alloc(c, ptrs, (size_t)(4 * np + 2 * n_cta) * sizeof(double*)));
+  TRY(tmp_alloc(c, orbd, n_orbs * sizeof(int)));
+  TRY(tmp_alloc(c, pe, (np + 1) * sizeof(double)));
+  TRY(tmp_alloc(c, pu, (np + 1) * sizeof(double)));
+  std::vector<double*> hp(4 * np + 2 * n_cta);
+  size_t off = 0;
+  for (int q = 0; q < np; q++) {
+    const size_t m2 = (size_t)pair_dim_h(c, req[q].first, req[q].second) * pair_dim_h(c, req[q].first, req[q].second);
+    for (int u = 0; u < 4; u++) { hp[u * np + q] = (double*)mem.p + off; off += m2; }
+  }
+  for (int u = 0; u < 2 * n_cta; u++) hp[4 * np + u] = (double*)wmem.p + (size_t)u * max_m * max_m;
+  CK(cudaMemcpyAsync(ptrs.p, hp.data(), hp.size() * sizeof(double*), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(orbd.p, orbs, n_orbs * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  double** P = (double**)ptrs.p;
+  SubDev sd{n_orbs, (const int*)orbd.p, P, P + np, P + 2 * np, P + 3 * np, P + 4 * np, (double*)pe.p, (double*)pu.p};
+  const Tables t = tables(c);
+  launch_sub_prepare(t, sd, np, n_cta, c->st);
+  CK(cudaGetLastError());
+  double e_prev = 0.0, e = 0.0, um = 0.0;
+  int it = 1;
+  bool conv = false;
+  for (; it <= c->opts.max_iter; it++) {
+    launch_sub_residual(t, sd, np, n_cta, c->st);
+    launch_sub_update(t, sd, np, n_cta, c->st);
+    CK(cudaGetLastError());
+    double h[2];
+    CK(cudaMemcpyAsync(&h[0], (double*)pe.p + np, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(&h[1], (double*)pu.p + np, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    e = h[0];
+    um = h[1];
+    if (!std::isfinite(e) || !std::isfinite(um)) return fail(c, OSVMP2_E_NUMERIC, "non-finite energy in solve");
+    if (um < c->opts.tol_update && std::fabs(e - e_prev) < c->opts.tol_energy) { conv = true; break; }
+    e_prev = e;
+  }
+  *e_out = e;
+  if (iters_out) *iters_out = std::min(it, c->opts.max_iter);
+  if (pair_e_out) {
+    CK(cudaMemcpyAsync(pair_e_out, pe.p, np * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
+  if (!conv) return fail(c, OSVMP2_E_NOCONV, "solve did not converge in %d iterations (max|update| %.3e)",
+                         c->opts.max_iter, um);
+  return OSVMP2_OK;
+}
+
+int osvmp2_mbe3_fragments(const double* r_occ, int32_t n_occ, double r2, double r3, int64_t cap, int32_t* orbs_out,
+                          int32_t* weights_out, int64_t* n_out) {
+  if (!r_occ || n_occ <= 0 || !n_out || r2 < 0 || r3 < 0) return OSVMP2_E_ARG;
+  std::vector<Frag> fr;
+  enumerate_fragments(r_occ, n_occ, r2, r3, fr);
+  *n_out = (int64_t)fr.size();
+  if (orbs_out || weights_out) {
+    if (cap < (int64_t)fr.size()) return OSVMP2_E_ARG;
+    for (size_t f = 0; f < fr.size(); f++) {
+      if (orbs_out)
+        for (int u = 0; u < 3; u++) orbs_out[3 * f + u] = fr[f].orbs[u];
+      if (weights_out) weights_out[f] = fr[f].weight;
+    }
+  }
+  return OSVMP2_OK;
+}
+
+int osvmp2_mbe3_energy(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out,
+                       osvmp2_mbe_stats* stats) {
+  if (!c) return OSVMP2_E_ARG;
+  c->err.clear();
+  if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "osvmp2_build_osv has not been called");
+  if (!e_out) return fail(c, OSVMP2_E_ARG, "e_out is required");
+  if (c->r_occ.empty()) return fail(c, OSVMP2_E_ARG, "system has no r_occ (needed for fragment lists)");
+  if (!(r2 >= 0) || !(r3 >= 0)) return fail(c, OSVMP2_E_ARG, "cutoffs must be >= 0");
+  CK(cudaSetDevice(c->device));
+  const int n = c->sys.n_occ;
+  enumerate_fragments(c->r_occ.data(), n, r2, r3, c->frags);
+  const int nf = (int)c->frags.size();
+  std::vector<std::pair<int, int>> req;
+  int64_t ns = 0, npair = 0, ntri = 0;
+  for (auto& f : c->frags) {
+    const int nc = (f.orbs[1] < 0) ? 1 : (f.orbs[2] < 0 ? 2 : 3);
+    if (nc == 1) { ns++; req.push_back({f.orbs[0], f.orbs[0]}); }
+    else if (nc == 2) { npair++; req.push_back({f.orbs[0], f.orbs[1]}); }
+    else ntri++;
+  }
+  TRY(ensure_pairs(c, req, prec));
+  // processing order: largest estimated cost first
+  std::vector<int> order(nf);
+  std::vector<double> cost(nf, 0.0);
+  int max_m = 0;
+  for (int f = 0; f < nf; f++) {
+    order[f] = f;
+    const Frag& fr = c->frags[f];
+    for (int a = 0; a < 3; a++)
+      for (int b = a; b < 3; b++) {
+        if (fr.orbs[a] < 0 || fr.orbs[b] < 0) continue;
+        const double m = pair_dim_h(c, fr.orbs[a], fr.orbs[b]);
+        cost[f] += m * m * m;
+        max_m = std::max(max_m, (int)m);
+      }
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<int> orbs_h(3 * (size_t)nf), w_h(nf);
+  for (int f = 0; f < nf; f++) {
+    for (int u = 0; u < 3; u++) orbs_h[3 * f + u] = c->frags[f].orbs[u];
+    w_h[f] = c->frags[f].weight;
+  }
+  const int n_cta = std::max(1, std::min(nf, 2 * c->num_sms));
+  Tmp d_orbs, d_order, d_w, d_out, d_cnt, d_scr;
+  TRY(tmp_alloc(c, d_orbs, orbs_h.size() * sizeof(int)));
+  TRY(tmp_alloc(c, d_order, nf * sizeof(int)));
+  TRY(tmp_alloc(c, d_w, nf * sizeof(int)));
+  TRY(tmp_alloc(c, d_out, nf * sizeof(FragOut)));
+  TRY(tmp_alloc(c, d_cnt, sizeof(int)));
+  TRY(tmp_alloc(c, d_scr, (size_t)n_cta * frag_scratch_doubles(max_m) * sizeof(double)));
+  CK(cudaMemcpyAsync(d_orbs.p, orbs_h.data(), orbs_h.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(d_order.p, order.data(), nf * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(d_w.p, w_h.data(), nf * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  SolveOpts so{c->opts.tol_update, c->opts.tol_energy, c->opts.max_iter};
+  launch_frag_solve(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, (double*)d_scr.p, n_cta,
+                    (int*)d_cnt.p, (FragOut*)d_out.p, c->st);
+  CK(cudaGetLastError());
+  launch_weighted_sum((const FragOut*)d_out.p, (const int*)d_w.p, nf, c->scal_d, c->st);
+  CK(cudaGetLastError());
+  c->frag_out.resize(nf);
+  CK(cudaMemcpyAsync(c->frag_out.data(), d_out.p, nf * sizeof(FragOut), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(e_out, c->scal_d, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  int unconv = 0, maxit = 0;
+  int64_t worst = -1;
+  double maxu = 0.0;
+  for (int f = 0; f < nf; f++) {
+    const FragOut& o = c->frag_out[f];
+    maxit = std::max(maxit, o.iters);
+    maxu = std::max(maxu, o.umax);
+    if (o.status) {
+      unconv++;
+      if (worst < 0) worst = f;
+    }
+  }
+  if (stats) {
+    stats->n_single = ns;
+    stats->n_pair = npair;
+    stats->n_triple = ntri;
+    stats->n_pair_blocks = (int64_t)c->K_h.size();
+    stats->max_iter_used = maxit;
+    stats->n_unconverged = unconv;
+    stats->worst_fragment = worst;
+    stats->max_update = maxu;
+    stats->flops = 0.0;
+  }
+  if (unconv)
+    return fail(c, OSVMP2_E_NOCONV, "%d fragment(s) did not converge; first is fragment %lld", unconv,
+                (long long)worst);
+  return OSVMP2_OK;
+}
+
+int osvmp2_fragment_results(osvmp2_ctx* c, int64_t* n_out, int32_t* orbs, int32_t* weights, double* energies) {
+  if (!c || !n_out) return OSVMP2_E_ARG;
+  const size_t nf = c->frags.size();
+  *n_out = (int64_t)nf;
+  for (size_t f = 0; f < nf; f++) {
+    if (orbs)
+      for (int u = 0; u < 3; u++) orbs[3 * f + u] = c->frags[f].orbs[u];
+    if (weights) weights[f] = c->frags[f].weight;
+    if (energies) energies[f] = (f < c->frag_out.size()) ? c->frag_out[f].energy : 0.0;
+  }
+  return OSVMP2_OK;
+}
+
+int osvmp2_energy_grad(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out, double* dE_dB,
+                       double* dE_df, double* dE_de, osvmp2_mbe_stats* stats) {
+  (void)dE_dB; (void)dE_df; (void)dE_de;
+  if (!c) return OSVMP2_E_ARG;
+  int s = osvmp2_mbe3_energy(c, r2, r3, prec, e_out, stats);
+  if (s) return s;
+  return fail(c, OSVMP2_E_STATE, "gradient kernels not available yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Shared device building blocks of libosvmp2: block-matrix views, a CTA-wide
+// FP64 tiled GEMM, deterministic CTA reductions and the device form of the
+// counter-based generator that regenerates the RI integrals B.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace osv {
+
+constexpr int NT = 256;          // threads of every CTA that calls the CTA routines
+constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int GEMM_SMEM_DOUBLES = TK * (TM + TN);
+
+// ---------------------------------------------------------------- views
+// One dense block: element (r,c) at p[r*ld + c], or at p[c*ld + r] when tr.
+struct Blk {
+  const double* p;
+  int ld;
+  int tr;
+};
+
+// A matrix of up to 2x2 dense blocks.  Rows [0,rs) use block row 0, rows
+// [rs,rows) block row 1; columns likewise with cs.  This is exactly the shape
+// of the 4-block OSV pair matrices A_(ij,kl) (Eq. 4block_osv).
+struct View {
+  int rows, cols, rs, cs;
+  Blk b[2][2];
+  __device__ __forceinline__ double get(int r, int c) const {
+    const int br = r >= rs, bc = c >= cs;
+    const Blk& B = b[br][bc];
+    const int rr = br ? r - rs : r, cc = bc ? c - cs : c;
+    return B.tr ? B.p[(size_t)cc * B.ld + rr] : B.p[(size_t)rr * B.ld + cc];
+  }
+};
+
+__host__ __device__ inline View dense_view(const double* p, int rows, int cols, int ld, int tr = 0) {
+  View v;
+  v.rows = rows; v.cols = cols; v.rs = rows; v.cs = cols;
+  for (int a = 0; a < 2; a++)
+    for (int c = 0; c < 2; c++) v.b[a][c] = Blk{p, ld, tr};
+  return v;
+}
+
+// Transpose of a view (no data movement).
+__host__ __device__ inline View transpose(const View& v) {
+  View t;
+  t.rows = v.cols; t.cols = v.rows; t.rs = v.cs; t.cs = v.rs;
+  for (int a = 0; a < 2; a++)
+    for (int c = 0; c < 2; c++) {
+      t.b[a][c] = v.b[c][a];
+      t.b[a][c].tr ^= 1;
+    }
+  return t;
+}
+
+// ---------------------------------------------------------------- GEMM
+// Accumulate one TM x TN output tile at (m0, n0) of A[MxK] * B[KxN] into acc.
+// Thread (ty, tx) = (tid/16, tid%16) owns rows m0+ty+16i and cols n0+tx+16j.
+template <class VA, class VB>
+__device__ __forceinline__ void tile_mma(int M, int N, int K, int m0, int n0, const VA& A, const VB& B,
+                                         double acc[4][4], double* sm) {
+  double* As = sm;             // [TK][TM]
+  double* Bs = sm + TK * TM;   // [TK][TN]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int k0 = 0; k0 < K; k0 += TK) {
+#pragma unroll
+    for (int t = 0; t < TM * TK / NT; t++) {
+      const int e = tid + t * NT, m = e % TM, k = e / TM;
+      const int gm = m0 + m, gk = k0 + k;
+      As[k * TM + m] = (gm < M && gk < K) ? A.get(gm, gk) : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < TN * TK / NT; t++) {
+      const int e = tid + t * NT, n = e % TN, k = e / TN;
+      const int gn = n0 + n, gk = k0 + k;
+      Bs[k * TN + n] = (gn < N && gk < K) ? B.get(gk, gn) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < TK; k++) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = As[k * TM + ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = Bs[k * TN + tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+}
+
+// C[MxN] (row-major, ldc) = beta*C + alpha*A*B with the whole CTA (NT threads).
+// beta == 0 never reads C.
+template <class VA, class VB>
+__device__ void cta_gemm(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta,
+                         double* C, int ldc, double* sm) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += TM)
+    for (int n0 = 0; n0 < N; n0 += TN) {
+      double acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+      tile_mma(M, N, K, m0, n0, A, B, acc, sm);
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
+          if (r < M && c < N) {
+            double* cp = C + (size_t)r * ldc + c;
+            *cp = (beta == 0.0 ? 0.0 : beta * *cp) + alpha * acc[i][j];
+          }
+        }
+    }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- reductions
+// Deterministic CTA sum / max (fixed shuffle tree, then fixed order over warps).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// red: >= 33 doubles of shared memory. Result returned to every thread.
+__device__ inline double cta_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < nw; k++) s += red[k];
+    red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+__device__ inline double cta_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = red[0];
+    for (int k = 1; k < nw; k++) s = fmax(s, red[k]);
+    red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// ---------------------------------------------------------------- generator
+// SplitMix64 output finaliser (Steele, Lea & Flood 2014) and the draws built on
+// it; B[i,a,P] = env[i,a] * z with z the Irwin-Hall sum of twelve 16-bit fields
+// of three consecutive draws, shifted and scaled exactly by 2^-16.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t draw(uint64_t key, uint64_t c) {
+  return mix64(key + (c + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+__device__ __forceinline__ double ih12(uint64_t key, uint64_t ctr) {
+  int64_t s = 0;
+#pragma unroll
+  for (int t = 0; t < 3; t++) {
+    const uint64_t h = draw(key, 3ull * ctr + (uint64_t)t);
+    s += (int64_t)(h & 0xFFFFull) + (int64_t)((h >> 16) & 0xFFFFull) + (int64_t)((h >> 32) & 0xFFFFull) +
+         (int64_t)(h >> 48);
+  }
+  return (double)(s - 393210) * 0x1p-16;
+}
+
+// Source of B: stored array, or regeneration from (key, env).
+struct BSrc {
+  const double* B;
+  const double* env;
+  uint64_t key;
+  int n_vir, n_aux;
+  __device__ __forceinline__ double get(int i, int a, int P) const {
+    const size_t idx = ((size_t)i * n_vir + a) * n_aux + P;
+    if (B) return B[idx];
+    return env[(size_t)i * n_vir + a] * ih12(key, (uint64_t)idx);
+  }
+};
+
+// Device-side error flag bits written by kernels (read by the host after sync).
+enum : int { ERR_EIG = 1, ERR_NONFINITE = 2, ERR_NOCONV = 4, ERR_SIZE = 8 };
+
+}  // namespace osv

@@ -1,0 +1,282 @@
+// CTA-wide FP64 symmetric eigen-solvers used by the OSV build (Eq. osv_gen)
+// and by the pair preconditioner (Eq. prec_eig).
+//
+//  * cta_tridiag     Householder reduction A = Z T Z^T to tridiagonal form
+//                    (reflectors H_k = I - tau_k v_k v_k^T, v_k[0] = 1, stored
+//                    below the sub-diagonal of A).
+//  * cta_form_z      Z = H_0 H_1 ... H_{n-3} by backward accumulation.
+//  * cta_tridiag_qr  implicit symmetric QR steps with the Wilkinson shift
+//                    (Golub & Van Loan, Matrix Computations, Alg. 8.3.2/8.3.3),
+//                    rotations accumulated into the columns of Z.
+//  * sturm_count / bisection / inverse iteration + back-transformation for the
+//    eigenpairs above a threshold, used when only a few OSVs out of a large
+//    virtual space are kept.
+// All routines are called by every thread of a CTA of NT threads.
+#pragma once
+#include "common.cuh"
+
+namespace osv {
+
+// Householder tridiagonalisation of the symmetric n x n matrix A (row-major,
+// lda; global or shared memory), in place.  Outputs d[n], e[n-1] (any memory)
+// and tau[n]; v and p are shared scratch of n doubles each, red >= 33 doubles.
+__device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double* e, double* tau,
+                                   double* v, double* p, double* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NT / 32;
+  __shared__ double s_tau;
+  for (int k = 0; k + 2 < n; k++) {
+    const int L = n - k - 1;          // trailing block rows/cols k+1 .. n-1
+    double* Ak = A + (size_t)(k + 1) * lda + (k + 1);   // trailing block origin
+    double part = 0.0;
+    for (int t = tid; t < L; t += NT) {
+      const double x = A[(size_t)(k + 1 + t) * lda + k];
+      v[t] = x;
+      if (t > 0) part += x * x;
+    }
+    const double sigma = cta_sum(part, red);
+    if (tid == 0) {
+      const double alpha = v[0];
+      double tu = 0.0, beta = alpha;
+      if (sigma > 0.0) {
+        const double mu = sqrt(alpha * alpha + sigma);
+        beta = alpha <= 0.0 ? mu : -mu;
+        tu = (beta - alpha) / beta;
+        const double v0 = alpha - beta;
+        red[0] = 1.0 / v0;   // scale for v[1..]
+      }
+      s_tau = tu;
+      d[k] = A[(size_t)k * lda + k];
+      e[k] = beta;
+      tau[k] = tu;
+    }
+    __syncthreads();
+    const double tk = s_tau;
+    if (tk != 0.0) {
+      const double sc = red[0];
+      for (int t = tid; t < L; t += NT) v[t] = (t == 0) ? 1.0 : v[t] * sc;
+      __syncthreads();
+      // p = tau * A' v  (warp per row, lanes over columns)
+      for (int r = warp; r < L; r += nwarp) {
+        const double* row = Ak + (size_t)r * lda;
+        double s = 0.0;
+        for (int c = lane; c < L; c += 32) s += row[c] * v[c];
+        s = warp_sum(s);
+        if (lane == 0) p[r] = tk * s;
+      }
+      __syncthreads();
+      double pv = 0.0;
+      for (int t = tid; t < L; t += NT) pv += p[t] * v[t];
+      const double Kc = 0.5 * tk * cta_sum(pv, red);
+      for (int t = tid; t < L; t += NT) p[t] -= Kc * v[t];   // p becomes w
+      __syncthreads();
+      // A' -= v w^T + w v^T
+      for (int r = warp; r < L; r += nwarp) {
+        double* row = Ak + (size_t)r * lda;
+        const double vr = v[r], wr = p[r];
+        for (int c = lane; c < L; c += 32) row[c] -= vr * p[c] + wr * v[c];
+      }
+      // keep the reflector below the sub-diagonal of column k
+      for (int t = tid + 1; t < L; t += NT) A[(size_t)(k + 1 + t) * lda + k] = v[t];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = A[(size_t)(n - 2) * lda + (n - 2)];
+      e[n - 2] = A[(size_t)(n - 1) * lda + (n - 2)];
+      if (n >= 3) tau[n - 2] = 0.0;
+    }
+    d[n - 1] = A[(size_t)(n - 1) * lda + (n - 1)];
+    tau[n - 1] = 0.0;
+  }
+  __syncthreads();
+}
+
+// Z (n x n, row-major, ldz) = H_0 H_1 ... H_{n-3} from the reflectors left in A.
+// y: shared scratch of n doubles.
+__device__ inline void cta_form_z(const double* A, int n, int lda, const double* tau, double* Z, int ldz,
+                                  double* y) {
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n * n; t += NT) Z[(size_t)(t / n) * ldz + (t % n)] = (t / n == t % n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = n - 3; k >= 0; k--) {
+    const double tk = tau[k];
+    if (tk == 0.0) continue;
+    const int L = n - k - 1;
+    // y_c = sum_r v_r Z[k+1+r][k+1+c]   (v_0 = 1, v_r = A[k+1+r][k])
+    for (int c = tid; c < L; c += NT) {
+      double s = Z[(size_t)(k + 1) * ldz + (k + 1 + c)];
+      for (int r = 1; r < L; r++) s += A[(size_t)(k + 1 + r) * lda + k] * Z[(size_t)(k + 1 + r) * ldz + (k + 1 + c)];
+      y[c] = tk * s;
+    }
+    __syncthreads();
+    for (int t = tid; t < L * L; t += NT) {
+      const int r = t / L, c = t % L;
+      const double vr = (r == 0) ? 1.0 : A[(size_t)(k + 1 + r) * lda + k];
+      Z[(size_t)(k + 1 + r) * ldz + (k + 1 + c)] -= vr * y[c];
+    }
+    __syncthreads();
+  }
+}
+
+// Implicit symmetric QR on the tridiagonal (d[n], e[n-1]) with rotations
+// accumulated into the columns of Z (n x n, row-major, ldz).  d, e must be in
+// shared or global memory visible to thread 0; cs is shared scratch of 2n
+// doubles.  Returns 0 on convergence (d holds the eigenvalues, columns of Z the
+// eigenvectors), 1 otherwise.  Every thread returns the same value.
+__device__ inline int cta_tridiag_qr(double* d, double* e, int n, double* Z, int ldz, double* cs) {
+  __shared__ int s_l, s_h, s_done;
+  const int tid = threadIdx.x;
+  const double eps = 2.220446049250313e-16;
+  int sweeps = 0;
+  const int max_sweeps = 40 * n + 100;
+  while (true) {
+    if (tid == 0) {
+      int h = n - 1, l = 0, done = 0;
+      // deflate negligible couplings from the bottom
+      while (h > 0) {
+        if (fabs(e[h - 1]) <= eps * (fabs(d[h - 1]) + fabs(d[h]))) { e[h - 1] = 0.0; h--; }
+        else break;
+      }
+      if (h == 0) done = 1;
+      else {
+        l = h - 1;
+        while (l > 0) {
+          if (fabs(e[l - 1]) <= eps * (fabs(d[l - 1]) + fabs(d[l]))) { e[l - 1] = 0.0; break; }
+          l--;
+        }
+        // Wilkinson shift from the trailing 2x2 of the unreduced block [l, h]
+        const double delta = 0.5 * (d[h - 1] - d[h]);
+        const double eh = e[h - 1];
+        const double den = delta + copysign(hypot(delta, eh), delta);
+        const double mu = d[h] - (den != 0.0 ? eh * eh / den : 0.0);
+        double x = d[l] - mu, z = e[l];
+        for (int k = l; k < h; k++) {
+          const double r = hypot(x, z);
+          double c = 1.0, s = 0.0;
+          if (r != 0.0) { c = x / r; s = z / r; }
+          if (k > l) e[k - 1] = r;
+          const double a = d[k], b = e[k], cc = d[k + 1];
+          d[k] = c * c * a + 2.0 * c * s * b + s * s * cc;
+          d[k + 1] = s * s * a - 2.0 * c * s * b + c * c * cc;
+          e[k] = c * s * (cc - a) + (c * c - s * s) * b;
+          if (k + 1 < h) {
+            x = e[k];
+            z = s * e[k + 1];
+            e[k + 1] = c * e[k + 1];
+          }
+          cs[2 * k] = c;
+          cs[2 * k + 1] = s;
+        }
+      }
+      s_l = l; s_h = h; s_done = done;
+    }
+    __syncthreads();
+    if (s_done) return 0;
+    if (++sweeps > max_sweeps) return 1;
+    const int l = s_l, h = s_h;
+    // Z <- Z R_l^T R_{l+1}^T ... : column pair (k, k+1) rotated for k = l..h-1
+    for (int row = tid; row < n; row += NT) {
+      double* zr = Z + (size_t)row * ldz;
+      double carry = zr[l];
+      for (int k = l; k < h; k++) {
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        const double y = zr[k + 1];
+        zr[k] = c * carry + s * y;
+        carry = -s * carry + c * y;
+      }
+      zr[h] = carry;
+    }
+    __syncthreads();
+  }
+}
+
+// Full symmetric eigen-decomposition of A (n x n, row-major lda, destroyed).
+// On return w[0..n) holds the eigenvalues and column t of Z the eigenvector
+// of w[t] (unordered).  d/e/tau: n doubles each (any memory visible to the
+// CTA); sm: shared scratch of >= 4n + 33 doubles.  Returns 0 on success.
+__device__ inline int cta_syev(double* A, int n, int lda, double* w, double* Z, int ldz, double* e,
+                               double* tau, double* sm) {
+  double* v = sm;
+  double* p = sm + n;
+  double* cs = sm + 2 * n;      // 2n
+  double* red = sm + 4 * n;     // 33
+  if (n == 1) {
+    if (threadIdx.x == 0) { w[0] = A[0]; Z[0] = 1.0; }
+    __syncthreads();
+    return 0;
+  }
+  cta_tridiag(A, n, lda, w, e, tau, v, p, red);
+  cta_form_z(A, n, lda, tau, Z, ldz, v);
+  return cta_tridiag_qr(w, e, n, Z, ldz, cs);
+}
+
+// ---------------------------------------------------------------- top-k
+// Number of eigenvalues of the tridiagonal (d, e) strictly below x
+// (Sturm sequence of the LDL^T pivots).
+__device__ inline int sturm_count(const double* d, const double* e, int n, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int i = 1; i < n; i++) {
+    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
+// Eigenvalue with ascending index j of (d, e) by bisection on the Sturm count.
+__device__ inline double bisect_eig(const double* d, const double* e, int n, int j, double lo, double hi,
+                                    double pivmin) {
+  const double eps = 2.220446049250313e-16;
+  for (int it = 0; it < 200; it++) {
+    const double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi) break;
+    if (sturm_count(d, e, n, mid, pivmin) <= j) lo = mid;
+    else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// One solve (T - lam I) x = y by Gaussian elimination with partial pivoting on
+// the tridiagonal; y is overwritten by x.  u0,u1,u2,mul: n doubles; piv: n ints.
+__device__ inline void tri_factor(const double* d, const double* e, int n, double lam, double small,
+                                  double* u0, double* u1, double* u2, double* mul, int* piv) {
+  double wa = d[0] - lam, wb = (n > 1) ? e[0] : 0.0;     // working row (col i, col i+1)
+  for (int i = 0; i + 1 < n; i++) {
+    const double c = e[i], a1 = d[i + 1] - lam, b1 = (i + 2 < n) ? e[i + 1] : 0.0;
+    if (fabs(wa) >= fabs(c)) {
+      double a = wa;
+      if (a == 0.0) a = small;
+      u0[i] = a; u1[i] = wb; u2[i] = 0.0;
+      const double m = c / a;
+      mul[i] = m; piv[i] = 0;
+      wa = a1 - m * wb;
+      wb = b1;
+    } else {
+      u0[i] = c; u1[i] = a1; u2[i] = b1;
+      const double m = wa / c;
+      mul[i] = m; piv[i] = 1;
+      const double na = wb - m * a1, nb = -m * b1;
+      wa = na; wb = nb;
+    }
+  }
+  u0[n - 1] = (wa == 0.0) ? small : wa;
+}
+__device__ inline void tri_solve(int n, const double* u0, const double* u1, const double* u2,
+                                 const double* mul, const int* piv, double* y) {
+  for (int i = 0; i + 1 < n; i++) {
+    if (piv[i]) { const double t = y[i]; y[i] = y[i + 1]; y[i + 1] = t; }
+    y[i + 1] -= mul[i] * y[i];
+  }
+  for (int i = n - 1; i >= 0; i--) {
+    double s = y[i];
+    if (i + 1 < n) s -= u1[i] * y[i + 1];
+    if (i + 2 < n) s -= u2[i] * y[i + 2];
+    y[i] = s / u0[i];
+  }
+}
+
+}  // namespace osv

@@ -1,0 +1,120 @@
+// Internal interfaces between the host runtime (api.cu) and the kernel
+// translation units of libosvmp2.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "common.cuh"
+
+namespace osv {
+
+// Device-resident lookup tables of the pair store (all pointers are device).
+struct Tables {
+  int n_occ;
+  int n_vir;
+  const int* n_osv;             // [n_occ]
+  const double* const* Q;       // [n_occ] -> Q_i [n_vir][n_osv_i]
+  const int* sf_id;             // [n_occ*n_occ]: (x<=y) -> S/F block id, -1 if absent
+  const double* const* S;       // [n_blocks] S_(x,y) [n_x][n_y]
+  const double* const* F;       // [n_blocks] F_(x,y)
+  const int* pair_id;           // [n_occ*n_occ]: (i<=j) -> pair id, -1 if absent
+  const double* const* K;       // [n_pairs] K_(ij,ij) [m][m]
+  const double* const* X;       // [n_pairs] X [m][m] (first r columns valid)
+  const double* const* et;      // [n_pairs] e~ [m] (first r valid)
+  const int* r;                 // [n_pairs]
+  const double* f_occ;          // [n_occ][n_occ]
+};
+
+struct SolveOpts {
+  double tol_update, tol_energy;
+  int max_iter;
+};
+
+// Per-fragment result record written by the solvers.
+struct FragOut {
+  double energy;
+  double umax;
+  int iters;
+  int status;   // 0 ok, ERR_* bits otherwise
+};
+
+// ---- A0 (osv_build.cu)
+// T_ii of orbitals [i0, i0+nb) into T [nb][nv][nv].
+void launch_tii(const BSrc& src, const double* e_vir, const double* f_occ, int n_occ, int i0, int nb,
+                double* T, cudaStream_t st);
+// Eigen-decomposition of each T[b] and selection omega >= thr (all if thr <= 0),
+// at most kmax per orbital: V [nb][nv][kmax], w [nb][kmax], k [nb], err |= ERR_*.
+// e, tau, w (3 nv) + Z (nv*nv, global path) + 8 warps x 7 nv (inverse iteration)
+__host__ __device__ inline size_t eig_osv_scratch_doubles(int nv, int kmax) {
+  (void)kmax;
+  return (size_t)3 * nv + (size_t)nv * nv + (size_t)8 * 7 * nv + 64;
+}
+void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, double* w, int* k,
+                    double* scratch, int* err, cudaStream_t st);
+// Copy V[b][:, :k_b] into the packed Q store (Q[i0+b] as [nv][k]).
+void launch_pack_q(const double* V, const double* w, int nb, int nv, int kmax, const int* k,
+                   double* const* Qdst, double* const* wdst, cudaStream_t st);
+
+// ---- A1-A2 (pair_integrals.cu)
+struct ProjJob {         // B~_{i}^{(x)} = B[i]^T Q_x  -> out [n_aux][n_x]
+  int i, x;
+  double* out;
+};
+void launch_project(const BSrc& src, const Tables& t, const ProjJob* jobs, int n_jobs, int max_nx,
+                    cudaStream_t st);
+struct KJob {            // K_(ij,ij) from the projections
+  int i, j;
+  const double* Bii;     // B~_i^(i)  [n_aux][n_i]
+  const double* Bij;     // B~_i^(j)  [n_aux][n_j]   (NULL if i == j)
+  const double* Bji;     // B~_j^(i)
+  const double* Bjj;     // B~_j^(j)
+  double* out;           // [m][m]
+};
+void launch_exchange(const Tables& t, int n_aux, const KJob* jobs, int n_jobs, int max_m, cudaStream_t st);
+struct SFJob {           // S_(x,y), F_(x,y)
+  int x, y;
+  double* S;
+  double* F;
+};
+void launch_sf(const Tables& t, const double* e_vir, const SFJob* jobs, int n_jobs, int max_n,
+               cudaStream_t st);
+
+// ---- A3 (precond.cu)
+struct PJob {            // preconditioner of pair (i,j): X, e~, r
+  int i, j;
+  double* X;
+  double* et;
+  int* r;
+};
+__host__ __device__ inline size_t precond_scratch_doubles(int max_m) {
+  return 6 * (size_t)max_m * max_m + 4 * (size_t)max_m + 64;
+}
+void launch_precond(const Tables& t, double tau_s, const PJob* jobs, int n_jobs, int max_m, double* scratch,
+                    int n_cta, int* err, cudaStream_t st);
+
+// ---- A4-A5 (solve.cu)
+// Fragments: orbs [n][3] (-1 padded, ascending), order[] = processing order.
+// per CTA: T, R, G1, G2 for six pairs + two work matrices
+__host__ __device__ inline size_t frag_scratch_doubles(int max_m) { return 26 * (size_t)max_m * max_m + 64; }
+void launch_frag_solve(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
+                       SolveOpts o, double* scratch, int n_cta, int* counter, FragOut* out,
+                       cudaStream_t st);
+// E = sum_f w_f * E_f in a fixed order -> e_out (device scalar)
+void launch_weighted_sum(const FragOut* out, const int* weights, int n, double* e_out, cudaStream_t st);
+
+// General subsystem solve: one kernel per Jacobi sweep over pairs.
+struct SubDev {
+  int nc;
+  const int* orbs;          // [nc]
+  double* const* T;         // [np] amplitude per local pair
+  double* const* R;         // [np]
+  double* const* G1;        // [np] F_p - f_ii S_p
+  double* const* G2;        // [np] F_p - f_jj S_p
+  double* const* W;         // [n_cta] work matrices (2 per CTA: W, Rt)
+  double* pe;               // [np] pair energies
+  double* pu;               // [np] pair max|update|
+};
+void launch_sub_prepare(const Tables& t, const SubDev& s, int np, int n_cta, cudaStream_t st);
+void launch_sub_residual(const Tables& t, const SubDev& s, int np, int n_cta, cudaStream_t st);
+void launch_sub_update(const Tables& t, const SubDev& s, int np, int n_cta, cudaStream_t st);
+
+}  // namespace osv

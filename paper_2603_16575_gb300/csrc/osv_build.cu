@@ -1,0 +1,298 @@
+// A0: OSV generation.  T_ii from the RI integrals (Eq. mp2_tkk, positive
+// denominator e_a + e_b - 2 f_ii), its FP64 eigen-decomposition (Eq. osv_gen)
+// and the selection omega >= l_osv of Algorithm 3, all on the GPU.
+#include "eig.cuh"
+#include "internal.h"
+
+namespace osv {
+
+// A(a, P) = B[i,a,P] and its transpose, read straight from the source (stored
+// or regenerated).
+struct BiRows {
+  BSrc s;
+  int i;
+  __device__ __forceinline__ double get(int a, int P) const { return s.get(i, a, P); }
+};
+struct BiCols {
+  BSrc s;
+  int i;
+  __device__ __forceinline__ double get(int P, int b) const { return s.get(i, b, P); }
+};
+
+// One 64x64 tile (tr >= tc) of T_i = (B_i B_i^T) / (e_a + e_b - 2 f_ii); the
+// mirror tile is written from the same accumulators.
+__global__ void __launch_bounds__(NT) k_tii(BSrc src, const double* __restrict__ e_vir,
+                                            const double* __restrict__ f_occ, int n_occ, int i0,
+                                            double* __restrict__ T) {
+  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  const int nv = src.n_vir, nx = src.n_aux;
+  const int b = blockIdx.y, i = i0 + b;
+  int t = blockIdx.x, tr = 0;
+  while ((tr + 1) * (tr + 2) / 2 <= t) tr++;
+  const int tc = t - tr * (tr + 1) / 2;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) acc[u][v] = 0.0;
+  tile_mma(nv, nv, nx, tr * TM, tc * TN, BiRows{src, i}, BiCols{src, i}, acc, sm);
+  const double f2 = 2.0 * f_occ[(size_t)i * n_occ + i];
+  double* Ti = T + (size_t)b * nv * nv;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const int a = tr * TM + ty + 16 * u, c = tc * TN + tx + 16 * v;
+      if (a < nv && c < nv) {
+        const double val = acc[u][v] / (e_vir[a] + e_vir[c] - f2);
+        Ti[(size_t)a * nv + c] = val;
+        Ti[(size_t)c * nv + a] = val;
+      }
+    }
+}
+
+void launch_tii(const BSrc& src, const double* e_vir, const double* f_occ, int n_occ, int i0, int nb,
+                double* T, cudaStream_t st) {
+  const int nt = (src.n_vir + TM - 1) / TM;
+  dim3 grid(nt * (nt + 1) / 2, nb);
+  k_tii<<<grid, NT, 0, st>>>(src, e_vir, f_occ, n_occ, i0, T);
+}
+
+// ---------------------------------------------------------------- eigen
+constexpr int ZSMEM_MAX = 160;   // Z kept in shared memory up to this order
+
+// Sign column t of V (n rows, ld) so that its largest-magnitude entry (lowest
+// row on ties) is positive.  One warp per column.
+__device__ inline void sign_columns(double* V, int n, int ld, int k) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = warp; t < k; t += NT / 32) {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int r = lane; r < n; r += 32) {
+      const double a = fabs(V[(size_t)r * ld + t]);
+      if (a > best) { best = a; bi = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    const double sg = (V[(size_t)bi * ld + t] < 0.0) ? -1.0 : 1.0;
+    if (sg < 0.0)
+      for (int r = lane; r < n; r += 32) V[(size_t)r * ld + t] = -V[(size_t)r * ld + t];
+  }
+  __syncthreads();
+}
+
+// Full decomposition path (n <= ZSMEM_MAX with Z in shared memory, or any n
+// with Z in global scratch): eigenvalues sorted descending, then selection.
+__device__ void eig_full_select(double* A, int n, double thr, int kmax, double* V, double* w, int* kout,
+                                double* scr, int* err, double* Zs, int ldz, double* sm) {
+  double* e = scr;
+  double* tau = scr + n;
+  double* ww = scr + 2 * n;
+  int rc = cta_syev(A, n, n, ww, Zs, ldz, e, tau, sm);
+  __shared__ int s_k;
+  int* perm = reinterpret_cast<int*>(sm);   // sm reused: n ints (n <= 4n doubles)
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < n; t++) perm[t] = t;
+    for (int t = 1; t < n; t++) {           // insertion sort, descending, stable
+      const int pv = perm[t];
+      const double x = ww[pv];
+      int u = t - 1;
+      while (u >= 0 && ww[perm[u]] < x) { perm[u + 1] = perm[u]; u--; }
+      perm[u + 1] = pv;
+    }
+    int k = 0;
+    if (thr > 0.0) { while (k < n && ww[perm[k]] >= thr) k++; }
+    else k = n;
+    if (k > kmax) { k = kmax; atomicOr(err, ERR_SIZE); }
+    bool bad = rc != 0;
+    for (int t = 0; t < n; t++) bad |= !isfinite(ww[t]);
+    if (bad) atomicOr(err, rc ? ERR_EIG : ERR_NONFINITE);
+    s_k = k;
+    *kout = k;
+    for (int t = 0; t < k; t++) w[t] = ww[perm[t]];
+  }
+  __syncthreads();
+  const int k = s_k;
+  for (int idx = threadIdx.x; idx < n * k; idx += NT) {
+    const int r = idx / k, t = idx % k;
+    V[(size_t)r * kmax + t] = Zs[(size_t)r * ldz + perm[t]];
+  }
+  __syncthreads();
+  sign_columns(V, n, kmax, k);
+}
+
+// Eigenpairs with eigenvalue >= thr only: tridiagonalise, count by Sturm
+// sequence, bisection for the kept eigenvalues, inverse iteration with
+// Gram-Schmidt inside clusters of close eigenvalues, back-transformation.
+__device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, double* w, int* kout,
+                         double* scr, int* err, double* sm) {
+  double* d = scr;
+  double* e = scr + n;
+  double* tau = scr + 2 * n;
+  double* wk = scr + 3 * n + (size_t)n * n;   // per-warp inverse-iteration scratch (7n each)
+  double* v = sm;
+  double* p = sm + n;
+  double* red = sm + 2 * n;
+  __shared__ int s_k, s_nclu;
+  __shared__ double s_lo, s_hi, s_piv, s_norm;
+  cta_tridiag(A, n, n, d, e, tau, v, p, red);
+  // Gershgorin bounds and a pivot floor
+  double glo = 1e300, ghi = -1e300, nrm = 0.0, emax = 0.0;
+  for (int t = threadIdx.x; t < n; t += NT) {
+    const double off = (t > 0 ? fabs(e[t - 1]) : 0.0) + (t + 1 < n ? fabs(e[t]) : 0.0);
+    glo = fmin(glo, d[t] - off);
+    ghi = fmax(ghi, d[t] + off);
+    nrm = fmax(nrm, fabs(d[t]) + off);
+    if (t + 1 < n) emax = fmax(emax, e[t] * e[t]);
+  }
+  glo = -cta_max(-glo, red);
+  ghi = cta_max(ghi, red);
+  nrm = cta_max(nrm, red);
+  emax = cta_max(emax, red);
+  int* clu = reinterpret_cast<int*>(p);     // cluster starts (reuses p)
+  if (threadIdx.x == 0) {
+    const double piv = 1e-290 * fmax(1.0, emax);
+    const double span = ghi - glo;
+    s_lo = glo - 1e-14 * span - piv;
+    s_hi = ghi + 1e-14 * span + piv;
+    s_piv = piv;
+    s_norm = nrm;
+    int k = n - sturm_count(d, e, n, thr, piv);
+    if (k > kmax) { k = kmax; atomicOr(err, ERR_SIZE); }
+    s_k = k;
+    *kout = k;
+  }
+  __syncthreads();
+  const int k = s_k;
+  for (int t = threadIdx.x; t < k; t += NT) w[t] = bisect_eig(d, e, n, n - 1 - t, s_lo, s_hi, s_piv);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double ortol = 1e-3 * s_norm;
+    int nc = 0;
+    for (int t = 0; t < k; t++)
+      if (t == 0 || w[t - 1] - w[t] > ortol) clu[nc++] = t;
+    clu[nc] = k;
+    s_nclu = nc;
+    for (int t = 0; t < k; t++)
+      if (!isfinite(w[t])) atomicOr(err, ERR_NONFINITE);
+  }
+  __syncthreads();
+  // inverse iteration: warp per cluster, vectors of a cluster in order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* u0 = wk + (size_t)warp * 7 * n;
+  double* u1 = u0 + n;
+  double* u2 = u1 + n;
+  double* mu = u2 + n;
+  double* y = mu + n;
+  int* piv = reinterpret_cast<int*>(y + n);   // n ints fit in 2n doubles' room
+  const double small = 2.220446049250313e-16 * fmax(s_norm, 1e-300);
+  for (int c = warp; c < s_nclu; c += NT / 32) {
+    const int t0 = clu[c], t1 = clu[c + 1];
+    for (int t = t0; t < t1; t++) {
+      if (lane == 0) tri_factor(d, e, n, w[t], small, u0, u1, u2, mu, piv);
+      for (int r = lane; r < n; r += 32) {
+        const uint64_t h = draw(0x5eedull + (uint64_t)t, (uint64_t)r);
+        y[r] = (double)(h >> 11) * 0x1p-53 - 0.5;
+      }
+      __syncwarp();
+      for (int it = 0; it < 3; it++) {
+        if (lane == 0) tri_solve(n, u0, u1, u2, mu, piv, y);
+        __syncwarp();
+        for (int s = t0; s < t; s++) {          // Gram-Schmidt against the cluster's earlier vectors
+          double dot = 0.0;
+          for (int r = lane; r < n; r += 32) dot += y[r] * V[(size_t)r * kmax + s];
+          dot = warp_sum(dot);
+          for (int r = lane; r < n; r += 32) y[r] -= dot * V[(size_t)r * kmax + s];
+          __syncwarp();
+        }
+        double nn = 0.0;
+        for (int r = lane; r < n; r += 32) nn += y[r] * y[r];
+        nn = warp_sum(nn);
+        const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+        for (int r = lane; r < n; r += 32) y[r] *= sc;
+        __syncwarp();
+      }
+      for (int r = lane; r < n; r += 32) V[(size_t)r * kmax + t] = y[r];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // back-transformation V <- H_0 ... H_{n-3} V
+  for (int kk = n - 3; kk >= 0; kk--) {
+    const double tk = tau[kk];
+    if (tk == 0.0) continue;
+    const int L = n - kk - 1;
+    for (int r = threadIdx.x; r < L; r += NT) v[r] = (r == 0) ? 1.0 : A[(size_t)(kk + 1 + r) * n + kk];
+    __syncthreads();
+    for (int t = warp; t < k; t += NT / 32) {
+      double s = 0.0;
+      for (int r = lane; r < L; r += 32) s += v[r] * V[(size_t)(kk + 1 + r) * kmax + t];
+      s = warp_sum(s);
+      if (lane == 0) p[t] = tk * s;   // p reused (clusters no longer needed)
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < L * k; idx += NT) {
+      const int r = idx / k, t = idx % k;
+      V[(size_t)(kk + 1 + r) * kmax + t] -= v[r] * p[t];
+    }
+    __syncthreads();
+  }
+  sign_columns(V, n, kmax, k);
+}
+
+__global__ void __launch_bounds__(NT) k_eig_osv(double* T, int nv, double thr, int kmax, double* V, double* w,
+                                                int* kout, double* scratch, int* err, int zsmem) {
+  extern __shared__ double dyn[];
+  const int b = blockIdx.x;
+  double* A = T + (size_t)b * nv * nv;
+  double* Vb = V + (size_t)b * nv * kmax;
+  double* wb = w + (size_t)b * kmax;
+  double* scr = scratch + (size_t)b * eig_osv_scratch_doubles(nv, kmax);
+  if (zsmem) {
+    const int ldz = nv + 1;
+    double* Zs = dyn;
+    double* sm = dyn + (size_t)nv * ldz;
+    eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zs, ldz, sm);
+  } else if (thr > 0.0) {
+    eig_topk(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, dyn);
+  } else {
+    double* Zg = scr + 3 * nv;
+    eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zg, nv, dyn);
+  }
+}
+
+void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, double* w, int* k,
+                    double* scratch, int* err, cudaStream_t st) {
+  const int zsmem = nv <= ZSMEM_MAX;
+  size_t smem = (size_t)(4 * nv + 64) * sizeof(double);
+  if (zsmem) smem += (size_t)nv * (nv + 1) * sizeof(double);
+  cudaFuncSetAttribute(k_eig_osv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_eig_osv<<<nb, NT, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem);
+}
+
+__global__ void k_pack_q(const double* V, const double* w, int nv, int kmax, const int* k,
+                         double* const* Qdst, double* const* wdst) {
+  const int b = blockIdx.y;
+  const int kb = k[b];
+  const double* Vb = V + (size_t)b * nv * kmax;
+  double* Q = Qdst[b];
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nv * kb; idx += gridDim.x * blockDim.x) {
+    const int r = idx / kb, t = idx % kb;
+    Q[idx] = Vb[(size_t)r * kmax + t];
+  }
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < kb; t += blockDim.x) wdst[b][t] = w[(size_t)b * kmax + t];
+}
+
+void launch_pack_q(const double* V, const double* w, int nb, int nv, int kmax, const int* k,
+                   double* const* Qdst, double* const* wdst, cudaStream_t st) {
+  dim3 grid(32, nb);
+  k_pack_q<<<grid, 256, 0, st>>>(V, w, nv, kmax, k, Qdst, wdst);
+}
+
+}  // namespace osv

@@ -1,0 +1,138 @@
+// A1-A2 in FP64: OSV projection of the RI integrals (Eq. osv_imua),
+// exchange blocks K_(ij,ij) (Eq. osv_close_k, columns from LMO j) and the OSV
+// overlap / Fock blocks of Algorithm 5 (Eq. 4block_osv with A = S, F).
+#include "internal.h"
+
+namespace osv {
+
+struct ProjA {            // A(P, a) = B[i,a,P]
+  BSrc s;
+  int i;
+  __device__ __forceinline__ double get(int P, int a) const { return s.get(i, a, P); }
+};
+struct RowMajor {         // B(r, c) = p[r*ld + c]
+  const double* p;
+  int ld;
+  __device__ __forceinline__ double get(int r, int c) const { return p[(size_t)r * ld + c]; }
+};
+
+// grid: (job, P tile, mu tile)
+__global__ void __launch_bounds__(NT) k_project(BSrc src, Tables t, const ProjJob* __restrict__ jobs) {
+  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  const ProjJob jb = jobs[blockIdx.x];
+  const int nx = t.n_osv[jb.x];
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.z * TN;
+  if (n0 >= nx) return;
+  const int M = src.n_aux, N = nx, K = src.n_vir;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) acc[u][v] = 0.0;
+  tile_mma(M, N, K, m0, n0, ProjA{src, jb.i}, RowMajor{t.Q[jb.x], nx}, acc, sm);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const int r = m0 + ty + 16 * u, c = n0 + tx + 16 * v;
+      if (r < M && c < N) jb.out[(size_t)r * N + c] = acc[u][v];
+    }
+}
+
+void launch_project(const BSrc& src, const Tables& t, const ProjJob* jobs, int n_jobs, int max_nx,
+                    cudaStream_t st) {
+  if (n_jobs == 0) return;
+  dim3 grid(n_jobs, (src.n_aux + TM - 1) / TM, (max_nx + TN - 1) / TN);
+  k_project<<<grid, NT, 0, st>>>(src, t, jobs);
+}
+
+// K_(ij,ij)[mu][nu] = sum_P L[P][mu] R[P][nu] with L = [B~_i^(i) B~_i^(j)],
+// R = [B~_j^(i) B~_j^(j)] (aux x OSV, row-major).  grid: (job, tile r, tile c)
+__global__ void __launch_bounds__(NT) k_exchange(Tables t, int n_aux, const KJob* __restrict__ jobs) {
+  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  const KJob jb = jobs[blockIdx.x];
+  const int ni = t.n_osv[jb.i];
+  const int nj = (jb.i == jb.j) ? 0 : t.n_osv[jb.j];
+  const int m = ni + nj;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.z * TN;
+  if (m0 >= m || n0 >= m) return;
+  View A, B;
+  A.rows = m; A.cols = n_aux; A.rs = ni; A.cs = n_aux;
+  A.b[0][0] = A.b[0][1] = Blk{jb.Bii, ni, 1};
+  A.b[1][0] = A.b[1][1] = Blk{jb.Bij ? jb.Bij : jb.Bii, nj > 0 ? nj : ni, 1};
+  B.rows = n_aux; B.cols = m; B.rs = n_aux; B.cs = ni;
+  if (nj == 0) {
+    B.b[0][0] = B.b[0][1] = B.b[1][0] = B.b[1][1] = Blk{jb.Bii, ni, 0};
+  } else {
+    B.b[0][0] = B.b[1][0] = Blk{jb.Bji, ni, 0};
+    B.b[0][1] = B.b[1][1] = Blk{jb.Bjj, nj, 0};
+  }
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) acc[u][v] = 0.0;
+  tile_mma(m, m, n_aux, m0, n0, A, B, acc, sm);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const int r = m0 + ty + 16 * u, c = n0 + tx + 16 * v;
+      if (r < m && c < m) jb.out[(size_t)r * m + c] = acc[u][v];
+    }
+}
+
+void launch_exchange(const Tables& t, int n_aux, const KJob* jobs, int n_jobs, int max_m, cudaStream_t st) {
+  if (n_jobs == 0) return;
+  const int nt = (max_m + TM - 1) / TM;
+  dim3 grid(n_jobs, nt, nt);
+  k_exchange<<<grid, NT, 0, st>>>(t, n_aux, jobs);
+}
+
+struct QtScaled {         // A(mu, a) = Q_x[a][mu] * (e ? e[a] : 1)
+  const double* q;
+  int ld;
+  const double* e;
+  __device__ __forceinline__ double get(int mu, int a) const {
+    const double v = q[(size_t)a * ld + mu];
+    return e ? v * e[a] : v;
+  }
+};
+
+// S_(x,y) = Q_x^T Q_y and F_(x,y) = Q_x^T diag(e) Q_y.  grid: (job, tile r, tile c, 2)
+__global__ void __launch_bounds__(NT) k_sf(Tables t, const double* __restrict__ e_vir,
+                                           const SFJob* __restrict__ jobs) {
+  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  const SFJob jb = jobs[blockIdx.x];
+  const int nx = t.n_osv[jb.x], ny = t.n_osv[jb.y];
+  const int m0 = blockIdx.y * TM, n0 = (blockIdx.z >> 1) * TN;
+  const int isF = blockIdx.z & 1;
+  if (m0 >= nx || n0 >= ny) return;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) acc[u][v] = 0.0;
+  tile_mma(nx, ny, t.n_vir, m0, n0, QtScaled{t.Q[jb.x], nx, isF ? e_vir : nullptr}, RowMajor{t.Q[jb.y], ny},
+           acc, sm);
+  double* out = isF ? jb.F : jb.S;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const int r = m0 + ty + 16 * u, c = n0 + tx + 16 * v;
+      if (r < nx && c < ny) out[(size_t)r * ny + c] = acc[u][v];
+    }
+}
+
+void launch_sf(const Tables& t, const double* e_vir, const SFJob* jobs, int n_jobs, int max_n, cudaStream_t st) {
+  if (n_jobs == 0) return;
+  const int nt = (max_n + TM - 1) / TM;
+  dim3 grid(n_jobs, nt, 2 * nt);
+  k_sf<<<grid, NT, 0, st>>>(t, e_vir, jobs);
+}
+
+}  // namespace osv

@@ -1,0 +1,266 @@
+"""Python binding of libosvmp2 (C ABI in include/osvmp2.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI.  PyTorch supplies device memory and streams; the
+library never falls back to a CPU path -- if ``libosvmp2.so`` is missing or a
+call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libosvmp2.so")
+
+OSVMP2_FP64 = 0
+OSVMP2_MIXED = 1
+PREC = {"fp64": OSVMP2_FP64, "mixed": OSVMP2_MIXED}
+
+STATUS = {0: "OK", 1: "E_ARG", 2: "E_CUDA", 3: "E_NOMEM", 4: "E_NOCONV", 5: "E_NUMERIC", 6: "E_STATE"}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tau_s", ctypes.c_double), ("tol_update", ctypes.c_double), ("tol_energy", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class System(ctypes.Structure):
+    _fields_ = [("n_occ", ctypes.c_int32), ("n_vir", ctypes.c_int32), ("n_aux", ctypes.c_int32),
+                ("B", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("env", ctypes.c_void_p),
+                ("f_occ", ctypes.c_void_p), ("e_vir", ctypes.c_void_p), ("r_occ", ctypes.c_void_p)]
+
+
+class MbeStats(ctypes.Structure):
+    _fields_ = [("n_single", ctypes.c_int64), ("n_pair", ctypes.c_int64), ("n_triple", ctypes.c_int64),
+                ("n_pair_blocks", ctypes.c_int64), ("max_iter_used", ctypes.c_int32),
+                ("n_unconverged", ctypes.c_int32), ("worst_fragment", ctypes.c_int64),
+                ("max_update", ctypes.c_double), ("flops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# name -> (restype, argtypes); every function declared in include/osvmp2.h
+_P = ctypes.c_void_p
+_I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+SIGNATURES = {
+    "osvmp2_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.POINTER(Opts)]),
+    "osvmp2_destroy": (None, [_P]),
+    "osvmp2_last_error": (ctypes.c_char_p, [_P]),
+    "osvmp2_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "osvmp2_build_osv": (ctypes.c_int, [_P, ctypes.POINTER(System), _D, _P]),
+    "osvmp2_get_osv": (ctypes.c_int, [_P, _I32, _P, _P]),
+    "osvmp2_pair_integrals": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int]),
+    "osvmp2_get_pair_blocks": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P]),
+    "osvmp2_solve": (ctypes.c_int, [_P, _P, _I32, ctypes.c_int, _P, _P, _P]),
+    "osvmp2_mbe3_energy": (ctypes.c_int, [_P, _D, _D, ctypes.c_int, _P, ctypes.POINTER(MbeStats)]),
+    "osvmp2_fragment_results": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "osvmp2_mbe3_fragments": (ctypes.c_int, [_P, _I32, _D, _D, _I64, _P, _P, _P]),
+    "osvmp2_energy_grad": (ctypes.c_int, [_P, _D, _D, ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(MbeStats)]),
+    "osvmp2_generate_B": (ctypes.c_int, [_I32, _I32, _I32, ctypes.c_uint64, _P, _I32, _I32, _P, _P]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libosvmp2.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class OSVMP2Error(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__(f"{fn} -> {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(x) -> Optional[int]:
+    """Device pointer of a torch tensor, host pointer of a numpy array, or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _need_f64_cuda(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    lib().osvmp2_default_opts(ctypes.byref(o))
+    return o
+
+
+def mbe3_fragments(r_occ: np.ndarray, r2_cut: float, r3_cut: float):
+    """Host-only fragment enumeration (same rule as osvmp2_mbe3_energy).
+    Returns (orbs [n,3] int32, -1 padded; weights [n] int32)."""
+    r = np.ascontiguousarray(r_occ, dtype=np.float64)
+    n = ctypes.c_int64(0)
+    s = lib().osvmp2_mbe3_fragments(_ptr(r), r.shape[0], r2_cut, r3_cut, 0, None, None, ctypes.byref(n))
+    if s:
+        raise OSVMP2Error("osvmp2_mbe3_fragments", s, "bad arguments")
+    orbs = np.empty((n.value, 3), dtype=np.int32)
+    w = np.empty(n.value, dtype=np.int32)
+    s = lib().osvmp2_mbe3_fragments(_ptr(r), r.shape[0], r2_cut, r3_cut, n.value, _ptr(orbs), _ptr(w),
+                                    ctypes.byref(n))
+    if s:
+        raise OSVMP2Error("osvmp2_mbe3_fragments", s, "bad arguments")
+    return orbs, w
+
+
+def generate_B(n_occ, n_vir, n_aux, seed, env, i0=0, n_i=None, out=None, stream=None):
+    """B[i0:i0+n_i] regenerated on the device (torch float64 CUDA tensor)."""
+    import torch
+    _need_f64_cuda(env, "env")
+    n_i = n_occ - i0 if n_i is None else n_i
+    if out is None:
+        out = torch.empty((n_i, n_vir, n_aux), dtype=torch.float64, device=env.device)
+    st = stream if stream is not None else torch.cuda.current_stream(env.device).cuda_stream
+    s = lib().osvmp2_generate_B(n_occ, n_vir, n_aux, seed, _ptr(env), i0, n_i, _ptr(out), st)
+    if s:
+        raise OSVMP2Error("osvmp2_generate_B", s, "launch failed")
+    return out
+
+
+class Context:
+    """One osvmp2_ctx on a CUDA device and stream (defaults: current device/stream)."""
+
+    def __init__(self, device: int = 0, stream=None, opts: Optional[Opts] = None, **kw):
+        import torch
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        o = opts or default_opts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        self.opts = o
+        h = ctypes.c_void_p()
+        s = lib().osvmp2_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(o))
+        if s:
+            raise OSVMP2Error("osvmp2_create", s, "could not create context")
+        self._h = h
+        self._keep = ()
+        self.n_occ = self.n_vir = self.n_aux = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().osvmp2_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, fn, code):
+        if code:
+            raise OSVMP2Error(fn, code, lib().osvmp2_last_error(self._h).decode())
+
+    # ---- A0
+    def build_osv(self, f_occ, e_vir, l_osv: float, B=None, env=None, seed: int = 0,
+                  r_occ: Optional[np.ndarray] = None, n_aux: Optional[int] = None) -> np.ndarray:
+        """OSVs of every orbital.  Device tensors: B [n_occ,n_vir,n_aux] or env [n_occ,n_vir]
+        (then B is regenerated from ``seed``), f_occ [n_occ,n_occ], e_vir [n_vir].
+        r_occ: host [n_occ,3].  Returns n_osv (numpy int32)."""
+        _need_f64_cuda(f_occ, "f_occ")
+        _need_f64_cuda(e_vir, "e_vir")
+        if B is not None:
+            _need_f64_cuda(B, "B")
+            n_occ, n_vir, nx = B.shape
+        else:
+            _need_f64_cuda(env, "env")
+            n_occ, n_vir = env.shape
+            if n_aux is None:
+                raise ValueError("n_aux is required when B is regenerated")
+            nx = n_aux
+        r = None if r_occ is None else np.ascontiguousarray(r_occ, dtype=np.float64)
+        sysd = System(n_occ, n_vir, nx, _ptr(B), seed, _ptr(env), _ptr(f_occ), _ptr(e_vir), _ptr(r))
+        n_osv = np.zeros(n_occ, dtype=np.int32)
+        self._check("osvmp2_build_osv", lib().osvmp2_build_osv(self._h, ctypes.byref(sysd), l_osv, _ptr(n_osv)))
+        self._keep = (B, env, f_occ, e_vir, r)
+        self.n_occ, self.n_vir, self.n_aux = n_occ, n_vir, nx
+        self.n_osv = n_osv
+        return n_osv
+
+    def get_osv(self, i: int):
+        import torch
+        k = int(self.n_osv[i])
+        Q = torch.empty((self.n_vir, k), dtype=torch.float64, device=f"cuda:{self.device}")
+        w = torch.empty(k, dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check("osvmp2_get_osv", lib().osvmp2_get_osv(self._h, i, _ptr(Q), _ptr(w)))
+        return Q, w
+
+    # ---- A1-A3
+    def pair_integrals(self, pairs: Sequence[Sequence[int]], prec: str = "fp64"):
+        p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        self._check("osvmp2_pair_integrals",
+                    lib().osvmp2_pair_integrals(self._h, _ptr(p), p.shape[0], PREC[prec]))
+
+    def get_pair_blocks(self, i: int, j: int):
+        import torch
+        m = int(self.n_osv[i] + (self.n_osv[j] if i != j else 0))
+        K, S, F = (torch.empty((m, m), dtype=torch.float64, device=f"cuda:{self.device}") for _ in range(3))
+        self._check("osvmp2_get_pair_blocks", lib().osvmp2_get_pair_blocks(self._h, i, j, _ptr(K), _ptr(S), _ptr(F)))
+        return K, S, F
+
+    # ---- A3-A4
+    def solve(self, orbs: Sequence[int], prec: str = "fp64"):
+        """Returns (E, pair energies [n(n+1)/2] for i<=j in orbs order, iterations)."""
+        o = np.ascontiguousarray(np.asarray(orbs, dtype=np.int32))
+        n = o.shape[0]
+        e = ctypes.c_double(0.0)
+        it = ctypes.c_int32(0)
+        pe = np.zeros(n * (n + 1) // 2)
+        self._check("osvmp2_solve", lib().osvmp2_solve(self._h, _ptr(o), n, PREC[prec], ctypes.addressof(e),
+                                                       _ptr(pe), ctypes.addressof(it)))
+        return e.value, pe, it.value
+
+    # ---- A5
+    def mbe3_energy(self, r2_cut: float, r3_cut: float, prec: str = "fp64"):
+        e = ctypes.c_double(0.0)
+        st = MbeStats()
+        self._check("osvmp2_mbe3_energy", lib().osvmp2_mbe3_energy(self._h, r2_cut, r3_cut, PREC[prec],
+                                                                   ctypes.addressof(e), ctypes.byref(st)))
+        return e.value, st.as_dict()
+
+    def fragment_results(self):
+        n = ctypes.c_int64(0)
+        self._check("osvmp2_fragment_results", lib().osvmp2_fragment_results(self._h, ctypes.byref(n), None, None, None))
+        orbs = np.empty((n.value, 3), dtype=np.int32)
+        w = np.empty(n.value, dtype=np.int32)
+        e = np.empty(n.value)
+        self._check("osvmp2_fragment_results",
+                    lib().osvmp2_fragment_results(self._h, ctypes.byref(n), _ptr(orbs), _ptr(w), _ptr(e)))
+        return orbs, w, e
+
+    # ---- A6
+    def energy_grad(self, r2_cut: float, r3_cut: float, prec: str = "fp64", want_dB: bool = True):
+        import torch
+        dev = f"cuda:{self.device}"
+        dB = torch.empty((self.n_occ, self.n_vir, self.n_aux), dtype=torch.float64, device=dev) if want_dB else None
+        df = torch.empty((self.n_occ, self.n_occ), dtype=torch.float64, device=dev)
+        de = torch.empty(self.n_vir, dtype=torch.float64, device=dev)
+        e = ctypes.c_double(0.0)
+        st = MbeStats()
+        self._check("osvmp2_energy_grad",
+                    lib().osvmp2_energy_grad(self._h, r2_cut, r3_cut, PREC[prec], ctypes.addressof(e), _ptr(dB),
+                                             _ptr(df), _ptr(de), ctypes.byref(st)))
+        return e.value, dB, df, de, st.as_dict()

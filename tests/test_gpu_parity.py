@@ -1,0 +1,119 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _ctx(**kw):
+    from paper_2603_16575_gb300 import Context
+    return Context(0, **kw)
+
+
+def _t(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=DEV)
+
+
+def _build(ctx, s, l_osv, stored=False):
+    if stored:
+        return ctx.build_osv(_t(s.f_occ), _t(s.e_vir), l_osv, B=_t(s.B_full()), r_occ=s.r_occ)
+    return ctx.build_osv(_t(s.f_occ), _t(s.e_vir), l_osv, env=_t(s.env), seed=s.seed, n_aux=s.n_aux, r_occ=s.r_occ)
+
+
+# ---------------------------------------------------------------- generator
+@pytest.mark.parametrize("shape", [(3, 17, 45), (2, 64, 130)])
+def test_generator_bit_exact(shape):
+    from paper_2603_16575_gb300 import generate_B
+    s = synth.make_system(*shape, seed=9, lam=2.0)
+    B = generate_B(s.n_occ, s.n_vir, s.n_aux, s.seed, _t(s.env)).cpu().numpy()
+    ref = s.B_full()
+    assert np.array_equal(B.view(np.uint64), ref.view(np.uint64))
+
+
+# ---------------------------------------------------------------- OSVs
+@pytest.mark.parametrize("n_vir,l_osv,lam", [(40, 0.0, 3.0), (70, 1e-4, 1.5), (200, 1e-4, 1.0), (260, 1e-3, 1.5)])
+def test_osv_match_oracle(n_vir, l_osv, lam):
+    s = synth.make_system(3, n_vir, 3 * n_vir // 2 + 7, seed=4, lam=lam)
+    o = oracle.OSVSystem(s.B_block, 3, s.e_vir, s.f_occ, l_osv=l_osv)
+    ctx = _ctx()
+    n_osv = _build(ctx, s, l_osv)
+    assert list(n_osv) == [q.shape[1] for q in o.Q]
+    for i in range(3):
+        Q, w = ctx.get_osv(i)
+        Q, w = Q.cpu().numpy(), w.cpu().numpy()
+        wr = o.omega[i]
+        assert np.allclose(w, wr, rtol=1e-10, atol=1e-13 * wr.max())
+        assert np.allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-11)
+        # the kept space: projectors agree
+        Pr = o.Q[i] @ o.Q[i].T
+        assert np.abs(Q @ Q.T - Pr).max() < 1e-9
+    ctx.close()
+
+
+# ---------------------------------------------------------------- pair blocks
+def test_pair_blocks_match_dense_definition():
+    s = synth.make_system(4, 50, 80, seed=6, lam=2.0)
+    ctx = _ctx()
+    _build(ctx, s, 1e-4)
+    pairs = [(0, 1), (1, 3), (2, 2)]
+    ctx.pair_integrals(pairs)
+    Qs = [ctx.get_osv(i)[0].cpu().numpy() for i in range(4)]
+    for (i, j) in pairs:
+        K, S, F = (x.cpu().numpy() for x in ctx.get_pair_blocks(i, j))
+        P = oracle.pair_basis(Qs, i, j)
+        Kr = oracle.exchange_block(P, s.B_block(i), s.B_block(j))
+        assert np.allclose(K, Kr, rtol=1e-11, atol=1e-12 * np.abs(Kr).max())
+        assert np.allclose(S, P.T @ P, atol=1e-13)
+        assert np.allclose(F, P.T @ (s.e_vir[:, None] * P), atol=1e-12)
+    ctx.close()
+
+
+# ---------------------------------------------------------------- full solve
+@pytest.mark.parametrize("stored", [False, True])
+def test_untruncated_solve_equals_closed_form(stored):
+    s = synth.make_system(5, 14, 40, seed=11, lam=3.0, f_off=1e-2)
+    ctx = _ctx()
+    _build(ctx, s, 0.0, stored=stored)
+    E, pe, it = ctx.solve(range(5))
+    e_cf = oracle.canonical_mp2_energy(s.B_block, 5, s.f_occ, s.e_vir)
+    assert abs(E - e_cf) < 1e-9 and abs(E - e_cf) < 1e-11 * abs(e_cf)
+    r = oracle.OSVSystem(s.B_block, 5, s.e_vir, s.f_occ, l_osv=0.0).solve(range(5))
+    ref = [r.pair_energy[(a, b)] for a in range(5) for b in range(a, 5)]
+    assert np.allclose(pe, ref, rtol=1e-9, atol=1e-12)
+    ctx.close()
+
+
+def test_truncated_solve_matches_oracle():
+    s = synth.make_system(6, 60, 100, seed=12, lam=1.5, f_off=2e-2)
+    ctx = _ctx()
+    _build(ctx, s, 1e-4)
+    orbs = [0, 2, 3, 5]
+    E, pe, it = ctx.solve(orbs)
+    o = oracle.OSVSystem(s.B_block, 6, s.e_vir, s.f_occ, l_osv=1e-4)
+    r = o.solve(orbs)
+    assert abs(E - r.energy) < 1e-9
+    ctx.close()
+
+
+# ---------------------------------------------------------------- MBE(3)
+def test_mbe3_energy_matches_oracle():
+    s = synth.make_system(10, 64, 120, seed=21, lam=1.2)
+    ctx = _ctx()
+    _build(ctx, s, 1e-4)
+    E, st = ctx.mbe3_energy(4.0, 3.5)
+    o = oracle.OSVSystem(s.B_block, 10, s.e_vir, s.f_occ, l_osv=1e-4)
+    E_ref, per = o.mbe3_energy(s.r_occ, 4.0, 3.5)
+    orbs, w, ef = ctx.fragment_results()
+    assert len(per) == len(orbs)
+    for (ob, c, e_ref), ogpu, cg, eg in zip(per, orbs, w, ef):
+        assert tuple(int(x) for x in ogpu if x >= 0) == ob and int(cg) == c
+        assert abs(eg - e_ref) < 1e-10
+    assert st["n_unconverged"] == 0
+    assert abs(E - E_ref) < 1e-9
+    ctx.close()
