@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""MBE(3)-OSV-MP2 throughput on GB300: fragments/s of the whole pair-solve path.
+
+One step = the full hot path over one synthetic system: OSV build (A0), OSV
+projection and pair blocks (A1-A2), preconditioners (A3), the persistent
+fragment solve (A4) and the MBE(3) energy (A5) -- and, with --grad, the
+frozen-OSV adjoint (A6).  Workload (default): 128 occupied LMOs, 640 virtuals,
+2400 auxiliary functions, envelope length 1 A, l_osv = 1e-4, pairs within 8 A
+and triples within 6 A; B is regenerated on the device from its seed (never
+stored) unless --b-mode stored.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+R2_CUT, R3_CUT, L_OSV = 8.0, 6.0, 1e-4
+# Measured on this GB300 pool (peaks file + FP64 unit count x clock):
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 DFMA/clk/SM at the 2070 MHz maximum -> 1.258
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "_fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import paper_2603_16575_gb300 as pkg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    # every rank solves its own independent system (weak scaling, no data-path collective)
+    s = synth.workload(args.workload, seed=args.seed + rank)
+    stream = torch.cuda.Stream(dev)
+    peaks = load_peaks()
+    with torch.cuda.stream(stream):
+        env = torch.tensor(s.env, device=dev)
+        f_occ = torch.tensor(s.f_occ, device=dev)
+        e_vir = torch.tensor(s.e_vir, device=dev)
+        B = None
+        if args.b_mode == "stored":
+            B = pkg.generate_B(s.n_occ, s.n_vir, s.n_aux, s.seed, env, stream=stream.cuda_stream)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
+    stream.synchronize()
+    ctx = pkg.Context(local, stream=stream)
+
+    def step(B_in=B, env_in=env, f_in=f_occ, e_in=e_vir):
+        kw = dict(B=B_in) if B_in is not None else dict(env=env_in, seed=s.seed, n_aux=s.n_aux)
+        n_osv = ctx.build_osv(f_in, e_in, L_OSV, r_occ=s.r_occ, **kw)
+        if args.grad:
+            E, dB, df, de, st = ctx.energy_grad(R2_CUT, R3_CUT, args.prec)
+        else:
+            E, st = ctx.mbe3_energy(R2_CUT, R3_CUT, args.prec)
+        return E, st, n_osv
+
+    for _ in range(args.warmup):
+        E, st, n_osv = step()
+    n_frag = int(st["n_single"] + st["n_pair"] + st["n_triple"])
+    ctx.profile(reset=True)
+    launches0 = pkg.osvmp2.kernel_launches()
+    t_steps = []
+    with ClockSampler(local) as clk:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()                       # evict L2 between timed steps (untimed)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            E, st, n_osv = step()
+            ev1.record(stream)
+            ev1.synchronize()
+            t_steps.append(ev0.elapsed_time(ev1) / 1e3)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    launches = pkg.osvmp2.kernel_launches() - launches0
+    prof = ctx.profile(reset=True)
+    t_tot = sum(t_steps)
+    if world > 1:
+        tt = torch.tensor([t_tot], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_tot = float(tt.item())
+    value = world * n_frag * args.steps / t_tot
+
+    # ---- end to end: host (pinned) inputs copied in and the energy read back every step
+    pin = lambda a: torch.tensor(a).pin_memory()
+    h_env, h_f, h_e = pin(s.env), pin(s.f_occ), pin(s.e_vir)
+    h_B = B.cpu().pin_memory() if B is not None else None
+    d_env, d_f, d_e = torch.empty_like(env), torch.empty_like(f_occ), torch.empty_like(e_vir)
+    d_B = torch.empty_like(B) if B is not None else None
+    h2d = sum(x.numel() * 8 for x in (h_env, h_f, h_e)) + (h_B.numel() * 8 if h_B is not None else 0)
+    e2e_t = []
+    for _ in range(max(1, args.steps)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            d_env.copy_(h_env, non_blocking=True)
+            d_f.copy_(h_f, non_blocking=True)
+            d_e.copy_(h_e, non_blocking=True)
+            if h_B is not None:
+                d_B.copy_(h_B, non_blocking=True)
+        E2, _, _ = step(B_in=d_B, env_in=d_env, f_in=d_f, e_in=d_e)   # E2 is read back to the host
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = world * n_frag / statistics.median(e2e_t)
+
+    # ---- roofline of the dominant kernel (largest device time in the timed region)
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (ms, fl, by, calls) = dom
+    per_launch_s = ms / 1e3 / max(calls, 1)
+    if fl > 0:
+        achieved = fl / max(calls, 1) / per_launch_s / 1e12
+        bound, unit, peak = "alu", "TFLOP/s", FP64_PEAK_TFLOPS
+        if args.prec == "mixed" and name in ("project", "exchange", "tii"):
+            bound, peak = "tensor", float(peaks.get("bf16_tflops_sustained", 1753.8)) / 2.0
+    else:
+        achieved, bound, unit, peak = None, "alu", "TFLOP/s", FP64_PEAK_TFLOPS
+    traffic = None
+    roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal 1.25 TF; cuBLAS DGEMM measured 1.10)"}
+    phases = {k: {"ms_per_step": v[0] / args.steps, "tflops": (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 and v[1] else None}
+              for k, v in prof.items()}
+
+    out = {
+        "metric": "MBE(3) fragments/s",
+        "value": value,
+        "unit": "fragments/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_tot / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.prec == "fp64" else "f64+split-f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} (n_occ={s.n_occ}, n_vir={s.n_vir}, n_aux={s.n_aux}, "
+                               f"lambda={s.lam} A, l_osv={L_OSV}, r2={R2_CUT} A, r3={R3_CUT} A)",
+                   "prec": args.prec, "b_mode": args.b_mode, "grad": bool(args.grad),
+                   "fragments": n_frag, "n_single": int(st["n_single"]), "n_pair": int(st["n_pair"]),
+                   "n_triple": int(st["n_triple"]), "n_osv_mean": float(np.mean(n_osv)),
+                   "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
+        "energy": E,
+        "e2e": {"value": e2e_value, "unit": "fragments/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": 8},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "phases": phases,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_sample(args, budget_s: float):
+    """Oracle on a bounded sample: the k orbitals nearest to orbital 0 and every
+    fragment of the workload's MBE(3) list whose orbitals all lie in that set
+    (OSV build of those orbitals + all their fragment solves)."""
+    import oracle
+    s = synth.workload(args.workload, seed=args.seed)
+    d = np.linalg.norm(s.r_occ - s.r_occ[0], axis=1)
+    k = args.cpu_orbitals
+    near = sorted(np.argsort(d, kind="stable")[:k].tolist())
+    sel = set(near)
+    frags = [(o, c) for o, c in oracle.mbe3_fragments(s.r_occ, R2_CUT, R3_CUT) if set(o) <= sel]
+    t0 = time.perf_counter()
+    osys = oracle.OSVSystem(s.B_block, s.n_occ, s.e_vir, s.f_occ, l_osv=L_OSV, orbitals=near)
+    done = 0
+    for orbs, c in frags:
+        osys.solve(orbs)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt, k
+
+
+def cpu_baseline(args, budget_s: float):
+    done, dt, k = cpu_sample(args, budget_s)
+    return {"value": done / dt, "unit": "fragments/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"OSV build of the {k} orbitals nearest orbital 0 + the {done} MBE(3) fragments inside "
+                      f"that set ({dt:.1f} s, NumPy FP64, BLAS threads = all cores)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_sample(args, args.cpu_budget)
+    vals, times, frags = [], [], 0
+    for _ in range(args.steps):
+        done, dt, k = cpu_sample(args, args.cpu_budget)
+        vals.append(done / dt)
+        times.append(dt)
+        frags = done
+    v = statistics.median(vals)
+    print(json.dumps({
+        "impl": "reference", "metric": "MBE(3) fragments/s", "value": v, "unit": "fragments/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} (bounded sample, {args.cpu_orbitals} orbitals)"},
+        "cpu_baseline": {"value": v, "unit": "fragments/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{frags} fragments among the {args.cpu_orbitals} orbitals nearest orbital 0"},
+        "e2e": {"value": v, "unit": "fragments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--workload", default="mbe3_n128", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--b-mode", choices=["regen", "stored"], default="regen")
+    ap.add_argument("--grad", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-orbitals", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -64,8 +64,10 @@ typedef enum {
 
 typedef struct {
   double tau_s;       /* drop S_(ij,ij) eigenvalues below tau_s * max eigenvalue (default 1e-10) */
-  double tol_update;  /* stop when max |R~ / D| below this ...                (default 1e-11) */
+  double tol_update;  /* stop when max |R~ / D| below this ...                (default 1e-7)  */
   double tol_energy;  /* ... and |E_C(it) - E_C(it-1)| below this, Eh         (default 1e-13) */
+                      /* (the energy test does the fine convergence: the update
+                          has a rounding floor of ~eps*cond(S_(ij,ij)))       */
   int32_t max_iter;   /* amplitude iterations per fragment                    (default 100) */
   int32_t reserved[7];
 } osvmp2_opts;
@@ -104,6 +106,8 @@ void osvmp2_destroy(osvmp2_ctx *ctx);
 const char *osvmp2_last_error(const osvmp2_ctx *ctx);
 /* Fill opts with the defaults listed in osvmp2_opts. */
 void osvmp2_default_opts(osvmp2_opts *opts);
+/* Number of CUDA kernels this library has launched in this process (all ctxs). */
+int64_t osvmp2_kernel_launches(void);
 
 /* ---- A0: OSV generation (Eq. mp2_tkk, Eq. osv_gen, Algorithm 3's output) --
  * For every occupied i: T_ii[a][b] = sum_P B[i,a,P] B[i,b,P] / (e_a + e_b - 2 f_ii),
@@ -130,6 +134,12 @@ int osvmp2_pair_integrals(osvmp2_ctx *ctx, const int32_t *pairs, int64_t n_pairs
  * m = n_i + n_j (n_i if i == j); any output may be NULL. */
 int osvmp2_get_pair_blocks(osvmp2_ctx *ctx, int32_t i, int32_t j, double *K_dev, double *S_dev,
                            double *F_dev);
+
+/* Preconditioner of built pair (i,j) (Eq. prec_eig): X (device [m][m], row-major;
+ * columns 0..r-1 valid) with X^T S X = 1 and X^T F X = diag(e~), e~ (device [m],
+ * first r valid), r (host scalar) = number of S_(ij,ij) eigenvalues above
+ * tau_s * max.  Any output may be NULL. */
+int osvmp2_get_precond(osvmp2_ctx *ctx, int32_t i, int32_t j, double *X_dev, double *et_dev, int32_t *r_out);
 
 /* ---- A3-A4: OSV-MP2 solve of one subsystem (Eq. res_close, Algorithm 7) ----
  * orbs: host [n_orbs] distinct occupied indices (e.g. all of them).  Solves the
@@ -175,6 +185,27 @@ int osvmp2_mbe3_fragments(const double *r_occ, int32_t n_occ, double r2_cut, dou
 int osvmp2_energy_grad(osvmp2_ctx *ctx, double r2_cut, double r3_cut, osvmp2_prec prec,
                        double *e_out, double *dE_dB, double *dE_df, double *dE_de,
                        osvmp2_mbe_stats *stats);
+
+/* ---- profiling -----------------------------------------------------------
+ * Phases timed with CUDA events on the ctx stream around their kernels. */
+enum {
+  OSVMP2_PH_TII = 0,       /* A0: T_ii from B (Eq. mp2_tkk) */
+  OSVMP2_PH_EIG = 1,       /* A0: eigen-decomposition and selection (Eq. osv_gen) */
+  OSVMP2_PH_SF = 2,        /* A2: S_(x,y), F_(x,y) */
+  OSVMP2_PH_PROJECT = 3,   /* A1: B~ = B^T Q (Eq. osv_imua) */
+  OSVMP2_PH_EXCHANGE = 4,  /* A2: K_(ij,ij) (Eq. osv_close_k) */
+  OSVMP2_PH_PRECOND = 5,   /* A3: Eq. prec_eig */
+  OSVMP2_PH_SOLVE = 6,     /* A4: persistent fragment solve (Algorithm 7) */
+  OSVMP2_PH_MBE_SUM = 7,   /* A5: weighted fragment-energy sum */
+  OSVMP2_PH_SUBSOLVE = 8,  /* A4: pair-parallel subsystem solve (osvmp2_solve) */
+  OSVMP2_PH_GRAD = 9,      /* A6: adjoint kernels */
+  OSVMP2_NPHASE = 12
+};
+/* Accumulated since the last reset, per phase (host arrays of OSVMP2_NPHASE, any
+ * may be NULL): device milliseconds, algorithmic FP operations (GEMM-shaped
+ * phases; 0 where not counted), DRAM bytes the phase must read at least
+ * (0 where not counted) and number of timed launches.  Synchronises the ctx stream. */
+int osvmp2_profile(osvmp2_ctx *ctx, double *ms, double *flops, double *bytes, int64_t *calls, int reset);
 
 /* ---- generator ---------------------------------------------------------
  * Materialise B[i0:i0+n_i][n_vir][n_aux] = env[i][a] * z(seed,i,a,P) on the

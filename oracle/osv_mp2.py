@@ -79,13 +79,12 @@ def osv_from_tii(T_ii: np.ndarray, l_osv: float) -> Tuple[np.ndarray, np.ndarray
 
 
 def build_osv(Bfun: Callable[[int], np.ndarray], n_occ: int, e_vir: np.ndarray,
-              f_occ: np.ndarray, l_osv: float) -> Tuple[List[np.ndarray], List[np.ndarray]]:
-    """OSVs of every occupied orbital (Algorithm 3's output, by exact eigh)."""
-    Q, W = [], []
-    for i in range(n_occ):
-        q, w = osv_from_tii(semicanonical_tii(Bfun(i), e_vir, f_occ[i, i]), l_osv)
-        Q.append(q)
-        W.append(w)
+              f_occ: np.ndarray, l_osv: float, orbitals=None) -> Tuple[List, List]:
+    """OSVs of every occupied orbital (Algorithm 3's output, by exact eigh);
+    with ``orbitals`` only those entries are built (the rest stay None)."""
+    Q, W = [None] * n_occ, [None] * n_occ
+    for i in (range(n_occ) if orbitals is None else orbitals):
+        Q[i], W[i] = osv_from_tii(semicanonical_tii(Bfun(i), e_vir, f_occ[i, i]), l_osv)
     return Q, W
 
 
@@ -217,7 +216,7 @@ class Fragment:
         return float(sum(self.pair_energy(T, p) for p in self.pairs))
 
 
-def solve_fragment(frag: Fragment, tol: float = 1e-13, e_tol: float = 1e-15,
+def solve_fragment(frag: Fragment, tol: float = 1e-7, e_tol: float = 1e-14,
                    max_iter: int = 500) -> FragmentResult:
     """Algorithm 7 (close clusters): R, R~ = X^T R X, T += X (R~ / D) X^T, E.
 
@@ -342,7 +341,8 @@ class OSVSystem:
     """Oracle-side state of one system: inputs plus OSVs."""
 
     def __init__(self, Bfun: Callable[[int], np.ndarray], n_occ: int, e_vir: np.ndarray,
-                 f_occ: np.ndarray, l_osv: float, tau_s: float = 1e-10, cache_B: bool = True):
+                 f_occ: np.ndarray, l_osv: float, tau_s: float = 1e-10, cache_B: bool = True,
+                 orbitals=None):
         self._B: Dict[int, np.ndarray] = {}
         self._Bsrc = Bfun
         self.cache = cache_B
@@ -350,7 +350,7 @@ class OSVSystem:
         self.e_vir = np.asarray(e_vir, dtype=np.float64)
         self.f_occ = np.asarray(f_occ, dtype=np.float64)
         self.tau_s = tau_s
-        self.Q, self.omega = build_osv(self.B, n_occ, self.e_vir, self.f_occ, l_osv)
+        self.Q, self.omega = build_osv(self.B, n_occ, self.e_vir, self.f_occ, l_osv, orbitals)
 
     def B(self, i: int) -> np.ndarray:
         if i in self._B:

@@ -2,6 +2,7 @@
 // device-resident OSV / pair store, job lists for the kernels, and the MBE(3)
 // fragment enumeration.  All arithmetic of the method runs in the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -13,6 +14,11 @@
 #include "internal.h"
 
 using namespace osv;
+
+namespace osv {
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace osv
 
 namespace {
 
@@ -64,6 +70,15 @@ struct osvmp2_ctx {
   // last MBE call
   std::vector<Frag> frags;
   std::vector<FragOut> frag_out;
+  // per-phase device time (CUDA events on st) and algorithmic flops, accumulated
+  cudaEvent_t ev0[OSVMP2_NPHASE] = {}, ev1[OSVMP2_NPHASE] = {};
+  bool pending[OSVMP2_NPHASE] = {};
+  double ms[OSVMP2_NPHASE] = {};
+  double flops[OSVMP2_NPHASE] = {};
+  double bytes[OSVMP2_NPHASE] = {};
+  long long calls[OSVMP2_NPHASE] = {};
+  std::vector<int> r_h;               // preconditioner ranks (host copy)
+  std::vector<double> f_h;            // occupied Fock block (host copy, flop counts)
 };
 
 namespace {
@@ -162,15 +177,37 @@ BSrc bsrc(const osvmp2_ctx* c) {
   return BSrc{c->sys.B, c->sys.env, c->key, c->sys.n_vir, c->sys.n_aux};
 }
 
+void ph_collect(osvmp2_ctx* c);
+
 int check_err_flag(osvmp2_ctx* c, const char* where) {
   int h = 0;
   CK(cudaMemcpyAsync(&h, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   CK(cudaGetLastError());
+  ph_collect(c);
   if (h & ERR_EIG) return fail(c, OSVMP2_E_NUMERIC, "%s: eigen-solver did not converge", where);
   if (h & ERR_NONFINITE) return fail(c, OSVMP2_E_NUMERIC, "%s: non-finite values", where);
   if (h & ERR_SIZE) return fail(c, OSVMP2_E_NUMERIC, "%s: size limit exceeded", where);
   return 0;
+}
+
+void ph_begin(osvmp2_ctx* c, int ph) { cudaEventRecord(c->ev0[ph], c->st); }
+void ph_end(osvmp2_ctx* c, int ph, double flops, double bytes = 0.0) {
+  cudaEventRecord(c->ev1[ph], c->st);
+  c->pending[ph] = true;
+  c->flops[ph] += flops;
+  c->bytes[ph] += bytes;
+  c->calls[ph]++;
+}
+// Call after a stream synchronisation: fold finished phase timings in.
+void ph_collect(osvmp2_ctx* c) {
+  for (int ph = 0; ph < OSVMP2_NPHASE; ph++)
+    if (c->pending[ph]) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, c->ev0[ph], c->ev1[ph]) == cudaSuccess) c->ms[ph] += t;
+      else cudaGetLastError();
+      c->pending[ph] = false;
+    }
 }
 
 template <class T>
@@ -230,6 +267,38 @@ void enumerate_fragments(const double* r, int n, double r2, double r3, std::vect
 }
 
 int pair_dim_h(const osvmp2_ctx* c, int i, int j) { return c->n_osv[i] + (i != j ? c->n_osv[j] : 0); }
+
+// FP operations of one Jacobi sweep of a fragment as the solver performs it:
+// per pair p (m x m, rank r) 4 GEMMs m^3 for G1 T S + S T G2, two GEMMs per
+// coupling term (q != p, coefficient != 0), the four GEMMs of the
+// preconditioned update and the energy contraction.
+double fragment_iter_flops(const osvmp2_ctx* c, const Frag& f) {
+  const int n = c->sys.n_occ;
+  int orbs[3], nc = 0;
+  for (int u = 0; u < 3; u++)
+    if (f.orbs[u] >= 0) orbs[nc++] = f.orbs[u];
+  double fl = 0.0;
+  for (int a = 0; a < nc; a++)
+    for (int b = a; b < nc; b++) {
+      const int i = orbs[a], j = orbs[b];
+      const double m = pair_dim_h(c, i, j);
+      const int pid = c->pair_id[(size_t)i * n + j];
+      const double r = (pid >= 0 && pid < (int)c->r_h.size()) ? c->r_h[pid] : m;
+      fl += 8.0 * m * m * m + 4.0 * m * m * r + 4.0 * m * r * r + 3.0 * m * m;
+      for (int cc = 0; cc < nc; cc++)
+        for (int s2 = 0; s2 < 2; s2++) {
+          if (s2 == 0 && cc == b) continue;
+          if (s2 == 1 && cc == a) continue;
+          const int x = (s2 == 0) ? a : cc, y = (s2 == 0) ? cc : b;
+          const int k = orbs[cc];
+          const double coef = (s2 == 0) ? c->f_h[(size_t)k * n + j] : c->f_h[(size_t)i * n + k];
+          if (coef == 0.0) continue;
+          const double mq = pair_dim_h(c, orbs[std::min(x, y)], orbs[std::max(x, y)]);
+          fl += 2.0 * mq * mq * m + 2.0 * m * m * mq;
+        }
+    }
+  return fl;
+}
 
 // Build S/F blocks, projections, K and preconditioners for every listed pair
 // (and the diagonal pairs of its orbitals) that is not built yet.
@@ -365,20 +434,35 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   CK(cudaMemcpyAsync(jp.p, pjb.data(), pjb.size() * sizeof(PJob), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
   const Tables t = tables(c);
+  double f_sf = 0, f_pj = 0, f_k = 0;
+  for (auto& j : sfj) f_sf += 4.0 * nv * (double)c->n_osv[j.x] * c->n_osv[j.y];
+  for (auto& j : pj) f_pj += 2.0 * nx * (double)nv * c->n_osv[j.x];
+  for (auto& j : kj) { const double m = pair_dim_h(c, j.i, j.j); f_k += 2.0 * nx * m * m; }
+  ph_begin(c, OSVMP2_PH_SF);
   launch_sf(t, c->sys.e_vir, (const SFJob*)jsf.p, (int)sfj.size(), max_n, c->st);
+  ph_end(c, OSVMP2_PH_SF, f_sf);
   CK(cudaGetLastError());
+  ph_begin(c, OSVMP2_PH_PROJECT);
   launch_project(bsrc(c), t, (const ProjJob*)jpj.p, (int)pj.size(), max_nx, c->st);
+  ph_end(c, OSVMP2_PH_PROJECT, f_pj, c->sys.B ? 8.0 * (double)pj.size() * nx * nv : 0.0);
   CK(cudaGetLastError());
+  ph_begin(c, OSVMP2_PH_EXCHANGE);
   launch_exchange(t, nx, (const KJob*)jk.p, (int)kj.size(), max_m, c->st);
+  ph_end(c, OSVMP2_PH_EXCHANGE, f_k);
   CK(cudaGetLastError());
   const int n_cta = std::min<int>((int)pjb.size(), 2 * c->num_sms);
   TRY(tmp_alloc(c, scr, (size_t)n_cta * precond_scratch_doubles(max_m) * sizeof(double)));
+  ph_begin(c, OSVMP2_PH_PRECOND);
   launch_precond(t, c->opts.tau_s, (const PJob*)jp.p, (int)pjb.size(), max_m, (double*)scr.p, n_cta, c->err_d,
                  c->st);
+  ph_end(c, OSVMP2_PH_PRECOND, 0.0);
   CK(cudaGetLastError());
-  (void)nv;
   (void)prec;
-  return check_err_flag(c, "pair integrals");
+  TRY(check_err_flag(c, "pair integrals"));
+  c->r_h.resize(c->K_h.size());
+  CK(cudaMemcpyAsync(c->r_h.data(), c->r_d, c->r_h.size() * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return 0;
 }
 
 }  // namespace
@@ -386,11 +470,13 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
 // ============================================================== C ABI
 extern "C" {
 
+int64_t osvmp2_kernel_launches(void) { return (int64_t)osv::g_launches.load(); }
+
 void osvmp2_default_opts(osvmp2_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof *o);
   o->tau_s = 1e-10;
-  o->tol_update = 1e-11;
+  o->tol_update = 1e-7;
   o->tol_energy = 1e-13;
   o->max_iter = 100;
 }
@@ -411,6 +497,10 @@ int osvmp2_create(osvmp2_ctx** out, int device, void* cuda_stream, const osvmp2_
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc(&c->err_d, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->scal_d, 16 * sizeof(double));
+  for (int ph = 0; ph < OSVMP2_NPHASE && e == cudaSuccess; ph++) {
+    e = cudaEventCreate(&c->ev0[ph]);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1[ph]);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -426,6 +516,10 @@ void osvmp2_destroy(osvmp2_ctx* c) {
   free_system(c);
   if (c->err_d) cudaFree(c->err_d);
   if (c->scal_d) cudaFree(c->scal_d);
+  for (int ph = 0; ph < OSVMP2_NPHASE; ph++) {
+    if (c->ev0[ph]) cudaEventDestroy(c->ev0[ph]);
+    if (c->ev1[ph]) cudaEventDestroy(c->ev1[ph]);
+  }
   delete c;
 }
 
@@ -446,6 +540,8 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   c->key = mix64((uint64_t)s->seed ^ (STREAM_B * STREAM_MUL));
   c->r_occ.clear();
   if (s->r_occ) c->r_occ.assign(s->r_occ, s->r_occ + 3 * (size_t)s->n_occ);
+  c->f_h.resize((size_t)s->n_occ * s->n_occ);
+  CK(cudaMemcpy(c->f_h.data(), s->f_occ, c->f_h.size() * sizeof(double), cudaMemcpyDeviceToHost));
   const int n = s->n_occ, nv = s->n_vir;
   c->cap_pairs = n * (n + 1) / 2;
   TRY(dalloc_t(c, &c->n_osv_d, n));
@@ -483,13 +579,18 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   std::vector<int> kh(nb);
   for (int i0 = 0; i0 < n; i0 += nb) {
     const int b = std::min(nb, n - i0);
+    ph_begin(c, OSVMP2_PH_TII);
     launch_tii(bsrc(c), s->e_vir, s->f_occ, n, i0, b, (double*)Tm.p, c->st);
+    ph_end(c, OSVMP2_PH_TII, (double)b * nv * (double)nv * s->n_aux, s->B ? 8.0 * b * (double)nv * s->n_aux : 0.0);
     CK(cudaGetLastError());
+    ph_begin(c, OSVMP2_PH_EIG);
     launch_eig_osv((double*)Tm.p, b, nv, l_osv, kmax, (double*)Vm.p, (double*)wm.p, (int*)km.p, (double*)sm.p,
                    c->err_d, c->st);
+    ph_end(c, OSVMP2_PH_EIG, 0.0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(kh.data(), km.p, b * sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
+    ph_collect(c);
     size_t tot = 0;
     for (int u = 0; u < b; u++) tot += (size_t)kh[u] * (nv + 1);
     double* mem = nullptr;
@@ -588,6 +689,21 @@ int osvmp2_get_pair_blocks(osvmp2_ctx* c, int32_t i, int32_t j, double* K, doubl
   return OSVMP2_OK;
 }
 
+int osvmp2_get_precond(osvmp2_ctx* c, int32_t i, int32_t j, double* X, double* et, int32_t* r_out) {
+  if (!c) return OSVMP2_E_ARG;
+  if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "no OSVs built");
+  const int n = c->sys.n_occ;
+  if (i < 0 || j < i || j >= n) return fail(c, OSVMP2_E_ARG, "pair (%d,%d) invalid", i, j);
+  const int pid = c->pair_id[(size_t)i * n + j];
+  if (pid < 0) return fail(c, OSVMP2_E_STATE, "pair (%d,%d) not built", i, j);
+  const int m = c->m_h[pid];
+  if (X) CK(cudaMemcpyAsync(X, c->X_h[pid], (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  if (et) CK(cudaMemcpyAsync(et, c->et_h[pid], (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (r_out) *r_out = c->r_h[pid];
+  return OSVMP2_OK;
+}
+
 int osvmp2_solve(osvmp2_ctx* c, const int32_t* orbs, int32_t n_orbs, osvmp2_prec prec, double* e_out,
                  double* pair_e_out, int32_t* iters_out) {
   if (!c) return OSVMP2_E_ARG;
@@ -638,13 +754,16 @@ int osvmp2_solve(osvmp2_ctx* c, const int32_t* orbs, int32_t n_orbs, osvmp2_prec
   int it = 1;
   bool conv = false;
   for (; it <= c->opts.max_iter; it++) {
+    ph_begin(c, OSVMP2_PH_SUBSOLVE);
     launch_sub_residual(t, sd, np, n_cta, c->st);
     launch_sub_update(t, sd, np, n_cta, c->st);
+    ph_end(c, OSVMP2_PH_SUBSOLVE, 0.0);
     CK(cudaGetLastError());
     double h[2];
     CK(cudaMemcpyAsync(&h[0], (double*)pe.p + np, sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(&h[1], (double*)pu.p + np, sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
+    ph_collect(c);
     e = h[0];
     um = h[1];
     if (!std::isfinite(e) || !std::isfinite(um)) return fail(c, OSVMP2_E_NUMERIC, "non-finite energy in solve");
@@ -733,15 +852,23 @@ int osvmp2_mbe3_energy(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, do
   CK(cudaMemcpyAsync(d_order.p, order.data(), nf * sizeof(int), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(d_w.p, w_h.data(), nf * sizeof(int), cudaMemcpyHostToDevice, c->st));
   SolveOpts so{c->opts.tol_update, c->opts.tol_energy, c->opts.max_iter};
+  ph_begin(c, OSVMP2_PH_SOLVE);
   launch_frag_solve(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, (double*)d_scr.p, n_cta,
                     (int*)d_cnt.p, (FragOut*)d_out.p, c->st);
   CK(cudaGetLastError());
+  ph_end(c, OSVMP2_PH_SOLVE, 0.0);
+  ph_begin(c, OSVMP2_PH_MBE_SUM);
   launch_weighted_sum((const FragOut*)d_out.p, (const int*)d_w.p, nf, c->scal_d, c->st);
+  ph_end(c, OSVMP2_PH_MBE_SUM, 2.0 * nf);
   CK(cudaGetLastError());
   c->frag_out.resize(nf);
   CK(cudaMemcpyAsync(c->frag_out.data(), d_out.p, nf * sizeof(FragOut), cudaMemcpyDeviceToHost, c->st));
   CK(cudaMemcpyAsync(e_out, c->scal_d, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  ph_collect(c);
+  double f_solve = 0.0;
+  for (int f = 0; f < nf; f++) f_solve += c->frag_out[f].iters * fragment_iter_flops(c, c->frags[f]);
+  c->flops[OSVMP2_PH_SOLVE] += f_solve;
   int unconv = 0, maxit = 0;
   int64_t worst = -1;
   double maxu = 0.0;
@@ -763,11 +890,25 @@ int osvmp2_mbe3_energy(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, do
     stats->n_unconverged = unconv;
     stats->worst_fragment = worst;
     stats->max_update = maxu;
-    stats->flops = 0.0;
+    stats->flops = f_solve;
   }
   if (unconv)
     return fail(c, OSVMP2_E_NOCONV, "%d fragment(s) did not converge; first is fragment %lld", unconv,
                 (long long)worst);
+  return OSVMP2_OK;
+}
+
+int osvmp2_profile(osvmp2_ctx* c, double* ms, double* flops, double* bytes, int64_t* calls, int reset) {
+  if (!c) return OSVMP2_E_ARG;
+  CK(cudaStreamSynchronize(c->st));
+  ph_collect(c);
+  for (int ph = 0; ph < OSVMP2_NPHASE; ph++) {
+    if (ms) ms[ph] = c->ms[ph];
+    if (flops) flops[ph] = c->flops[ph];
+    if (bytes) bytes[ph] = c->bytes[ph];
+    if (calls) calls[ph] = c->calls[ph];
+    if (reset) { c->ms[ph] = 0.0; c->flops[ph] = 0.0; c->bytes[ph] = 0.0; c->calls[ph] = 0; }
+  }
   return OSVMP2_OK;
 }
 

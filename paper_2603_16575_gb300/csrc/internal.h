@@ -24,6 +24,9 @@ struct Tables {
   const double* f_occ;          // [n_occ][n_occ]
 };
 
+// Process-wide count of kernel launches issued by the library.
+void note_launch(int n);
+
 struct SolveOpts {
   double tol_update, tol_energy;
   int max_iter;

@@ -57,6 +57,7 @@ void launch_tii(const BSrc& src, const double* e_vir, const double* f_occ, int n
   const int nt = (src.n_vir + TM - 1) / TM;
   dim3 grid(nt * (nt + 1) / 2, nb);
   k_tii<<<grid, NT, 0, st>>>(src, e_vir, f_occ, n_occ, i0, T);
+  note_launch(1);
 }
 
 // ---------------------------------------------------------------- eigen
@@ -273,6 +274,7 @@ void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, 
   if (zsmem) smem += (size_t)nv * (nv + 1) * sizeof(double);
   cudaFuncSetAttribute(k_eig_osv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_eig_osv<<<nb, NT, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem);
+  note_launch(1);
 }
 
 __global__ void k_pack_q(const double* V, const double* w, int nv, int kmax, const int* k,
@@ -293,6 +295,7 @@ void launch_pack_q(const double* V, const double* w, int nb, int nv, int kmax, c
                    double* const* Qdst, double* const* wdst, cudaStream_t st) {
   dim3 grid(32, nb);
   k_pack_q<<<grid, 256, 0, st>>>(V, w, nv, kmax, k, Qdst, wdst);
+  note_launch(1);
 }
 
 }  // namespace osv

@@ -45,6 +45,7 @@ void launch_project(const BSrc& src, const Tables& t, const ProjJob* jobs, int n
   if (n_jobs == 0) return;
   dim3 grid(n_jobs, (src.n_aux + TM - 1) / TM, (max_nx + TN - 1) / TN);
   k_project<<<grid, NT, 0, st>>>(src, t, jobs);
+  note_launch(1);
 }
 
 // K_(ij,ij)[mu][nu] = sum_P L[P][mu] R[P][nu] with L = [B~_i^(i) B~_i^(j)],
@@ -89,6 +90,7 @@ void launch_exchange(const Tables& t, int n_aux, const KJob* jobs, int n_jobs, i
   const int nt = (max_m + TM - 1) / TM;
   dim3 grid(n_jobs, nt, nt);
   k_exchange<<<grid, NT, 0, st>>>(t, n_aux, jobs);
+  note_launch(1);
 }
 
 struct QtScaled {         // A(mu, a) = Q_x[a][mu] * (e ? e[a] : 1)
@@ -133,6 +135,7 @@ void launch_sf(const Tables& t, const double* e_vir, const SFJob* jobs, int n_jo
   const int nt = (max_n + TM - 1) / TM;
   dim3 grid(n_jobs, nt, 2 * nt);
   k_sf<<<grid, NT, 0, st>>>(t, e_vir, jobs);
+  note_launch(1);
 }
 
 }  // namespace osv

@@ -82,6 +82,7 @@ void launch_precond(const Tables& t, double tau_s, const PJob* jobs, int n_jobs,
   const size_t smem = (size_t)(GEMM_SMEM_DOUBLES + 4 * max_m + 64 + ZMAX_P * (ZMAX_P + 1)) * sizeof(double);
   cudaFuncSetAttribute(k_precond, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_precond<<<n_cta, NT, smem, st>>>(t, tau_s, jobs, n_jobs, max_m, scratch, err);
+  note_launch(1);
 }
 
 }  // namespace osv

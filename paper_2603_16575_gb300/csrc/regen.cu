@@ -26,5 +26,6 @@ extern "C" int osvmp2_generate_B(int32_t n_occ, int32_t n_vir, int32_t n_aux, ui
   const uint64_t key = osv::mix64(seed ^ (5ull * 0xD1B54A32D192ED03ull));
   osv::BSrc src{nullptr, env, key, n_vir, n_aux};
   osv::k_generate_B<<<1184, 256, 0, (cudaStream_t)cuda_stream>>>(src, i0, n_i, out);
+  osv::note_launch(1);
   return cudaGetLastError() == cudaSuccess ? OSVMP2_OK : OSVMP2_E_CUDA;
 }

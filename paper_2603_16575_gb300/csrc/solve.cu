@@ -178,6 +178,7 @@ void launch_frag_solve(const Tables& t, const int* frag_orbs, const int* order, 
   if (n_frag == 0) return;
   cudaMemsetAsync(counter, 0, sizeof(int), st);
   k_frag_solve<<<n_cta, NT, 0, st>>>(t, frag_orbs, order, n_frag, max_m, o, scratch, counter, out);
+  note_launch(1);
 }
 
 // E = sum_f w_f E_f, one CTA, fixed order (strided partial sums, fixed tree).
@@ -191,6 +192,7 @@ __global__ void k_weighted_sum(const FragOut* out, const int* w, int n, double* 
 
 void launch_weighted_sum(const FragOut* out, const int* weights, int n, double* e_out, cudaStream_t st) {
   k_weighted_sum<<<1, NT, 0, st>>>(out, weights, n, e_out);
+  note_launch(1);
 }
 
 // ---------------------------------------------------------------- subsystem
@@ -240,13 +242,17 @@ __global__ void k_sub_reduce(SubDev s, int np) {
 
 void launch_sub_prepare(const Tables& t, const SubDev& s, int np, int n_cta, cudaStream_t st) {
   k_sub_prepare<<<n_cta, NT, 0, st>>>(t, s, np);
+  note_launch(1);
 }
 void launch_sub_residual(const Tables& t, const SubDev& s, int np, int n_cta, cudaStream_t st) {
   k_sub_residual<<<n_cta, NT, 0, st>>>(t, s, np);
+  note_launch(1);
 }
 void launch_sub_update(const Tables& t, const SubDev& s, int np, int n_cta, cudaStream_t st) {
   k_sub_update<<<n_cta, NT, 0, st>>>(t, s, np);
+  note_launch(1);
   k_sub_reduce<<<1, NT, 0, st>>>(s, np);
+  note_launch(1);
 }
 
 }  // namespace osv

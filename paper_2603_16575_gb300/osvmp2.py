@@ -52,13 +52,16 @@ SIGNATURES = {
     "osvmp2_destroy": (None, [_P]),
     "osvmp2_last_error": (ctypes.c_char_p, [_P]),
     "osvmp2_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "osvmp2_kernel_launches": (ctypes.c_int64, []),
     "osvmp2_build_osv": (ctypes.c_int, [_P, ctypes.POINTER(System), _D, _P]),
     "osvmp2_get_osv": (ctypes.c_int, [_P, _I32, _P, _P]),
     "osvmp2_pair_integrals": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int]),
     "osvmp2_get_pair_blocks": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P]),
+    "osvmp2_get_precond": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _P]),
     "osvmp2_solve": (ctypes.c_int, [_P, _P, _I32, ctypes.c_int, _P, _P, _P]),
     "osvmp2_mbe3_energy": (ctypes.c_int, [_P, _D, _D, ctypes.c_int, _P, ctypes.POINTER(MbeStats)]),
     "osvmp2_fragment_results": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "osvmp2_profile": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
     "osvmp2_mbe3_fragments": (ctypes.c_int, [_P, _I32, _D, _D, _I64, _P, _P, _P]),
     "osvmp2_energy_grad": (ctypes.c_int, [_P, _D, _D, ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(MbeStats)]),
     "osvmp2_generate_B": (ctypes.c_int, [_I32, _I32, _I32, ctypes.c_uint64, _P, _I32, _I32, _P, _P]),
@@ -107,6 +110,11 @@ def default_opts() -> Opts:
     o = Opts()
     lib().osvmp2_default_opts(ctypes.byref(o))
     return o
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libosvmp2 in this process so far."""
+    return int(lib().osvmp2_kernel_launches())
 
 
 def mbe3_fragments(r_occ: np.ndarray, r2_cut: float, r3_cut: float):
@@ -221,6 +229,16 @@ class Context:
         self._check("osvmp2_get_pair_blocks", lib().osvmp2_get_pair_blocks(self._h, i, j, _ptr(K), _ptr(S), _ptr(F)))
         return K, S, F
 
+    def get_precond(self, i: int, j: int):
+        """(X [m, r], e~ [r]) of built pair (i, j)."""
+        import torch
+        m = int(self.n_osv[i] + (self.n_osv[j] if i != j else 0))
+        X = torch.empty((m, m), dtype=torch.float64, device=f"cuda:{self.device}")
+        et = torch.empty(m, dtype=torch.float64, device=f"cuda:{self.device}")
+        r = ctypes.c_int32(0)
+        self._check("osvmp2_get_precond", lib().osvmp2_get_precond(self._h, i, j, _ptr(X), _ptr(et), ctypes.addressof(r)))
+        return X[:, :r.value], et[:r.value]
+
     # ---- A3-A4
     def solve(self, orbs: Sequence[int], prec: str = "fp64"):
         """Returns (E, pair energies [n(n+1)/2] for i<=j in orbs order, iterations)."""
@@ -240,6 +258,17 @@ class Context:
         self._check("osvmp2_mbe3_energy", lib().osvmp2_mbe3_energy(self._h, r2_cut, r3_cut, PREC[prec],
                                                                    ctypes.addressof(e), ctypes.byref(st)))
         return e.value, st.as_dict()
+
+    PHASES = ["tii", "eig", "sf", "project", "exchange", "precond", "solve", "mbe_sum", "subsolve", "grad",
+              "spare10", "spare11"]
+
+    def profile(self, reset: bool = False):
+        """Per-phase {name: (ms, flops, bytes, calls)} accumulated since the last reset."""
+        n = len(self.PHASES)
+        ms, fl, by = np.zeros(n), np.zeros(n), np.zeros(n)
+        calls = np.zeros(n, dtype=np.int64)
+        self._check("osvmp2_profile", lib().osvmp2_profile(self._h, _ptr(ms), _ptr(fl), _ptr(by), _ptr(calls), int(reset)))
+        return {self.PHASES[k]: (float(ms[k]), float(fl[k]), float(by[k]), int(calls[k])) for k in range(n) if calls[k]}
 
     def fragment_results(self):
         n = ctypes.c_int64(0)

@@ -40,7 +40,7 @@ def test_exports_every_declared_symbol(lib):
 def test_default_opts(lib):
     from paper_2603_16575_gb300 import osvmp2
     o = osvmp2.default_opts()
-    assert o.tau_s == 1e-10 and o.max_iter == 100 and o.tol_update == 1e-11
+    assert o.tau_s == 1e-10 and o.max_iter == 100 and o.tol_update == 1e-7
 
 
 @pytest.mark.parametrize("seed,n,r2,r3", [(0, 40, 8.0, 6.0), (1, 64, 6.0, 4.5), (2, 30, 5.0, 6.0)])

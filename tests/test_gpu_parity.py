@@ -74,6 +74,24 @@ def test_pair_blocks_match_dense_definition():
     ctx.close()
 
 
+def test_preconditioner_invariants_and_spectrum():
+    """Eq. prec_eig: X^T S X = 1, X^T F X = diag(e~); e~ equals the oracle's generalized eigenvalues."""
+    s = synth.make_system(4, 60, 90, seed=8, lam=1.5)
+    ctx = _ctx()
+    _build(ctx, s, 1e-4)
+    ctx.pair_integrals([(0, 1), (0, 3), (2, 2)])
+    for (i, j) in [(0, 1), (0, 3), (2, 2), (1, 1)]:
+        X, et = (x.cpu().numpy() for x in ctx.get_precond(i, j))
+        _, S, F = (x.cpu().numpy() for x in ctx.get_pair_blocks(i, j))
+        r = X.shape[1]
+        assert np.allclose(X.T @ S @ X, np.eye(r), atol=1e-9)
+        assert np.allclose(X.T @ F @ X, np.diag(et), atol=1e-8 * max(1.0, np.abs(et).max()))
+        Xr, er = oracle.preconditioner(S, F, 1e-10)
+        assert Xr.shape[1] == r
+        assert np.allclose(np.sort(et), np.sort(er), rtol=1e-10, atol=1e-12)
+    ctx.close()
+
+
 # ---------------------------------------------------------------- full solve
 @pytest.mark.parametrize("stored", [False, True])
 def test_untruncated_solve_equals_closed_form(stored):
