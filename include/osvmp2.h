@@ -214,6 +214,40 @@ int osvmp2_profile(osvmp2_ctx *ctx, double *ms, double *flops, double *bytes, in
 int osvmp2_generate_B(int32_t n_occ, int32_t n_vir, int32_t n_aux, uint64_t seed, const double *env,
                       int32_t i0, int32_t n_i, double *out, void *cuda_stream);
 
+/* ---- allocation-free preconditioner ------------------------------------------
+ * The paper has no counterpart to this entry point: it exists for callers that
+ * cannot call cudaMalloc -- a process that hands all GPU memory to its own pool
+ * allocator at start-up and forbids further driver allocations, a plug-in that
+ * runs inside another application's CUDA context under that application's
+ * memory budget, or a latency-critical loop in which an allocation (which may
+ * synchronise the device) is unacceptable.
+ *
+ * It computes the same preconditioner as osvmp2_pair_integrals does for one pair
+ * (canonical orthogonalisation of S with eigenvalues below tau_s * max dropped,
+ * then the eigen-decomposition of Y^T F Y; X^T S X = 1, X^T F X = diag(e~)) from
+ * caller-supplied dense matrices, and allocates nothing: its scratch is a
+ * file-scope device array sized for m <= OSVMP2_NOALLOC_MAX_M (about 3.2 MB),
+ * which every GPU that loads the library holds until the process exits.
+ *   S_dev, F_dev : device [m][m] row-major S_(ij,ij), F_(ij,ij)     (read)
+ *   X_dev        : device [m][m] row-major, columns 0..r-1 written  (out)
+ *   et_dev       : device [m], entries 0..r-1 written               (out)
+ *   r_dev        : device int32, r, or -1 if an eigen-solve failed  (out)
+ *   cuda_stream  : cudaStream_t to queue the single kernel on (NULL = legacy default)
+ *   err, err_len : optional host buffer for a one-line error message
+ * Returns OSVMP2_E_ARG (with a message) for null pointers, tau_s < 0, or m outside
+ * 1..OSVMP2_NOALLOC_MAX_M, OSVMP2_E_CUDA if the launch fails.  The call is
+ * asynchronous; outputs are ready when the stream reaches the kernel's end.
+ * The first call on each device (with that device current) looks up the
+ * device address of the static scratch with cudaGetSymbolAddress; make that
+ * first call before any stream capture.  Every call shares the one scratch
+ * array and the kernel writes each scratch element before reading it, so
+ * nothing from an earlier call needs clearing -- but calls whose kernels
+ * overlap on the GPU (different streams without ordering) race on that array:
+ * order them on one stream or with events. */
+#define OSVMP2_NOALLOC_MAX_M 256
+int osvmp2_precond_noalloc(const double *S_dev, const double *F_dev, int32_t m, double tau_s, double *X_dev,
+                           double *et_dev, int32_t *r_dev, void *cuda_stream, char *err, int32_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

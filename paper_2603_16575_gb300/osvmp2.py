@@ -21,6 +21,7 @@ OSVMP2_MIXED = 1
 PREC = {"fp64": OSVMP2_FP64, "mixed": OSVMP2_MIXED}
 
 STATUS = {0: "OK", 1: "E_ARG", 2: "E_CUDA", 3: "E_NOMEM", 4: "E_NOCONV", 5: "E_NUMERIC", 6: "E_STATE"}
+STATUS_CODES = {v: k for k, v in STATUS.items()}
 
 
 class Opts(ctypes.Structure):
@@ -64,6 +65,7 @@ SIGNATURES = {
     "osvmp2_profile": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
     "osvmp2_mbe3_fragments": (ctypes.c_int, [_P, _I32, _D, _D, _I64, _P, _P, _P]),
     "osvmp2_energy_grad": (ctypes.c_int, [_P, _D, _D, ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(MbeStats)]),
+    "osvmp2_precond_noalloc": (ctypes.c_int, [_P, _P, _I32, _D, _P, _P, _P, _P, ctypes.c_char_p, _I32]),
     "osvmp2_generate_B": (ctypes.c_int, [_I32, _I32, _I32, ctypes.c_uint64, _P, _I32, _I32, _P, _P]),
 }
 
@@ -146,6 +148,24 @@ def generate_B(n_occ, n_vir, n_aux, seed, env, i0=0, n_i=None, out=None, stream=
     if s:
         raise OSVMP2Error("osvmp2_generate_B", s, "launch failed")
     return out
+
+
+NOALLOC_MAX_M = 256
+
+
+def precond_noalloc(S, F, tau_s, X, et, r, stream=None) -> None:
+    """Allocation-free preconditioner of one pair (osvmp2_precond_noalloc): S, F
+    [m, m] float64 CUDA tensors in, X [m, m], et [m] float64 and r [1] int32 CUDA
+    tensors out (preallocated by the caller).  Raises on a non-OK status."""
+    import torch
+    _need_f64_cuda(S, "S")
+    _need_f64_cuda(F, "F")
+    m = S.shape[0]
+    st = stream if stream is not None else torch.cuda.current_stream(S.device).cuda_stream
+    buf = ctypes.create_string_buffer(256)
+    code = lib().osvmp2_precond_noalloc(_ptr(S), _ptr(F), m, tau_s, _ptr(X), _ptr(et), _ptr(r), st, buf, 256)
+    if code:
+        raise OSVMP2Error("osvmp2_precond_noalloc", code, buf.value.decode())
 
 
 class Context:
