@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -798,8 +799,10 @@ int osvmp2_mbe3_fragments(const double* r_occ, int32_t n_occ, double r2, double 
   return OSVMP2_OK;
 }
 
-int osvmp2_mbe3_energy(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out,
-                       osvmp2_mbe_stats* stats) {
+// MBE(3) energy; with tstore != NULL the converged amplitudes of every fragment
+// are kept (fragment f at tstore + toff[f], local pairs a<=b in order).
+static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out,
+                     osvmp2_mbe_stats* stats, Tmp* tstore, std::vector<long long>* toff) {
   if (!c) return OSVMP2_E_ARG;
   c->err.clear();
   if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "osvmp2_build_osv has not been called");
@@ -851,10 +854,30 @@ int osvmp2_mbe3_energy(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, do
   CK(cudaMemcpyAsync(d_orbs.p, orbs_h.data(), orbs_h.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(d_order.p, order.data(), nf * sizeof(int), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(d_w.p, w_h.data(), nf * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  Tmp d_toff;
+  double* tdst = nullptr;
+  if (tstore) {
+    toff->assign(nf, 0);
+    long long tot = 0;
+    for (int f = 0; f < nf; f++) {
+      (*toff)[f] = tot;
+      const Frag& fr = c->frags[f];
+      for (int a = 0; a < 3; a++)
+        for (int b = a; b < 3; b++)
+          if (fr.orbs[a] >= 0 && fr.orbs[b] >= 0) {
+            const long long m = pair_dim_h(c, fr.orbs[a], fr.orbs[b]);
+            tot += m * m;
+          }
+    }
+    TRY(tmp_alloc(c, *tstore, (size_t)tot * sizeof(double)));
+    TRY(tmp_alloc(c, d_toff, nf * sizeof(long long)));
+    CK(cudaMemcpyAsync(d_toff.p, toff->data(), nf * sizeof(long long), cudaMemcpyHostToDevice, c->st));
+    tdst = (double*)tstore->p;
+  }
   SolveOpts so{c->opts.tol_update, c->opts.tol_energy, c->opts.max_iter};
   ph_begin(c, OSVMP2_PH_SOLVE);
   launch_frag_solve(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, (double*)d_scr.p, n_cta,
-                    (int*)d_cnt.p, (FragOut*)d_out.p, c->st);
+                    (int*)d_cnt.p, (FragOut*)d_out.p, tdst, (const long long*)d_toff.p, c->st);
   CK(cudaGetLastError());
   ph_end(c, OSVMP2_PH_SOLVE, 0.0);
   ph_begin(c, OSVMP2_PH_MBE_SUM);
@@ -898,6 +921,11 @@ int osvmp2_mbe3_energy(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, do
   return OSVMP2_OK;
 }
 
+int osvmp2_mbe3_energy(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out,
+                       osvmp2_mbe_stats* stats) {
+  return mbe3_core(c, r2, r3, prec, e_out, stats, nullptr, nullptr);
+}
+
 int osvmp2_profile(osvmp2_ctx* c, double* ms, double* flops, double* bytes, int64_t* calls, int reset) {
   if (!c) return OSVMP2_E_ARG;
   CK(cudaStreamSynchronize(c->st));
@@ -927,11 +955,199 @@ int osvmp2_fragment_results(osvmp2_ctx* c, int64_t* n_out, int32_t* orbs, int32_
 
 int osvmp2_energy_grad(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out, double* dE_dB,
                        double* dE_df, double* dE_de, osvmp2_mbe_stats* stats) {
-  (void)dE_dB; (void)dE_df; (void)dE_de;
   if (!c) return OSVMP2_E_ARG;
-  int s = osvmp2_mbe3_energy(c, r2, r3, prec, e_out, stats);
-  if (s) return s;
-  return fail(c, OSVMP2_E_STATE, "gradient kernels not available yet");
+  Tmp tstore;
+  std::vector<long long> toff;
+  TRY(mbe3_core(c, r2, r3, prec, e_out, stats, &tstore, &toff));
+  const int n = c->sys.n_occ, nv = c->sys.n_vir, nx = c->sys.n_aux;
+  const int nf = (int)c->frags.size();
+  // unique pairs of the fragment list, each with its (fragment-ordered) contributions
+  std::vector<int> pidx((size_t)n * n, -1);
+  std::vector<std::pair<int, int>> plist;
+  std::vector<std::vector<GradContrib>> contr;
+  int max_m = 0;
+  for (int f = 0; f < nf; f++) {
+    const Frag& fr = c->frags[f];
+    int orbs[3], nc = 0;
+    for (int u = 0; u < 3; u++)
+      if (fr.orbs[u] >= 0) orbs[nc++] = fr.orbs[u];
+    long long off = toff[f];
+    for (int a = 0; a < nc; a++)
+      for (int b = a; b < nc; b++) {
+        const int i = orbs[a], j = orbs[b];
+        const long long m = pair_dim_h(c, i, j);
+        max_m = std::max(max_m, (int)m);
+        int& q = pidx[(size_t)i * n + j];
+        if (q < 0) {
+          q = (int)plist.size();
+          plist.push_back({i, j});
+          contr.emplace_back();
+        }
+        if (fr.weight != 0) contr[q].push_back(GradContrib{(const double*)tstore.p + off, fr.weight});
+        off += m * m;
+      }
+  }
+  const int np = (int)plist.size();
+  size_t wh = 0;
+  for (auto& p : plist) wh += 2 * (size_t)pair_dim_h(c, p.first, p.second) * pair_dim_h(c, p.first, p.second);
+  std::vector<GradPairJob> pjobs;
+  std::vector<GradContrib> cflat;
+  Tmp whm;
+  TRY(tmp_alloc(c, whm, wh * sizeof(double)));
+  {
+    size_t o = 0;
+    for (int q = 0; q < np; q++) {
+      const size_t m2 = (size_t)pair_dim_h(c, plist[q].first, plist[q].second) *
+                        pair_dim_h(c, plist[q].first, plist[q].second);
+      GradPairJob jb{plist[q].first, plist[q].second, (int)cflat.size(), 0, (double*)whm.p + o,
+                     (double*)whm.p + o + m2};
+      for (auto& cb : contr[q]) cflat.push_back(cb);
+      jb.c1 = (int)cflat.size();
+      o += 2 * m2;
+      pjobs.push_back(jb);
+    }
+  }
+  const Tables t = tables(c);
+  const int n_cta = std::max(1, std::min(np, 2 * c->num_sms));
+  Tmp d_pj, d_cf, scr;
+  TRY(tmp_alloc(c, d_pj, pjobs.size() * sizeof(GradPairJob)));
+  TRY(tmp_alloc(c, d_cf, std::max<size_t>(1, cflat.size()) * sizeof(GradContrib)));
+  const size_t scr_d = std::max((size_t)2 * max_m * max_m, (size_t)nv * max_m);
+  TRY(tmp_alloc(c, scr, (size_t)n_cta * scr_d * sizeof(double)));
+  CK(cudaMemcpyAsync(d_pj.p, pjobs.data(), pjobs.size() * sizeof(GradPairJob), cudaMemcpyHostToDevice, c->st));
+  if (!cflat.empty())
+    CK(cudaMemcpyAsync(d_cf.p, cflat.data(), cflat.size() * sizeof(GradContrib), cudaMemcpyHostToDevice, c->st));
+  double fl = 0.0;
+  for (int q = 0; q < np; q++) {
+    const double m = pair_dim_h(c, plist[q].first, plist[q].second);
+    fl += (double)contr[q].size() * (plist[q].first == plist[q].second ? 4.0 : 8.0) * m * m * m;
+  }
+  ph_begin(c, OSVMP2_PH_GRAD);
+  launch_grad_pair(t, (const GradPairJob*)d_pj.p, np, (const GradContrib*)d_cf.p, (double*)scr.p, n_cta, max_m,
+                   c->st);
+  CK(cudaGetLastError());
+  Tmp dpair;
+  if (dE_de) {
+    TRY(tmp_alloc(c, dpair, (size_t)np * nv * sizeof(double)));
+    launch_grad_de(t, (const GradPairJob*)d_pj.p, np, (double*)scr.p, n_cta, max_m, (double*)dpair.p, dE_de, c->st);
+    CK(cudaGetLastError());
+  }
+  Tmp gfrag, d_fptr, d_flist, d_orbs, d_w, d_toff;
+  if (dE_df) {
+    std::vector<int> fptr(n + 1, 0), flist, orbs_h(3 * (size_t)nf), w_h(nf);
+    std::vector<std::vector<int>> per(n);
+    for (int f = 0; f < nf; f++) {
+      for (int u = 0; u < 3; u++) {
+        orbs_h[3 * f + u] = c->frags[f].orbs[u];
+        if (c->frags[f].orbs[u] >= 0) per[c->frags[f].orbs[u]].push_back(f);
+      }
+      w_h[f] = c->frags[f].weight;
+    }
+    for (int k = 0; k < n; k++) {
+      fptr[k + 1] = fptr[k] + (int)per[k].size();
+      for (int f : per[k]) flist.push_back(f);
+    }
+    TRY(tmp_alloc(c, gfrag, (size_t)nf * 9 * sizeof(double)));
+    TRY(tmp_alloc(c, d_fptr, fptr.size() * sizeof(int)));
+    TRY(tmp_alloc(c, d_flist, std::max<size_t>(1, flist.size()) * sizeof(int)));
+    TRY(tmp_alloc(c, d_orbs, orbs_h.size() * sizeof(int)));
+    TRY(tmp_alloc(c, d_w, w_h.size() * sizeof(int)));
+    TRY(tmp_alloc(c, d_toff, toff.size() * sizeof(long long)));
+    CK(cudaMemcpyAsync(d_fptr.p, fptr.data(), fptr.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    if (!flist.empty())
+      CK(cudaMemcpyAsync(d_flist.p, flist.data(), flist.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(d_orbs.p, orbs_h.data(), orbs_h.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(d_w.p, w_h.data(), w_h.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(d_toff.p, toff.data(), toff.size() * sizeof(long long), cudaMemcpyHostToDevice, c->st));
+    const int n_cta_f = std::max(1, std::min(nf, 2 * c->num_sms));
+    Tmp scr_f;
+    TRY(tmp_alloc(c, scr_f, (size_t)n_cta_f * 2 * max_m * max_m * sizeof(double)));
+    launch_grad_df(t, (const int*)d_orbs.p, (const int*)d_w.p, (const double*)tstore.p,
+                   (const long long*)d_toff.p, nf, max_m, (double*)scr_f.p, n_cta_f, (double*)gfrag.p,
+                   (const int*)d_fptr.p, (const int*)d_flist.p, dE_df, c->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+  }
+  Tmp ymem, d_yj, d_yt, d_bj, d_bt;
+  if (dE_dB) {
+    // combos (o, x): x = o and every partner of o in the pair list
+    std::vector<std::vector<int>> partners(n);
+    for (auto& p : plist)
+      if (p.first != p.second) {
+        partners[p.first].push_back(p.second);
+        partners[p.second].push_back(p.first);
+      }
+    auto bt = [&](int a, int x) { return (const double*)c->bt_h[c->bt_id[(size_t)a * n + x]]; };
+    auto Wp = [&](int i, int j) { return (const double*)pjobs[pidx[(size_t)i * n + j]].W; };
+    std::vector<GradYJob> yj;
+    std::vector<GradYTerm> yt;
+    std::vector<GradBJob> bj;
+    std::vector<GradBTerm> btm;
+    size_t ysz = 0;
+    int max_n = 0;
+    std::vector<int> has(n, 0);
+    for (auto& p : plist) { has[p.first] = 1; has[p.second] = 1; }
+    for (int o = 0; o < n; o++) {
+      if (!has[o]) continue;
+      std::sort(partners[o].begin(), partners[o].end());
+      std::vector<int> xs;
+      xs.push_back(o);
+      for (int x : partners[o]) xs.push_back(x);
+      std::sort(xs.begin(), xs.end());
+      GradBJob b{o, (int)btm.size(), 0};
+      for (int x : xs) {
+        GradYJob y{o, x, (int)yt.size(), 0, nullptr};
+        if (x == o) {
+          for (auto& p : plist) {
+            if (p.first == o && p.second == o) yt.push_back(GradYTerm{o, o, 0, 0, Wp(o, o), bt(o, o), nullptr});
+            else if (p.first == o) yt.push_back(GradYTerm{o, p.second, 0, 0, Wp(o, p.second), bt(p.second, o),
+                                                          bt(p.second, p.second)});
+            else if (p.second == o) yt.push_back(GradYTerm{p.first, o, 1, c->n_osv[p.first], Wp(p.first, o),
+                                                           bt(p.first, p.first), bt(p.first, o)});
+          }
+        } else if (o < x) {
+          yt.push_back(GradYTerm{o, x, 0, c->n_osv[o], Wp(o, x), bt(x, o), bt(x, x)});
+        } else {
+          yt.push_back(GradYTerm{x, o, 1, 0, Wp(x, o), bt(x, x), bt(x, o)});
+        }
+        y.t1 = (int)yt.size();
+        y.Y = (double*)(uintptr_t)ysz;    // offset, fixed below
+        ysz += (size_t)c->n_osv[x] * nx;
+        max_n = std::max(max_n, c->n_osv[x]);
+        btm.push_back(GradBTerm{x, (const double*)(uintptr_t)(ysz - (size_t)c->n_osv[x] * nx)});
+        yj.push_back(y);
+      }
+      b.t1 = (int)btm.size();
+      bj.push_back(b);
+    }
+    TRY(tmp_alloc(c, ymem, ysz * sizeof(double)));
+    for (auto& y : yj) y.Y = (double*)ymem.p + (uintptr_t)y.Y;
+    for (auto& b : btm) b.Y = (const double*)ymem.p + (uintptr_t)b.Y;
+    TRY(tmp_alloc(c, d_yj, yj.size() * sizeof(GradYJob)));
+    TRY(tmp_alloc(c, d_yt, yt.size() * sizeof(GradYTerm)));
+    TRY(tmp_alloc(c, d_bj, bj.size() * sizeof(GradBJob)));
+    TRY(tmp_alloc(c, d_bt, btm.size() * sizeof(GradBTerm)));
+    CK(cudaMemcpyAsync(d_yj.p, yj.data(), yj.size() * sizeof(GradYJob), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(d_yt.p, yt.data(), yt.size() * sizeof(GradYTerm), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(d_bj.p, bj.data(), bj.size() * sizeof(GradBJob), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(d_bt.p, btm.data(), btm.size() * sizeof(GradBTerm), cudaMemcpyHostToDevice, c->st));
+    for (auto& tm : yt) {
+      const double m = pair_dim_h(c, tm.pi, tm.pj);
+      (void)m;
+    }
+    for (auto& y : yj)
+      for (int q = y.t0; q < y.t1; q++) fl += 2.0 * c->n_osv[y.x] * (double)pair_dim_h(c, yt[q].pi, yt[q].pj) * nx;
+    for (auto& b : btm) fl += 2.0 * nv * (double)c->n_osv[b.x] * nx;
+    CK(cudaMemsetAsync(dE_dB, 0, (size_t)n * nv * nx * sizeof(double), c->st));
+    launch_grad_Y(t, nx, (const GradYJob*)d_yj.p, (int)yj.size(), (const GradYTerm*)d_yt.p, max_n, c->st);
+    CK(cudaGetLastError());
+    launch_grad_dB(t, nx, (const GradBJob*)d_bj.p, (int)bj.size(), (const GradBTerm*)d_bt.p, dE_dB, c->st);
+    CK(cudaGetLastError());
+  }
+  ph_end(c, OSVMP2_PH_GRAD, fl);
+  CK(cudaStreamSynchronize(c->st));
+  ph_collect(c);
+  return check_err_flag(c, "gradient");
 }
 
 }  // extern "C"

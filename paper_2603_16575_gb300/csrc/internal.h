@@ -98,9 +98,11 @@ void launch_precond(const Tables& t, double tau_s, const PJob* jobs, int n_jobs,
 // Fragments: orbs [n][3] (-1 padded, ascending), order[] = processing order.
 // per CTA: T, R, G1, G2 for six pairs + two work matrices
 __host__ __device__ inline size_t frag_scratch_doubles(int max_m) { return 26 * (size_t)max_m * max_m + 64; }
+// Tstore (may be NULL): converged amplitudes of fragment f are written at
+// Tstore + Toff[f], local pairs (a<=b) in order, each m_p x m_p.
 void launch_frag_solve(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
                        SolveOpts o, double* scratch, int n_cta, int* counter, FragOut* out,
-                       cudaStream_t st);
+                       double* Tstore, const long long* Toff, cudaStream_t st);
 // E = sum_f w_f * E_f in a fixed order -> e_out (device scalar)
 void launch_weighted_sum(const FragOut* out, const int* weights, int n, double* e_out, cudaStream_t st);
 
@@ -119,5 +121,49 @@ struct SubDev {
 void launch_sub_prepare(const Tables& t, const SubDev& s, int np, int n_cta, cudaStream_t st);
 void launch_sub_residual(const Tables& t, const SubDev& s, int np, int n_cta, cudaStream_t st);
 void launch_sub_update(const Tables& t, const SubDev& s, int np, int n_cta, cudaStream_t st);
+
+// ---- A6 (grad.cu)
+struct GradContrib {       // one fragment's amplitude of a pair and the fragment weight
+  const double* T;
+  int weight;
+};
+struct GradPairJob {       // W_p = sum c T~, H_p = sum c (T~ S T^T + [i!=j] T~^T S T)
+  int i, j;
+  int c0, c1;              // contributions [c0, c1)
+  double* W;
+  double* H;
+};
+struct GradYTerm {         // rows [row0, row0+n_x) of W'_p (W or W^T) times P_p^T B_partner
+  int pi, pj;
+  int trans;
+  int row0;
+  const double* W;
+  const double* Bt_i;      // B~_partner^(pi)  [n_aux][n_pi]
+  const double* Bt_j;      // B~_partner^(pj)  [n_aux][n_pj]  (unused when pi == pj)
+};
+struct GradYJob {          // Y_o^(x) [n_x][n_aux] = sum of terms [t0, t1)
+  int o, x;
+  int t0, t1;
+  double* Y;
+};
+struct GradBTerm {
+  int x;
+  const double* Y;
+};
+struct GradBJob {          // dB_i = 4 sum_x Q_x Y_i^(x) over terms [t0, t1)
+  int i;
+  int t0, t1;
+};
+void launch_grad_pair(const Tables& t, const GradPairJob* jobs, int n_jobs, const GradContrib* contrib,
+                      double* scratch, int n_cta, int max_m, cudaStream_t st);
+void launch_grad_de(const Tables& t, const GradPairJob* jobs, int n_jobs, double* scratch, int n_cta, int max_m,
+                    double* dpair, double* de, cudaStream_t st);
+void launch_grad_df(const Tables& t, const int* frag_orbs, const int* weights, const double* Tstore,
+                    const long long* Toff, int n_frag, int max_m, double* scratch, int n_cta, double* gfrag,
+                    const int* fptr, const int* flist, double* df, cudaStream_t st);
+void launch_grad_Y(const Tables& t, int n_aux, const GradYJob* jobs, int n_jobs, const GradYTerm* terms, int max_n,
+                   cudaStream_t st);
+void launch_grad_dB(const Tables& t, int n_aux, const GradBJob* jobs, int n_jobs, const GradBTerm* terms, double* dB,
+                    cudaStream_t st);
 
 }  // namespace osv

@@ -108,7 +108,8 @@ __device__ void pair_prepare(const Tables& t, int i, int j, double* Tp, double* 
 
 __global__ void __launch_bounds__(NT) k_frag_solve(Tables t, const int* __restrict__ frag_orbs,
                                                    const int* __restrict__ order, int n_frag, int max_m,
-                                                   SolveOpts o, double* scratch, int* counter, FragOut* out) {
+                                                   SolveOpts o, double* scratch, int* counter, FragOut* out,
+                                                   double* Tstore, const long long* __restrict__ Toff) {
   __shared__ double sm[GEMM_SMEM_DOUBLES];
   __shared__ double red[40];
   __shared__ int s_f;
@@ -169,15 +170,26 @@ __global__ void __launch_bounds__(NT) k_frag_solve(Tables t, const int* __restri
       e_prev = e;
     }
     if (threadIdx.x == 0) out[fid] = FragOut{e, um, iters, status};
+    if (Tstore) {
+      double* dst = Tstore + Toff[fid];
+      for (int a = 0; a < nc; a++)
+        for (int b = a; b < nc; b++) {
+          const int mp = pair_dim(t, orbs[a], orbs[b]);
+          const double* src = T[lpair(a, b, nc)];
+          for (int idx = threadIdx.x; idx < mp * mp; idx += NT) dst[idx] = src[idx];
+          dst += (size_t)mp * mp;
+        }
+    }
     __syncthreads();
   }
 }
 
 void launch_frag_solve(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
-                       SolveOpts o, double* scratch, int n_cta, int* counter, FragOut* out, cudaStream_t st) {
+                       SolveOpts o, double* scratch, int n_cta, int* counter, FragOut* out,
+                       double* Tstore, const long long* Toff, cudaStream_t st) {
   if (n_frag == 0) return;
   cudaMemsetAsync(counter, 0, sizeof(int), st);
-  k_frag_solve<<<n_cta, NT, 0, st>>>(t, frag_orbs, order, n_frag, max_m, o, scratch, counter, out);
+  k_frag_solve<<<n_cta, NT, 0, st>>>(t, frag_orbs, order, n_frag, max_m, o, scratch, counter, out, Tstore, Toff);
   note_launch(1);
 }
 

@@ -313,3 +313,28 @@ class Context:
                     lib().osvmp2_energy_grad(self._h, r2_cut, r3_cut, PREC[prec], ctypes.addressof(e), _ptr(dB),
                                              _ptr(df), _ptr(de), ctypes.byref(st)))
         return e.value, dB, df, de, st.as_dict()
+
+
+def mbe3_energy_function():
+    """torch.autograd.Function around osvmp2_energy_grad.
+
+    forward(ctx_obj, B, f_occ, e_vir, r2, r3, prec, l_osv) -> E (0-dim float64 tensor)
+    backward: dE/dB, dE/df_occ (symmetrised) and dE/de_vir from the adjoint kernels,
+    with the OSVs held fixed, each scaled by the incoming gradient.
+    """
+    import torch
+
+    class _MBE3Energy(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, ctx_obj, B, f_occ, e_vir, r_occ, r2, r3, prec="fp64", l_osv=1e-4):
+            ctx_obj.build_osv(f_occ, e_vir, l_osv, B=B, r_occ=r_occ)
+            E, dB, df, de, _ = ctx_obj.energy_grad(r2, r3, prec, want_dB=True)
+            fctx.save_for_backward(dB, df, de)
+            return torch.tensor(E, dtype=torch.float64, device=B.device)
+
+        @staticmethod
+        def backward(fctx, g):
+            dB, df, de = fctx.saved_tensors
+            return None, g * dB, g * df, g * de, None, None, None, None, None
+
+    return _MBE3Energy

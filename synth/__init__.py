@@ -191,6 +191,7 @@ WORKLOADS = {
     "canonical_n20": dict(n_occ=20, n_vir=100, n_aux=400, lam=3.0, geometry="box"),
     "osv_n256": dict(n_occ=256, n_vir=1200, n_aux=4800, lam=1.0, geometry="box"),
     "mbe3_n128": dict(n_occ=128, n_vir=640, n_aux=2400, lam=1.0, geometry="box"),
+    "mbe3_n32": dict(n_occ=32, n_vir=160, n_aux=600, lam=1.0, geometry="box"),
     "grad_n64": dict(n_occ=64, n_vir=320, n_aux=1200, lam=1.0, geometry="box"),
     "chain_n800": dict(n_occ=800, n_vir=6000, n_aux=16000, lam=1.0, geometry="chain"),
 }

@@ -135,3 +135,37 @@ def test_mbe3_energy_matches_oracle():
     assert st["n_unconverged"] == 0
     assert abs(E - E_ref) < 1e-9
     ctx.close()
+
+
+# ---------------------------------------------------------------- gradient
+def test_gradient_matches_oracle():
+    """Frozen-OSV adjoint (dE/dB, dE/de, dE/df) against the oracle gradient, which is pinned
+    by central finite differences in the CPU tests."""
+    s = synth.make_system(6, 40, 80, seed=29, lam=1.5, f_off=3e-2)
+    r2, r3 = 4.5, 4.0
+    ctx = _ctx()
+    _build(ctx, s, 1e-3)
+    E, dB, df, de, st = ctx.energy_grad(r2, r3)
+    o = oracle.OSVSystem(s.B_block, 6, s.e_vir, s.f_occ, l_osv=1e-3)
+    E_ref, dB_ref, de_ref, df_ref = oracle.mbe3_energy_gradient(o, s.r_occ, r2, r3, 40, 80)
+    assert abs(E - E_ref) < 1e-9
+    dB, df, de = dB.cpu().numpy(), df.cpu().numpy(), de.cpu().numpy()
+    assert np.abs(dB - dB_ref).max() < 1e-9 * np.abs(dB_ref).max()
+    assert np.abs(de - de_ref).max() < 1e-9 * np.abs(de_ref).max()
+    assert np.abs(df - df_ref).max() < 1e-9 * np.abs(df_ref).max()
+    ctx.close()
+
+
+def test_autograd_function_backward():
+    from paper_2603_16575_gb300 import osvmp2
+    s = synth.make_system(5, 36, 70, seed=31, lam=1.5)
+    ctx = _ctx()
+    B = _t(s.B_full()).requires_grad_(True)
+    f = _t(s.f_occ).requires_grad_(True)
+    e = _t(s.e_vir).requires_grad_(True)
+    Fn = osvmp2.mbe3_energy_function()
+    E = Fn.apply(ctx, B, f, e, s.r_occ, 4.5, 4.0, "fp64", 1e-3)
+    (3.0 * E).backward()
+    E2, dB, df, de, _ = ctx.energy_grad(4.5, 4.0)
+    assert torch.allclose(B.grad, 3.0 * dB) and torch.allclose(f.grad, 3.0 * df) and torch.allclose(e.grad, 3.0 * de)
+    ctx.close()
