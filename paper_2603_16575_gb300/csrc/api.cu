@@ -40,6 +40,8 @@ struct osvmp2_ctx {
   std::string err;
   int num_sms = 148;
   std::vector<void*> sys_allocs;     // freed when a new system is set
+  std::vector<void*> pair_allocs;    // pair store; freed with the system or on a precision change
+  int pair_prec = -1;                // precision the pair store was built with
   // system
   bool have_sys = false;
   osvmp2_system sys{};
@@ -60,12 +62,13 @@ struct osvmp2_ctx {
   double** K_d = nullptr;
   double** X_d = nullptr;
   double** et_d = nullptr;
+  double** Kt_d = nullptr;
   int* r_d = nullptr;
   int* err_d = nullptr;
   double* scal_d = nullptr;          // device scalars (energies)
   // host mirrors
   std::vector<int> sf_id, pair_id, bt_id;
-  std::vector<double*> S_h, F_h, K_h, X_h, et_h, bt_h;
+  std::vector<double*> S_h, F_h, K_h, X_h, et_h, bt_h, Kt_h;
   std::vector<int> m_h;
   std::vector<int> pi_h, pj_h;       // pair id -> (i, j)
   // last MBE call
@@ -146,14 +149,17 @@ void free_system(osvmp2_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   for (void* p : c->sys_allocs) cudaFree(p);
   c->sys_allocs.clear();
+  for (void* p : c->pair_allocs) cudaFree(p);
+  c->pair_allocs.clear();
+  c->pair_prec = -1;
   c->have_sys = c->have_osv = false;
   c->n_osv.clear(); c->Qp.clear(); c->Wp.clear();
   c->sf_id.clear(); c->pair_id.clear(); c->bt_id.clear();
-  c->S_h.clear(); c->F_h.clear(); c->K_h.clear(); c->X_h.clear(); c->et_h.clear(); c->bt_h.clear();
+  c->S_h.clear(); c->F_h.clear(); c->K_h.clear(); c->X_h.clear(); c->et_h.clear(); c->bt_h.clear(); c->Kt_h.clear();
   c->m_h.clear(); c->pi_h.clear(); c->pj_h.clear();
   c->frags.clear(); c->frag_out.clear();
   c->n_osv_d = nullptr; c->Q_d = nullptr; c->sf_id_d = nullptr; c->S_d = c->F_d = nullptr;
-  c->pair_id_d = nullptr; c->K_d = c->X_d = c->et_d = nullptr; c->r_d = nullptr;
+  c->pair_id_d = nullptr; c->K_d = c->X_d = c->et_d = c->Kt_d = nullptr; c->r_d = nullptr;
 }
 
 Tables tables(const osvmp2_ctx* c) {
@@ -170,6 +176,7 @@ Tables tables(const osvmp2_ctx* c) {
   t.X = c->X_d;
   t.et = c->et_d;
   t.r = c->r_d;
+  t.Kt = c->Kt_d;
   t.f_occ = c->sys.f_occ;
   return t;
 }
@@ -269,6 +276,35 @@ void enumerate_fragments(const double* r, int n, double r2, double r3, std::vect
 
 int pair_dim_h(const osvmp2_ctx* c, int i, int j) { return c->n_osv[i] + (i != j ? c->n_osv[j] : 0); }
 
+int palloc(osvmp2_ctx* c, double** p, size_t n) {
+  *p = nullptr;
+  const size_t bytes = std::max<size_t>(16, n * sizeof(double));
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, OSVMP2_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->pair_allocs.push_back(*p);
+  return 0;
+}
+
+// Drop every built pair (blocks, projections, K, preconditioners).
+int reset_pairs(osvmp2_ctx* c) {
+  CK(cudaStreamSynchronize(c->st));
+  for (void* p : c->pair_allocs) cudaFree(p);
+  c->pair_allocs.clear();
+  const size_t nn = (size_t)c->sys.n_occ * c->sys.n_occ;
+  c->sf_id.assign(nn, -1);
+  c->pair_id.assign(nn, -1);
+  c->bt_id.assign(nn, -1);
+  c->S_h.clear(); c->F_h.clear(); c->K_h.clear(); c->X_h.clear(); c->et_h.clear(); c->bt_h.clear(); c->Kt_h.clear();
+  c->m_h.clear(); c->pi_h.clear(); c->pj_h.clear(); c->r_h.clear();
+  TRY(upload(c, c->sf_id_d, c->sf_id));
+  TRY(upload(c, c->pair_id_d, c->pair_id));
+  c->pair_prec = -1;
+  return 0;
+}
+
 // FP operations of one Jacobi sweep of a fragment as the solver performs it:
 // per pair p (m x m, rank r) 4 GEMMs m^3 for G1 T S + S T G2, two GEMMs per
 // coupling term (q != p, coefficient != 0), the four GEMMs of the
@@ -301,11 +337,53 @@ double fragment_iter_flops(const osvmp2_ctx* c, const Frag& f) {
   return fl;
 }
 
+// FP operations of the preconditioner-basis solve of a fragment: the Sigma_pq
+// set-up (S X_q, then X_p^T (S X_q)) once, then per sweep two GEMMs per
+// coupling term (op(Y_q) Sigma^T, Sigma (...)), plus the element-wise update.
+double fragment_mixed_flops(const osvmp2_ctx* c, const Frag& f, int iters) {
+  const int n = c->sys.n_occ;
+  int orbs[3], nc = 0;
+  for (int u = 0; u < 3; u++)
+    if (f.orbs[u] >= 0) orbs[nc++] = f.orbs[u];
+  auto rr = [&](int i, int j) {
+    const int pid = c->pair_id[(size_t)i * n + j];
+    return (double)((pid >= 0 && pid < (int)c->r_h.size()) ? c->r_h[pid] : pair_dim_h(c, i, j));
+  };
+  double setup = 0.0, sweep = 0.0;
+  std::vector<std::pair<int, int>> seen;
+  for (int a = 0; a < nc; a++)
+    for (int b = a; b < nc; b++) {
+      const int i = orbs[a], j = orbs[b];
+      const double mp = pair_dim_h(c, i, j), rp = rr(i, j);
+      sweep += 6.0 * rp * rp;
+      for (int cc = 0; cc < nc; cc++)
+        for (int s2 = 0; s2 < 2; s2++) {
+          if (s2 == 0 && cc == b) continue;
+          if (s2 == 1 && cc == a) continue;
+          const int x = (s2 == 0) ? a : cc, y = (s2 == 0) ? cc : b;
+          const int k = orbs[cc];
+          const double coef = (s2 == 0) ? c->f_h[(size_t)k * n + j] : c->f_h[(size_t)i * n + k];
+          if (coef == 0.0) continue;
+          const int qi = orbs[std::min(x, y)], qj = orbs[std::max(x, y)];
+          const double mq = pair_dim_h(c, qi, qj), rq = rr(qi, qj);
+          sweep += 2.0 * rq * rq * rp + 2.0 * rp * rq * rp;
+          const std::pair<int, int> key{a * 3 + b, qi * n + qj};
+          if (std::find(seen.begin(), seen.end(), key) == seen.end()) {
+            seen.push_back(key);
+            setup += 2.0 * mp * mq * rq + 2.0 * rp * mp * rq;
+          }
+        }
+    }
+  return setup + iters * sweep;
+}
+
 // Build S/F blocks, projections, K and preconditioners for every listed pair
 // (and the diagonal pairs of its orbitals) that is not built yet.
 int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osvmp2_prec prec) {
   if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "osvmp2_build_osv has not been called");
   if (prec != OSVMP2_FP64 && prec != OSVMP2_MIXED) return fail(c, OSVMP2_E_ARG, "unknown precision %d", (int)prec);
+  if (c->pair_prec >= 0 && c->pair_prec != (int)prec) TRY(reset_pairs(c));
+  c->pair_prec = (int)prec;
   const int n = c->sys.n_occ;
   std::vector<std::pair<int, int>> newp;
   auto want = [&](int i, int j) {
@@ -359,15 +437,15 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   int max_m = 0, max_n = 0, max_nx = 0;
   for (auto& p : newp) {
     const int m = pair_dim_h(c, p.first, p.second);
-    k_doubles += 2 * (size_t)m * m + m;
+    k_doubles += 3 * (size_t)m * m + m;
     max_m = std::max(max_m, m);
   }
   for (int i = 0; i < n; i++) max_n = std::max(max_n, c->n_osv[i]);
   max_nx = max_n;
   double *sf_mem = nullptr, *bt_mem = nullptr, *k_mem = nullptr;
-  TRY(dalloc_t(c, &sf_mem, sf_doubles));
-  TRY(dalloc_t(c, &bt_mem, bt_doubles));
-  TRY(dalloc_t(c, &k_mem, k_doubles));
+  TRY(palloc(c, &sf_mem, sf_doubles));
+  TRY(palloc(c, &bt_mem, bt_doubles));
+  TRY(palloc(c, &k_mem, k_doubles));
   {
     size_t off = 0;
     for (auto& j : sfj) {
@@ -401,7 +479,9 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
       double* K = k_mem + off;
       double* X = K + (size_t)m * m;
       double* et = X + (size_t)m * m;
-      off += 2 * (size_t)m * m + m;
+      double* Kt = et + m;
+      off += 3 * (size_t)m * m + m;
+      c->Kt_h.push_back(Kt);
       c->pair_id[(size_t)i * n + j] = pid;
       c->K_h.push_back(K);
       c->X_h.push_back(X);
@@ -423,6 +503,7 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   TRY(upload(c, c->K_d, c->K_h));
   TRY(upload(c, c->X_d, c->X_h));
   TRY(upload(c, c->et_d, c->et_h));
+  TRY(upload(c, c->Kt_d, c->Kt_h));
   // job arrays
   Tmp jsf, jpj, jk, jp, scr;
   TRY(tmp_alloc(c, jsf, sfj.size() * sizeof(SFJob)));
@@ -444,11 +525,12 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   ph_end(c, OSVMP2_PH_SF, f_sf);
   CK(cudaGetLastError());
   ph_begin(c, OSVMP2_PH_PROJECT);
-  launch_project(bsrc(c), t, (const ProjJob*)jpj.p, (int)pj.size(), max_nx, c->st);
+  const int fp32 = prec == OSVMP2_MIXED;
+  launch_project(bsrc(c), t, (const ProjJob*)jpj.p, (int)pj.size(), max_nx, fp32, c->st);
   ph_end(c, OSVMP2_PH_PROJECT, f_pj, c->sys.B ? 8.0 * (double)pj.size() * nx * nv : 0.0);
   CK(cudaGetLastError());
   ph_begin(c, OSVMP2_PH_EXCHANGE);
-  launch_exchange(t, nx, (const KJob*)jk.p, (int)kj.size(), max_m, c->st);
+  launch_exchange(t, nx, (const KJob*)jk.p, (int)kj.size(), max_m, fp32, c->st);
   ph_end(c, OSVMP2_PH_EXCHANGE, f_k);
   CK(cudaGetLastError());
   const int n_cta = std::min<int>((int)pjb.size(), 2 * c->num_sms);
@@ -458,6 +540,16 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
                  c->st);
   ph_end(c, OSVMP2_PH_PRECOND, 0.0);
   CK(cudaGetLastError());
+  {   // K~ = X^T K X for the preconditioner-basis (mixed) solver
+    std::vector<KtJob> ktj;
+    for (size_t q = 0; q < kj.size(); q++) ktj.push_back(KtJob{kj[q].i, kj[q].j, c->Kt_h[c->pair_id[(size_t)kj[q].i * n + kj[q].j]]});
+    Tmp jkt;
+    TRY(tmp_alloc(c, jkt, ktj.size() * sizeof(KtJob)));
+    CK(cudaMemcpyAsync(jkt.p, ktj.data(), ktj.size() * sizeof(KtJob), cudaMemcpyHostToDevice, c->st));
+    launch_ktilde(t, (const KtJob*)jkt.p, (int)ktj.size(), (double*)scr.p, n_cta, max_m, c->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+  }
   (void)prec;
   TRY(check_err_flag(c, "pair integrals"));
   c->r_h.resize(c->K_h.size());
@@ -555,6 +647,7 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   TRY(dalloc_t(c, &c->X_d, c->cap_pairs));
   TRY(dalloc_t(c, &c->et_d, c->cap_pairs));
   TRY(dalloc_t(c, &c->r_d, c->cap_pairs));
+  TRY(dalloc_t(c, &c->Kt_d, c->cap_pairs));
   c->sf_id.assign((size_t)n * n, -1);
   c->pair_id.assign((size_t)n * n, -1);
   c->bt_id.assign((size_t)n * n, -1);
@@ -850,7 +943,8 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
   TRY(tmp_alloc(c, d_w, nf * sizeof(int)));
   TRY(tmp_alloc(c, d_out, nf * sizeof(FragOut)));
   TRY(tmp_alloc(c, d_cnt, sizeof(int)));
-  TRY(tmp_alloc(c, d_scr, (size_t)n_cta * frag_scratch_doubles(max_m) * sizeof(double)));
+  const size_t per_cta = (prec == OSVMP2_MIXED) ? frag_mixed_scratch_doubles(max_m) : frag_scratch_doubles(max_m);
+  TRY(tmp_alloc(c, d_scr, (size_t)n_cta * per_cta * sizeof(double)));
   CK(cudaMemcpyAsync(d_orbs.p, orbs_h.data(), orbs_h.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(d_order.p, order.data(), nf * sizeof(int), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(d_w.p, w_h.data(), nf * sizeof(int), cudaMemcpyHostToDevice, c->st));
@@ -876,8 +970,12 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
   }
   SolveOpts so{c->opts.tol_update, c->opts.tol_energy, c->opts.max_iter};
   ph_begin(c, OSVMP2_PH_SOLVE);
-  launch_frag_solve(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, (double*)d_scr.p, n_cta,
-                    (int*)d_cnt.p, (FragOut*)d_out.p, tdst, (const long long*)d_toff.p, c->st);
+  if (prec == OSVMP2_MIXED)
+    launch_frag_solve_mixed(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, (double*)d_scr.p,
+                            n_cta, (int*)d_cnt.p, (FragOut*)d_out.p, tdst, (const long long*)d_toff.p, c->st);
+  else
+    launch_frag_solve(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, (double*)d_scr.p, n_cta,
+                      (int*)d_cnt.p, (FragOut*)d_out.p, tdst, (const long long*)d_toff.p, c->st);
   CK(cudaGetLastError());
   ph_end(c, OSVMP2_PH_SOLVE, 0.0);
   ph_begin(c, OSVMP2_PH_MBE_SUM);
@@ -890,7 +988,9 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
   CK(cudaStreamSynchronize(c->st));
   ph_collect(c);
   double f_solve = 0.0;
-  for (int f = 0; f < nf; f++) f_solve += c->frag_out[f].iters * fragment_iter_flops(c, c->frags[f]);
+  for (int f = 0; f < nf; f++)
+    f_solve += (prec == OSVMP2_MIXED) ? fragment_mixed_flops(c, c->frags[f], c->frag_out[f].iters)
+                                      : c->frag_out[f].iters * fragment_iter_flops(c, c->frags[f]);
   c->flops[OSVMP2_PH_SOLVE] += f_solve;
   int unconv = 0, maxit = 0;
   int64_t worst = -1;

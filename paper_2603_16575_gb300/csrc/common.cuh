@@ -54,31 +54,33 @@ __host__ __device__ inline View transpose(const View& v) {
 }
 
 // ---------------------------------------------------------------- GEMM
-// Accumulate one TM x TN output tile at (m0, n0) of A[MxK] * B[KxN] into acc.
+// Accumulate one TM x TN output tile at (m0, n0) of A[MxK] * B[KxN] into acc,
+// in the arithmetic of V (double, or float for the low-precision products);
+// views may hold either type and are converted on load.
 // Thread (ty, tx) = (tid/16, tid%16) owns rows m0+ty+16i and cols n0+tx+16j.
-template <class VA, class VB>
-__device__ __forceinline__ void tile_mma(int M, int N, int K, int m0, int n0, const VA& A, const VB& B,
-                                         double acc[4][4], double* sm) {
-  double* As = sm;             // [TK][TM]
-  double* Bs = sm + TK * TM;   // [TK][TN]
+template <class V, class VA, class VB>
+__device__ __forceinline__ void tile_mma_t(int M, int N, int K, int m0, int n0, const VA& A, const VB& B,
+                                           V acc[4][4], V* sm) {
+  V* As = sm;             // [TK][TM]
+  V* Bs = sm + TK * TM;   // [TK][TN]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int k0 = 0; k0 < K; k0 += TK) {
 #pragma unroll
     for (int t = 0; t < TM * TK / NT; t++) {
       const int e = tid + t * NT, m = e % TM, k = e / TM;
       const int gm = m0 + m, gk = k0 + k;
-      As[k * TM + m] = (gm < M && gk < K) ? A.get(gm, gk) : 0.0;
+      As[k * TM + m] = (gm < M && gk < K) ? static_cast<V>(A.get(gm, gk)) : V(0);
     }
 #pragma unroll
     for (int t = 0; t < TN * TK / NT; t++) {
       const int e = tid + t * NT, n = e % TN, k = e / TN;
       const int gn = n0 + n, gk = k0 + k;
-      Bs[k * TN + n] = (gn < N && gk < K) ? B.get(gk, gn) : 0.0;
+      Bs[k * TN + n] = (gn < N && gk < K) ? static_cast<V>(B.get(gk, gn)) : V(0);
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < TK; k++) {
-      double a[4], b[4];
+      V a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; i++) a[i] = As[k * TM + ty + 16 * i];
 #pragma unroll
@@ -92,33 +94,54 @@ __device__ __forceinline__ void tile_mma(int M, int N, int K, int m0, int n0, co
   }
 }
 
-// C[MxN] (row-major, ldc) = beta*C + alpha*A*B with the whole CTA (NT threads).
-// beta == 0 never reads C.
 template <class VA, class VB>
-__device__ void cta_gemm(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta,
-                         double* C, int ldc, double* sm) {
+__device__ __forceinline__ void tile_mma(int M, int N, int K, int m0, int n0, const VA& A, const VB& B,
+                                         double acc[4][4], double* sm) {
+  tile_mma_t<double>(M, N, K, m0, n0, A, B, acc, sm);
+}
+
+// C[MxN] (row-major, ldc, element type CT) = beta*C + alpha*A*B with the whole
+// CTA (NT threads), products in the arithmetic of V.  beta == 0 never reads C.
+template <class V, class CT, class VA, class VB>
+__device__ void cta_gemm_t(int M, int N, int K, V alpha, const VA& A, const VB& B, V beta, CT* C, int ldc, V* sm) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int m0 = 0; m0 < M; m0 += TM)
     for (int n0 = 0; n0 < N; n0 += TN) {
-      double acc[4][4];
+      V acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
-      tile_mma(M, N, K, m0, n0, A, B, acc, sm);
+        for (int j = 0; j < 4; j++) acc[i][j] = V(0);
+      tile_mma_t<V>(M, N, K, m0, n0, A, B, acc, sm);
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) {
           const int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
           if (r < M && c < N) {
-            double* cp = C + (size_t)r * ldc + c;
-            *cp = (beta == 0.0 ? 0.0 : beta * *cp) + alpha * acc[i][j];
+            CT* cp = C + (size_t)r * ldc + c;
+            *cp = static_cast<CT>((beta == V(0) ? V(0) : beta * static_cast<V>(*cp)) + alpha * acc[i][j]);
           }
         }
     }
   __syncthreads();
 }
+
+template <class VA, class VB>
+__device__ void cta_gemm(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, double* C,
+                         int ldc, double* sm) {
+  cta_gemm_t<double, double>(M, N, K, alpha, A, B, beta, C, ldc, sm);
+}
+
+// Dense float matrix view (element (r,c) at p[r*ld+c], or p[c*ld+r] when tr).
+struct ViewF {
+  const float* p;
+  int ld;
+  int tr;
+  __device__ __forceinline__ float get(int r, int c) const {
+    return tr ? p[(size_t)c * ld + r] : p[(size_t)r * ld + c];
+  }
+};
 
 // ---------------------------------------------------------------- reductions
 // Deterministic CTA sum / max (fixed shuffle tree, then fixed order over warps).

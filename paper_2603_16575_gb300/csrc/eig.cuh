@@ -58,9 +58,17 @@ __device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double*
       // p = tau * A' v  (warp per row, lanes over columns)
       for (int r = warp; r < L; r += nwarp) {
         const double* row = Ak + (size_t)r * lda;
-        double s = 0.0;
-        for (int c = lane; c < L; c += 32) s += row[c] * v[c];
-        s = warp_sum(s);
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int c = lane;
+        for (; c + 96 < L; c += 128) {       // four independent loads in flight per lane
+          const double a0 = row[c], a1 = row[c + 32], a2 = row[c + 64], a3 = row[c + 96];
+          s0 += a0 * v[c];
+          s1 += a1 * v[c + 32];
+          s2 += a2 * v[c + 64];
+          s3 += a3 * v[c + 96];
+        }
+        for (; c < L; c += 32) s0 += row[c] * v[c];
+        const double s = warp_sum((s0 + s1) + (s2 + s3));
         if (lane == 0) p[r] = tk * s;
       }
       __syncthreads();
@@ -73,7 +81,15 @@ __device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double*
       for (int r = warp; r < L; r += nwarp) {
         double* row = Ak + (size_t)r * lda;
         const double vr = v[r], wr = p[r];
-        for (int c = lane; c < L; c += 32) row[c] -= vr * p[c] + wr * v[c];
+        int c = lane;
+        for (; c + 96 < L; c += 128) {
+          const double a0 = row[c], a1 = row[c + 32], a2 = row[c + 64], a3 = row[c + 96];
+          row[c] = a0 - (vr * p[c] + wr * v[c]);
+          row[c + 32] = a1 - (vr * p[c + 32] + wr * v[c + 32]);
+          row[c + 64] = a2 - (vr * p[c + 64] + wr * v[c + 64]);
+          row[c + 96] = a3 - (vr * p[c + 96] + wr * v[c + 96]);
+        }
+        for (; c < L; c += 32) row[c] -= vr * p[c] + wr * v[c];
       }
       // keep the reflector below the sub-diagonal of column k
       for (int t = tid + 1; t < L; t += NT) A[(size_t)(k + 1 + t) * lda + k] = v[t];
@@ -93,9 +109,9 @@ __device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double*
 }
 
 // Z (n x n, row-major, ldz) = H_0 H_1 ... H_{n-3} from the reflectors left in A.
-// y: shared scratch of n doubles.
+// y, vs: shared scratch of n doubles each.
 __device__ inline void cta_form_z(const double* A, int n, int lda, const double* tau, double* Z, int ldz,
-                                  double* y) {
+                                  double* y, double* vs) {
   const int tid = threadIdx.x;
   for (int t = tid; t < n * n; t += NT) Z[(size_t)(t / n) * ldz + (t % n)] = (t / n == t % n) ? 1.0 : 0.0;
   __syncthreads();
@@ -103,17 +119,18 @@ __device__ inline void cta_form_z(const double* A, int n, int lda, const double*
     const double tk = tau[k];
     if (tk == 0.0) continue;
     const int L = n - k - 1;
-    // y_c = sum_r v_r Z[k+1+r][k+1+c]   (v_0 = 1, v_r = A[k+1+r][k])
+    for (int r = tid; r < L; r += NT) vs[r] = (r == 0) ? 1.0 : A[(size_t)(k + 1 + r) * lda + k];
+    __syncthreads();
+    // y_c = tau * sum_r v_r Z[k+1+r][k+1+c]
     for (int c = tid; c < L; c += NT) {
-      double s = Z[(size_t)(k + 1) * ldz + (k + 1 + c)];
-      for (int r = 1; r < L; r++) s += A[(size_t)(k + 1 + r) * lda + k] * Z[(size_t)(k + 1 + r) * ldz + (k + 1 + c)];
+      double s = 0.0;
+      for (int r = 0; r < L; r++) s += vs[r] * Z[(size_t)(k + 1 + r) * ldz + (k + 1 + c)];
       y[c] = tk * s;
     }
     __syncthreads();
     for (int t = tid; t < L * L; t += NT) {
       const int r = t / L, c = t % L;
-      const double vr = (r == 0) ? 1.0 : A[(size_t)(k + 1 + r) * lda + k];
-      Z[(size_t)(k + 1 + r) * ldz + (k + 1 + c)] -= vr * y[c];
+      Z[(size_t)(k + 1 + r) * ldz + (k + 1 + c)] -= vs[r] * y[c];
     }
     __syncthreads();
   }
@@ -207,8 +224,17 @@ __device__ inline int cta_syev(double* A, int n, int lda, double* w, double* Z, 
     return 0;
   }
   cta_tridiag(A, n, lda, w, e, tau, v, p, red);
-  cta_form_z(A, n, lda, tau, Z, ldz, v);
-  return cta_tridiag_qr(w, e, n, Z, ldz, cs);
+  cta_form_z(A, n, lda, tau, Z, ldz, v, p);
+  // the bulge chase is sequential: run it on shared-memory copies of d and e
+  for (int t = threadIdx.x; t < n; t += NT) {
+    v[t] = w[t];
+    p[t] = (t + 1 < n) ? e[t] : 0.0;
+  }
+  __syncthreads();
+  const int rc = cta_tridiag_qr(v, p, n, Z, ldz, cs);
+  for (int t = threadIdx.x; t < n; t += NT) w[t] = v[t];
+  __syncthreads();
+  return rc;
 }
 
 // ---------------------------------------------------------------- top-k

@@ -21,6 +21,7 @@ struct Tables {
   const double* const* X;       // [n_pairs] X [m][m] (first r columns valid)
   const double* const* et;      // [n_pairs] e~ [m] (first r valid)
   const int* r;                 // [n_pairs]
+  const double* const* Kt;      // [n_pairs] K~ = X^T K X  [r][r]
   const double* f_occ;          // [n_occ][n_occ]
 };
 
@@ -62,7 +63,7 @@ struct ProjJob {         // B~_{i}^{(x)} = B[i]^T Q_x  -> out [n_aux][n_x]
   int i, x;
   double* out;
 };
-void launch_project(const BSrc& src, const Tables& t, const ProjJob* jobs, int n_jobs, int max_nx,
+void launch_project(const BSrc& src, const Tables& t, const ProjJob* jobs, int n_jobs, int max_nx, int fp32,
                     cudaStream_t st);
 struct KJob {            // K_(ij,ij) from the projections
   int i, j;
@@ -72,7 +73,7 @@ struct KJob {            // K_(ij,ij) from the projections
   const double* Bjj;     // B~_j^(j)
   double* out;           // [m][m]
 };
-void launch_exchange(const Tables& t, int n_aux, const KJob* jobs, int n_jobs, int max_m, cudaStream_t st);
+void launch_exchange(const Tables& t, int n_aux, const KJob* jobs, int n_jobs, int max_m, int fp32, cudaStream_t st);
 struct SFJob {           // S_(x,y), F_(x,y)
   int x, y;
   double* S;
@@ -103,6 +104,23 @@ __host__ __device__ inline size_t frag_scratch_doubles(int max_m) { return 26 * 
 void launch_frag_solve(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
                        SolveOpts o, double* scratch, int n_cta, int* counter, FragOut* out,
                        double* Tstore, const long long* Toff, cudaStream_t st);
+// Mixed form (solve_mixed.cu): per pair K~ = X^T K X, then the fragment solve in
+// the preconditioner basis with FP32 coupling products.
+struct KtJob {
+  int i, j;
+  double* Kt;
+};
+void launch_ktilde(const Tables& t, const KtJob* jobs, int n_jobs, double* scratch, int n_cta, int max_m,
+                   cudaStream_t st);
+// per CTA: Y (6 FP64) + Y32, C32 (6 + 6 FP32) + 24 Sigma + 1 work (FP32) + 1 FP64 work
+__host__ __device__ inline size_t frag_mixed_scratch_doubles(int max_m) {
+  const size_t M2 = (size_t)max_m * max_m;
+  return 6 * M2 + (37 * M2 + 1) / 2 + M2 + 64;
+}
+void launch_frag_solve_mixed(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
+                             SolveOpts o, double* scratch, int n_cta, int* counter, FragOut* out, double* Tstore,
+                             const long long* Toff, cudaStream_t st);
+
 // E = sum_f w_f * E_f in a fixed order -> e_out (device scalar)
 void launch_weighted_sum(const FragOut* out, const int* weights, int n, double* e_out, cudaStream_t st);
 

@@ -16,42 +16,46 @@ struct RowMajor {         // B(r, c) = p[r*ld + c]
   __device__ __forceinline__ double get(int r, int c) const { return p[(size_t)r * ld + c]; }
 };
 
-// grid: (job, P tile, mu tile)
+// grid: (job, P tile, mu tile).  V = double (FP64 form) or float (mixed form:
+// FP32 products and accumulation, result stored as FP64).
+template <class V>
 __global__ void __launch_bounds__(NT) k_project(BSrc src, Tables t, const ProjJob* __restrict__ jobs) {
-  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  __shared__ V sm[GEMM_SMEM_DOUBLES];
   const ProjJob jb = jobs[blockIdx.x];
   const int nx = t.n_osv[jb.x];
   const int m0 = blockIdx.y * TM, n0 = blockIdx.z * TN;
   if (n0 >= nx) return;
   const int M = src.n_aux, N = nx, K = src.n_vir;
-  double acc[4][4];
+  V acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; u++)
 #pragma unroll
-    for (int v = 0; v < 4; v++) acc[u][v] = 0.0;
-  tile_mma(M, N, K, m0, n0, ProjA{src, jb.i}, RowMajor{t.Q[jb.x], nx}, acc, sm);
+    for (int v = 0; v < 4; v++) acc[u][v] = V(0);
+  tile_mma_t<V>(M, N, K, m0, n0, ProjA{src, jb.i}, RowMajor{t.Q[jb.x], nx}, acc, sm);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int u = 0; u < 4; u++)
 #pragma unroll
     for (int v = 0; v < 4; v++) {
       const int r = m0 + ty + 16 * u, c = n0 + tx + 16 * v;
-      if (r < M && c < N) jb.out[(size_t)r * N + c] = acc[u][v];
+      if (r < M && c < N) jb.out[(size_t)r * N + c] = (double)acc[u][v];
     }
 }
 
-void launch_project(const BSrc& src, const Tables& t, const ProjJob* jobs, int n_jobs, int max_nx,
+void launch_project(const BSrc& src, const Tables& t, const ProjJob* jobs, int n_jobs, int max_nx, int fp32,
                     cudaStream_t st) {
   if (n_jobs == 0) return;
   dim3 grid(n_jobs, (src.n_aux + TM - 1) / TM, (max_nx + TN - 1) / TN);
-  k_project<<<grid, NT, 0, st>>>(src, t, jobs);
+  if (fp32) k_project<float><<<grid, NT, 0, st>>>(src, t, jobs);
+  else k_project<double><<<grid, NT, 0, st>>>(src, t, jobs);
   note_launch(1);
 }
 
 // K_(ij,ij)[mu][nu] = sum_P L[P][mu] R[P][nu] with L = [B~_i^(i) B~_i^(j)],
 // R = [B~_j^(i) B~_j^(j)] (aux x OSV, row-major).  grid: (job, tile r, tile c)
+template <class V>
 __global__ void __launch_bounds__(NT) k_exchange(Tables t, int n_aux, const KJob* __restrict__ jobs) {
-  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  __shared__ V sm[GEMM_SMEM_DOUBLES];
   const KJob jb = jobs[blockIdx.x];
   const int ni = t.n_osv[jb.i];
   const int nj = (jb.i == jb.j) ? 0 : t.n_osv[jb.j];
@@ -69,27 +73,28 @@ __global__ void __launch_bounds__(NT) k_exchange(Tables t, int n_aux, const KJob
     B.b[0][0] = B.b[1][0] = Blk{jb.Bji, ni, 0};
     B.b[0][1] = B.b[1][1] = Blk{jb.Bjj, nj, 0};
   }
-  double acc[4][4];
+  V acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; u++)
 #pragma unroll
-    for (int v = 0; v < 4; v++) acc[u][v] = 0.0;
-  tile_mma(m, m, n_aux, m0, n0, A, B, acc, sm);
+    for (int v = 0; v < 4; v++) acc[u][v] = V(0);
+  tile_mma_t<V>(m, m, n_aux, m0, n0, A, B, acc, sm);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int u = 0; u < 4; u++)
 #pragma unroll
     for (int v = 0; v < 4; v++) {
       const int r = m0 + ty + 16 * u, c = n0 + tx + 16 * v;
-      if (r < m && c < m) jb.out[(size_t)r * m + c] = acc[u][v];
+      if (r < m && c < m) jb.out[(size_t)r * m + c] = (double)acc[u][v];
     }
 }
 
-void launch_exchange(const Tables& t, int n_aux, const KJob* jobs, int n_jobs, int max_m, cudaStream_t st) {
+void launch_exchange(const Tables& t, int n_aux, const KJob* jobs, int n_jobs, int max_m, int fp32, cudaStream_t st) {
   if (n_jobs == 0) return;
   const int nt = (max_m + TM - 1) / TM;
   dim3 grid(n_jobs, nt, nt);
-  k_exchange<<<grid, NT, 0, st>>>(t, n_aux, jobs);
+  if (fp32) k_exchange<float><<<grid, NT, 0, st>>>(t, n_aux, jobs);
+  else k_exchange<double><<<grid, NT, 0, st>>>(t, n_aux, jobs);
   note_launch(1);
 }
 

@@ -1,0 +1,226 @@
+// A4 in the mixed form.  Algorithm 7 updates T_p += X_p (R~_p / D_p) X_p^T with
+// R~_p = X_p^T R_p X_p.  Writing T_p = X_p Y_p X_p^T (T starts at 0 and every
+// update lies in the span of X_p), Eq. (res_close) becomes, in the
+// preconditioner basis,
+//     R~_p = K~_p - D_p o Y_p + C_p,   C_p = sum_terms c_t Sigma_pq op(Y_q) Sigma_pq^T,
+// with K~_p = X_p^T K_p X_p, Sigma_pq = X_p^T S_(p,q) X_q (entries bounded by 1,
+// since P_p X_p has orthonormal columns) and D_p the update denominators; the
+// pair-diagonal F/S terms collapse to -D o Y exactly (X^T S X = 1,
+// X^T F X = diag(e~)).  The update is Y_p <- (K~_p + C_p) / D_p.
+//
+// Precision: the coupling C_p carries the off-diagonal occupied Fock elements
+// (|c_t| ~ 1e-2 against |D| ~ 1), so its FP32 rounding perturbs Y by
+// ~ eps_32 |c| / |D| ~ 1e-9 relative.  C_p and the Sigma_pq are therefore FP32
+// products; K~_p, D_p, Y_p (master copy) and the energy <K~_p, 2Y_p - Y_p^T> are FP64.
+#include "pairview.cuh"
+
+namespace osv {
+
+// K~_p = X_p^T K_p X_p (FP64), one CTA per pair (grid-stride).
+__global__ void __launch_bounds__(NT) k_ktilde(Tables t, const KtJob* __restrict__ jobs, int n_jobs, double* scratch,
+                                               int max_m) {
+  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  double* W = scratch + (size_t)blockIdx.x * max_m * max_m;
+  for (int jid = blockIdx.x; jid < n_jobs; jid += gridDim.x) {
+    const KtJob jb = jobs[jid];
+    const int m = pair_dim(t, jb.i, jb.j);
+    const int pid = t.pair_id[jb.i * t.n_occ + jb.j];
+    const int r = t.r[pid];
+    const View Xv = dense_view(t.X[pid], m, r, m);
+    cta_gemm(m, r, m, 1.0, dense_view(t.K[pid], m, m, m), Xv, 0.0, W, r, sm);
+    cta_gemm(r, r, m, 1.0, transpose(Xv), dense_view(W, m, r, r), 0.0, jb.Kt, r, sm);
+  }
+}
+
+void launch_ktilde(const Tables& t, const KtJob* jobs, int n_jobs, double* scratch, int n_cta, int max_m,
+                   cudaStream_t st) {
+  if (!n_jobs) return;
+  k_ktilde<<<n_cta, NT, 0, st>>>(t, jobs, n_jobs, scratch, max_m);
+  note_launch(1);
+}
+
+struct MTerm {     // one coupling term of local pair p: coef * Sigma[sig] op(Y_q) Sigma[sig]^T
+  int q;           // local stored pair
+  int tr;          // op = transpose
+  int sig;         // index of Sigma_(p,q) in the fragment's list
+  double coef;
+};
+
+constexpr int MAX_TERMS = 24;   // 6 pairs x 4 coupling terms (three-orbital fragments)
+
+__global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __restrict__ frag_orbs,
+                                                         const int* __restrict__ order, int n_frag, int max_m,
+                                                         SolveOpts o, double* scratch, int* counter, FragOut* out,
+                                                         double* Tstore, const long long* __restrict__ Toff) {
+  __shared__ float fsm[GEMM_SMEM_DOUBLES];
+  __shared__ double dsm[GEMM_SMEM_DOUBLES];
+  __shared__ double red[40];
+  __shared__ int s_f;
+  __shared__ MTerm terms[6][8];
+  __shared__ int nterm[6];
+  __shared__ int sig_p[MAX_TERMS], sig_q[MAX_TERMS];
+  __shared__ int s_nsig;
+  const size_t M2 = (size_t)max_m * max_m;
+  double* base = scratch + (size_t)blockIdx.x * frag_mixed_scratch_doubles(max_m);
+  double* Y64[6];
+  float* Y32[6];
+  float* C32[6];
+  float* Sig[MAX_TERMS];
+  for (int u = 0; u < 6; u++) Y64[u] = base + u * M2;
+  float* fb = reinterpret_cast<float*>(base + 6 * M2);
+  for (int u = 0; u < 6; u++) {
+    Y32[u] = fb + u * M2;
+    C32[u] = fb + (6 + u) * M2;
+  }
+  for (int u = 0; u < MAX_TERMS; u++) Sig[u] = fb + (12 + u) * M2;
+  float* W32 = fb + (12 + MAX_TERMS) * M2;
+  double* W64 = base + 6 * M2 + (37 * M2 + 1) / 2;   // after 6 + 6 + 24 + 1 float matrices
+  const double* f = t.f_occ;
+  const int n = t.n_occ;
+  while (true) {
+    if (threadIdx.x == 0) s_f = atomicAdd(counter, 1);
+    __syncthreads();
+    const int fi = s_f;
+    __syncthreads();
+    if (fi >= n_frag) break;
+    const int fid = order[fi];
+    int orbs[3];
+    int nc = 0;
+    for (int u = 0; u < 3; u++) {
+      const int v = frag_orbs[3 * fid + u];
+      if (v >= 0) orbs[nc++] = v;
+    }
+    const int np = nc * (nc + 1) / 2;
+    int pa[6], pb[6], pm[6], pr[6], pid[6];
+    for (int a = 0, lp = 0; a < nc; a++)
+      for (int b = a; b < nc; b++, lp++) {
+        pa[lp] = a;
+        pb[lp] = b;
+        pm[lp] = pair_dim(t, orbs[a], orbs[b]);
+        pid[lp] = t.pair_id[orbs[a] * n + orbs[b]];
+        pr[lp] = t.r[pid[lp]];
+      }
+    // coupling terms of every pair and the distinct (p, q) overlaps they use
+    if (threadIdx.x == 0) {
+      int ns = 0;
+      for (int p = 0; p < np; p++) {
+        const int a = pa[p], b = pb[p], i = orbs[a], j = orbs[b];
+        int nt = 0;
+        for (int c = 0; c < nc; c++) {
+          const int k = orbs[c];
+          for (int s2 = 0; s2 < 2; s2++) {
+            int x, y;
+            double coef;
+            if (s2 == 0) {
+              if (c == b) continue;
+              x = a; y = c; coef = -f[k * n + j];
+            } else {
+              if (c == a) continue;
+              x = c; y = b; coef = -f[i * n + k];
+            }
+            if (coef == 0.0) continue;
+            const int qa = min(x, y), qb = max(x, y);
+            const int q = qa * nc - qa * (qa - 1) / 2 + (qb - qa);
+            int sg = -1;
+            for (int u = 0; u < ns; u++)
+              if (sig_p[u] == p && sig_q[u] == q) sg = u;
+            if (sg < 0) { sg = ns; sig_p[ns] = p; sig_q[ns] = q; ns++; }
+            terms[p][nt++] = MTerm{q, x > y, sg, coef};
+          }
+        }
+        nterm[p] = nt;
+      }
+      s_nsig = ns;
+    }
+    __syncthreads();
+    // Sigma_pq = X_p^T S_(p,q) X_q  (FP32 products)
+    for (int u = 0; u < s_nsig; u++) {
+      const int p = sig_p[u], q = sig_q[u];
+      const View Spq = pair_view(t, t.S, orbs[pa[p]], orbs[pb[p]], orbs[pa[q]], orbs[pb[q]]);
+      cta_gemm_t<float, float>(pm[p], pr[q], pm[q], 1.f, Spq, dense_view(t.X[pid[q]], pm[q], pr[q], pm[q]), 0.f, W32,
+                               pr[q], fsm);
+      cta_gemm_t<float, float>(pr[p], pr[q], pm[p], 1.f, transpose(dense_view(t.X[pid[p]], pm[p], pr[p], pm[p])),
+                               ViewF{W32, pr[q], 0}, 0.f, Sig[u], pr[q], fsm);
+    }
+    for (int p = 0; p < np; p++)
+      for (int idx = threadIdx.x; idx < pr[p] * pr[p]; idx += NT) {
+        Y64[p][idx] = 0.0;
+        Y32[p][idx] = 0.f;
+      }
+    __syncthreads();
+    double e_prev = 0.0, e = 0.0, um = 0.0;
+    int status = ERR_NOCONV, iters = o.max_iter;
+    for (int it = 1; it <= o.max_iter; it++) {
+      // C_p from the previous sweep's amplitudes (Jacobi)
+      for (int p = 0; p < np; p++) {
+        const int rp = pr[p];
+        for (int idx = threadIdx.x; idx < rp * rp; idx += NT) C32[p][idx] = 0.f;
+        __syncthreads();
+        for (int u = 0; u < nterm[p]; u++) {
+          const MTerm tm = terms[p][u];
+          const int rq = pr[tm.q];
+          const ViewF S{Sig[tm.sig], rq, 0};
+          cta_gemm_t<float, float>(rq, rp, rq, 1.f, ViewF{Y32[tm.q], rq, tm.tr}, ViewF{Sig[tm.sig], rq, 1}, 0.f, W32,
+                                   rp, fsm);
+          cta_gemm_t<float, float>(rp, rp, rq, (float)tm.coef, S, ViewF{W32, rp, 0}, 1.f, C32[p], rp, fsm);
+        }
+      }
+      // Y_p <- (K~_p + C_p) / D_p in FP64; energy <K~_p, 2Y_p - Y_p^T>
+      um = 0.0;
+      e = 0.0;
+      for (int p = 0; p < np; p++) {
+        const int rp = pr[p];
+        const int i = orbs[pa[p]], j = orbs[pb[p]];
+        const double fij = f[i * n + i] + f[j * n + j];
+        const double* et = t.et[pid[p]];
+        const double* Kt = t.Kt[pid[p]];
+        double du = 0.0;
+        for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
+          const int r = idx / rp, c = idx % rp;
+          const double y = (Kt[idx] + (double)C32[p][idx]) / (fij - et[r] - et[c]);
+          du = fmax(du, fabs(y - Y64[p][idx]));
+          Y64[p][idx] = y;
+        }
+        um = fmax(um, cta_max(du, red));
+        double s = 0.0;
+        for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
+          const int r = idx / rp, c = idx % rp;
+          s += Kt[idx] * (2.0 * Y64[p][idx] - Y64[p][(size_t)c * rp + r]);
+          Y32[p][idx] = (float)Y64[p][idx];
+        }
+        s = cta_sum(s, red);
+        e += (pa[p] == pb[p]) ? s : 2.0 * s;
+      }
+      if (!isfinite(e) || !isfinite(um)) { status = ERR_NONFINITE; iters = it; break; }
+      if (um < o.tol_update && fabs(e - e_prev) < fmax(o.tol_energy, 1e-11 * fabs(e))) {
+        status = 0;
+        iters = it;
+        break;
+      }
+      e_prev = e;
+    }
+    if (threadIdx.x == 0) out[fid] = FragOut{e, um, iters, status};
+    if (Tstore) {   // T_p = X_p Y_p X_p^T (FP64) for the gradient
+      double* dst = Tstore + Toff[fid];
+      for (int p = 0; p < np; p++) {
+        const int mp = pm[p], rp = pr[p];
+        const View Xv = dense_view(t.X[pid[p]], mp, rp, mp);
+        cta_gemm(rp, mp, rp, 1.0, dense_view(Y64[p], rp, rp, rp), transpose(Xv), 0.0, W64, mp, dsm);
+        cta_gemm(mp, mp, rp, 1.0, Xv, dense_view(W64, rp, mp, mp), 0.0, dst, mp, dsm);
+        dst += (size_t)mp * mp;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_frag_solve_mixed(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
+                             SolveOpts o, double* scratch, int n_cta, int* counter, FragOut* out, double* Tstore,
+                             const long long* Toff, cudaStream_t st) {
+  if (n_frag == 0) return;
+  cudaMemsetAsync(counter, 0, sizeof(int), st);
+  k_frag_solve_mixed<<<n_cta, NT, 0, st>>>(t, frag_orbs, order, n_frag, max_m, o, scratch, counter, out, Tstore, Toff);
+  note_launch(1);
+}
+
+}  // namespace osv

@@ -169,3 +169,36 @@ def test_autograd_function_backward():
     E2, dB, df, de, _ = ctx.energy_grad(4.5, 4.0)
     assert torch.allclose(B.grad, 3.0 * dB) and torch.allclose(f.grad, 3.0 * df) and torch.allclose(e.grad, 3.0 * de)
     ctx.close()
+
+
+# ---------------------------------------------------------------- mixed form
+def test_mixed_mbe3_energy_within_one_microhartree():
+    """Preconditioner-basis solve with FP32 coupling products: total and per-fragment
+    energies against the FP64 oracle (target 1 uEh total)."""
+    s = synth.make_system(12, 70, 130, seed=41, lam=1.2)
+    ctx = _ctx()
+    _build(ctx, s, 1e-4)
+    E, st = ctx.mbe3_energy(4.5, 3.8, "mixed")
+    o = oracle.OSVSystem(s.B_block, 12, s.e_vir, s.f_occ, l_osv=1e-4)
+    E_ref, per = o.mbe3_energy(s.r_occ, 4.5, 3.8)
+    _, _, ef = ctx.fragment_results()
+    assert st["n_unconverged"] == 0
+    assert max(abs(a - b[2]) for a, b in zip(ef, per)) < 1e-8
+    assert abs(E - E_ref) < 1e-6
+    E64, _ = ctx.mbe3_energy(4.5, 3.8, "fp64")
+    assert abs(E64 - E_ref) < 1e-9
+    ctx.close()
+
+
+def test_mixed_gradient_close_to_oracle():
+    s = synth.make_system(6, 40, 80, seed=29, lam=1.5, f_off=3e-2)
+    ctx = _ctx()
+    _build(ctx, s, 1e-3)
+    E, dB, df, de, st = ctx.energy_grad(4.5, 4.0, "mixed")
+    o = oracle.OSVSystem(s.B_block, 6, s.e_vir, s.f_occ, l_osv=1e-3)
+    E_ref, dB_ref, de_ref, df_ref = oracle.mbe3_energy_gradient(o, s.r_occ, 4.5, 4.0, 40, 80)
+    assert abs(E - E_ref) < 1e-6
+    for g, r in ((dB, dB_ref), (df, df_ref), (de, de_ref)):
+        g = g.cpu().numpy()
+        assert np.abs(g - r).max() < 1e-6 * np.abs(r).max()
+    ctx.close()
