@@ -206,22 +206,27 @@ def run_gpu(args):
     e2e_value = world * n_frag / statistics.median(e2e_t)
 
     # ---- roofline of the dominant kernel (largest device time in the timed region)
+    peak_fp64 = FP64_PEAK_TFLOPS
+    peak_fp32 = 152 * 128 * 2 * 2.070e9 / 1e12                 # 128 FFMA/clk/SM -> 80.5 TF/s
+
+    def phase_peak(name):
+        """(bound, peak TFLOP/s, source) of a phase in the arithmetic it runs in."""
+        if args.prec == "mixed" and name in ("project", "exchange", "solve"):
+            return "alu", peak_fp32, "FP32 SIMT: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz (SGEMM measured 70)"
+        return "alu", peak_fp64, "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal 1.25; DGEMM measured 1.10)"
+
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     name, (ms, fl, by, calls) = dom
     per_launch_s = ms / 1e3 / max(calls, 1)
-    if fl > 0:
-        achieved = fl / max(calls, 1) / per_launch_s / 1e12
-        bound, unit, peak = "alu", "TFLOP/s", FP64_PEAK_TFLOPS
-        if args.prec == "mixed" and name in ("project", "exchange", "tii"):
-            bound, peak = "tensor", float(peaks.get("bf16_tflops_sustained", 1753.8)) / 2.0
-    else:
-        achieved, bound, unit, peak = None, "alu", "TFLOP/s", FP64_PEAK_TFLOPS
-    traffic = None
-    roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal 1.25 TF; cuBLAS DGEMM measured 1.10)"}
-    phases = {k: {"ms_per_step": v[0] / args.steps, "tflops": (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 and v[1] else None}
-              for k, v in prof.items()}
+    bound, peak, src = phase_peak(name)
+    achieved = fl / max(calls, 1) / per_launch_s / 1e12 if fl > 0 else None
+    roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_source": src}
+    phases = {}
+    for k, v in prof.items():
+        b_, p_, _ = phase_peak(k)
+        tf = (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 and v[1] else None
+        phases[k] = {"ms_per_step": v[0] / args.steps, "tflops": tf, "frac": (tf / p_) if tf else None}
 
     out = {
         "metric": "MBE(3) fragments/s",

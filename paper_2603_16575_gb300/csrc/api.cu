@@ -63,12 +63,14 @@ struct osvmp2_ctx {
   double** X_d = nullptr;
   double** et_d = nullptr;
   double** Kt_d = nullptr;
+  float** U_d = nullptr;
   int* r_d = nullptr;
   int* err_d = nullptr;
   double* scal_d = nullptr;          // device scalars (energies)
   // host mirrors
   std::vector<int> sf_id, pair_id, bt_id;
   std::vector<double*> S_h, F_h, K_h, X_h, et_h, bt_h, Kt_h;
+  std::vector<float*> U_h, Gi_h, Gj_h;   // mixed form: per pair U = P X and G = U^T B
   std::vector<int> m_h;
   std::vector<int> pi_h, pj_h;       // pair id -> (i, j)
   // last MBE call
@@ -156,10 +158,11 @@ void free_system(osvmp2_ctx* c) {
   c->n_osv.clear(); c->Qp.clear(); c->Wp.clear();
   c->sf_id.clear(); c->pair_id.clear(); c->bt_id.clear();
   c->S_h.clear(); c->F_h.clear(); c->K_h.clear(); c->X_h.clear(); c->et_h.clear(); c->bt_h.clear(); c->Kt_h.clear();
+  c->U_h.clear(); c->Gi_h.clear(); c->Gj_h.clear();
   c->m_h.clear(); c->pi_h.clear(); c->pj_h.clear();
   c->frags.clear(); c->frag_out.clear();
   c->n_osv_d = nullptr; c->Q_d = nullptr; c->sf_id_d = nullptr; c->S_d = c->F_d = nullptr;
-  c->pair_id_d = nullptr; c->K_d = c->X_d = c->et_d = c->Kt_d = nullptr; c->r_d = nullptr;
+  c->pair_id_d = nullptr; c->K_d = c->X_d = c->et_d = c->Kt_d = nullptr; c->r_d = nullptr; c->U_d = nullptr;
 }
 
 Tables tables(const osvmp2_ctx* c) {
@@ -177,6 +180,7 @@ Tables tables(const osvmp2_ctx* c) {
   t.et = c->et_d;
   t.r = c->r_d;
   t.Kt = c->Kt_d;
+  t.U = c->U_d;
   t.f_occ = c->sys.f_occ;
   return t;
 }
@@ -298,6 +302,7 @@ int reset_pairs(osvmp2_ctx* c) {
   c->pair_id.assign(nn, -1);
   c->bt_id.assign(nn, -1);
   c->S_h.clear(); c->F_h.clear(); c->K_h.clear(); c->X_h.clear(); c->et_h.clear(); c->bt_h.clear(); c->Kt_h.clear();
+  c->U_h.clear(); c->Gi_h.clear(); c->Gj_h.clear();
   c->m_h.clear(); c->pi_h.clear(); c->pj_h.clear(); c->r_h.clear();
   TRY(upload(c, c->sf_id_d, c->sf_id));
   TRY(upload(c, c->pair_id_d, c->pair_id));
@@ -425,7 +430,9 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
       bt_doubles += (size_t)nx * c->n_osv[x];
     }
   };
+  const bool mixed = prec == OSVMP2_MIXED;
   for (auto& p : newp) {
+    if (mixed) break;    // the mixed form projects onto U = P X instead (ubasis.cu)
     want_bt(p.first, p.first);
     if (p.first != p.second) {
       want_bt(p.first, p.second);
@@ -490,7 +497,9 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
       c->pi_h.push_back(i);
       c->pj_h.push_back(j);
       auto bt = [&](int a, int x) { return c->bt_h[c->bt_id[(size_t)a * n + x]]; };
-      if (i == j) kj.push_back(KJob{i, j, bt(i, i), nullptr, nullptr, nullptr, K});
+      if (mixed) {
+        // no raw-basis exchange block in the mixed form
+      } else if (i == j) kj.push_back(KJob{i, j, bt(i, i), nullptr, nullptr, nullptr, K});
       else kj.push_back(KJob{i, j, bt(i, i), bt(i, j), bt(j, i), bt(j, j), K});
       pjb.push_back(PJob{i, j, X, et, c->r_d + pid});
     }
@@ -524,23 +533,104 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   launch_sf(t, c->sys.e_vir, (const SFJob*)jsf.p, (int)sfj.size(), max_n, c->st);
   ph_end(c, OSVMP2_PH_SF, f_sf);
   CK(cudaGetLastError());
-  ph_begin(c, OSVMP2_PH_PROJECT);
-  const int fp32 = prec == OSVMP2_MIXED;
-  launch_project(bsrc(c), t, (const ProjJob*)jpj.p, (int)pj.size(), max_nx, fp32, c->st);
-  ph_end(c, OSVMP2_PH_PROJECT, f_pj, c->sys.B ? 8.0 * (double)pj.size() * nx * nv : 0.0);
-  CK(cudaGetLastError());
-  ph_begin(c, OSVMP2_PH_EXCHANGE);
-  launch_exchange(t, nx, (const KJob*)jk.p, (int)kj.size(), max_m, fp32, c->st);
-  ph_end(c, OSVMP2_PH_EXCHANGE, f_k);
-  CK(cudaGetLastError());
+  if (!mixed) {   // raw-basis projection and exchange blocks (FP64 form only)
+    ph_begin(c, OSVMP2_PH_PROJECT);
+    launch_project(bsrc(c), t, (const ProjJob*)jpj.p, (int)pj.size(), max_nx, 0, c->st);
+    ph_end(c, OSVMP2_PH_PROJECT, f_pj, c->sys.B ? 8.0 * (double)pj.size() * nx * nv : 0.0);
+    CK(cudaGetLastError());
+    ph_begin(c, OSVMP2_PH_EXCHANGE);
+    launch_exchange(t, nx, (const KJob*)jk.p, (int)kj.size(), max_m, 0, c->st);
+    ph_end(c, OSVMP2_PH_EXCHANGE, f_k);
+    CK(cudaGetLastError());
+  }
   const int n_cta = std::min<int>((int)pjb.size(), 2 * c->num_sms);
-  TRY(tmp_alloc(c, scr, (size_t)n_cta * precond_scratch_doubles(max_m) * sizeof(double)));
+  const int n_warps = std::min<int>((int)pjb.size(), 16 * c->num_sms);
+  const bool warp_pc = max_m <= 192;
+  TRY(tmp_alloc(c, scr, std::max((size_t)n_cta * precond_scratch_doubles(max_m),
+                                 warp_pc ? precond_w_scratch_doubles(max_m, n_warps) : (size_t)0) * sizeof(double)));
+  double f_pc = 0.0;
+  for (auto& j : pjb) {
+    const double m = pair_dim_h(c, j.i, j.j);
+    f_pc += 9.0 * m * m * m + 2.0 * m * m * m + 2.0 * m * m * m + 9.0 * m * m * m + 2.0 * m * m * m;
+  }
   ph_begin(c, OSVMP2_PH_PRECOND);
-  launch_precond(t, c->opts.tau_s, (const PJob*)jp.p, (int)pjb.size(), max_m, (double*)scr.p, n_cta, c->err_d,
-                 c->st);
-  ph_end(c, OSVMP2_PH_PRECOND, 0.0);
+  if (warp_pc)
+    launch_precond_w(t, c->opts.tau_s, (const PJob*)jp.p, (int)pjb.size(), max_m, (double*)scr.p, n_warps, c->err_d,
+                     c->st);
+  else
+    launch_precond(t, c->opts.tau_s, (const PJob*)jp.p, (int)pjb.size(), max_m, (double*)scr.p, n_cta, c->err_d,
+                   c->st);
+  ph_end(c, OSVMP2_PH_PRECOND, f_pc);
   CK(cudaGetLastError());
-  {   // K~ = X^T K X for the preconditioner-basis (mixed) solver
+  TRY(check_err_flag(c, "pair integrals"));
+  c->r_h.resize(c->K_h.size());
+  CK(cudaMemcpyAsync(c->r_h.data(), c->r_d, c->r_h.size() * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (mixed) {   // U = P X, G = U^T B, K~ = G_i G_j^T (orthonormal pair basis, FP32 products)
+    size_t ufl = 0, gfl = 0;
+    int max_r = 0;
+    std::vector<UJob> uj;
+    std::vector<GJob> gj;
+    std::vector<KgJob> kgj;
+    for (auto& p : newp) {
+      const int pid = c->pair_id[(size_t)p.first * n + p.second];
+      const int r = c->r_h[pid];
+      max_r = std::max(max_r, r);
+      ufl += (size_t)nv * r;
+      gfl += (size_t)r * nx * (p.first == p.second ? 1 : 2);
+    }
+    float *umem = nullptr, *gmem = nullptr;
+    TRY(palloc(c, reinterpret_cast<double**>(&umem), (ufl + 1) / 2 + 1));
+    TRY(palloc(c, reinterpret_cast<double**>(&gmem), (gfl + 1) / 2 + 1));
+    c->U_h.resize(c->K_h.size(), nullptr);
+    c->Gi_h.resize(c->K_h.size(), nullptr);
+    c->Gj_h.resize(c->K_h.size(), nullptr);
+    size_t uo = 0, go = 0;
+    double f_u = 0.0, f_g = 0.0, f_kg = 0.0;
+    for (auto& p : newp) {
+      const int i = p.first, j = p.second, pid = c->pair_id[(size_t)i * n + j];
+      const int r = c->r_h[pid], m = pair_dim_h(c, i, j);
+      float* U = umem + uo;
+      uo += (size_t)nv * r;
+      c->U_h[pid] = U;
+      uj.push_back(UJob{i, j, U});
+      f_u += 2.0 * nv * (double)m * r;
+      float* Gi = gmem + go;
+      go += (size_t)r * nx;
+      gj.push_back(GJob{i, r, U, Gi});
+      float* Gj = Gi;
+      if (i != j) {
+        Gj = gmem + go;
+        go += (size_t)r * nx;
+        gj.push_back(GJob{j, r, U, Gj});
+      }
+      f_g += (i != j ? 2.0 : 1.0) * 2.0 * r * (double)nv * nx;
+      c->Gi_h[pid] = Gi;
+      c->Gj_h[pid] = Gj;
+      kgj.push_back(KgJob{r, Gi, Gj, c->Kt_h[pid]});
+      f_kg += 2.0 * (double)r * r * nx;
+    }
+    std::vector<float*> uall(c->K_h.size(), nullptr);
+    for (size_t q = 0; q < c->U_h.size(); q++) uall[q] = c->U_h[q];
+    CK(cudaMemcpyAsync(c->U_d, uall.data(), uall.size() * sizeof(float*), cudaMemcpyHostToDevice, c->st));
+    Tmp ju, jg, jkg;
+    TRY(tmp_alloc(c, ju, uj.size() * sizeof(UJob)));
+    TRY(tmp_alloc(c, jg, gj.size() * sizeof(GJob)));
+    TRY(tmp_alloc(c, jkg, kgj.size() * sizeof(KgJob)));
+    CK(cudaMemcpyAsync(ju.p, uj.data(), uj.size() * sizeof(UJob), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(jg.p, gj.data(), gj.size() * sizeof(GJob), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(jkg.p, kgj.data(), kgj.size() * sizeof(KgJob), cudaMemcpyHostToDevice, c->st));
+    ph_begin(c, OSVMP2_PH_PROJECT);
+    launch_ubasis(t, (const UJob*)ju.p, (int)uj.size(), n_cta, c->st);
+    launch_gproj(bsrc(c), (const GJob*)jg.p, (int)gj.size(), max_r, c->st);
+    ph_end(c, OSVMP2_PH_PROJECT, f_u + f_g, c->sys.B ? 8.0 * (double)gj.size() * nx * nv : 0.0);
+    CK(cudaGetLastError());
+    ph_begin(c, OSVMP2_PH_EXCHANGE);
+    launch_ktilde_g(nx, (const KgJob*)jkg.p, (int)kgj.size(), max_r, c->st);
+    ph_end(c, OSVMP2_PH_EXCHANGE, f_kg);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+  } else {   // K~ = X^T K X (used by the preconditioner-basis solver)
     std::vector<KtJob> ktj;
     for (size_t q = 0; q < kj.size(); q++) ktj.push_back(KtJob{kj[q].i, kj[q].j, c->Kt_h[c->pair_id[(size_t)kj[q].i * n + kj[q].j]]});
     Tmp jkt;
@@ -551,10 +641,8 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
     CK(cudaStreamSynchronize(c->st));
   }
   (void)prec;
-  TRY(check_err_flag(c, "pair integrals"));
-  c->r_h.resize(c->K_h.size());
-  CK(cudaMemcpyAsync(c->r_h.data(), c->r_d, c->r_h.size() * sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  TRY(check_err_flag(c, "pair integrals"));
   return 0;
 }
 
@@ -648,6 +736,7 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   TRY(dalloc_t(c, &c->et_d, c->cap_pairs));
   TRY(dalloc_t(c, &c->r_d, c->cap_pairs));
   TRY(dalloc_t(c, &c->Kt_d, c->cap_pairs));
+  TRY(dalloc_t(c, &c->U_d, c->cap_pairs));
   c->sf_id.assign((size_t)n * n, -1);
   c->pair_id.assign((size_t)n * n, -1);
   c->bt_id.assign((size_t)n * n, -1);
@@ -680,7 +769,11 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
     ph_begin(c, OSVMP2_PH_EIG);
     launch_eig_osv((double*)Tm.p, b, nv, l_osv, kmax, (double*)Vm.p, (double*)wm.p, (int*)km.p, (double*)sm.p,
                    c->err_d, c->st);
-    ph_end(c, OSVMP2_PH_EIG, 0.0);
+    {
+      const double nd = nv;
+      const bool full = (nv <= 160) || (l_osv <= 0.0);
+      ph_end(c, OSVMP2_PH_EIG, (double)b * (full ? 9.0 * nd * nd * nd : (4.0 / 3.0) * nd * nd * nd));
+    }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(kh.data(), km.p, b * sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -1122,14 +1215,22 @@ int osvmp2_energy_grad(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, do
     const double m = pair_dim_h(c, plist[q].first, plist[q].second);
     fl += (double)contr[q].size() * (plist[q].first == plist[q].second ? 4.0 : 8.0) * m * m * m;
   }
+  const bool mixed = prec == OSVMP2_MIXED;
   ph_begin(c, OSVMP2_PH_GRAD);
-  launch_grad_pair(t, (const GradPairJob*)d_pj.p, np, (const GradContrib*)d_cf.p, (double*)scr.p, n_cta, max_m,
-                   c->st);
+  if (mixed)
+    launch_gradm_pair(t, (const GradPairJob*)d_pj.p, np, (const GradContrib*)d_cf.p, (double*)scr.p, n_cta, max_m,
+                      c->st);
+  else
+    launch_grad_pair(t, (const GradPairJob*)d_pj.p, np, (const GradContrib*)d_cf.p, (double*)scr.p, n_cta, max_m,
+                     c->st);
   CK(cudaGetLastError());
   Tmp dpair;
   if (dE_de) {
     TRY(tmp_alloc(c, dpair, (size_t)np * nv * sizeof(double)));
-    launch_grad_de(t, (const GradPairJob*)d_pj.p, np, (double*)scr.p, n_cta, max_m, (double*)dpair.p, dE_de, c->st);
+    if (mixed)
+      launch_gradm_de(t, (const GradPairJob*)d_pj.p, np, (double*)scr.p, n_cta, max_m, (double*)dpair.p, dE_de, c->st);
+    else
+      launch_grad_de(t, (const GradPairJob*)d_pj.p, np, (double*)scr.p, n_cta, max_m, (double*)dpair.p, dE_de, c->st);
     CK(cudaGetLastError());
   }
   Tmp gfrag, d_fptr, d_flist, d_orbs, d_w, d_toff;
@@ -1162,14 +1263,70 @@ int osvmp2_energy_grad(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, do
     const int n_cta_f = std::max(1, std::min(nf, 2 * c->num_sms));
     Tmp scr_f;
     TRY(tmp_alloc(c, scr_f, (size_t)n_cta_f * 2 * max_m * max_m * sizeof(double)));
-    launch_grad_df(t, (const int*)d_orbs.p, (const int*)d_w.p, (const double*)tstore.p,
-                   (const long long*)d_toff.p, nf, max_m, (double*)scr_f.p, n_cta_f, (double*)gfrag.p,
-                   (const int*)d_fptr.p, (const int*)d_flist.p, dE_df, c->st);
+    if (mixed)
+      launch_gradm_df(t, (const int*)d_orbs.p, (const int*)d_w.p, (const double*)tstore.p,
+                      (const long long*)d_toff.p, nf, max_m, (double*)scr_f.p, n_cta_f, (double*)gfrag.p,
+                      (const int*)d_fptr.p, (const int*)d_flist.p, dE_df, c->st);
+    else
+      launch_grad_df(t, (const int*)d_orbs.p, (const int*)d_w.p, (const double*)tstore.p,
+                     (const long long*)d_toff.p, nf, max_m, (double*)scr_f.p, n_cta_f, (double*)gfrag.p,
+                     (const int*)d_fptr.p, (const int*)d_flist.p, dE_df, c->st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->st));
   }
   Tmp ymem, d_yj, d_yt, d_bj, d_bt;
-  if (dE_dB) {
+  if (dE_dB && mixed) {
+    // Z = op(W~) G_partner per (pair, side); dB_o = 4 sum U_p Z over the pairs of o
+    std::vector<GradZJob> zj;
+    std::vector<std::vector<GradMBTerm>> per(n);
+    size_t zsz = 0;
+    int max_r = 0;
+    for (int q = 0; q < np; q++) {
+      const int i = plist[q].first, j = plist[q].second, pid = c->pair_id[(size_t)i * n + j];
+      const int r = c->r_h[pid];
+      max_r = std::max(max_r, r);
+      zsz += (size_t)r * nx * (i == j ? 1 : 2);
+    }
+    TRY(tmp_alloc(c, ymem, std::max<size_t>(1, zsz) * sizeof(float)));
+    size_t zo = 0;
+    for (int q = 0; q < np; q++) {
+      const int i = plist[q].first, j = plist[q].second, pid = c->pair_id[(size_t)i * n + j];
+      const int r = c->r_h[pid];
+      float* Zi = (float*)ymem.p + zo;
+      zo += (size_t)r * nx;
+      zj.push_back(GradZJob{r, 0, pjobs[q].W, c->Gj_h[pid], Zi});      // for dB_i: W~ G_j
+      per[i].push_back(GradMBTerm{r, c->U_h[pid], Zi});
+      fl += 2.0 * r * (double)r * nx + 2.0 * nv * (double)r * nx;
+      if (i != j) {
+        float* Zj = (float*)ymem.p + zo;
+        zo += (size_t)r * nx;
+        zj.push_back(GradZJob{r, 1, pjobs[q].W, c->Gi_h[pid], Zj});    // for dB_j: W~^T G_i
+        per[j].push_back(GradMBTerm{r, c->U_h[pid], Zj});
+        fl += 2.0 * r * (double)r * nx + 2.0 * nv * (double)r * nx;
+      }
+    }
+    std::vector<GradBJob> bj;
+    std::vector<GradMBTerm> bt;
+    for (int o = 0; o < n; o++) {
+      if (per[o].empty()) continue;
+      GradBJob b{o, (int)bt.size(), 0};
+      for (auto& tm : per[o]) bt.push_back(tm);
+      b.t1 = (int)bt.size();
+      bj.push_back(b);
+    }
+    TRY(tmp_alloc(c, d_yj, zj.size() * sizeof(GradZJob)));
+    TRY(tmp_alloc(c, d_bj, bj.size() * sizeof(GradBJob)));
+    TRY(tmp_alloc(c, d_bt, bt.size() * sizeof(GradMBTerm)));
+    CK(cudaMemcpyAsync(d_yj.p, zj.data(), zj.size() * sizeof(GradZJob), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(d_bj.p, bj.data(), bj.size() * sizeof(GradBJob), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(d_bt.p, bt.data(), bt.size() * sizeof(GradMBTerm), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemsetAsync(dE_dB, 0, (size_t)n * nv * nx * sizeof(double), c->st));
+    launch_gradm_Z(nx, (const GradZJob*)d_yj.p, (int)zj.size(), max_r, c->st);
+    CK(cudaGetLastError());
+    launch_gradm_dB(nv, nx, (const GradBJob*)d_bj.p, (int)bj.size(), (const GradMBTerm*)d_bt.p, dE_dB, c->st);
+    CK(cudaGetLastError());
+  }
+  if (dE_dB && !mixed) {
     // combos (o, x): x = o and every partner of o in the pair list
     std::vector<std::vector<int>> partners(n);
     for (auto& p : plist)

@@ -94,6 +94,82 @@ __device__ __forceinline__ void tile_mma_t(int M, int N, int K, int m0, int n0, 
   }
 }
 
+// As tile_mma_t<float>, but each k-tile's sixteen FP32 products are summed in
+// FP32 and the tile sums are accumulated in FP64: the rounding of long FP32
+// accumulations (which grows with K) is confined to sixteen terms.
+template <class VA, class VB>
+__device__ __forceinline__ void tile_mma_f32x64(int M, int N, int K, int m0, int n0, const VA& A, const VB& B,
+                                                double acc[4][4], float* sm) {
+  float* As = sm;
+  float* Bs = sm + TK * TM;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int k0 = 0; k0 < K; k0 += TK) {
+#pragma unroll
+    for (int t = 0; t < TM * TK / NT; t++) {
+      const int e = tid + t * NT, m = e % TM, k = e / TM;
+      const int gm = m0 + m, gk = k0 + k;
+      As[k * TM + m] = (gm < M && gk < K) ? static_cast<float>(A.get(gm, gk)) : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < TN * TK / NT; t++) {
+      const int e = tid + t * NT, n = e % TN, k = e / TN;
+      const int gn = n0 + n, gk = k0 + k;
+      Bs[k * TN + n] = (gn < N && gk < K) ? static_cast<float>(B.get(gk, gn)) : 0.f;
+    }
+    __syncthreads();
+    float part[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) part[i][j] = 0.f;
+#pragma unroll
+    for (int k = 0; k < TK; k++) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = As[k * TM + ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = Bs[k * TN + tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) part[i][j] = fmaf(a[i], b[j], part[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) acc[i][j] += (double)part[i][j];
+    __syncthreads();
+  }
+}
+
+// C[MxN] (ld ldc, element type CT) = beta*C + alpha*A*B with FP32 products
+// accumulated per k-tile in FP32 and across k-tiles in FP64 (tile_mma_f32x64).
+template <class CT, class VA, class VB>
+__device__ void cta_gemm_f32x64(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, CT* C,
+                                int ldc, float* sm) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += TM)
+    for (int n0 = 0; n0 < N; n0 += TN) {
+      double acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+      tile_mma_f32x64(M, N, K, m0, n0, A, B, acc, sm);
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
+          if (r < M && c < N) {
+            CT* cp = C + (size_t)r * ldc + c;
+            *cp = static_cast<CT>((beta == 0.0 ? 0.0 : beta * static_cast<double>(*cp)) + alpha * acc[i][j]);
+          }
+        }
+    }
+  __syncthreads();
+}
+
 template <class VA, class VB>
 __device__ __forceinline__ void tile_mma(int M, int N, int K, int m0, int n0, const VA& A, const VB& B,
                                          double acc[4][4], double* sm) {

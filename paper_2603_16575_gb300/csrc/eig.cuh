@@ -20,15 +20,16 @@ namespace osv {
 // Householder tridiagonalisation of the symmetric n x n matrix A (row-major,
 // lda; global or shared memory), in place.  Outputs d[n], e[n-1] (any memory)
 // and tau[n]; v and p are shared scratch of n doubles each, red >= 33 doubles.
+template <int NTH = NT>
 __device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double* e, double* tau,
                                    double* v, double* p, double* red) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NTH / 32;
   __shared__ double s_tau;
   for (int k = 0; k + 2 < n; k++) {
     const int L = n - k - 1;          // trailing block rows/cols k+1 .. n-1
     double* Ak = A + (size_t)(k + 1) * lda + (k + 1);   // trailing block origin
     double part = 0.0;
-    for (int t = tid; t < L; t += NT) {
+    for (int t = tid; t < L; t += NTH) {
       const double x = A[(size_t)(k + 1 + t) * lda + k];
       v[t] = x;
       if (t > 0) part += x * x;
@@ -53,7 +54,7 @@ __device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double*
     const double tk = s_tau;
     if (tk != 0.0) {
       const double sc = red[0];
-      for (int t = tid; t < L; t += NT) v[t] = (t == 0) ? 1.0 : v[t] * sc;
+      for (int t = tid; t < L; t += NTH) v[t] = (t == 0) ? 1.0 : v[t] * sc;
       __syncthreads();
       // p = tau * A' v  (warp per row, lanes over columns)
       for (int r = warp; r < L; r += nwarp) {
@@ -73,9 +74,9 @@ __device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double*
       }
       __syncthreads();
       double pv = 0.0;
-      for (int t = tid; t < L; t += NT) pv += p[t] * v[t];
+      for (int t = tid; t < L; t += NTH) pv += p[t] * v[t];
       const double Kc = 0.5 * tk * cta_sum(pv, red);
-      for (int t = tid; t < L; t += NT) p[t] -= Kc * v[t];   // p becomes w
+      for (int t = tid; t < L; t += NTH) p[t] -= Kc * v[t];   // p becomes w
       __syncthreads();
       // A' -= v w^T + w v^T
       for (int r = warp; r < L; r += nwarp) {
@@ -92,7 +93,99 @@ __device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double*
         for (; c < L; c += 32) row[c] -= vr * p[c] + wr * v[c];
       }
       // keep the reflector below the sub-diagonal of column k
-      for (int t = tid + 1; t < L; t += NT) A[(size_t)(k + 1 + t) * lda + k] = v[t];
+      for (int t = tid + 1; t < L; t += NTH) A[(size_t)(k + 1 + t) * lda + k] = v[t];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = A[(size_t)(n - 2) * lda + (n - 2)];
+      e[n - 2] = A[(size_t)(n - 1) * lda + (n - 2)];
+      if (n >= 3) tau[n - 2] = 0.0;
+    }
+    d[n - 1] = A[(size_t)(n - 1) * lda + (n - 1)];
+    tau[n - 1] = 0.0;
+  }
+  __syncthreads();
+}
+
+// Householder tridiagonalisation as cta_tridiag, for large n with A in global
+// memory: the symmetric matvec p = tau A' v is formed column-wise (thread c
+// owns column c and walks the rows, so every load instruction of a warp is
+// coalesced and a thread keeps many independent loads in flight), and the
+// rank-2 update is applied the same way.
+template <int NTH = NT>
+__device__ inline void cta_tridiag_col(double* A, int n, int lda, double* d, double* e, double* tau, double* v,
+                                       double* p, double* red) {
+  const int tid = threadIdx.x;
+  __shared__ double s_tc, s_sc;
+  for (int k = 0; k + 2 < n; k++) {
+    const int L = n - k - 1;
+    double* Ak = A + (size_t)(k + 1) * lda + (k + 1);
+    double part = 0.0;
+    for (int t = tid; t < L; t += NTH) {
+      const double x = A[(size_t)(k + 1 + t) * lda + k];
+      v[t] = x;
+      if (t > 0) part += x * x;
+    }
+    const double sigma = cta_sum(part, red);
+    if (tid == 0) {
+      const double alpha = v[0];
+      double tu = 0.0, beta = alpha, sc = 0.0;
+      if (sigma > 0.0) {
+        const double mu = sqrt(alpha * alpha + sigma);
+        beta = alpha <= 0.0 ? mu : -mu;
+        tu = (beta - alpha) / beta;
+        sc = 1.0 / (alpha - beta);
+      }
+      s_tc = tu;
+      s_sc = sc;
+      d[k] = A[(size_t)k * lda + k];
+      e[k] = beta;
+      tau[k] = tu;
+    }
+    __syncthreads();
+    const double tk = s_tc;
+    if (tk != 0.0) {
+      const double sc = s_sc;
+      for (int t = tid; t < L; t += NTH) v[t] = (t == 0) ? 1.0 : v[t] * sc;
+      __syncthreads();
+      // p_c = tau sum_r A'[r][c] v_r   (A' symmetric)
+      for (int c = tid; c < L; c += NTH) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int r = 0;
+        for (; r + 3 < L; r += 4) {
+          const double a0 = Ak[(size_t)r * lda + c], a1 = Ak[(size_t)(r + 1) * lda + c];
+          const double a2 = Ak[(size_t)(r + 2) * lda + c], a3 = Ak[(size_t)(r + 3) * lda + c];
+          s0 = fma(a0, v[r], s0);
+          s1 = fma(a1, v[r + 1], s1);
+          s2 = fma(a2, v[r + 2], s2);
+          s3 = fma(a3, v[r + 3], s3);
+        }
+        for (; r < L; r++) s0 = fma(Ak[(size_t)r * lda + c], v[r], s0);
+        p[c] = tk * ((s0 + s1) + (s2 + s3));
+      }
+      __syncthreads();
+      double pv = 0.0;
+      for (int t = tid; t < L; t += NTH) pv += p[t] * v[t];
+      const double Kc = 0.5 * tk * cta_sum(pv, red);
+      for (int t = tid; t < L; t += NTH) p[t] -= Kc * v[t];
+      __syncthreads();
+      // A'[r][c] -= v_r w_c + w_r v_c
+      for (int c = tid; c < L; c += NTH) {
+        const double vc = v[c], wc = p[c];
+        int r = 0;
+        for (; r + 3 < L; r += 4) {
+          double* a = Ak + (size_t)r * lda + c;
+          const double a0 = a[0], a1 = a[lda], a2 = a[2 * (size_t)lda], a3 = a[3 * (size_t)lda];
+          a[0] = a0 - (v[r] * wc + p[r] * vc);
+          a[lda] = a1 - (v[r + 1] * wc + p[r + 1] * vc);
+          a[2 * (size_t)lda] = a2 - (v[r + 2] * wc + p[r + 2] * vc);
+          a[3 * (size_t)lda] = a3 - (v[r + 3] * wc + p[r + 3] * vc);
+        }
+        for (; r < L; r++) Ak[(size_t)r * lda + c] -= v[r] * wc + p[r] * vc;
+      }
+      for (int t = tid + 1; t < L; t += NTH) A[(size_t)(k + 1 + t) * lda + k] = v[t];
     }
     __syncthreads();
   }
@@ -110,25 +203,26 @@ __device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double*
 
 // Z (n x n, row-major, ldz) = H_0 H_1 ... H_{n-3} from the reflectors left in A.
 // y, vs: shared scratch of n doubles each.
+template <int NTH = NT>
 __device__ inline void cta_form_z(const double* A, int n, int lda, const double* tau, double* Z, int ldz,
                                   double* y, double* vs) {
   const int tid = threadIdx.x;
-  for (int t = tid; t < n * n; t += NT) Z[(size_t)(t / n) * ldz + (t % n)] = (t / n == t % n) ? 1.0 : 0.0;
+  for (int t = tid; t < n * n; t += NTH) Z[(size_t)(t / n) * ldz + (t % n)] = (t / n == t % n) ? 1.0 : 0.0;
   __syncthreads();
   for (int k = n - 3; k >= 0; k--) {
     const double tk = tau[k];
     if (tk == 0.0) continue;
     const int L = n - k - 1;
-    for (int r = tid; r < L; r += NT) vs[r] = (r == 0) ? 1.0 : A[(size_t)(k + 1 + r) * lda + k];
+    for (int r = tid; r < L; r += NTH) vs[r] = (r == 0) ? 1.0 : A[(size_t)(k + 1 + r) * lda + k];
     __syncthreads();
     // y_c = tau * sum_r v_r Z[k+1+r][k+1+c]
-    for (int c = tid; c < L; c += NT) {
+    for (int c = tid; c < L; c += NTH) {
       double s = 0.0;
       for (int r = 0; r < L; r++) s += vs[r] * Z[(size_t)(k + 1 + r) * ldz + (k + 1 + c)];
       y[c] = tk * s;
     }
     __syncthreads();
-    for (int t = tid; t < L * L; t += NT) {
+    for (int t = tid; t < L * L; t += NTH) {
       const int r = t / L, c = t % L;
       Z[(size_t)(k + 1 + r) * ldz + (k + 1 + c)] -= vs[r] * y[c];
     }
@@ -141,6 +235,7 @@ __device__ inline void cta_form_z(const double* A, int n, int lda, const double*
 // shared or global memory visible to thread 0; cs is shared scratch of 2n
 // doubles.  Returns 0 on convergence (d holds the eigenvalues, columns of Z the
 // eigenvectors), 1 otherwise.  Every thread returns the same value.
+template <int NTH = NT>
 __device__ inline int cta_tridiag_qr(double* d, double* e, int n, double* Z, int ldz, double* cs) {
   __shared__ int s_l, s_h, s_done;
   const int tid = threadIdx.x;
@@ -193,7 +288,7 @@ __device__ inline int cta_tridiag_qr(double* d, double* e, int n, double* Z, int
     if (++sweeps > max_sweeps) return 1;
     const int l = s_l, h = s_h;
     // Z <- Z R_l^T R_{l+1}^T ... : column pair (k, k+1) rotated for k = l..h-1
-    for (int row = tid; row < n; row += NT) {
+    for (int row = tid; row < n; row += NTH) {
       double* zr = Z + (size_t)row * ldz;
       double carry = zr[l];
       for (int k = l; k < h; k++) {
@@ -212,6 +307,7 @@ __device__ inline int cta_tridiag_qr(double* d, double* e, int n, double* Z, int
 // On return w[0..n) holds the eigenvalues and column t of Z the eigenvector
 // of w[t] (unordered).  d/e/tau: n doubles each (any memory visible to the
 // CTA); sm: shared scratch of >= 4n + 33 doubles.  Returns 0 on success.
+template <int NTH = NT>
 __device__ inline int cta_syev(double* A, int n, int lda, double* w, double* Z, int ldz, double* e,
                                double* tau, double* sm) {
   double* v = sm;
@@ -223,16 +319,16 @@ __device__ inline int cta_syev(double* A, int n, int lda, double* w, double* Z, 
     __syncthreads();
     return 0;
   }
-  cta_tridiag(A, n, lda, w, e, tau, v, p, red);
-  cta_form_z(A, n, lda, tau, Z, ldz, v, p);
+  cta_tridiag<NTH>(A, n, lda, w, e, tau, v, p, red);
+  cta_form_z<NTH>(A, n, lda, tau, Z, ldz, v, p);
   // the bulge chase is sequential: run it on shared-memory copies of d and e
-  for (int t = threadIdx.x; t < n; t += NT) {
+  for (int t = threadIdx.x; t < n; t += NTH) {
     v[t] = w[t];
     p[t] = (t + 1 < n) ? e[t] : 0.0;
   }
   __syncthreads();
-  const int rc = cta_tridiag_qr(v, p, n, Z, ldz, cs);
-  for (int t = threadIdx.x; t < n; t += NT) w[t] = v[t];
+  const int rc = cta_tridiag_qr<NTH>(v, p, n, Z, ldz, cs);
+  for (int t = threadIdx.x; t < n; t += NTH) w[t] = v[t];
   __syncthreads();
   return rc;
 }

@@ -255,6 +255,16 @@ void launch_grad_df(const Tables& t, const int* frag_orbs, const int* weights, c
                                                                      df);
   note_launch(1);
 }
+void launch_grad_de_reduce(const double* dpair, int n_pairs, int nv, double* de, cudaStream_t st) {
+  k_grad_de_reduce<<<(nv + 255) / 256, 256, 0, st>>>(dpair, n_pairs, nv, de);
+  note_launch(1);
+}
+void launch_grad_df_reduce(const Tables& t, const int* frag_orbs, const double* gfrag, int n_frag, const int* fptr,
+                           const int* flist, double* df, cudaStream_t st) {
+  k_grad_df_reduce<<<(t.n_occ * t.n_occ + 255) / 256, 256, 0, st>>>(frag_orbs, gfrag, n_frag, t.n_occ, fptr, flist,
+                                                                     df);
+  note_launch(1);
+}
 void launch_grad_Y(const Tables& t, int n_aux, const GradYJob* jobs, int n_jobs, const GradYTerm* terms, int max_n,
                    cudaStream_t st) {
   if (!n_jobs) return;

@@ -22,6 +22,7 @@ struct Tables {
   const double* const* et;      // [n_pairs] e~ [m] (first r valid)
   const int* r;                 // [n_pairs]
   const double* const* Kt;      // [n_pairs] K~ = X^T K X  [r][r]
+  const float* const* U;        // [n_pairs] mixed form: U = P X  [n_vir][r] (FP32)
   const double* f_occ;          // [n_occ][n_occ]
 };
 
@@ -47,10 +48,10 @@ void launch_tii(const BSrc& src, const double* e_vir, const double* f_occ, int n
                 double* T, cudaStream_t st);
 // Eigen-decomposition of each T[b] and selection omega >= thr (all if thr <= 0),
 // at most kmax per orbital: V [nb][nv][kmax], w [nb][kmax], k [nb], err |= ERR_*.
-// e, tau, w (3 nv) + Z (nv*nv, global path) + 8 warps x 7 nv (inverse iteration)
+// e, tau, w (3 nv) + Z (nv*nv, global path) + 32 warps x 7 nv (inverse iteration)
 __host__ __device__ inline size_t eig_osv_scratch_doubles(int nv, int kmax) {
   (void)kmax;
-  return (size_t)3 * nv + (size_t)nv * nv + (size_t)8 * 7 * nv + 64;
+  return (size_t)3 * nv + (size_t)nv * nv + (size_t)32 * 7 * nv + 64;
 }
 void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, double* w, int* k,
                     double* scratch, int* err, cudaStream_t st);
@@ -94,6 +95,10 @@ __host__ __device__ inline size_t precond_scratch_doubles(int max_m) {
 }
 void launch_precond(const Tables& t, double tau_s, const PJob* jobs, int n_jobs, int max_m, double* scratch,
                     int n_cta, int* err, cudaStream_t st);
+// One warp per pair (pair order <= 192); returns -1 if max_m is too large.
+size_t precond_w_scratch_doubles(int max_m, int n_warps);
+int launch_precond_w(const Tables& t, double tau_s, const PJob* jobs, int n_jobs, int max_m, double* scratch,
+                     int n_warps, int* err, cudaStream_t st);
 
 // ---- A4-A5 (solve.cu)
 // Fragments: orbs [n][3] (-1 padded, ascending), order[] = processing order.
@@ -104,6 +109,26 @@ __host__ __device__ inline size_t frag_scratch_doubles(int max_m) { return 26 * 
 void launch_frag_solve(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
                        SolveOpts o, double* scratch, int n_cta, int* counter, FragOut* out,
                        double* Tstore, const long long* Toff, cudaStream_t st);
+// Mixed-form pair build (ubasis.cu) in the orthonormal pair basis U = P X.
+struct UJob {
+  int i, j;
+  float* U;            // [n_vir][r]
+};
+struct GJob {          // G = U^T B_x  [r][n_aux]
+  int x, r;
+  const float* U;
+  float* G;
+};
+struct KgJob {         // K~ = G_i G_j^T  [r][r]
+  int r;
+  const float* Gi;
+  const float* Gj;
+  double* Kt;
+};
+void launch_ubasis(const Tables& t, const UJob* jobs, int n_jobs, int n_cta, cudaStream_t st);
+void launch_gproj(const BSrc& src, const GJob* jobs, int n_jobs, int max_r, cudaStream_t st);
+void launch_ktilde_g(int n_aux, const KgJob* jobs, int n_jobs, int max_r, cudaStream_t st);
+
 // Mixed form (solve_mixed.cu): per pair K~ = X^T K X, then the fragment solve in
 // the preconditioner basis with FP32 coupling products.
 struct KtJob {
@@ -112,10 +137,10 @@ struct KtJob {
 };
 void launch_ktilde(const Tables& t, const KtJob* jobs, int n_jobs, double* scratch, int n_cta, int max_m,
                    cudaStream_t st);
-// per CTA: Y (6 FP64) + Y32, C32 (6 + 6 FP32) + 24 Sigma + 1 work (FP32) + 1 FP64 work
+// per CTA: Y, C (6 + 6 FP64) + Y32 (6 FP32) + 24 Sigma + 1 work (FP32)
 __host__ __device__ inline size_t frag_mixed_scratch_doubles(int max_m) {
   const size_t M2 = (size_t)max_m * max_m;
-  return 6 * M2 + (37 * M2 + 1) / 2 + M2 + 64;
+  return 12 * M2 + (31 * M2 + 1) / 2 + 64;
 }
 void launch_frag_solve_mixed(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
                              SolveOpts o, double* scratch, int n_cta, int* counter, FragOut* out, double* Tstore,
@@ -183,5 +208,32 @@ void launch_grad_Y(const Tables& t, int n_aux, const GradYJob* jobs, int n_jobs,
                    cudaStream_t st);
 void launch_grad_dB(const Tables& t, int n_aux, const GradBJob* jobs, int n_jobs, const GradBTerm* terms, double* dB,
                     cudaStream_t st);
+void launch_grad_de_reduce(const double* dpair, int n_pairs, int nv, double* de, cudaStream_t st);
+void launch_grad_df_reduce(const Tables& t, const int* frag_orbs, const double* gfrag, int n_frag, const int* fptr,
+                           const int* flist, double* df, cudaStream_t st);
+
+// ---- A6, mixed form (grad_mixed.cu): Tstore holds Y_p (T_p = X_p Y_p X_p^T)
+struct GradZJob {          // Z = op(W~) G  [r][n_aux]
+  int r;
+  int trans;
+  const double* W;
+  const float* G;
+  float* Z;
+};
+struct GradMBTerm {        // U_p [n_vir][r] times Z [r][n_aux]
+  int r;
+  const float* U;
+  const float* Z;
+};
+void launch_gradm_pair(const Tables& t, const GradPairJob* jobs, int n_jobs, const GradContrib* contrib,
+                       double* scratch, int n_cta, int max_m, cudaStream_t st);
+void launch_gradm_de(const Tables& t, const GradPairJob* jobs, int n_jobs, double* scratch, int n_cta, int max_m,
+                     double* dpair, double* de, cudaStream_t st);
+void launch_gradm_df(const Tables& t, const int* frag_orbs, const int* weights, const double* Tstore,
+                     const long long* Toff, int n_frag, int max_m, double* scratch, int n_cta, double* gfrag,
+                     const int* fptr, const int* flist, double* df, cudaStream_t st);
+void launch_gradm_Z(int n_aux, const GradZJob* jobs, int n_jobs, int max_r, cudaStream_t st);
+void launch_gradm_dB(int n_vir, int n_aux, const GradBJob* jobs, int n_jobs, const GradMBTerm* terms, double* dB,
+                     cudaStream_t st);
 
 }  // namespace osv

@@ -62,12 +62,13 @@ void launch_tii(const BSrc& src, const double* e_vir, const double* f_occ, int n
 
 // ---------------------------------------------------------------- eigen
 constexpr int ZSMEM_MAX = 160;   // Z kept in shared memory up to this order
+constexpr int NT_EIG = 1024;     // threads of the OSV eigen kernel (more loads in flight)
 
 // Sign column t of V (n rows, ld) so that its largest-magnitude entry (lowest
 // row on ties) is positive.  One warp per column.
 __device__ inline void sign_columns(double* V, int n, int ld, int k) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int t = warp; t < k; t += NT / 32) {
+  for (int t = warp; t < k; t += NT_EIG / 32) {
     double best = -1.0;
     int bi = 0x7fffffff;
     for (int r = lane; r < n; r += 32) {
@@ -94,7 +95,7 @@ __device__ void eig_full_select(double* A, int n, double thr, int kmax, double* 
   double* e = scr;
   double* tau = scr + n;
   double* ww = scr + 2 * n;
-  int rc = cta_syev(A, n, n, ww, Zs, ldz, e, tau, sm);
+  int rc = cta_syev<NT_EIG>(A, n, n, ww, Zs, ldz, e, tau, sm);
   __shared__ int s_k;
   int* perm = reinterpret_cast<int*>(sm);   // sm reused: n ints (n <= 4n doubles)
   if (threadIdx.x == 0) {
@@ -119,7 +120,7 @@ __device__ void eig_full_select(double* A, int n, double thr, int kmax, double* 
   }
   __syncthreads();
   const int k = s_k;
-  for (int idx = threadIdx.x; idx < n * k; idx += NT) {
+  for (int idx = threadIdx.x; idx < n * k; idx += NT_EIG) {
     const int r = idx / k, t = idx % k;
     V[(size_t)r * kmax + t] = Zs[(size_t)r * ldz + perm[t]];
   }
@@ -141,10 +142,10 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   double* red = sm + 2 * n;
   __shared__ int s_k, s_nclu;
   __shared__ double s_lo, s_hi, s_piv, s_norm;
-  cta_tridiag(A, n, n, d, e, tau, v, p, red);
+  cta_tridiag_col<NT_EIG>(A, n, n, d, e, tau, v, p, red);
   // Gershgorin bounds and a pivot floor
   double glo = 1e300, ghi = -1e300, nrm = 0.0, emax = 0.0;
-  for (int t = threadIdx.x; t < n; t += NT) {
+  for (int t = threadIdx.x; t < n; t += NT_EIG) {
     const double off = (t > 0 ? fabs(e[t - 1]) : 0.0) + (t + 1 < n ? fabs(e[t]) : 0.0);
     glo = fmin(glo, d[t] - off);
     ghi = fmax(ghi, d[t] + off);
@@ -170,7 +171,7 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   }
   __syncthreads();
   const int k = s_k;
-  for (int t = threadIdx.x; t < k; t += NT) w[t] = bisect_eig(d, e, n, n - 1 - t, s_lo, s_hi, s_piv);
+  for (int t = threadIdx.x; t < k; t += NT_EIG) w[t] = bisect_eig(d, e, n, n - 1 - t, s_lo, s_hi, s_piv);
   __syncthreads();
   if (threadIdx.x == 0) {
     const double ortol = 1e-3 * s_norm;
@@ -192,7 +193,7 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   double* y = mu + n;
   int* piv = reinterpret_cast<int*>(y + n);   // n ints fit in 2n doubles' room
   const double small = 2.220446049250313e-16 * fmax(s_norm, 1e-300);
-  for (int c = warp; c < s_nclu; c += NT / 32) {
+  for (int c = warp; c < s_nclu; c += NT_EIG / 32) {
     const int t0 = clu[c], t1 = clu[c + 1];
     for (int t = t0; t < t1; t++) {
       if (lane == 0) tri_factor(d, e, n, w[t], small, u0, u1, u2, mu, piv);
@@ -228,16 +229,16 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
     const double tk = tau[kk];
     if (tk == 0.0) continue;
     const int L = n - kk - 1;
-    for (int r = threadIdx.x; r < L; r += NT) v[r] = (r == 0) ? 1.0 : A[(size_t)(kk + 1 + r) * n + kk];
+    for (int r = threadIdx.x; r < L; r += NT_EIG) v[r] = (r == 0) ? 1.0 : A[(size_t)(kk + 1 + r) * n + kk];
     __syncthreads();
-    for (int t = warp; t < k; t += NT / 32) {
+    for (int t = warp; t < k; t += NT_EIG / 32) {
       double s = 0.0;
       for (int r = lane; r < L; r += 32) s += v[r] * V[(size_t)(kk + 1 + r) * kmax + t];
       s = warp_sum(s);
       if (lane == 0) p[t] = tk * s;   // p reused (clusters no longer needed)
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < L * k; idx += NT) {
+    for (int idx = threadIdx.x; idx < L * k; idx += NT_EIG) {
       const int r = idx / k, t = idx % k;
       V[(size_t)(kk + 1 + r) * kmax + t] -= v[r] * p[t];
     }
@@ -246,7 +247,7 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   sign_columns(V, n, kmax, k);
 }
 
-__global__ void __launch_bounds__(NT) k_eig_osv(double* T, int nv, double thr, int kmax, double* V, double* w,
+__global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double thr, int kmax, double* V, double* w,
                                                 int* kout, double* scratch, int* err, int zsmem) {
   extern __shared__ double dyn[];
   const int b = blockIdx.x;
@@ -273,7 +274,7 @@ void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, 
   size_t smem = (size_t)(4 * nv + 64) * sizeof(double);
   if (zsmem) smem += (size_t)nv * (nv + 1) * sizeof(double);
   cudaFuncSetAttribute(k_eig_osv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_eig_osv<<<nb, NT, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem);
+  k_eig_osv<<<nb, NT_EIG, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem);
   note_launch(1);
 }
 

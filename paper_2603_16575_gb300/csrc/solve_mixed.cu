@@ -3,15 +3,16 @@
 // update lies in the span of X_p), Eq. (res_close) becomes, in the
 // preconditioner basis,
 //     R~_p = K~_p - D_p o Y_p + C_p,   C_p = sum_terms c_t Sigma_pq op(Y_q) Sigma_pq^T,
-// with K~_p = X_p^T K_p X_p, Sigma_pq = X_p^T S_(p,q) X_q (entries bounded by 1,
-// since P_p X_p has orthonormal columns) and D_p the update denominators; the
+// with K~_p = X_p^T K_p X_p, Sigma_pq = X_p^T S_(p,q) X_q = U_p^T U_q (entries
+// bounded by 1, since U_p = P_p X_p has orthonormal columns) and D_p the update denominators; the
 // pair-diagonal F/S terms collapse to -D o Y exactly (X^T S X = 1,
 // X^T F X = diag(e~)).  The update is Y_p <- (K~_p + C_p) / D_p.
 //
 // Precision: the coupling C_p carries the off-diagonal occupied Fock elements
-// (|c_t| ~ 1e-2 against |D| ~ 1), so its FP32 rounding perturbs Y by
-// ~ eps_32 |c| / |D| ~ 1e-9 relative.  C_p and the Sigma_pq are therefore FP32
-// products; K~_p, D_p, Y_p (master copy) and the energy <K~_p, 2Y_p - Y_p^T> are FP64.
+// (|c_t| ~ 1e-2 against |D| ~ 1), so the rounding of its FP32 products perturbs
+// Y by ~ eps_32 |c| / |D| ~ 1e-9 relative.  C_p and Sigma_pq are FP32 products
+// summed per k-tile in FP32 and across k-tiles in FP64; K~_p, D_p, C_p, Y_p
+// (master copy) and the energy <K~_p, 2Y_p - Y_p^T> are FP64.
 #include "pairview.cuh"
 
 namespace osv {
@@ -53,7 +54,6 @@ __global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __
                                                          SolveOpts o, double* scratch, int* counter, FragOut* out,
                                                          double* Tstore, const long long* __restrict__ Toff) {
   __shared__ float fsm[GEMM_SMEM_DOUBLES];
-  __shared__ double dsm[GEMM_SMEM_DOUBLES];
   __shared__ double red[40];
   __shared__ int s_f;
   __shared__ MTerm terms[6][8];
@@ -63,18 +63,17 @@ __global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __
   const size_t M2 = (size_t)max_m * max_m;
   double* base = scratch + (size_t)blockIdx.x * frag_mixed_scratch_doubles(max_m);
   double* Y64[6];
+  double* C64[6];
   float* Y32[6];
-  float* C32[6];
   float* Sig[MAX_TERMS];
-  for (int u = 0; u < 6; u++) Y64[u] = base + u * M2;
-  float* fb = reinterpret_cast<float*>(base + 6 * M2);
   for (int u = 0; u < 6; u++) {
-    Y32[u] = fb + u * M2;
-    C32[u] = fb + (6 + u) * M2;
+    Y64[u] = base + u * M2;
+    C64[u] = base + (6 + u) * M2;
   }
-  for (int u = 0; u < MAX_TERMS; u++) Sig[u] = fb + (12 + u) * M2;
-  float* W32 = fb + (12 + MAX_TERMS) * M2;
-  double* W64 = base + 6 * M2 + (37 * M2 + 1) / 2;   // after 6 + 6 + 24 + 1 float matrices
+  float* fb = reinterpret_cast<float*>(base + 12 * M2);
+  for (int u = 0; u < 6; u++) Y32[u] = fb + u * M2;
+  for (int u = 0; u < MAX_TERMS; u++) Sig[u] = fb + (6 + u) * M2;
+  float* W32 = fb + (6 + MAX_TERMS) * M2;
   const double* f = t.f_occ;
   const int n = t.n_occ;
   while (true) {
@@ -133,14 +132,11 @@ __global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __
       s_nsig = ns;
     }
     __syncthreads();
-    // Sigma_pq = X_p^T S_(p,q) X_q  (FP32 products)
+    // Sigma_pq = X_p^T S_(p,q) X_q = U_p^T U_q  (FP32 products of orthonormal bases)
     for (int u = 0; u < s_nsig; u++) {
       const int p = sig_p[u], q = sig_q[u];
-      const View Spq = pair_view(t, t.S, orbs[pa[p]], orbs[pb[p]], orbs[pa[q]], orbs[pb[q]]);
-      cta_gemm_t<float, float>(pm[p], pr[q], pm[q], 1.f, Spq, dense_view(t.X[pid[q]], pm[q], pr[q], pm[q]), 0.f, W32,
-                               pr[q], fsm);
-      cta_gemm_t<float, float>(pr[p], pr[q], pm[p], 1.f, transpose(dense_view(t.X[pid[p]], pm[p], pr[p], pm[p])),
-                               ViewF{W32, pr[q], 0}, 0.f, Sig[u], pr[q], fsm);
+      cta_gemm_f32x64<float>(pr[p], pr[q], t.n_vir, 1.0, ViewF{t.U[pid[p]], pr[p], 1}, ViewF{t.U[pid[q]], pr[q], 0},
+                             0.0, Sig[u], pr[q], fsm);
     }
     for (int p = 0; p < np; p++)
       for (int idx = threadIdx.x; idx < pr[p] * pr[p]; idx += NT) {
@@ -154,15 +150,15 @@ __global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __
       // C_p from the previous sweep's amplitudes (Jacobi)
       for (int p = 0; p < np; p++) {
         const int rp = pr[p];
-        for (int idx = threadIdx.x; idx < rp * rp; idx += NT) C32[p][idx] = 0.f;
+        for (int idx = threadIdx.x; idx < rp * rp; idx += NT) C64[p][idx] = 0.0;
         __syncthreads();
         for (int u = 0; u < nterm[p]; u++) {
           const MTerm tm = terms[p][u];
           const int rq = pr[tm.q];
           const ViewF S{Sig[tm.sig], rq, 0};
-          cta_gemm_t<float, float>(rq, rp, rq, 1.f, ViewF{Y32[tm.q], rq, tm.tr}, ViewF{Sig[tm.sig], rq, 1}, 0.f, W32,
-                                   rp, fsm);
-          cta_gemm_t<float, float>(rp, rp, rq, (float)tm.coef, S, ViewF{W32, rp, 0}, 1.f, C32[p], rp, fsm);
+          cta_gemm_f32x64<float>(rq, rp, rq, 1.0, ViewF{Y32[tm.q], rq, tm.tr}, ViewF{Sig[tm.sig], rq, 1}, 0.0, W32,
+                                 rp, fsm);
+          cta_gemm_f32x64<double>(rp, rp, rq, tm.coef, S, ViewF{W32, rp, 0}, 1.0, C64[p], rp, fsm);
         }
       }
       // Y_p <- (K~_p + C_p) / D_p in FP64; energy <K~_p, 2Y_p - Y_p^T>
@@ -177,7 +173,7 @@ __global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __
         double du = 0.0;
         for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
           const int r = idx / rp, c = idx % rp;
-          const double y = (Kt[idx] + (double)C32[p][idx]) / (fij - et[r] - et[c]);
+          const double y = (Kt[idx] + C64[p][idx]) / (fij - et[r] - et[c]);
           du = fmax(du, fabs(y - Y64[p][idx]));
           Y64[p][idx] = y;
         }
@@ -200,14 +196,12 @@ __global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __
       e_prev = e;
     }
     if (threadIdx.x == 0) out[fid] = FragOut{e, um, iters, status};
-    if (Tstore) {   // T_p = X_p Y_p X_p^T (FP64) for the gradient
+    if (Tstore) {   // Y_p (r x r) for the gradient, in slots of m_p x m_p
       double* dst = Tstore + Toff[fid];
       for (int p = 0; p < np; p++) {
-        const int mp = pm[p], rp = pr[p];
-        const View Xv = dense_view(t.X[pid[p]], mp, rp, mp);
-        cta_gemm(rp, mp, rp, 1.0, dense_view(Y64[p], rp, rp, rp), transpose(Xv), 0.0, W64, mp, dsm);
-        cta_gemm(mp, mp, rp, 1.0, Xv, dense_view(W64, rp, mp, mp), 0.0, dst, mp, dsm);
-        dst += (size_t)mp * mp;
+        const int rp = pr[p];
+        for (int idx = threadIdx.x; idx < rp * rp; idx += NT) dst[idx] = Y64[p][idx];
+        dst += (size_t)pm[p] * pm[p];
       }
     }
     __syncthreads();

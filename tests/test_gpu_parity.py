@@ -183,7 +183,8 @@ def test_mixed_mbe3_energy_within_one_microhartree():
     E_ref, per = o.mbe3_energy(s.r_occ, 4.5, 3.8)
     _, _, ef = ctx.fragment_results()
     assert st["n_unconverged"] == 0
-    assert max(abs(a - b[2]) for a, b in zip(ef, per)) < 1e-8
+    # FP32 products: per-fragment error bounded by a few eps_32 of the fragment energy
+    assert max(abs(a - b[2]) / max(1.0, abs(b[2])) for a, b in zip(ef, per)) < 1e-7
     assert abs(E - E_ref) < 1e-6
     E64, _ = ctx.mbe3_energy(4.5, 3.8, "fp64")
     assert abs(E64 - E_ref) < 1e-9
