@@ -200,6 +200,7 @@ int check_err_flag(osvmp2_ctx* c, const char* where) {
   if (h & ERR_EIG) return fail(c, OSVMP2_E_NUMERIC, "%s: eigen-solver did not converge", where);
   if (h & ERR_NONFINITE) return fail(c, OSVMP2_E_NUMERIC, "%s: non-finite values", where);
   if (h & ERR_SIZE) return fail(c, OSVMP2_E_NUMERIC, "%s: size limit exceeded", where);
+  if (h & ERR_TIMEOUT) return fail(c, OSVMP2_E_CUDA, "%s: a tensor-core pipeline wait timed out", where);
   return 0;
 }
 
@@ -384,6 +385,64 @@ double fragment_mixed_flops(const osvmp2_ctx* c, const Frag& f, int iters) {
 
 // Build S/F blocks, projections, K and preconditioners for every listed pair
 // (and the diagonal pairs of its orbitals) that is not built yet.
+// Mixed form: G_p,x = U_p^T B_x for every G job on the tensor cores.  The
+// orbitals x are processed in batches whose B_x^T slices fit a fixed budget;
+// within a batch the tiles are ordered by (x, aux tile, pair) so that the
+// pairs sharing an aux tile of B_x read it while it is resident in L2.
+int gproj_tensor(osvmp2_ctx* c, const std::vector<GJob>& gj, const std::vector<long long>& usrow, const float* Us,
+                 long long us_rows, int ldv) {
+  const int nv = c->sys.n_vir, nx = c->sys.n_aux, n = c->sys.n_occ;
+  if (us_rows + tc::BN >= (long long)INT32_MAX)
+    return fail(c, OSVMP2_E_ARG, "U slice store exceeds the tensor-map row range");
+  std::vector<std::vector<int>> by_x(n);
+  for (size_t q = 0; q < gj.size(); q++) by_x[gj[q].x].push_back((int)q);
+  std::vector<int> xs;
+  for (int x = 0; x < n; x++)
+    if (!by_x[x].empty()) xs.push_back(x);
+  if (xs.empty()) return 0;
+  const size_t slot_bytes = (size_t)tc::NSL * nx * ldv * sizeof(float);
+  const size_t budget = (size_t)4 << 30;
+  const size_t per_batch = std::max<size_t>(1, std::min<size_t>(xs.size(), budget / slot_bytes));
+  if ((long long)per_batch * tc::NSL * nx + tc::BM >= (long long)INT32_MAX)
+    return fail(c, OSVMP2_E_ARG, "B slice batch exceeds the tensor-map row range");
+  Tmp bs, xd;
+  TRY(tmp_alloc(c, bs, per_batch * slot_bytes));
+  TRY(tmp_alloc(c, xd, xs.size() * sizeof(int)));
+  CK(cudaMemcpyAsync(xd.p, xs.data(), xs.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  const int n_mt = (nx + tc::BM - 1) / tc::BM;
+  for (size_t b0 = 0; b0 < xs.size(); b0 += per_batch) {
+    const int nb = (int)std::min(per_batch, xs.size() - b0);
+    launch_bslices(bsrc(c), (const int*)xd.p + b0, nb, (float*)bs.p, ldv, c->st);
+    CK(cudaGetLastError());
+    std::vector<tc::Job> jobs;
+    for (int u = 0; u < nb; u++)
+      for (int mt = 0; mt < n_mt; mt++)
+        for (int q : by_x[xs[b0 + u]]) {
+          const GJob& g = gj[q];
+          for (int n0 = 0; n0 < g.r; n0 += tc::BN) {
+            tc::Job jb;
+            jb.a_row = u * tc::NSL * nx + mt * tc::BM;
+            jb.a_sstride = nx;
+            jb.b_row = (int)(usrow[q] + n0);
+            jb.b_sstride = g.r;
+            jb.m_valid = std::min(tc::BM, nx - mt * tc::BM);
+            jb.n_valid = std::min(tc::BN, g.r - n0);
+            jb.out = g.G + (size_t)n0 * nx + mt * tc::BM;
+            jb.ld_out = nx;
+            jobs.push_back(jb);
+          }
+        }
+    Tmp jd;
+    TRY(tmp_alloc(c, jd, jobs.size() * sizeof(tc::Job)));
+    CK(cudaMemcpyAsync(jd.p, jobs.data(), jobs.size() * sizeof(tc::Job), cudaMemcpyHostToDevice, c->st));
+    if (launch_gproj_tc((const float*)bs.p, (long long)nb * tc::NSL * nx, Us, us_rows, nv, ldv, (const tc::Job*)jd.p,
+                        (int)jobs.size(), c->err_d, c->st))
+      return fail(c, OSVMP2_E_CUDA, "tensor-map encoding for the G projection failed");
+    CK(cudaGetLastError());
+  }
+  return 0;
+}
+
 int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osvmp2_prec prec) {
   if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "osvmp2_build_osv has not been called");
   if (prec != OSVMP2_FP64 && prec != OSVMP2_MIXED) return fail(c, OSVMP2_E_ARG, "unknown precision %d", (int)prec);
@@ -566,11 +625,13 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   c->r_h.resize(c->K_h.size());
   CK(cudaMemcpyAsync(c->r_h.data(), c->r_d, c->r_h.size() * sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  if (mixed) {   // U = P X, G = U^T B, K~ = G_i G_j^T (orthonormal pair basis, FP32 products)
-    size_t ufl = 0, gfl = 0;
+  if (mixed) {   // U = P X, G = U^T B, K~ = G_i G_j^T (orthonormal pair basis)
+    size_t ufl = 0, gfl = 0, us_rows = 0;
     int max_r = 0;
+    const int ldv = (nv + 3) & ~3;     // TMA row stride: a multiple of 16 bytes
     std::vector<UJob> uj;
     std::vector<GJob> gj;
+    std::vector<long long> g_usrow;    // row of slice 0 of U_p^T in Us, per G job
     std::vector<KgJob> kgj;
     for (auto& p : newp) {
       const int pid = c->pair_id[(size_t)p.first * n + p.second];
@@ -578,14 +639,18 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
       max_r = std::max(max_r, r);
       ufl += (size_t)nv * r;
       gfl += (size_t)r * nx * (p.first == p.second ? 1 : 2);
+      us_rows += tc::NSL * (size_t)r;
     }
-    float *umem = nullptr, *gmem = nullptr;
+    float *umem = nullptr, *gmem = nullptr, *usmem = nullptr;
     TRY(palloc(c, reinterpret_cast<double**>(&umem), (ufl + 1) / 2 + 1));
     TRY(palloc(c, reinterpret_cast<double**>(&gmem), (gfl + 1) / 2 + 1));
+    TRY(palloc(c, reinterpret_cast<double**>(&usmem), (us_rows * ldv + 1) / 2 + 1));
+    // rows past a pair's r (read by the fixed-height TMA boxes) must hold finite values
+    CK(cudaMemsetAsync(usmem, 0, us_rows * ldv * sizeof(float), c->st));
     c->U_h.resize(c->K_h.size(), nullptr);
     c->Gi_h.resize(c->K_h.size(), nullptr);
     c->Gj_h.resize(c->K_h.size(), nullptr);
-    size_t uo = 0, go = 0;
+    size_t uo = 0, go = 0, urow = 0;
     double f_u = 0.0, f_g = 0.0, f_kg = 0.0;
     for (auto& p : newp) {
       const int i = p.first, j = p.second, pid = c->pair_id[(size_t)i * n + j];
@@ -593,17 +658,20 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
       float* U = umem + uo;
       uo += (size_t)nv * r;
       c->U_h[pid] = U;
-      uj.push_back(UJob{i, j, U});
+      uj.push_back(UJob{i, j, U, usmem + urow * ldv, ldv});
       f_u += 2.0 * nv * (double)m * r;
       float* Gi = gmem + go;
       go += (size_t)r * nx;
       gj.push_back(GJob{i, r, U, Gi});
+      g_usrow.push_back((long long)urow);
       float* Gj = Gi;
       if (i != j) {
         Gj = gmem + go;
         go += (size_t)r * nx;
         gj.push_back(GJob{j, r, U, Gj});
+        g_usrow.push_back((long long)urow);
       }
+      urow += tc::NSL * (size_t)r;
       f_g += (i != j ? 2.0 : 1.0) * 2.0 * r * (double)nv * nx;
       c->Gi_h[pid] = Gi;
       c->Gj_h[pid] = Gj;
@@ -620,16 +688,19 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
     CK(cudaMemcpyAsync(ju.p, uj.data(), uj.size() * sizeof(UJob), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(jg.p, gj.data(), gj.size() * sizeof(GJob), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(jkg.p, kgj.data(), kgj.size() * sizeof(KgJob), cudaMemcpyHostToDevice, c->st));
+    Tmp uscr;
+    TRY(tmp_alloc(c, uscr, (size_t)n_cta * nv * std::max(max_r, 1) * sizeof(double)));
     ph_begin(c, OSVMP2_PH_PROJECT);
-    launch_ubasis(t, (const UJob*)ju.p, (int)uj.size(), n_cta, c->st);
-    launch_gproj(bsrc(c), (const GJob*)jg.p, (int)gj.size(), max_r, c->st);
+    launch_ubasis(t, (const UJob*)ju.p, (int)uj.size(), n_cta, (double*)uscr.p, max_r, c->st);
+    CK(cudaGetLastError());
+    TRY(gproj_tensor(c, gj, g_usrow, usmem, (long long)us_rows, ldv));
     ph_end(c, OSVMP2_PH_PROJECT, f_u + f_g, c->sys.B ? 8.0 * (double)gj.size() * nx * nv : 0.0);
     CK(cudaGetLastError());
     ph_begin(c, OSVMP2_PH_EXCHANGE);
     launch_ktilde_g(nx, (const KgJob*)jkg.p, (int)kgj.size(), max_r, c->st);
     ph_end(c, OSVMP2_PH_EXCHANGE, f_kg);
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(c->st));
+    TRY(check_err_flag(c, "mixed pair build"));
   } else {   // K~ = X^T K X (used by the preconditioner-basis solver)
     std::vector<KtJob> ktj;
     for (size_t q = 0; q < kj.size(); q++) ktj.push_back(KtJob{kj[q].i, kj[q].j, c->Kt_h[c->pair_id[(size_t)kj[q].i * n + kj[q].j]]});

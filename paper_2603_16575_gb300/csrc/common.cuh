@@ -298,6 +298,6 @@ struct BSrc {
 };
 
 // Device-side error flag bits written by kernels (read by the host after sync).
-enum : int { ERR_EIG = 1, ERR_NONFINITE = 2, ERR_NOCONV = 4, ERR_SIZE = 8 };
+enum : int { ERR_EIG = 1, ERR_NONFINITE = 2, ERR_NOCONV = 4, ERR_SIZE = 8, ERR_TIMEOUT = 16 };
 
 }  // namespace osv

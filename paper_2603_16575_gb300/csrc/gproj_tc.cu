@@ -1,0 +1,99 @@
+// Mixed form, A1 in the orthonormal pair basis: G_p,x = U_p^T B_x on the
+// tcgen05 tensor cores (Eq. osv_imua with the preconditioner basis of
+// Eq. prec_eig).  Both operands enter as four fixed-point TF32 slices per
+// 32-virtual chunk (tf32_split.cuh); the leading slice products are summed
+// exactly by the tensor core (tc_tf32x3.cuh), so G carries ~35 bits of the
+// FP64 inputs before its final rounding to FP32.
+//
+// Layout (row-major, K = n_vir innermost, rows padded to ldv floats):
+//   Bs  [slot][slice][n_aux][ldv]   B_x^T slices of the orbitals of one batch
+//   Us  [pair][slice][r][ldv]       U_p^T slices (written by k_ubasis)
+// The tile M dimension is the aux index (128 per tile), N the pair-basis
+// index mu (<= 64 per tile), so the output G[mu][P] is stored with the TMEM
+// lane (aux) as the contiguous index.
+#include "internal.h"
+#include "tc_tf32x3.cuh"
+
+#include <cudaTypedefs.h>
+
+namespace osv {
+
+// B_x^T slices: one CTA per (32 virtuals x 32 aux functions) tile of one orbital
+// (the 32 virtuals are one k-chunk), transposed through shared memory so that
+// both the read of B (aux innermost) and the write of Bs (virtuals innermost)
+// are coalesced.
+__global__ void __launch_bounds__(256) k_bslices(BSrc src, const int* __restrict__ xs, float* __restrict__ Bs,
+                                                 int ldv) {
+  __shared__ double tile[32][33];
+  const int u = blockIdx.z, x = xs[u];
+  const int a0 = blockIdx.y * tc::CHUNK, P0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int da = ty; da < 32; da += 8) {
+    const int a = a0 + da, P = P0 + tx;
+    tile[tx][da] = (a < src.n_vir && P < src.n_aux) ? src.get(x, a, P) : 0.0;
+  }
+  __syncthreads();
+  const size_t slice = (size_t)src.n_aux * ldv;
+  float* base = Bs + (size_t)u * tc::NSL * slice;
+  for (int dP = ty; dP < 32; dP += 8) {       // warp-uniform: one aux row per warp step
+    const int P = P0 + dP, a = a0 + tx;
+    float v[tc::NSL];
+    tc::warp_fixed_slices(tile[dP][tx], v);
+    if (P < src.n_aux && a < src.n_vir) {
+      float* o = base + (size_t)P * ldv + a;
+#pragma unroll
+      for (int s = 0; s < tc::NSL; s++) o[s * slice] = v[s];
+    }
+  }
+}
+
+void launch_bslices(const BSrc& src, const int* xs, int n_x, float* Bs, int ldv, cudaStream_t st) {
+  if (!n_x) return;
+  dim3 grid((src.n_aux + 31) / 32, (src.n_vir + 31) / 32, n_x);
+  k_bslices<<<grid, 256, 0, st>>>(src, xs, Bs, ldv);
+  note_launch(1);
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D FP32 map over rows x n_vir (row stride ldv floats), 128-byte swizzle, box 32 x box_rows.
+bool make_map(CUtensorMap* m, const float* base, int n_vir, int ldv, long long rows, int box_rows) {
+  auto enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)n_vir, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ldv * 4};
+  cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int launch_gproj_tc(const float* Bs, long long a_rows, const float* Us, long long b_rows, int n_vir, int ldv,
+                    const tc::Job* jobs, int n_jobs, int* err, cudaStream_t st) {
+  if (!n_jobs) return 0;
+  if (cudaFuncSetAttribute(tc::k_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess)
+    return -1;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, Bs, n_vir, ldv, a_rows, tc::BM) || !make_map(&mb, Us, n_vir, ldv, b_rows, tc::BROWS)) return -1;
+  tc::k_tf32x3<<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_vir, err);
+  note_launch(1);
+  return 0;
+}
+
+}  // namespace osv

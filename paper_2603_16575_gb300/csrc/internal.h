@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "common.cuh"
+#include "tc_job.h"
 
 namespace osv {
 
@@ -113,6 +114,8 @@ void launch_frag_solve(const Tables& t, const int* frag_orbs, const int* order, 
 struct UJob {
   int i, j;
   float* U;            // [n_vir][r]
+  float* Us;           // TF32 slices of U^T (tf32_split.cuh): slice s row mu at Us + (s * r + mu) * ldv
+  int ldv;
 };
 struct GJob {          // G = U^T B_x  [r][n_aux]
   int x, r;
@@ -125,8 +128,16 @@ struct KgJob {         // K~ = G_i G_j^T  [r][r]
   const float* Gj;
   double* Kt;
 };
-void launch_ubasis(const Tables& t, const UJob* jobs, int n_jobs, int n_cta, cudaStream_t st);
+void launch_ubasis(const Tables& t, const UJob* jobs, int n_jobs, int n_cta, double* scratch, int max_r,
+                   cudaStream_t st);
 void launch_gproj(const BSrc& src, const GJob* jobs, int n_jobs, int max_r, cudaStream_t st);
+// B_x for the orbitals xs[0..n_x) as TF32 slices (tf32_split.cuh), transposed:
+// slot u, slice s, row P at Bs + ((u * tc::NSL + s) * n_aux + P) * ldv
+void launch_bslices(const BSrc& src, const int* xs, int n_x, float* Bs, int ldv, cudaStream_t st);
+// G tiles with the split-TF32 tensor-core kernel: A = Bs (rows a_rows), B = Us (rows b_rows), K = n_vir.
+// Returns 0, or -1 if a tensor map could not be encoded.
+int launch_gproj_tc(const float* Bs, long long a_rows, const float* Us, long long b_rows, int n_vir, int ldv,
+                    const tc::Job* jobs, int n_jobs, int* err, cudaStream_t st);
 void launch_ktilde_g(int n_aux, const KgJob* jobs, int n_jobs, int max_r, cudaStream_t st);
 
 // Mixed form (solve_mixed.cu): per pair K~ = X^T K X, then the fragment solve in
