@@ -130,7 +130,8 @@ def run_gpu(args):
             B = pkg.generate_B(s.n_occ, s.n_vir, s.n_aux, s.seed, env, stream=stream.cuda_stream)
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
     stream.synchronize()
-    ctx = pkg.Context(local, stream=stream)
+    osv_prec = "mixed" if args.prec == "mixed" else "fp64"
+    ctx = pkg.Context(local, stream=stream, osv_prec=osv_prec)
 
     def step(B_in=B, env_in=env, f_in=f_occ, e_in=e_vir):
         kw = dict(B=B_in) if B_in is not None else dict(env=env_in, seed=s.seed, n_aux=s.n_aux)
@@ -169,11 +170,23 @@ def run_gpu(args):
     a0_ms = sum(prof.get(k, (0.0,))[0] for k in ("tii", "eig")) / args.steps
     err = None
     if args.prec == "mixed":
-        # the same inputs through the FP64 form (parity with the FP64 oracle is a GPU test)
+        # the same inputs through the FP64 form, one step timed the same way (parity
+        # of the FP64 form with the FP64 oracle is a GPU test)
+        ctx.set_opts(osv_prec="fp64")
         kw = dict(B=B) if B is not None else dict(env=env, seed=s.seed, n_aux=s.n_aux)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
         ctx.build_osv(f_occ, e_vir, L_OSV, r_occ=s.r_occ, **kw)
         E64 = ctx.mbe3_energy(R2_CUT, R3_CUT, "fp64")[0]
-        err = {"energy_fp64_form": E64, "abs_err_eh": abs(E - E64), "rel_err": abs(E - E64) / abs(E64)}
+        ev1.record(stream)
+        ev1.synchronize()
+        t64 = ev0.elapsed_time(ev1) / 1e3
+        err = {"energy_fp64_form": E64, "abs_err_eh": abs(E - E64), "rel_err": abs(E - E64) / abs(E64),
+               "fp64_form_ms_per_step": 1e3 * t64, "fp64_form_fragments_per_s": n_frag / t64}
+        ctx.set_opts(osv_prec=osv_prec)
         ctx.profile(reset=True)
     t_tot = sum(t_steps)
     if world > 1:

@@ -69,7 +69,12 @@ typedef struct {
                       /* (the energy test does the fine convergence: the update
                           has a rounding floor of ~eps*cond(S_(ij,ij)))       */
   int32_t max_iter;   /* amplitude iterations per fragment                    (default 100) */
-  int32_t reserved[7];
+  int32_t osv_prec;   /* arithmetic of the T_ii contraction B_i B_i^T in osvmp2_build_osv
+                         (an osvmp2_prec; default OSVMP2_FP64).  OSVMP2_MIXED runs it on
+                         the tensor cores with split-precision operands (~35 significant
+                         bits); the eigen-decomposition stays FP64 in both.  Library
+                         extension: the paper forms T_ii in one precision only. */
+  int32_t reserved[6];
 } osvmp2_opts;
 
 /* Synthetic or caller-supplied system.  All arrays are read by the kernels. */
@@ -106,6 +111,10 @@ void osvmp2_destroy(osvmp2_ctx *ctx);
 const char *osvmp2_last_error(const osvmp2_ctx *ctx);
 /* Fill opts with the defaults listed in osvmp2_opts. */
 void osvmp2_default_opts(osvmp2_opts *opts);
+/* Replace the options of ctx (validated as in osvmp2_create; E_ARG leaves them
+ * unchanged).  Takes effect for the next call; built OSVs and pair blocks are
+ * kept. */
+int osvmp2_set_opts(osvmp2_ctx *ctx, const osvmp2_opts *opts);
 /* Number of CUDA kernels this library has launched in this process (all ctxs). */
 int64_t osvmp2_kernel_launches(void);
 

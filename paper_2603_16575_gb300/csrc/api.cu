@@ -429,6 +429,9 @@ int gproj_tensor(osvmp2_ctx* c, const std::vector<GJob>& gj, const std::vector<l
             jb.n_valid = std::min(tc::BN, g.r - n0);
             jb.out = g.G + (size_t)n0 * nx + mt * tc::BM;
             jb.ld_out = nx;
+            jb.m0 = mt * tc::BM;
+            jb.n0 = n0;
+            jb.s = 0.0;
             jobs.push_back(jb);
           }
         }
@@ -733,6 +736,19 @@ void osvmp2_default_opts(osvmp2_opts* o) {
   o->max_iter = 100;
 }
 
+static bool opts_valid(const osvmp2_opts& o) {
+  return o.max_iter > 0 && o.tau_s >= 0 && o.tol_update > 0 && o.tol_energy > 0 &&
+         (o.osv_prec == OSVMP2_FP64 || o.osv_prec == OSVMP2_MIXED);
+}
+
+int osvmp2_set_opts(osvmp2_ctx* c, const osvmp2_opts* opts) {
+  if (!c || !opts) return OSVMP2_E_ARG;
+  c->err.clear();
+  if (!opts_valid(*opts)) return fail(c, OSVMP2_E_ARG, "invalid options");
+  c->opts = *opts;
+  return OSVMP2_OK;
+}
+
 int osvmp2_create(osvmp2_ctx** out, int device, void* cuda_stream, const osvmp2_opts* opts) {
   if (!out) return OSVMP2_E_ARG;
   *out = nullptr;
@@ -741,7 +757,7 @@ int osvmp2_create(osvmp2_ctx** out, int device, void* cuda_stream, const osvmp2_
   c->st = (cudaStream_t)cuda_stream;
   osvmp2_default_opts(&c->opts);
   if (opts) c->opts = *opts;
-  if (c->opts.max_iter <= 0 || c->opts.tau_s < 0 || c->opts.tol_update <= 0 || c->opts.tol_energy <= 0) {
+  if (!opts_valid(c->opts)) {
     delete c;
     return OSVMP2_E_ARG;
   }
@@ -776,6 +792,46 @@ void osvmp2_destroy(osvmp2_ctx* c) {
 }
 
 const char* osvmp2_last_error(const osvmp2_ctx* c) { return c ? c->err.c_str() : "null ctx"; }
+
+// Mixed-form T_i of orbitals [i0, i0+b) on the tensor cores: B_i slices for up
+// to nsl orbitals at a time, then the lower-triangle tiles of each T_i.
+int tii_tensor(osvmp2_ctx* c, int i0, int b, double* T, float* Bt, int nsl, int ldx) {
+  const int nv = c->sys.n_vir, nx = c->sys.n_aux, n = c->sys.n_occ;
+  const int n_mt = (nv + tc::BM - 1) / tc::BM, n_nt = (nv + tc::BN - 1) / tc::BN;
+  for (int u0 = 0; u0 < b; u0 += nsl) {
+    const int nu = std::min(nsl, b - u0);
+    launch_rslices(bsrc(c), i0 + u0, nu, Bt, ldx, c->st);
+    CK(cudaGetLastError());
+    std::vector<tc::Job> jobs;
+    for (int u = 0; u < nu; u++) {
+      const int i = i0 + u0 + u;
+      for (int mt = 0; mt < n_mt; mt++)
+        for (int nt = 0; nt < n_nt && nt * tc::BN < (mt + 1) * tc::BM; nt++) {
+          tc::Job jb;
+          jb.a_row = u * tc::NSL * nv + mt * tc::BM;
+          jb.a_sstride = nv;
+          jb.b_row = u * tc::NSL * nv + nt * tc::BN;
+          jb.b_sstride = nv;
+          jb.m_valid = std::min(tc::BM, nv - mt * tc::BM);
+          jb.n_valid = std::min(tc::BN, nv - nt * tc::BN);
+          jb.out = T + (size_t)(u0 + u) * nv * nv;
+          jb.ld_out = nv;
+          jb.m0 = mt * tc::BM;
+          jb.n0 = nt * tc::BN;
+          jb.s = 2.0 * c->f_h[(size_t)i * n + i];
+          jobs.push_back(jb);
+        }
+    }
+    Tmp jd;
+    TRY(tmp_alloc(c, jd, jobs.size() * sizeof(tc::Job)));
+    CK(cudaMemcpyAsync(jd.p, jobs.data(), jobs.size() * sizeof(tc::Job), cudaMemcpyHostToDevice, c->st));
+    if (launch_tii_tc(Bt, (long long)nu * tc::NSL * nv, nx, ldx, (const tc::Job*)jd.p, (int)jobs.size(),
+                      c->sys.e_vir, c->err_d, c->st))
+      return fail(c, OSVMP2_E_CUDA, "tensor-map encoding for T_ii failed");
+    CK(cudaGetLastError());
+  }
+  return 0;
+}
 
 int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_t* n_osv_host) {
   if (!c || !s) return OSVMP2_E_ARG;
@@ -813,12 +869,22 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   c->bt_id.assign((size_t)n * n, -1);
   TRY(upload(c, c->sf_id_d, c->sf_id));
   TRY(upload(c, c->pair_id_d, c->pair_id));
-  // batch the orbitals so that T, V and the eigen scratch stay within ~4 GB
+  // batch the orbitals so that T, V and the eigen scratch stay within ~4 GB, in
+  // batches of equal size (one CTA per orbital in the eigen kernel)
   const int kmax = nv;
   const size_t per = ((size_t)nv * nv * 2 + kmax + eig_osv_scratch_doubles(nv, kmax)) * sizeof(double);
   int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, ((size_t)4 << 30) / per));
   nb = std::min(nb, 4 * c->num_sms);
-  Tmp Tm, Vm, wm, km, sm;
+  {
+    const int nbatch = (n + nb - 1) / nb;
+    nb = (n + nbatch - 1) / nbatch;
+  }
+  const bool tii_tc = c->opts.osv_prec == OSVMP2_MIXED;
+  const int ldx = (s->n_aux + 3) & ~3;
+  const size_t slot_bytes = (size_t)tc::NSL * nv * ldx * sizeof(float);
+  const int nsl = tii_tc ? (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, ((size_t)1 << 30) / slot_bytes)) : 0;
+  Tmp Tm, Vm, wm, km, sm, Bt;
+  if (tii_tc) TRY(tmp_alloc(c, Bt, (size_t)nsl * slot_bytes));
   TRY(tmp_alloc(c, Tm, (size_t)nb * nv * nv * sizeof(double)));
   TRY(tmp_alloc(c, Vm, (size_t)nb * nv * kmax * sizeof(double)));
   TRY(tmp_alloc(c, wm, (size_t)nb * kmax * sizeof(double)));
@@ -834,7 +900,10 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   for (int i0 = 0; i0 < n; i0 += nb) {
     const int b = std::min(nb, n - i0);
     ph_begin(c, OSVMP2_PH_TII);
-    launch_tii(bsrc(c), s->e_vir, s->f_occ, n, i0, b, (double*)Tm.p, c->st);
+    if (tii_tc)
+      TRY(tii_tensor(c, i0, b, (double*)Tm.p, (float*)Bt.p, nsl, ldx));
+    else
+      launch_tii(bsrc(c), s->e_vir, s->f_occ, n, i0, b, (double*)Tm.p, c->st);
     ph_end(c, OSVMP2_PH_TII, (double)b * nv * (double)nv * s->n_aux, s->B ? 8.0 * b * (double)nv * s->n_aux : 0.0);
     CK(cudaGetLastError());
     ph_begin(c, OSVMP2_PH_EIG);

@@ -94,15 +94,30 @@ __device__ __forceinline__ void tile_mma_t(int M, int N, int K, int m0, int n0, 
   }
 }
 
+// Error-free FP32 sum: s + e == a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 // As tile_mma_t<float>, but each k-tile's sixteen FP32 products are summed in
-// FP32 and the tile sums are accumulated in FP64: the rounding of long FP32
-// accumulations (which grows with K) is confined to sixteen terms.
+// FP32 and the tile sums are accumulated in a compensated (hi, lo) FP32 pair
+// (two-sum), added to acc in FP64 at the end: the rounding of long FP32
+// accumulations (which grows with K) is confined to sixteen terms, and the
+// accumulation across k-tiles costs FP32 operations only (FP64 throughput is
+// 1/64 of FP32 on this part).
 template <class VA, class VB>
 __device__ __forceinline__ void tile_mma_f32x64(int M, int N, int K, int m0, int n0, const VA& A, const VB& B,
                                                 double acc[4][4], float* sm) {
   float* As = sm;
   float* Bs = sm + TK * TM;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float hi[4][4], lo[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) hi[i][j] = lo[i][j] = 0.f;
   for (int k0 = 0; k0 < K; k0 += TK) {
 #pragma unroll
     for (int t = 0; t < TM * TK / NT; t++) {
@@ -137,13 +152,22 @@ __device__ __forceinline__ void tile_mma_f32x64(int M, int N, int K, int m0, int
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-      for (int j = 0; j < 4; j++) acc[i][j] += (double)part[i][j];
+      for (int j = 0; j < 4; j++) {
+        float e;
+        two_sum_f(hi[i][j], part[i][j], hi[i][j], e);
+        lo[i][j] += e;
+      }
     __syncthreads();
   }
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] += (double)hi[i][j] + (double)lo[i][j];
 }
 
 // C[MxN] (ld ldc, element type CT) = beta*C + alpha*A*B with FP32 products
-// accumulated per k-tile in FP32 and across k-tiles in FP64 (tile_mma_f32x64).
+// accumulated per k-tile in FP32 and across k-tiles in compensated FP32
+// (tile_mma_f32x64); the final scaling and the update of C are FP64.
 template <class CT, class VA, class VB>
 __device__ void cta_gemm_f32x64(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, CT* C,
                                 int ldc, float* sm) {

@@ -113,7 +113,10 @@ __device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double*
 // memory: the symmetric matvec p = tau A' v is formed column-wise (thread c
 // owns column c and walks the rows, so every load instruction of a warp is
 // coalesced and a thread keeps many independent loads in flight), and the
-// rank-2 update is applied the same way.
+// rank-2 update is applied the same way.  Reflector k is also stored
+// contiguously in row k to the right of the diagonal (A[k][k+1+t] = v_t,
+// v_0 = 1; that part of the upper triangle is not read again), for the
+// back-transformation.
 template <int NTH = NT>
 __device__ inline void cta_tridiag_col(double* A, int n, int lda, double* d, double* e, double* tau, double* v,
                                        double* p, double* red) {
@@ -186,6 +189,7 @@ __device__ inline void cta_tridiag_col(double* A, int n, int lda, double* d, dou
         for (; r < L; r++) Ak[(size_t)r * lda + c] -= v[r] * wc + p[r] * vc;
       }
       for (int t = tid + 1; t < L; t += NTH) A[(size_t)(k + 1 + t) * lda + k] = v[t];
+      for (int t = tid; t < L; t += NTH) A[(size_t)k * lda + (k + 1 + t)] = v[t];
     }
     __syncthreads();
   }

@@ -54,8 +54,14 @@ void launch_bslices(const BSrc& src, const int* xs, int n_x, float* Bs, int ldv,
   note_launch(1);
 }
 
-namespace {
+// G[mu][P] = hi + lo (TMEM lane = aux row P, column = mu)
+struct EpiG {
+  __device__ __forceinline__ void operator()(const tc::Job& jb, int r, int c, float h, float l) const {
+    static_cast<float*>(jb.out)[(size_t)c * jb.ld_out + r] = h + l;
+  }
+};
 
+namespace {
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -68,13 +74,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   }
   return fn;
 }
+}  // namespace
 
-// 2-D FP32 map over rows x n_vir (row stride ldv floats), 128-byte swizzle, box 32 x box_rows.
-bool make_map(CUtensorMap* m, const float* base, int n_vir, int ldv, long long rows, int box_rows) {
+// 2-D FP32 map over rows x n_k (row stride ldk floats), 128-byte swizzle, box 32 x box_rows.
+bool make_slice_map(CUtensorMap* m, const float* base, int n_k, int ldk, long long rows, int box_rows) {
   auto enc = encode_fn();
   if (!enc) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)n_vir, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ldv * 4};
+  cuuint64_t dims[2] = {(cuuint64_t)n_k, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ldk * 4};
   cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
@@ -82,16 +89,15 @@ bool make_map(CUtensorMap* m, const float* base, int n_vir, int ldv, long long r
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-}  // namespace
-
 int launch_gproj_tc(const float* Bs, long long a_rows, const float* Us, long long b_rows, int n_vir, int ldv,
                     const tc::Job* jobs, int n_jobs, int* err, cudaStream_t st) {
   if (!n_jobs) return 0;
-  if (cudaFuncSetAttribute(tc::k_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess)
+  if (cudaFuncSetAttribute(tc::k_tf32x3<EpiG>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess)
     return -1;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, Bs, n_vir, ldv, a_rows, tc::BM) || !make_map(&mb, Us, n_vir, ldv, b_rows, tc::BROWS)) return -1;
-  tc::k_tf32x3<<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_vir, err);
+  if (!make_slice_map(&ma, Bs, n_vir, ldv, a_rows, tc::BM) || !make_slice_map(&mb, Us, n_vir, ldv, b_rows, tc::BROWS))
+    return -1;
+  tc::k_tf32x3<EpiG><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_vir, err, EpiG{});
   note_launch(1);
   return 0;
 }

@@ -1,6 +1,7 @@
 // Internal interfaces between the host runtime (api.cu) and the kernel
 // translation units of libosvmp2.  Not part of the C ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "common.cuh"
@@ -47,8 +48,14 @@ struct FragOut {
 // T_ii of orbitals [i0, i0+nb) into T [nb][nv][nv].
 void launch_tii(const BSrc& src, const double* e_vir, const double* f_occ, int n_occ, int i0, int nb,
                 double* T, cudaStream_t st);
+// Mixed form (tii_tc.cu): slices of B_i along the aux index for orbitals
+// [i0, i0+nb): slot u, slice s, row a at Bt + ((u * tc::NSL + s) * n_vir + a) * ldx;
+// then the tensor-core tiles of T (jobs built by the host, out = T_i, s = 2 f_ii).
+void launch_rslices(const BSrc& src, int i0, int nb, float* Bt, int ldx, cudaStream_t st);
+int launch_tii_tc(const float* Bt, long long rows, int n_aux, int ldx, const tc::Job* jobs, int n_jobs,
+                  const double* e_vir, int* err, cudaStream_t st);
 // Eigen-decomposition of each T[b] and selection omega >= thr (all if thr <= 0),
-// at most kmax per orbital: V [nb][nv][kmax], w [nb][kmax], k [nb], err |= ERR_*.
+// at most kmax per orbital: V [nb][kmax][nv] (eigenvector-major), w [nb][kmax], k [nb], err |= ERR_*.
 // e, tau, w (3 nv) + Z (nv*nv, global path) + 32 warps x 7 nv (inverse iteration)
 __host__ __device__ inline size_t eig_osv_scratch_doubles(int nv, int kmax) {
   (void)kmax;
@@ -139,6 +146,9 @@ void launch_bslices(const BSrc& src, const int* xs, int n_x, float* Bs, int ldv,
 int launch_gproj_tc(const float* Bs, long long a_rows, const float* Us, long long b_rows, int n_vir, int ldv,
                     const tc::Job* jobs, int n_jobs, int* err, cudaStream_t st);
 void launch_ktilde_g(int n_aux, const KgJob* jobs, int n_jobs, int max_r, cudaStream_t st);
+// 2-D FP32 tensor map over rows x n_k (row stride ldk floats, a multiple of 4),
+// 128-byte swizzle, box tc::BK x box_rows; false if the driver rejects it.
+bool make_slice_map(CUtensorMap* m, const float* base, int n_k, int ldk, long long rows, int box_rows);
 
 // Mixed form (solve_mixed.cu): per pair K~ = X^T K X, then the fragment solve in
 // the preconditioner basis with FP32 coupling products.

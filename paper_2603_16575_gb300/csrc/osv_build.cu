@@ -64,15 +64,16 @@ void launch_tii(const BSrc& src, const double* e_vir, const double* f_occ, int n
 constexpr int ZSMEM_MAX = 160;   // Z kept in shared memory up to this order
 constexpr int NT_EIG = 1024;     // threads of the OSV eigen kernel (more loads in flight)
 
-// Sign column t of V (n rows, ld) so that its largest-magnitude entry (lowest
-// row on ties) is positive.  One warp per column.
-__device__ inline void sign_columns(double* V, int n, int ld, int k) {
+// Sign eigenvector t (V[t][0..n), eigenvector-major) so that its largest-magnitude
+// entry (lowest index on ties) is positive.  One warp per vector.
+__device__ inline void sign_vectors(double* V, int n, int k) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = warp; t < k; t += NT_EIG / 32) {
+    double* x = V + (size_t)t * n;
     double best = -1.0;
     int bi = 0x7fffffff;
     for (int r = lane; r < n; r += 32) {
-      const double a = fabs(V[(size_t)r * ld + t]);
+      const double a = fabs(x[r]);
       if (a > best) { best = a; bi = r; }
     }
 #pragma unroll
@@ -81,9 +82,8 @@ __device__ inline void sign_columns(double* V, int n, int ld, int k) {
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
-    const double sg = (V[(size_t)bi * ld + t] < 0.0) ? -1.0 : 1.0;
-    if (sg < 0.0)
-      for (int r = lane; r < n; r += 32) V[(size_t)r * ld + t] = -V[(size_t)r * ld + t];
+    if (x[bi] < 0.0)
+      for (int r = lane; r < n; r += 32) x[r] = -x[r];
   }
   __syncthreads();
 }
@@ -121,11 +121,11 @@ __device__ void eig_full_select(double* A, int n, double thr, int kmax, double* 
   __syncthreads();
   const int k = s_k;
   for (int idx = threadIdx.x; idx < n * k; idx += NT_EIG) {
-    const int r = idx / k, t = idx % k;
-    V[(size_t)r * kmax + t] = Zs[(size_t)r * ldz + perm[t]];
+    const int t = idx / n, r = idx % n;
+    V[(size_t)t * n + r] = Zs[(size_t)r * ldz + perm[t]];
   }
   __syncthreads();
-  sign_columns(V, n, kmax, k);
+  sign_vectors(V, n, k);
 }
 
 // Eigenpairs with eigenvalue >= thr only: tridiagonalise, count by Sturm
@@ -206,10 +206,11 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
         if (lane == 0) tri_solve(n, u0, u1, u2, mu, piv, y);
         __syncwarp();
         for (int s = t0; s < t; s++) {          // Gram-Schmidt against the cluster's earlier vectors
+          const double* Vs = V + (size_t)s * n;
           double dot = 0.0;
-          for (int r = lane; r < n; r += 32) dot += y[r] * V[(size_t)r * kmax + s];
+          for (int r = lane; r < n; r += 32) dot += y[r] * Vs[r];
           dot = warp_sum(dot);
-          for (int r = lane; r < n; r += 32) y[r] -= dot * V[(size_t)r * kmax + s];
+          for (int r = lane; r < n; r += 32) y[r] -= dot * Vs[r];
           __syncwarp();
         }
         double nn = 0.0;
@@ -219,32 +220,31 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
         for (int r = lane; r < n; r += 32) y[r] *= sc;
         __syncwarp();
       }
-      for (int r = lane; r < n; r += 32) V[(size_t)r * kmax + t] = y[r];
+      for (int r = lane; r < n; r += 32) V[(size_t)t * n + r] = y[r];
       __syncwarp();
     }
   }
   __syncthreads();
-  // back-transformation V <- H_0 ... H_{n-3} V
-  for (int kk = n - 3; kk >= 0; kk--) {
-    const double tk = tau[kk];
-    if (tk == 0.0) continue;
-    const int L = n - kk - 1;
-    for (int r = threadIdx.x; r < L; r += NT_EIG) v[r] = (r == 0) ? 1.0 : A[(size_t)(kk + 1 + r) * n + kk];
-    __syncthreads();
-    for (int t = warp; t < k; t += NT_EIG / 32) {
+  // back-transformation V <- H_0 ... H_{n-3} V: eigenvectors are independent, so
+  // each warp applies every reflector (stored contiguously in row kk of A) to
+  // its own vectors, with no CTA-wide barrier.
+  for (int t = warp; t < k; t += NT_EIG / 32) {
+    double* x = V + (size_t)t * n;
+    for (int kk = n - 3; kk >= 0; kk--) {
+      const double tk = tau[kk];
+      if (tk == 0.0) continue;
+      const int L = n - kk - 1;
+      const double* vr = A + (size_t)kk * n + kk + 1;
+      double* xs = x + kk + 1;
       double s = 0.0;
-      for (int r = lane; r < L; r += 32) s += v[r] * V[(size_t)(kk + 1 + r) * kmax + t];
-      s = warp_sum(s);
-      if (lane == 0) p[t] = tk * s;   // p reused (clusters no longer needed)
+      for (int r = lane; r < L; r += 32) s = fma(vr[r], xs[r], s);
+      s = tk * warp_sum(s);
+      for (int r = lane; r < L; r += 32) xs[r] = fma(-vr[r], s, xs[r]);
+      __syncwarp();
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < L * k; idx += NT_EIG) {
-      const int r = idx / k, t = idx % k;
-      V[(size_t)(kk + 1 + r) * kmax + t] -= v[r] * p[t];
-    }
-    __syncthreads();
   }
-  sign_columns(V, n, kmax, k);
+  __syncthreads();
+  sign_vectors(V, n, k);
 }
 
 __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double thr, int kmax, double* V, double* w,
@@ -286,7 +286,7 @@ __global__ void k_pack_q(const double* V, const double* w, int nv, int kmax, con
   double* Q = Qdst[b];
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nv * kb; idx += gridDim.x * blockDim.x) {
     const int r = idx / kb, t = idx % kb;
-    Q[idx] = Vb[(size_t)r * kmax + t];
+    Q[idx] = Vb[(size_t)t * nv + r];
   }
   if (blockIdx.x == 0)
     for (int t = threadIdx.x; t < kb; t += blockDim.x) wdst[b][t] = w[(size_t)b * kmax + t];

@@ -11,7 +11,8 @@
 // Precision: the coupling C_p carries the off-diagonal occupied Fock elements
 // (|c_t| ~ 1e-2 against |D| ~ 1), so the rounding of its FP32 products perturbs
 // Y by ~ eps_32 |c| / |D| ~ 1e-9 relative.  C_p and Sigma_pq are FP32 products
-// summed per k-tile in FP32 and across k-tiles in FP64; K~_p, D_p, C_p, Y_p
+// summed per k-tile in FP32 and across k-tiles in compensated FP32 (two-sum);
+// K~_p, D_p, C_p, Y_p
 // (master copy) and the energy <K~_p, 2Y_p - Y_p^T> are FP64.
 #include "pairview.cuh"
 

@@ -12,9 +12,11 @@ constexpr int CHUNK = 32;  // k-extent that shares one power-of-two scale per ro
 struct Job {
   int a_row, a_sstride;    // A slice s: rows a_row + s * a_sstride + [0, 128) of the A tensor map
   int b_row, b_sstride;    // B slice s: rows b_row + s * b_sstride + [0, n) of the B tensor map
-  int m_valid, n_valid;    // output rows (<= 128) and columns (<= 128) to store
-  float* out;              // out[n * ld_out + m]
+  int m_valid, n_valid;    // output rows (<= 128) and columns (<= 64) to store
+  void* out;               // output of the epilogue (its layout is the epilogue's)
   int ld_out;
+  int m0, n0;              // global row / column of the tile's first element
+  double s;                // epilogue scalar
 };
 
 }  // namespace tc

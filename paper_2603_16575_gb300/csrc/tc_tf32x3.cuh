@@ -8,7 +8,7 @@
 // MBE(3) energy.  The operands are therefore cut into fixed-point slices
 // (tf32_split.cuh): within each 32-wide k-chunk, row m of A is
 //   A[m][k] = 2^e_m * sum_{s=1..4} a_s[m][k] 2^(-9 s),  a_s integer, |a_s| <= 2^9,
-// with e_m common to the chunk (same for B).  A slice product of level
+// with e_m common to the chunk (same for B; tf32_split.cuh).  A slice product of level
 // l = s + t is then an integer multiple of 2^(e_m + e_n - 9 l) of magnitude
 // <= 2^18, and a chunk sum of the level-2 product (32 terms) or of the two
 // level-3 products (64 terms) stays below 2^24 units: it is computed EXACTLY
@@ -105,9 +105,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
                "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),  \
                "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]))
 
+// Epi: functor epi(job, row, col, hi, lo) storing the tile element (row < m_valid,
+// col < n_valid) whose value is hi + lo.
+template <class Epi>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-             const Job* __restrict__ jobs, int K, int* err) {
+             const Job* __restrict__ jobs, int K, int* err, Epi epi) {
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accf[2], bar_acce[2];
   __shared__ uint32_t s_tmem;
@@ -240,8 +243,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (row < jb.m_valid)
 #pragma unroll
         for (int u = 0; u < 16; u++)
-          if (n0 + u < jb.n_valid)
-            jb.out[(size_t)(n0 + u) * jb.ld_out + row] = __uint_as_float(h[u]) + __uint_as_float(l[u]);
+          if (n0 + u < jb.n_valid) epi(jb, row, n0 + u, __uint_as_float(h[u]), __uint_as_float(l[u]));
     }
   }
   if (!ok) atomicOr(err, ERR_TC_TIMEOUT);

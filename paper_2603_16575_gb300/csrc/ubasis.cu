@@ -15,7 +15,7 @@
 // that forms K~, and it shifts every pair energy by ~eps_32 relative.  The
 // rounding of G and of B, by contrast, is independent across P.
 // The FP32 contractions sum each k-tile of sixteen products in FP32 and the
-// tile sums in FP64 (tile_mma_f32x64): long FP32 accumulations would leave
+// tile sums in compensated FP32 (tile_mma_f32x64): long FP32 accumulations would leave
 // errors of ~eps_32 sqrt(K) that add up over the thousands of pairs of an
 // MBE(3) energy instead of averaging out.
 // (Eqs. osv_imua and osv_close_k evaluated in the preconditioner basis of
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(NT) k_gproj(BSrc src, const GJob* __restrict__
     }
 }
 
-// K~ = G_i G_j^T (FP32 products, FP64 accumulation over k-tiles of 16 aux
+// K~ = G_i G_j^T (FP32 products, compensated accumulation over k-tiles of 16 aux
 // functions: the aux sum is the final contraction of the energy and its FP32
 // accumulation error would not average out).  grid: (job, tile r, tile c)
 __global__ void __launch_bounds__(NT) k_ktilde_g(int n_aux, const KgJob* __restrict__ jobs) {

@@ -26,7 +26,7 @@ STATUS_CODES = {v: k for k, v in STATUS.items()}
 
 class Opts(ctypes.Structure):
     _fields_ = [("tau_s", ctypes.c_double), ("tol_update", ctypes.c_double), ("tol_energy", ctypes.c_double),
-                ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("max_iter", ctypes.c_int32), ("osv_prec", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class System(ctypes.Structure):
@@ -53,6 +53,7 @@ SIGNATURES = {
     "osvmp2_destroy": (None, [_P]),
     "osvmp2_last_error": (ctypes.c_char_p, [_P]),
     "osvmp2_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "osvmp2_set_opts": (ctypes.c_int, [_P, ctypes.POINTER(Opts)]),
     "osvmp2_kernel_launches": (ctypes.c_int64, []),
     "osvmp2_build_osv": (ctypes.c_int, [_P, ctypes.POINTER(System), _D, _P]),
     "osvmp2_get_osv": (ctypes.c_int, [_P, _I32, _P, _P]),
@@ -168,6 +169,13 @@ def precond_noalloc(S, F, tau_s, X, et, r, stream=None) -> None:
         raise OSVMP2Error("osvmp2_precond_noalloc", code, buf.value.decode())
 
 
+def _apply_opts(o: Opts, kw) -> None:
+    for k, v in kw.items():
+        if k == "osv_prec" and isinstance(v, str):
+            v = PREC[v]
+        setattr(o, k, v)
+
+
 class Context:
     """One osvmp2_ctx on a CUDA device and stream (defaults: current device/stream)."""
 
@@ -176,8 +184,7 @@ class Context:
         self.device = device
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         o = opts or default_opts()
-        for k, v in kw.items():
-            setattr(o, k, v)
+        _apply_opts(o, kw)
         self.opts = o
         h = ctypes.c_void_p()
         s = lib().osvmp2_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(o))
@@ -186,6 +193,14 @@ class Context:
         self._h = h
         self._keep = ()
         self.n_occ = self.n_vir = self.n_aux = 0
+
+    def set_opts(self, **kw):
+        """Change options (e.g. osv_prec="mixed") for the following calls."""
+        o = Opts()
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(self.opts), ctypes.sizeof(Opts))
+        _apply_opts(o, kw)
+        self._check("osvmp2_set_opts", lib().osvmp2_set_opts(self._h, ctypes.byref(o)))
+        self.opts = o
 
     def close(self):
         if getattr(self, "_h", None):

@@ -191,6 +191,42 @@ def test_mixed_mbe3_energy_within_one_microhartree():
     ctx.close()
 
 
+@pytest.mark.parametrize("n_vir,l_osv,lam", [(70, 1e-4, 1.5), (200, 1e-4, 1.0), (260, 1e-3, 1.5)])
+def test_mixed_osv_build_matches_oracle(n_vir, l_osv, lam):
+    """T_ii on the tensor cores (split-precision operands, ~35 bits): OSV counts exact,
+    eigenvalues and kept spaces close to the FP64 oracle."""
+    s = synth.make_system(3, n_vir, 3 * n_vir // 2 + 7, seed=4, lam=lam)
+    o = oracle.OSVSystem(s.B_block, 3, s.e_vir, s.f_occ, l_osv=l_osv)
+    ctx = _ctx(osv_prec="mixed")
+    n_osv = _build(ctx, s, l_osv)
+    assert list(n_osv) == [q.shape[1] for q in o.Q]
+    for i in range(3):
+        Q, w = ctx.get_osv(i)
+        Q, w = Q.cpu().numpy(), w.cpu().numpy()
+        wr = o.omega[i]
+        assert np.abs(w - wr).max() < 1e-9 * wr.max()
+        assert np.allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-11)
+    ctx.close()
+
+
+def test_mixed_osv_and_energy_within_one_microhartree():
+    """Mixed OSV build and mixed pair solve together against the FP64 oracle."""
+    s = synth.make_system(12, 70, 130, seed=41, lam=1.2)
+    ctx = _ctx(osv_prec="mixed")
+    _build(ctx, s, 1e-4)
+    E, st = ctx.mbe3_energy(4.5, 3.8, "mixed")
+    o = oracle.OSVSystem(s.B_block, 12, s.e_vir, s.f_occ, l_osv=1e-4)
+    E_ref, _ = o.mbe3_energy(s.r_occ, 4.5, 3.8)
+    assert st["n_unconverged"] == 0
+    assert abs(E - E_ref) < 1e-6
+    # switching back to the FP64 build restores the FP64-form parity
+    ctx.set_opts(osv_prec="fp64")
+    _build(ctx, s, 1e-4)
+    E64, _ = ctx.mbe3_energy(4.5, 3.8, "fp64")
+    assert abs(E64 - E_ref) < 1e-9
+    ctx.close()
+
+
 def test_mixed_gradient_close_to_oracle():
     s = synth.make_system(6, 40, 80, seed=29, lam=1.5, f_off=3e-2)
     ctx = _ctx()
