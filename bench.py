@@ -222,9 +222,17 @@ def run_gpu(args):
     peak_fp64 = FP64_PEAK_TFLOPS
     peak_fp32 = 152 * 128 * 2 * 2.070e9 / 1e12                 # 128 FFMA/clk/SM -> 80.5 TF/s
 
+    # split-precision tensor-core contractions: 10 TF32 slice products per algorithmic
+    # product; TF32 peak = measured BF16 peak x nominal TF32/BF16 ratio (1.1/2.25 PF)
+    peak_tf32 = peaks["bf16_tflops"] * 1.1 / 2.25
+    peak_split = peak_tf32 / 10.0
+
     def phase_peak(name):
         """(bound, peak TFLOP/s, source) of a phase in the arithmetic it runs in."""
-        if args.prec == "mixed" and name in ("project", "exchange", "solve"):
+        if args.prec == "mixed" and name in ("tii", "project"):
+            return ("tensor", peak_split, f"split-TF32 on tcgen05: TF32 peak {peak_tf32:.0f} TF/s (measured BF16 "
+                    f"{peaks['bf16_tflops']:.0f} x 1.1/2.25) / 10 slice products")
+        if args.prec == "mixed" and name in ("exchange", "solve"):
             return "alu", peak_fp32, "FP32 SIMT: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz (SGEMM measured 70)"
         return "alu", peak_fp64, "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal 1.25; DGEMM measured 1.10)"
 

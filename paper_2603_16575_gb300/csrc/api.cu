@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -71,6 +72,10 @@ struct osvmp2_ctx {
   std::vector<int> sf_id, pair_id, bt_id;
   std::vector<double*> S_h, F_h, K_h, X_h, et_h, bt_h, Kt_h;
   std::vector<float*> U_h, Gi_h, Gj_h;   // mixed form: per pair U = P X and G = U^T B
+  // mixed form: where the TF32 slices of U_p^T live (allocation base, its rows, first row)
+  std::vector<float*> us_base_h;
+  std::vector<long long> us_alloc_rows_h, us_row_h;
+  int us_ldv = 0;
   std::vector<int> m_h;
   std::vector<int> pi_h, pj_h;       // pair id -> (i, j)
   // last MBE call
@@ -159,6 +164,7 @@ void free_system(osvmp2_ctx* c) {
   c->sf_id.clear(); c->pair_id.clear(); c->bt_id.clear();
   c->S_h.clear(); c->F_h.clear(); c->K_h.clear(); c->X_h.clear(); c->et_h.clear(); c->bt_h.clear(); c->Kt_h.clear();
   c->U_h.clear(); c->Gi_h.clear(); c->Gj_h.clear();
+  c->us_base_h.clear(); c->us_alloc_rows_h.clear(); c->us_row_h.clear();
   c->m_h.clear(); c->pi_h.clear(); c->pj_h.clear();
   c->frags.clear(); c->frag_out.clear();
   c->n_osv_d = nullptr; c->Q_d = nullptr; c->sf_id_d = nullptr; c->S_d = c->F_d = nullptr;
@@ -304,6 +310,7 @@ int reset_pairs(osvmp2_ctx* c) {
   c->bt_id.assign(nn, -1);
   c->S_h.clear(); c->F_h.clear(); c->K_h.clear(); c->X_h.clear(); c->et_h.clear(); c->bt_h.clear(); c->Kt_h.clear();
   c->U_h.clear(); c->Gi_h.clear(); c->Gj_h.clear();
+  c->us_base_h.clear(); c->us_alloc_rows_h.clear(); c->us_row_h.clear();
   c->m_h.clear(); c->pi_h.clear(); c->pj_h.clear(); c->r_h.clear();
   TRY(upload(c, c->sf_id_d, c->sf_id));
   TRY(upload(c, c->pair_id_d, c->pair_id));
@@ -653,6 +660,10 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
     c->U_h.resize(c->K_h.size(), nullptr);
     c->Gi_h.resize(c->K_h.size(), nullptr);
     c->Gj_h.resize(c->K_h.size(), nullptr);
+    c->us_base_h.resize(c->K_h.size(), nullptr);
+    c->us_alloc_rows_h.resize(c->K_h.size(), 0);
+    c->us_row_h.resize(c->K_h.size(), 0);
+    c->us_ldv = ldv;
     size_t uo = 0, go = 0, urow = 0;
     double f_u = 0.0, f_g = 0.0, f_kg = 0.0;
     for (auto& p : newp) {
@@ -662,6 +673,9 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
       uo += (size_t)nv * r;
       c->U_h[pid] = U;
       uj.push_back(UJob{i, j, U, usmem + urow * ldv, ldv});
+      c->us_base_h[pid] = usmem;
+      c->us_alloc_rows_h[pid] = (long long)us_rows;
+      c->us_row_h[pid] = (long long)urow;
       f_u += 2.0 * nv * (double)m * r;
       float* Gi = gmem + go;
       go += (size_t)r * nx;
@@ -1125,6 +1139,98 @@ int osvmp2_mbe3_fragments(const double* r_occ, int32_t n_occ, double r2, double 
   return OSVMP2_OK;
 }
 
+// Mixed form: the overlaps Sigma_(lo,hi) = U_lo^T U_hi of every pair couple that
+// a coupling term of some fragment uses (pair p with the pairs (a,c), (c,b) of
+// its fragment), each computed once on the tensor cores from the U slices.
+struct SigmaStore {
+  Tmp data, off, hi, pos;
+  SigmaTable tab{};
+};
+int build_sigma_table(osvmp2_ctx* c, SigmaStore& ss) {
+  const int n = c->sys.n_occ, npairs = (int)c->K_h.size();
+  std::vector<std::pair<int, int>> cps;
+  for (const Frag& fr : c->frags) {
+    int orbs[3], nc = 0;
+    for (int u = 0; u < 3; u++)
+      if (fr.orbs[u] >= 0) orbs[nc++] = fr.orbs[u];
+    auto pid_of = [&](int x, int y) {
+      const int a = std::min(orbs[x], orbs[y]), b = std::max(orbs[x], orbs[y]);
+      return c->pair_id[(size_t)a * n + b];
+    };
+    for (int a = 0; a < nc; a++)
+      for (int b = a; b < nc; b++) {
+        const int P = pid_of(a, b);
+        for (int k = 0; k < nc; k++) {
+          if (k != b) { const int Q = pid_of(a, k); if (Q != P) cps.push_back({std::min(P, Q), std::max(P, Q)}); }
+          if (k != a) { const int Q = pid_of(k, b); if (Q != P) cps.push_back({std::min(P, Q), std::max(P, Q)}); }
+        }
+      }
+  }
+  std::sort(cps.begin(), cps.end());
+  cps.erase(std::unique(cps.begin(), cps.end()), cps.end());
+  std::vector<int> off(npairs + 1, 0), hi(cps.size());
+  std::vector<long long> pos(cps.size());
+  long long tot = 0;
+  for (size_t u = 0; u < cps.size(); u++) {
+    off[cps[u].first + 1]++;
+    hi[u] = cps[u].second;
+    pos[u] = tot;
+    tot += (long long)c->r_h[cps[u].first] * c->r_h[cps[u].second];
+  }
+  for (int q = 0; q < npairs; q++) off[q + 1] += off[q];
+  TRY(tmp_alloc(c, ss.data, (size_t)std::max<long long>(tot, 1) * sizeof(float)));
+  TRY(tmp_alloc(c, ss.off, off.size() * sizeof(int)));
+  TRY(tmp_alloc(c, ss.hi, std::max<size_t>(hi.size(), 1) * sizeof(int)));
+  TRY(tmp_alloc(c, ss.pos, std::max<size_t>(pos.size(), 1) * sizeof(long long)));
+  CK(cudaMemcpyAsync(ss.off.p, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  if (!cps.empty()) {
+    CK(cudaMemcpyAsync(ss.hi.p, hi.data(), hi.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(ss.pos.p, pos.data(), pos.size() * sizeof(long long), cudaMemcpyHostToDevice, c->st));
+  }
+  ss.tab = SigmaTable{(const int*)ss.off.p, (const int*)ss.hi.p, (const long long*)ss.pos.p, (const float*)ss.data.p};
+  // tensor-core tiles, grouped by the U slice stores of the two pairs
+  std::map<std::pair<const float*, const float*>, std::vector<tc::Job>> groups;
+  for (size_t u = 0; u < cps.size(); u++) {
+    const int lo = cps[u].first, hq = cps[u].second;
+    const int rl = c->r_h[lo], rh = c->r_h[hq];
+    if (!c->us_base_h[lo] || !c->us_base_h[hq]) return fail(c, OSVMP2_E_STATE, "pair without U slices");
+    auto& js = groups[{c->us_base_h[lo], c->us_base_h[hq]}];
+    for (int m0 = 0; m0 < rl; m0 += tc::BM)
+      for (int n0 = 0; n0 < rh; n0 += tc::BN) {
+        tc::Job jb;
+        jb.a_row = (int)(c->us_row_h[lo] + m0);
+        jb.a_sstride = rl;
+        jb.b_row = (int)(c->us_row_h[hq] + n0);
+        jb.b_sstride = rh;
+        jb.m_valid = std::min(tc::BM, rl - m0);
+        jb.n_valid = std::min(tc::BN, rh - n0);
+        jb.out = (float*)ss.data.p + pos[u] + (size_t)m0 * rh + n0;
+        jb.ld_out = rh;
+        jb.m0 = m0;
+        jb.n0 = n0;
+        jb.s = 0.0;
+        js.push_back(jb);
+      }
+  }
+  for (auto& g : groups) {
+    const float* A = g.first.first;
+    const float* B = g.first.second;
+    long long ar = 0, br = 0;
+    for (int q = 0; q < npairs; q++) {
+      if (c->us_base_h[q] == A) ar = c->us_alloc_rows_h[q];
+      if (c->us_base_h[q] == B) br = c->us_alloc_rows_h[q];
+    }
+    Tmp jd;
+    TRY(tmp_alloc(c, jd, g.second.size() * sizeof(tc::Job)));
+    CK(cudaMemcpyAsync(jd.p, g.second.data(), g.second.size() * sizeof(tc::Job), cudaMemcpyHostToDevice, c->st));
+    if (launch_rows_tc(A, ar, B, br, c->sys.n_vir, c->us_ldv, (const tc::Job*)jd.p, (int)g.second.size(), c->err_d,
+                       c->st))
+      return fail(c, OSVMP2_E_CUDA, "tensor-map encoding for the pair-couple overlaps failed");
+    CK(cudaGetLastError());
+  }
+  return 0;
+}
+
 // MBE(3) energy; with tstore != NULL the converged amplitudes of every fragment
 // are kept (fragment f at tstore + toff[f], local pairs a<=b in order).
 static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out,
@@ -1202,11 +1308,15 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
     tdst = (double*)tstore->p;
   }
   SolveOpts so{c->opts.tol_update, c->opts.tol_energy, c->opts.max_iter};
+  SigmaStore sig;
   ph_begin(c, OSVMP2_PH_SOLVE);
-  if (prec == OSVMP2_MIXED)
-    launch_frag_solve_mixed(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, (double*)d_scr.p,
-                            n_cta, (int*)d_cnt.p, (FragOut*)d_out.p, tdst, (const long long*)d_toff.p, c->st);
-  else
+  if (prec == OSVMP2_MIXED) {
+    CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
+    TRY(build_sigma_table(c, sig));
+    launch_frag_solve_mixed(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, sig.tab,
+                            (double*)d_scr.p, n_cta, (int*)d_cnt.p, (FragOut*)d_out.p, tdst,
+                            (const long long*)d_toff.p, c->err_d, c->st);
+  } else
     launch_frag_solve(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, (double*)d_scr.p, n_cta,
                       (int*)d_cnt.p, (FragOut*)d_out.p, tdst, (const long long*)d_toff.p, c->st);
   CK(cudaGetLastError());
@@ -1220,6 +1330,7 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
   CK(cudaMemcpyAsync(e_out, c->scal_d, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   ph_collect(c);
+  if (prec == OSVMP2_MIXED) TRY(check_err_flag(c, "mixed fragment solve"));
   double f_solve = 0.0;
   for (int f = 0; f < nf; f++)
     f_solve += (prec == OSVMP2_MIXED) ? fragment_mixed_flops(c, c->frags[f], c->frag_out[f].iters)

@@ -10,6 +10,7 @@ namespace osv {
 constexpr int NT = 256;          // threads of every CTA that calls the CTA routines
 constexpr int TM = 64, TN = 64, TK = 16;
 constexpr int GEMM_SMEM_DOUBLES = TK * (TM + TN);
+constexpr int GEMM_SMEM_F32 = TK * 2 * 96;   // floats: the 96 x 96 tiles of cta_gemm_f32x64
 
 // ---------------------------------------------------------------- views
 // One dense block: element (r,c) at p[r*ld + c], or at p[c*ld + r] when tr.
@@ -163,6 +164,87 @@ __device__ __forceinline__ void tile_mma_f32x64(int M, int N, int K, int m0, int
   for (int i = 0; i < 4; i++)
 #pragma unroll
     for (int j = 0; j < 4; j++) acc[i][j] += (double)hi[i][j] + (double)lo[i][j];
+}
+
+// FP32 tile of (16 R) x (16 R) outputs, R x R per thread (thread (ty, tx) owns
+// rows m0 + ty + 16 i and columns n0 + tx + 16 j), accumulated in FP32 over
+// the whole K: for the short contractions (K ~ a pair order) of the coupling
+// terms, whose FP32 rounding is scaled down by the off-diagonal Fock
+// elements.  sm: 2 TK 16R floats.
+template <int R, class VA, class VB>
+__device__ __forceinline__ void tile_mma_f32r(int M, int N, int K, int m0, int n0, const VA& A, const VB& B,
+                                              float acc[R][R], float* sm) {
+  constexpr int TMR = 16 * R;
+  float* As = sm;
+  float* Bs = sm + TK * TMR;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int k0 = 0; k0 < K; k0 += TK) {
+#pragma unroll
+    for (int t = 0; t < TMR * TK / NT; t++) {
+      const int e = tid + t * NT, m = e % TMR, k = e / TMR;
+      const int gm = m0 + m, gk = k0 + k;
+      As[k * TMR + m] = (gm < M && gk < K) ? static_cast<float>(A.get(gm, gk)) : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < TMR * TK / NT; t++) {
+      const int e = tid + t * NT, n = e % TMR, k = e / TMR;
+      const int gn = n0 + n, gk = k0 + k;
+      Bs[k * TMR + n] = (gn < N && gk < K) ? static_cast<float>(B.get(gk, gn)) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < TK; k++) {
+      float a[R], b[R];
+#pragma unroll
+      for (int i = 0; i < R; i++) a[i] = As[k * TMR + ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < R; j++) b[j] = Bs[k * TMR + tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int j = 0; j < R; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+}
+
+template <int R, class CT, class VA, class VB>
+__device__ void cta_gemm_f32r(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, CT* C, int ldc,
+                              float* sm) {
+  constexpr int TMR = 16 * R;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += TMR)
+    for (int n0 = 0; n0 < N; n0 += TMR) {
+      float acc[R][R];
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int j = 0; j < R; j++) acc[i][j] = 0.f;
+      tile_mma_f32r<R>(M, N, K, m0, n0, A, B, acc, sm);
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+          const int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
+          if (r < M && c < N) {
+            CT* cp = C + (size_t)r * ldc + c;
+            *cp = static_cast<CT>((beta == 0.0 ? 0.0 : beta * static_cast<double>(*cp)) + alpha * (double)acc[i][j]);
+          }
+        }
+    }
+  __syncthreads();
+}
+
+// C = beta C + alpha A B for short K (<= a few hundred) in FP32 (tile_mma_f32r),
+// 64 x 64 tiles for outputs up to 64 x 64 and 96 x 96 tiles (one pass over
+// the usual pair orders ~80) above; sm holds GEMM_SMEM_F32 floats.
+template <class CT, class VA, class VB>
+__device__ void cta_gemm_f32s(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, CT* C, int ldc,
+                              float* sm) {
+  if (M > TM || N > TN)
+    cta_gemm_f32r<6>(M, N, K, alpha, A, B, beta, C, ldc, sm);
+  else
+    cta_gemm_f32r<4>(M, N, K, alpha, A, B, beta, C, ldc, sm);
 }
 
 // C[MxN] (ld ldc, element type CT) = beta*C + alpha*A*B with FP32 products

@@ -61,6 +61,13 @@ struct EpiG {
   }
 };
 
+// out[row][col] = hi + lo (row-major)
+struct EpiRow {
+  __device__ __forceinline__ void operator()(const tc::Job& jb, int r, int c, float h, float l) const {
+    static_cast<float*>(jb.out)[(size_t)r * jb.ld_out + c] = h + l;
+  }
+};
+
 namespace {
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -98,6 +105,20 @@ int launch_gproj_tc(const float* Bs, long long a_rows, const float* Us, long lon
   if (!make_slice_map(&ma, Bs, n_vir, ldv, a_rows, tc::BM) || !make_slice_map(&mb, Us, n_vir, ldv, b_rows, tc::BROWS))
     return -1;
   tc::k_tf32x3<EpiG><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_vir, err, EpiG{});
+  note_launch(1);
+  return 0;
+}
+
+int launch_rows_tc(const float* A, long long a_rows, const float* B, long long b_rows, int n_vir, int ldv,
+                   const tc::Job* jobs, int n_jobs, int* err, cudaStream_t st) {
+  if (!n_jobs) return 0;
+  if (cudaFuncSetAttribute(tc::k_tf32x3<EpiRow>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) !=
+      cudaSuccess)
+    return -1;
+  CUtensorMap ma, mb;
+  if (!make_slice_map(&ma, A, n_vir, ldv, a_rows, tc::BM) || !make_slice_map(&mb, B, n_vir, ldv, b_rows, tc::BROWS))
+    return -1;
+  tc::k_tf32x3<EpiRow><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_vir, err, EpiRow{});
   note_launch(1);
   return 0;
 }

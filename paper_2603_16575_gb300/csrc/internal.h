@@ -158,14 +158,27 @@ struct KtJob {
 };
 void launch_ktilde(const Tables& t, const KtJob* jobs, int n_jobs, double* scratch, int n_cta, int max_m,
                    cudaStream_t st);
-// per CTA: Y, C (6 + 6 FP64) + Y32 (6 FP32) + 24 Sigma + 1 work (FP32)
+// per CTA: Y, C, 1/D (6 + 6 + 6 FP64) + Y32 (6 FP32) + 1 work (FP32)
 __host__ __device__ inline size_t frag_mixed_scratch_doubles(int max_m) {
   const size_t M2 = (size_t)max_m * max_m;
-  return 12 * M2 + (31 * M2 + 1) / 2 + 64;
+  return 18 * M2 + (7 * M2 + 1) / 2 + 64;
 }
+// Pair-couple overlaps Sigma_(lo,hi) = U_lo^T U_hi (pair ids lo < hi) of one MBE
+// call, stored [r_lo][r_hi] at base + pos[id]; the ids of couples (lo, *) are
+// off[lo] .. off[lo+1]-1 with partner hi[id] ascending.
+struct SigmaTable {
+  const int* off;
+  const int* hi;
+  const long long* pos;
+  const float* base;
+};
 void launch_frag_solve_mixed(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
-                             SolveOpts o, double* scratch, int n_cta, int* counter, FragOut* out, double* Tstore,
-                             const long long* Toff, cudaStream_t st);
+                             SolveOpts o, const SigmaTable& sgt, double* scratch, int n_cta, int* counter,
+                             FragOut* out, double* Tstore, const long long* Toff, int* err, cudaStream_t st);
+// Row-major tiles of U-slice products (gproj_tc.cu): out[row * ld_out + col] = A_row . B_col,
+// A and B tensor maps over (possibly different) U slice stores with K = n_vir.
+int launch_rows_tc(const float* A, long long a_rows, const float* B, long long b_rows, int n_vir, int ldv,
+                   const tc::Job* jobs, int n_jobs, int* err, cudaStream_t st);
 
 // E = sum_f w_f * E_f in a fixed order -> e_out (device scalar)
 void launch_weighted_sum(const FragOut* out, const int* weights, int n, double* e_out, cudaStream_t st);

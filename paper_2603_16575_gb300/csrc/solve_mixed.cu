@@ -50,31 +50,47 @@ struct MTerm {     // one coupling term of local pair p: coef * Sigma[sig] op(Y_
 
 constexpr int MAX_TERMS = 24;   // 6 pairs x 4 coupling terms (three-orbital fragments)
 
-__global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __restrict__ frag_orbs,
+// Sigma_(lo,hi) = U_lo^T U_hi of pair ids lo < hi, stored [r_lo][r_hi]: entry
+// id of (lo, hi) is found in hi_id[off[lo] .. off[lo+1]) (ascending), its data
+// at base + pos[id].
+__device__ __forceinline__ const float* sigma_lookup(const SigmaTable& st, int lo, int hi) {
+  int a = st.off[lo], b = st.off[lo + 1];
+  while (a < b) {
+    const int mid = (a + b) >> 1;
+    if (st.hi[mid] < hi) a = mid + 1;
+    else b = mid;
+  }
+  return (a < st.off[lo + 1] && st.hi[a] == hi) ? st.base + st.pos[a] : nullptr;
+}
+
+__global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int* __restrict__ frag_orbs,
                                                          const int* __restrict__ order, int n_frag, int max_m,
-                                                         SolveOpts o, double* scratch, int* counter, FragOut* out,
-                                                         double* Tstore, const long long* __restrict__ Toff) {
-  __shared__ float fsm[GEMM_SMEM_DOUBLES];
+                                                         SolveOpts o, SigmaTable sgt, double* scratch, int* counter,
+                                                         FragOut* out, double* Tstore,
+                                                         const long long* __restrict__ Toff, int* err) {
+  __shared__ float fsm[GEMM_SMEM_F32];
   __shared__ double red[40];
   __shared__ int s_f;
   __shared__ MTerm terms[6][8];
   __shared__ int nterm[6];
   __shared__ int sig_p[MAX_TERMS], sig_q[MAX_TERMS];
   __shared__ int s_nsig;
+  __shared__ const float* sig_ptr[MAX_TERMS];   // Sigma_pq = sig_ptr (ld sig_ld), transposed when sig_tr
+  __shared__ int sig_ld[MAX_TERMS], sig_tr[MAX_TERMS];
   const size_t M2 = (size_t)max_m * max_m;
   double* base = scratch + (size_t)blockIdx.x * frag_mixed_scratch_doubles(max_m);
   double* Y64[6];
   double* C64[6];
+  double* invD[6];
   float* Y32[6];
-  float* Sig[MAX_TERMS];
   for (int u = 0; u < 6; u++) {
     Y64[u] = base + u * M2;
     C64[u] = base + (6 + u) * M2;
+    invD[u] = base + (12 + u) * M2;
   }
-  float* fb = reinterpret_cast<float*>(base + 12 * M2);
+  float* fb = reinterpret_cast<float*>(base + 18 * M2);
   for (int u = 0; u < 6; u++) Y32[u] = fb + u * M2;
-  for (int u = 0; u < MAX_TERMS; u++) Sig[u] = fb + (6 + u) * M2;
-  float* W32 = fb + (6 + MAX_TERMS) * M2;
+  float* W32 = fb + 6 * M2;
   const double* f = t.f_occ;
   const int n = t.n_occ;
   while (true) {
@@ -133,17 +149,30 @@ __global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __
       s_nsig = ns;
     }
     __syncthreads();
-    // Sigma_pq = X_p^T S_(p,q) X_q = U_p^T U_q  (FP32 products of orthonormal bases)
-    for (int u = 0; u < s_nsig; u++) {
-      const int p = sig_p[u], q = sig_q[u];
-      cta_gemm_f32x64<float>(pr[p], pr[q], t.n_vir, 1.0, ViewF{t.U[pid[p]], pr[p], 1}, ViewF{t.U[pid[q]], pr[q], 0},
-                             0.0, Sig[u], pr[q], fsm);
+    // Sigma_pq = X_p^T S_(p,q) X_q = U_p^T U_q from the table built before the
+    // launch (split-precision tensor-core products, one per pair couple)
+    for (int u = threadIdx.x; u < s_nsig; u += NT) {
+      const int P = pid[sig_p[u]], Q = pid[sig_q[u]];
+      const int lo = min(P, Q), hi = max(P, Q);
+      const float* sp = sigma_lookup(sgt, lo, hi);
+      if (!sp) atomicOr(err, ERR_SIZE);
+      sig_ptr[u] = sp;
+      sig_ld[u] = t.r[hi];
+      sig_tr[u] = (P != lo);
     }
-    for (int p = 0; p < np; p++)
-      for (int idx = threadIdx.x; idx < pr[p] * pr[p]; idx += NT) {
+    __syncthreads();
+    bool sig_ok = true;
+    for (int u = 0; u < s_nsig; u++) sig_ok &= sig_ptr[u] != nullptr;
+    for (int p = 0; p < np; p++) {
+      const int rp = pr[p];
+      const double fij = f[orbs[pa[p]] * n + orbs[pa[p]]] + f[orbs[pb[p]] * n + orbs[pb[p]]];
+      const double* et = t.et[pid[p]];
+      for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
         Y64[p][idx] = 0.0;
         Y32[p][idx] = 0.f;
+        invD[p][idx] = 1.0 / (fij - et[idx / rp] - et[idx % rp]);   // update denominators, once per fragment
       }
+    }
     __syncthreads();
     double e_prev = 0.0, e = 0.0, um = 0.0;
     int status = ERR_NOCONV, iters = o.max_iter;
@@ -153,13 +182,13 @@ __global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __
         const int rp = pr[p];
         for (int idx = threadIdx.x; idx < rp * rp; idx += NT) C64[p][idx] = 0.0;
         __syncthreads();
-        for (int u = 0; u < nterm[p]; u++) {
+        for (int u = 0; u < nterm[p] && sig_ok; u++) {
           const MTerm tm = terms[p][u];
           const int rq = pr[tm.q];
-          const ViewF S{Sig[tm.sig], rq, 0};
-          cta_gemm_f32x64<float>(rq, rp, rq, 1.0, ViewF{Y32[tm.q], rq, tm.tr}, ViewF{Sig[tm.sig], rq, 1}, 0.0, W32,
-                                 rp, fsm);
-          cta_gemm_f32x64<double>(rp, rp, rq, tm.coef, S, ViewF{W32, rp, 0}, 1.0, C64[p], rp, fsm);
+          const ViewF S{sig_ptr[tm.sig], sig_ld[tm.sig], sig_tr[tm.sig]};        // Sigma_pq   (r_p x r_q)
+          const ViewF St{sig_ptr[tm.sig], sig_ld[tm.sig], !sig_tr[tm.sig]};      // Sigma_pq^T (r_q x r_p)
+          cta_gemm_f32s<float>(rq, rp, rq, 1.0, ViewF{Y32[tm.q], rq, tm.tr}, St, 0.0, W32, rp, fsm);
+          cta_gemm_f32s<double>(rp, rp, rq, tm.coef, S, ViewF{W32, rp, 0}, 1.0, C64[p], rp, fsm);
         }
       }
       // Y_p <- (K~_p + C_p) / D_p in FP64; energy <K~_p, 2Y_p - Y_p^T>
@@ -167,14 +196,10 @@ __global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __
       e = 0.0;
       for (int p = 0; p < np; p++) {
         const int rp = pr[p];
-        const int i = orbs[pa[p]], j = orbs[pb[p]];
-        const double fij = f[i * n + i] + f[j * n + j];
-        const double* et = t.et[pid[p]];
         const double* Kt = t.Kt[pid[p]];
         double du = 0.0;
         for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
-          const int r = idx / rp, c = idx % rp;
-          const double y = (Kt[idx] + C64[p][idx]) / (fij - et[r] - et[c]);
+          const double y = (Kt[idx] + C64[p][idx]) * invD[p][idx];
           du = fmax(du, fabs(y - Y64[p][idx]));
           Y64[p][idx] = y;
         }
@@ -210,11 +235,12 @@ __global__ void __launch_bounds__(NT) k_frag_solve_mixed(Tables t, const int* __
 }
 
 void launch_frag_solve_mixed(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
-                             SolveOpts o, double* scratch, int n_cta, int* counter, FragOut* out, double* Tstore,
-                             const long long* Toff, cudaStream_t st) {
+                             SolveOpts o, const SigmaTable& sgt, double* scratch, int n_cta, int* counter,
+                             FragOut* out, double* Tstore, const long long* Toff, int* err, cudaStream_t st) {
   if (n_frag == 0) return;
   cudaMemsetAsync(counter, 0, sizeof(int), st);
-  k_frag_solve_mixed<<<n_cta, NT, 0, st>>>(t, frag_orbs, order, n_frag, max_m, o, scratch, counter, out, Tstore, Toff);
+  k_frag_solve_mixed<<<n_cta, NT, 0, st>>>(t, frag_orbs, order, n_frag, max_m, o, sgt, scratch, counter, out, Tstore,
+                                           Toff, err);
   note_launch(1);
 }
 
