@@ -260,7 +260,7 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.prec == "fp64" else "f64+split-f32",
+        "dtype": "f64" if args.prec == "fp64" else "split-tf32+f32+f64",
         "data": "synthetic",
         "config": {"workload": f"{args.workload} (n_occ={s.n_occ}, n_vir={s.n_vir}, n_aux={s.n_aux}, "
                                f"lambda={s.lam} A, l_osv={L_OSV}, r2={R2_CUT} A, r3={R3_CUT} A)",
@@ -348,7 +348,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--prec", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--workload", default="mbe3_n128", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--b-mode", choices=["regen", "stored"], default="regen")
     ap.add_argument("--grad", action="store_true")

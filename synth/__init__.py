@@ -192,6 +192,8 @@ WORKLOADS = {
     "osv_n256": dict(n_occ=256, n_vir=1200, n_aux=4800, lam=1.0, geometry="box"),
     "mbe3_n128": dict(n_occ=128, n_vir=640, n_aux=2400, lam=1.0, geometry="box"),
     "mbe3_n32": dict(n_occ=32, n_vir=160, n_aux=600, lam=1.0, geometry="box"),
+    # the per-orbital shapes of mbe3_n128 on fewer orbitals (kernel captures of a few GB)
+    "mbe3_n48": dict(n_occ=48, n_vir=640, n_aux=2400, lam=1.0, geometry="box"),
     "grad_n64": dict(n_occ=64, n_vir=320, n_aux=1200, lam=1.0, geometry="box"),
     "chain_n800": dict(n_occ=800, n_vir=6000, n_aux=16000, lam=1.0, geometry="chain"),
 }
