@@ -15,6 +15,10 @@
 #include "osvmp2.h"
 #include "internal.h"
 
+namespace {
+constexpr int PW_MAX_ORDER = 192;   // largest pair order of the one-warp preconditioners
+}
+
 using namespace osv;
 
 namespace osv {
@@ -65,6 +69,8 @@ struct osvmp2_ctx {
   double** et_d = nullptr;
   double** Kt_d = nullptr;
   float** U_d = nullptr;
+  float** Sh_d = nullptr;
+  float** Gh_d = nullptr;
   int* r_d = nullptr;
   int* err_d = nullptr;
   double* scal_d = nullptr;          // device scalars (energies)
@@ -72,6 +78,7 @@ struct osvmp2_ctx {
   std::vector<int> sf_id, pair_id, bt_id;
   std::vector<double*> S_h, F_h, K_h, X_h, et_h, bt_h, Kt_h;
   std::vector<float*> U_h, Gi_h, Gj_h;   // mixed form: per pair U = P X and G = U^T B
+  std::vector<float*> Sh_h, Gh_h;        // mixed form: preconditioner leftovers (NULL: exact X)
   // mixed form: where the TF32 slices of U_p^T live (allocation base, its rows, first row)
   std::vector<float*> us_base_h;
   std::vector<long long> us_alloc_rows_h, us_row_h;
@@ -163,12 +170,13 @@ void free_system(osvmp2_ctx* c) {
   c->n_osv.clear(); c->Qp.clear(); c->Wp.clear();
   c->sf_id.clear(); c->pair_id.clear(); c->bt_id.clear();
   c->S_h.clear(); c->F_h.clear(); c->K_h.clear(); c->X_h.clear(); c->et_h.clear(); c->bt_h.clear(); c->Kt_h.clear();
-  c->U_h.clear(); c->Gi_h.clear(); c->Gj_h.clear();
+  c->U_h.clear(); c->Gi_h.clear(); c->Gj_h.clear(); c->Sh_h.clear(); c->Gh_h.clear();
   c->us_base_h.clear(); c->us_alloc_rows_h.clear(); c->us_row_h.clear();
   c->m_h.clear(); c->pi_h.clear(); c->pj_h.clear();
   c->frags.clear(); c->frag_out.clear();
   c->n_osv_d = nullptr; c->Q_d = nullptr; c->sf_id_d = nullptr; c->S_d = c->F_d = nullptr;
   c->pair_id_d = nullptr; c->K_d = c->X_d = c->et_d = c->Kt_d = nullptr; c->r_d = nullptr; c->U_d = nullptr;
+  c->Sh_d = c->Gh_d = nullptr;
 }
 
 Tables tables(const osvmp2_ctx* c) {
@@ -187,6 +195,8 @@ Tables tables(const osvmp2_ctx* c) {
   t.r = c->r_d;
   t.Kt = c->Kt_d;
   t.U = c->U_d;
+  t.Sh = c->Sh_d;
+  t.Gh = c->Gh_d;
   t.f_occ = c->sys.f_occ;
   return t;
 }
@@ -309,7 +319,7 @@ int reset_pairs(osvmp2_ctx* c) {
   c->pair_id.assign(nn, -1);
   c->bt_id.assign(nn, -1);
   c->S_h.clear(); c->F_h.clear(); c->K_h.clear(); c->X_h.clear(); c->et_h.clear(); c->bt_h.clear(); c->Kt_h.clear();
-  c->U_h.clear(); c->Gi_h.clear(); c->Gj_h.clear();
+  c->U_h.clear(); c->Gi_h.clear(); c->Gj_h.clear(); c->Sh_h.clear(); c->Gh_h.clear();
   c->us_base_h.clear(); c->us_alloc_rows_h.clear(); c->us_row_h.clear();
   c->m_h.clear(); c->pi_h.clear(); c->pj_h.clear(); c->r_h.clear();
   TRY(upload(c, c->sf_id_d, c->sf_id));
@@ -546,8 +556,21 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   std::vector<KJob> kj;
   std::vector<PJob> pjb;
   std::vector<int> new_ids;
+  // mixed form with the warp preconditioner: leftovers Sh, Gh (m^2 floats each per pair)
+  const bool mixed_pc = mixed && max_m <= PW_MAX_ORDER;
+  float* shmem = nullptr;
+  if (mixed_pc) {
+    size_t shf = 0;
+    for (auto& p : newp) {
+      const size_t m = pair_dim_h(c, p.first, p.second);
+      shf += 2 * m * m;
+    }
+    TRY(palloc(c, reinterpret_cast<double**>(&shmem), (shf + 1) / 2 + 1));
+  }
+  c->Sh_h.resize(c->K_h.size(), nullptr);
+  c->Gh_h.resize(c->K_h.size(), nullptr);
   {
-    size_t off = 0;
+    size_t off = 0, shoff = 0;
     for (auto& p : newp) {
       const int i = p.first, j = p.second, m = pair_dim_h(c, i, j);
       const int pid = (int)c->K_h.size();
@@ -570,7 +593,16 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
         // no raw-basis exchange block in the mixed form
       } else if (i == j) kj.push_back(KJob{i, j, bt(i, i), nullptr, nullptr, nullptr, K});
       else kj.push_back(KJob{i, j, bt(i, i), bt(i, j), bt(j, i), bt(j, j), K});
-      pjb.push_back(PJob{i, j, X, et, c->r_d + pid});
+      float* Sh = nullptr;
+      float* Gh = nullptr;
+      if (mixed_pc) {
+        Sh = shmem + shoff;
+        Gh = Sh + (size_t)m * m;
+        shoff += 2 * (size_t)m * m;
+      }
+      c->Sh_h.push_back(Sh);
+      c->Gh_h.push_back(Gh);
+      pjb.push_back(PJob{i, j, X, et, c->r_d + pid, Sh, Gh});
     }
   }
   // device tables
@@ -582,6 +614,8 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   TRY(upload(c, c->X_d, c->X_h));
   TRY(upload(c, c->et_d, c->et_h));
   TRY(upload(c, c->Kt_d, c->Kt_h));
+  TRY(upload(c, c->Sh_d, c->Sh_h));
+  TRY(upload(c, c->Gh_d, c->Gh_h));
   // job arrays
   Tmp jsf, jpj, jk, jp, scr;
   TRY(tmp_alloc(c, jsf, sfj.size() * sizeof(SFJob)));
@@ -614,16 +648,44 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   }
   const int n_cta = std::min<int>((int)pjb.size(), 2 * c->num_sms);
   const int n_warps = std::min<int>((int)pjb.size(), 16 * c->num_sms);
-  const bool warp_pc = max_m <= 192;
-  TRY(tmp_alloc(c, scr, std::max((size_t)n_cta * precond_scratch_doubles(max_m),
-                                 warp_pc ? precond_w_scratch_doubles(max_m, n_warps) : (size_t)0) * sizeof(double)));
+  const bool warp_pc = max_m <= PW_MAX_ORDER;
+  TRY(tmp_alloc(c, scr, std::max({(size_t)n_cta * precond_scratch_doubles(max_m),
+                                  warp_pc ? precond_w_scratch_doubles(max_m, n_warps) : (size_t)0,
+                                  mixed_pc ? precond_mixed_scratch_doubles(max_m, n_warps, n_cta) : (size_t)0}) *
+                                     sizeof(double)));
+  Tmp pm_slots, pm_off, pm_m;
+  if (mixed_pc) {
+    std::vector<long long> off(pjb.size());
+    std::vector<int> md(pjb.size());
+    long long tot = 0;
+    for (size_t q = 0; q < pjb.size(); q++) {
+      md[q] = pair_dim_h(c, pjb[q].i, pjb[q].j);
+      off[q] = tot;
+      tot += (long long)precond_mixed_slot_doubles(md[q]);
+    }
+    TRY(tmp_alloc(c, pm_slots, (size_t)tot * sizeof(double)));
+    TRY(tmp_alloc(c, pm_off, off.size() * sizeof(long long)));
+    TRY(tmp_alloc(c, pm_m, md.size() * sizeof(int)));
+    CK(cudaMemcpyAsync(pm_off.p, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(pm_m.p, md.data(), md.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  }
   double f_pc = 0.0;
   for (auto& j : pjb) {
     const double m = pair_dim_h(c, j.i, j.j);
-    f_pc += 9.0 * m * m * m + 2.0 * m * m * m + 2.0 * m * m * m + 9.0 * m * m * m + 2.0 * m * m * m;
+    if (mixed_pc) {   // FP64: 1 - M^T M, its eigen-decomposition, Y^T F Y, X = Y W, W^T S W, W^T F W
+      const double ni = c->n_osv[j.i], nj = (j.i == j.j) ? 0.0 : c->n_osv[j.j];
+      f_pc += 2.0 * ni * nj * nj + 9.0 * nj * nj * nj + 2.0 * (m * m * nj + m * m * m) + 2.0 * m * m * m +
+              8.0 * m * m * m;
+    } else {
+      f_pc += 9.0 * m * m * m + 2.0 * m * m * m + 2.0 * m * m * m + 9.0 * m * m * m + 2.0 * m * m * m;
+    }
   }
   ph_begin(c, OSVMP2_PH_PRECOND);
-  if (warp_pc)
+  if (mixed_pc)
+    launch_precond_mixed(t, c->opts.tau_s, (const PJob*)jp.p, (int)pjb.size(), max_m, (double*)pm_slots.p,
+                         (const long long*)pm_off.p, (const int*)pm_m.p, (double*)scr.p, n_warps, n_cta, c->err_d,
+                         c->st);
+  else if (warp_pc)
     launch_precond_w(t, c->opts.tau_s, (const PJob*)jp.p, (int)pjb.size(), max_m, (double*)scr.p, n_warps, c->err_d,
                      c->st);
   else
@@ -878,6 +940,8 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   TRY(dalloc_t(c, &c->r_d, c->cap_pairs));
   TRY(dalloc_t(c, &c->Kt_d, c->cap_pairs));
   TRY(dalloc_t(c, &c->U_d, c->cap_pairs));
+  TRY(dalloc_t(c, &c->Sh_d, c->cap_pairs));
+  TRY(dalloc_t(c, &c->Gh_d, c->cap_pairs));
   c->sf_id.assign((size_t)n * n, -1);
   c->pair_id.assign((size_t)n * n, -1);
   c->bt_id.assign((size_t)n * n, -1);

@@ -8,7 +8,7 @@
 //  * cta_tridiag_qr  implicit symmetric QR steps with the Wilkinson shift
 //                    (Golub & Van Loan, Matrix Computations, Alg. 8.3.2/8.3.3),
 //                    rotations accumulated into the columns of Z.
-//  * sturm_count / bisection / inverse iteration + back-transformation for the
+//  * sturm_count / multisection / inverse iteration + back-transformation for the
 //    eigenpairs above a threshold, used when only a few OSVs out of a large
 //    virtual space are kept.
 // All routines are called by every thread of a CTA of NT threads.
@@ -353,17 +353,46 @@ __device__ inline int sturm_count(const double* d, const double* e, int n, doubl
   return cnt;
 }
 
-// Eigenvalue with ascending index j of (d, e) by bisection on the Sturm count.
-__device__ inline double bisect_eig(const double* d, const double* e, int n, int j, double lo, double hi,
-                                    double pivmin) {
+// Eigenvalues with ascending indices n-1-t, t < k, of (d, e) by multisection
+// on the Sturm count, called by one warp that handles t = t0, t0 + tstride, ...:
+// g = lane / L lanes per eigenvalue split its interval at L points per step
+// (log2(L+1) bits per Sturm sequence instead of one).  w[t] receives the
+// eigenvalue.
+__device__ inline void multisect_eigs(const double* d, const double* e, int n, int k, int t0, int tstride,
+                                      double lo0, double hi0, double pivmin, double* w) {
+  const int lane = threadIdx.x & 31;
+  const int ng = (k - t0 + tstride - 1) / tstride;          // eigenvalues of this warp
+  if (ng <= 0) return;
+  const int L = max(1, 32 / ng);
+  const int gmax = 32 / L;                                  // groups per pass
   const double eps = 2.220446049250313e-16;
-  for (int it = 0; it < 200; it++) {
-    const double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin || mid <= lo || mid >= hi) break;
-    if (sturm_count(d, e, n, mid, pivmin) <= j) lo = mid;
-    else hi = mid;
+  for (int gb = 0; gb < ng; gb += gmax) {
+    const int g = gb + lane / L, q = lane % L;
+    const int t = t0 + g * tstride;
+    const bool mine = (lane / L < gmax) && (g < ng) && (t < k);
+    const int j = n - 1 - t;
+    double lo = lo0, hi = hi0;
+    bool done = !mine;
+    for (int it = 0; it < 200; it++) {
+      if (!__any_sync(0xffffffffu, !done)) break;
+      const double x = lo + (hi - lo) * (double)(q + 1) / (double)(L + 1);
+      bool above = false;   // more than j eigenvalues below x: eigenvalue j lies below x
+      if (!done) above = sturm_count(d, e, n, x, pivmin) > j;
+      const unsigned bal = __ballot_sync(0xffffffffu, above);
+      if (!done) {
+        const unsigned bits = (bal >> ((lane / L) * L)) & ((L == 32) ? 0xffffffffu : ((1u << L) - 1u));
+        const int qs = bits ? (__ffs(bits) - 1) : L;        // first split point above eigenvalue j
+        const double nlo = (qs == 0) ? lo : lo + (hi - lo) * (double)qs / (double)(L + 1);
+        const double nhi = (qs == L) ? hi : lo + (hi - lo) * (double)(qs + 1) / (double)(L + 1);
+        if (!(nlo > lo || nhi < hi)) done = true;           // no progress at this precision
+        lo = nlo;
+        hi = nhi;
+        if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin) done = true;
+      }
+    }
+    if (mine && q == 0) w[t] = 0.5 * (lo + hi);
   }
-  return 0.5 * (lo + hi);
+  __syncwarp();
 }
 
 // One solve (T - lam I) x = y by Gaussian elimination with partial pivoting on

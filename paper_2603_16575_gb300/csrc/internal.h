@@ -25,6 +25,8 @@ struct Tables {
   const int* r;                 // [n_pairs]
   const double* const* Kt;      // [n_pairs] K~ = X^T K X  [r][r]
   const float* const* U;        // [n_pairs] mixed form: U = P X  [n_vir][r] (FP32)
+  const float* const* Sh;       // [n_pairs] mixed form: X^T S X - 1 [r][r] (FP32), NULL if X is exact
+  const float* const* Gh;       // [n_pairs] mixed form: X^T F X - diag(e~) - (f_ii+f_jj)/2 Sh [r][r]
   const double* f_occ;          // [n_occ][n_occ]
 };
 
@@ -92,11 +94,13 @@ void launch_sf(const Tables& t, const double* e_vir, const SFJob* jobs, int n_jo
                cudaStream_t st);
 
 // ---- A3 (precond.cu)
-struct PJob {            // preconditioner of pair (i,j): X, e~, r
+struct PJob {            // preconditioner of pair (i,j): X, e~, r (+ the mixed form's leftovers)
   int i, j;
   double* X;
   double* et;
   int* r;
+  float* Sh;             // mixed form only: X^T S X - 1          [r][r]
+  float* Gh;             // mixed form only: X^T F X - diag(e~) - (f_ii+f_jj)/2 Sh
 };
 __host__ __device__ inline size_t precond_scratch_doubles(int max_m) {
   return 6 * (size_t)max_m * max_m + 4 * (size_t)max_m + 64;
@@ -107,6 +111,15 @@ void launch_precond(const Tables& t, double tau_s, const PJob* jobs, int n_jobs,
 size_t precond_w_scratch_doubles(int max_m, int n_warps);
 int launch_precond_w(const Tables& t, double tau_s, const PJob* jobs, int n_jobs, int max_m, double* scratch,
                      int n_warps, int* err, cudaStream_t st);
+// Mixed form (precond_mixed.cu): block-structured canonical orthogonalisation in
+// FP64, F' diagonalised in FP32, exact leftovers Sh/Gh; -1 if max_m is too large.
+// Per-pair intermediates: one slot of precond_mixed_slot_doubles(m) at slots + off[job];
+// mdim[job] = pair order m.
+size_t precond_mixed_slot_doubles(int m);
+size_t precond_mixed_scratch_doubles(int max_m, int n_warps, int n_cta);
+int launch_precond_mixed(const Tables& t, double tau_s, const PJob* jobs, int n_jobs, int max_m, double* slots,
+                         const long long* off, const int* mdim, double* scratch, int n_warps, int n_cta, int* err,
+                         cudaStream_t st);
 
 // ---- A4-A5 (solve.cu)
 // Fragments: orbs [n][3] (-1 padded, ascending), order[] = processing order.
@@ -158,10 +171,10 @@ struct KtJob {
 };
 void launch_ktilde(const Tables& t, const KtJob* jobs, int n_jobs, double* scratch, int n_cta, int max_m,
                    cudaStream_t st);
-// per CTA: Y, C, 1/D (6 + 6 + 6 FP64) + Y32 (6 FP32) + 1 work (FP32)
+// per CTA: Y, C, 1/D (6 + 6 + 6 FP64) + Y32 (6 FP32) + 3 work (FP32)
 __host__ __device__ inline size_t frag_mixed_scratch_doubles(int max_m) {
   const size_t M2 = (size_t)max_m * max_m;
-  return 18 * M2 + (7 * M2 + 1) / 2 + 64;
+  return 18 * M2 + (9 * M2 + 1) / 2 + 64;
 }
 // Pair-couple overlaps Sigma_(lo,hi) = U_lo^T U_hi (pair ids lo < hi) of one MBE
 // call, stored [r_lo][r_hi] at base + pos[id]; the ids of couples (lo, *) are

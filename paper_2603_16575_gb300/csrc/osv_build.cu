@@ -1,6 +1,8 @@
 // A0: OSV generation.  T_ii from the RI integrals (Eq. mp2_tkk, positive
 // denominator e_a + e_b - 2 f_ii), its FP64 eigen-decomposition (Eq. osv_gen)
 // and the selection omega >= l_osv of Algorithm 3, all on the GPU.
+#include <algorithm>
+
 #include "eig.cuh"
 #include "internal.h"
 
@@ -129,10 +131,10 @@ __device__ void eig_full_select(double* A, int n, double thr, int kmax, double* 
 }
 
 // Eigenpairs with eigenvalue >= thr only: tridiagonalise, count by Sturm
-// sequence, bisection for the kept eigenvalues, inverse iteration with
+// sequence, multisection for the kept eigenvalues, inverse iteration with
 // Gram-Schmidt inside clusters of close eigenvalues, back-transformation.
 __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, double* w, int* kout,
-                         double* scr, int* err, double* sm) {
+                         double* scr, int* err, double* sm, int vpp) {
   double* d = scr;
   double* e = scr + n;
   double* tau = scr + 2 * n;
@@ -171,7 +173,9 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   }
   __syncthreads();
   const int k = s_k;
-  for (int t = threadIdx.x; t < k; t += NT_EIG) w[t] = bisect_eig(d, e, n, n - 1 - t, s_lo, s_hi, s_piv);
+  // kept eigenvalues by multisection: warps 0-3 (one per SM sub-partition, whose
+  // FP64 pipes work in parallel), several lanes per eigenvalue
+  if ((threadIdx.x >> 5) < 4) multisect_eigs(d, e, n, k, threadIdx.x >> 5, 4, s_lo, s_hi, s_piv, w);
   __syncthreads();
   if (threadIdx.x == 0) {
     const double ortol = 1e-3 * s_norm;
@@ -227,28 +231,55 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   __syncthreads();
   // back-transformation V <- H_0 ... H_{n-3} V: eigenvectors are independent, so
   // each warp applies every reflector (stored contiguously in row kk of A) to
-  // its own vectors, with no CTA-wide barrier.
-  for (int t = warp; t < k; t += NT_EIG / 32) {
-    double* x = V + (size_t)t * n;
-    for (int kk = n - 3; kk >= 0; kk--) {
-      const double tk = tau[kk];
-      if (tk == 0.0) continue;
-      const int L = n - kk - 1;
-      const double* vr = A + (size_t)kk * n + kk + 1;
-      double* xs = x + kk + 1;
-      double s = 0.0;
-      for (int r = lane; r < L; r += 32) s = fma(vr[r], xs[r], s);
-      s = tk * warp_sum(s);
-      for (int r = lane; r < L; r += 32) xs[r] = fma(-vr[r], s, xs[r]);
-      __syncwarp();
+  // its own vector, held in shared memory (vpp vectors per pass), with no
+  // CTA-wide barrier inside a pass.
+  double* xsm = sm + 4 * n + 64;
+  if (vpp == 0) {   // no room in shared memory: the vectors stay in global memory
+    for (int t = warp; t < k; t += NT_EIG / 32) {
+      double* x = V + (size_t)t * n;
+      for (int kk = n - 3; kk >= 0; kk--) {
+        const double tk = tau[kk];
+        if (tk == 0.0) continue;
+        const int L = n - kk - 1;
+        const double* vr = A + (size_t)kk * n + kk + 1;
+        double* xs = x + kk + 1;
+        double s = 0.0;
+        for (int r = lane; r < L; r += 32) s = fma(vr[r], xs[r], s);
+        s = tk * warp_sum(s);
+        for (int r = lane; r < L; r += 32) xs[r] = fma(-vr[r], s, xs[r]);
+        __syncwarp();
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
+  for (int t0 = 0; vpp > 0 && t0 < k; t0 += vpp) {
+    const int nvp = min(vpp, k - t0);
+    for (int idx = threadIdx.x; idx < nvp * n; idx += NT_EIG) xsm[idx] = V[(size_t)t0 * n + idx];
+    __syncthreads();
+    for (int u = warp; u < nvp; u += NT_EIG / 32) {
+      double* x = xsm + (size_t)u * n;
+      for (int kk = n - 3; kk >= 0; kk--) {
+        const double tk = tau[kk];
+        if (tk == 0.0) continue;
+        const int L = n - kk - 1;
+        const double* vr = A + (size_t)kk * n + kk + 1;
+        double* xs = x + kk + 1;
+        double s = 0.0;
+        for (int r = lane; r < L; r += 32) s = fma(vr[r], xs[r], s);
+        s = tk * warp_sum(s);
+        for (int r = lane; r < L; r += 32) xs[r] = fma(-vr[r], s, xs[r]);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nvp * n; idx += NT_EIG) V[(size_t)t0 * n + idx] = xsm[idx];
+    __syncthreads();
+  }
   sign_vectors(V, n, k);
 }
 
 __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double thr, int kmax, double* V, double* w,
-                                                int* kout, double* scratch, int* err, int zsmem) {
+                                                int* kout, double* scratch, int* err, int zsmem, int vpp) {
   extern __shared__ double dyn[];
   const int b = blockIdx.x;
   double* A = T + (size_t)b * nv * nv;
@@ -261,7 +292,7 @@ __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double th
     double* sm = dyn + (size_t)nv * ldz;
     eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zs, ldz, sm);
   } else if (thr > 0.0) {
-    eig_topk(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, dyn);
+    eig_topk(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, dyn, vpp);
   } else {
     double* Zg = scr + 3 * nv;
     eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zg, nv, dyn);
@@ -272,9 +303,16 @@ void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, 
                     double* scratch, int* err, cudaStream_t st) {
   const int zsmem = nv <= ZSMEM_MAX;
   size_t smem = (size_t)(4 * nv + 64) * sizeof(double);
+  int vpp = 0;
   if (zsmem) smem += (size_t)nv * (nv + 1) * sizeof(double);
+  else if (thr > 0.0) {   // eigenvectors of the back-transformation in shared memory, one per warp and pass
+    const size_t cap = (size_t)200 * 1024;
+    const size_t avail = cap > smem ? cap - smem : 0;
+    vpp = (int)std::min<size_t>(NT_EIG / 32, avail / ((size_t)nv * sizeof(double)));
+    smem += (size_t)vpp * nv * sizeof(double);
+  }
   cudaFuncSetAttribute(k_eig_osv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_eig_osv<<<nb, NT_EIG, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem);
+  k_eig_osv<<<nb, NT_EIG, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem, vpp);
   note_launch(1);
 }
 

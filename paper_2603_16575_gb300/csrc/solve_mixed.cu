@@ -8,6 +8,12 @@
 // pair-diagonal F/S terms collapse to -D o Y exactly (X^T S X = 1,
 // X^T F X = diag(e~)).  The update is Y_p <- (K~_p + C_p) / D_p.
 //
+// When the preconditioner basis is only approximate (X^T S X = 1 + Sh,
+// X^T F X = diag(e~) + Fh, see precond_mixed.cu) the pair-diagonal terms give
+// -D o Y_p + P_p(Y_p) with P = Gh (Y S~) + (S~ Y) Gh + G0 (Y Sh) + (Sh Y) G0,
+// Gh = Fh - (f_ii+f_jj)/2 Sh, G0 = diag(e~) - (f_ii+f_jj)/2; P is added to C_p,
+// so the fixed point is the exact one.  Sh and Gh are ~1e-7, their products FP32.
+//
 // Precision: the coupling C_p carries the off-diagonal occupied Fock elements
 // (|c_t| ~ 1e-2 against |D| ~ 1), so the rounding of its FP32 products perturbs
 // Y by ~ eps_32 |c| / |D| ~ 1e-9 relative.  C_p and Sigma_pq are FP32 products
@@ -91,6 +97,8 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
   float* fb = reinterpret_cast<float*>(base + 18 * M2);
   for (int u = 0; u < 6; u++) Y32[u] = fb + u * M2;
   float* W32 = fb + 6 * M2;
+  float* A1 = fb + 7 * M2;
+  float* A2 = fb + 8 * M2;
   const double* f = t.f_occ;
   const int n = t.n_occ;
   while (true) {
@@ -189,6 +197,25 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
           const ViewF St{sig_ptr[tm.sig], sig_ld[tm.sig], !sig_tr[tm.sig]};      // Sigma_pq^T (r_q x r_p)
           cta_gemm_f32s<float>(rq, rp, rq, 1.0, ViewF{Y32[tm.q], rq, tm.tr}, St, 0.0, W32, rp, fsm);
           cta_gemm_f32s<double>(rp, rp, rq, tm.coef, S, ViewF{W32, rp, 0}, 1.0, C64[p], rp, fsm);
+        }
+        // leftovers of an inexact preconditioner basis (S~ = 1 + Sh, G0 = diag(e~) - (f_ii+f_jj)/2):
+        // P = Gh (Y S~) + (S~ Y) Gh + G0 (Y Sh) + (Sh Y) G0
+        const float* Sh = t.Sh ? t.Sh[pid[p]] : nullptr;
+        if (Sh) {
+          const float* Gh = t.Gh[pid[p]];
+          const double* et = t.et[pid[p]];
+          const double fh = 0.5 * (f[orbs[pa[p]] * n + orbs[pa[p]]] + f[orbs[pb[p]] * n + orbs[pb[p]]]);
+          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Y32[p], rp, 0}, ViewF{Sh, rp, 0}, 0.0, A1, rp, fsm);
+          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Sh, rp, 0}, ViewF{Y32[p], rp, 0}, 0.0, A2, rp, fsm);
+          for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
+            const int a = idx / rp, b = idx % rp;
+            C64[p][idx] += (et[a] - fh) * (double)A1[idx] + (et[b] - fh) * (double)A2[idx];
+            A1[idx] += Y32[p][idx];
+            A2[idx] += Y32[p][idx];
+          }
+          __syncthreads();
+          cta_gemm_f32s<double>(rp, rp, rp, 1.0, ViewF{Gh, rp, 0}, ViewF{A1, rp, 0}, 1.0, C64[p], rp, fsm);
+          cta_gemm_f32s<double>(rp, rp, rp, 1.0, ViewF{A2, rp, 0}, ViewF{Gh, rp, 0}, 1.0, C64[p], rp, fsm);
         }
       }
       // Y_p <- (K~_p + C_p) / D_p in FP64; energy <K~_p, 2Y_p - Y_p^T>

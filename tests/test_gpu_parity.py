@@ -92,6 +92,28 @@ def test_preconditioner_invariants_and_spectrum():
     ctx.close()
 
 
+def test_mixed_preconditioner_spans_and_spectrum():
+    """Mixed form: block-structured canonical orthogonalisation (FP64) and F' diagonalised
+    in FP32: same rank and spectrum as the oracle to FP32 accuracy; the leftovers
+    X^T S X - 1 and X^T F X - diag(e~) are small (the solver adds them exactly)."""
+    s = synth.make_system(4, 60, 90, seed=8, lam=1.5)
+    ctx = _ctx()
+    _build(ctx, s, 1e-4)
+    pairs = [(0, 1), (0, 3), (2, 2)]
+    ctx.pair_integrals(pairs, prec="mixed")
+    for (i, j) in pairs:
+        X, et = (x.cpu().numpy() for x in ctx.get_precond(i, j))
+        _, S, F = (x.cpu().numpy() for x in ctx.get_pair_blocks(i, j))
+        r = X.shape[1]
+        Xr, er = oracle.preconditioner(S, F, 1e-10)
+        assert Xr.shape[1] == r
+        scale = max(1.0, np.abs(er).max())
+        assert np.abs(X.T @ S @ X - np.eye(r)).max() < 1e-4
+        assert np.abs(X.T @ F @ X - np.diag(et)).max() < 1e-4 * scale
+        assert np.allclose(np.sort(et), np.sort(er), atol=1e-5 * scale)
+    ctx.close()
+
+
 # ---------------------------------------------------------------- full solve
 @pytest.mark.parametrize("stored", [False, True])
 def test_untruncated_solve_equals_closed_form(stored):
