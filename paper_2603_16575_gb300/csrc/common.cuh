@@ -235,6 +235,47 @@ __device__ void cta_gemm_f32r(int M, int N, int K, double alpha, const VA& A, co
   __syncthreads();
 }
 
+// (Chi, Clo) += alpha A B for short K in FP32 (tile_mma_f32r), each product
+// folded into the compensated pair (Chi, Clo) with a two-sum: accumulation
+// across many calls without FP64 arithmetic.
+template <int R, class VA, class VB>
+__device__ void cta_gemm_f32r_acc2(int M, int N, int K, float alpha, const VA& A, const VB& B, float* Chi, float* Clo,
+                                   int ldc, float* sm) {
+  constexpr int TMR = 16 * R;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += TMR)
+    for (int n0 = 0; n0 < N; n0 += TMR) {
+      float acc[R][R];
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int j = 0; j < R; j++) acc[i][j] = 0.f;
+      tile_mma_f32r<R>(M, N, K, m0, n0, A, B, acc, sm);
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+          const int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
+          if (r < M && c < N) {
+            const size_t o = (size_t)r * ldc + c;
+            float s, e;
+            two_sum_f(Chi[o], alpha * acc[i][j], s, e);
+            Chi[o] = s;
+            Clo[o] += e;
+          }
+        }
+    }
+  __syncthreads();
+}
+template <class VA, class VB>
+__device__ void cta_gemm_f32s_acc2(int M, int N, int K, float alpha, const VA& A, const VB& B, float* Chi, float* Clo,
+                                   int ldc, float* sm) {
+  if (M > TM || N > TN)
+    cta_gemm_f32r_acc2<6>(M, N, K, alpha, A, B, Chi, Clo, ldc, sm);
+  else
+    cta_gemm_f32r_acc2<4>(M, N, K, alpha, A, B, Chi, Clo, ldc, sm);
+}
+
 // C = beta C + alpha A B for short K (<= a few hundred) in FP32 (tile_mma_f32r),
 // 64 x 64 tiles for outputs up to 64 x 64 and 96 x 96 tiles (one pass over
 // the usual pair orders ~80) above; sm holds GEMM_SMEM_F32 floats.

@@ -205,6 +205,150 @@ __device__ inline void cta_tridiag_col(double* A, int n, int lda, double* d, dou
   __syncthreads();
 }
 
+// Householder tridiagonalisation of the symmetric A (row-major, lda, global
+// memory) keeping only its lower triangle, for the OSV eigenproblem.  Each
+// step fuses the rank-2 update of the previous reflector with the symmetric
+// matvec of the current one, in one pass over the lower triangle of the
+// trailing block: per stored element two FMAs of the update and two of the
+// matvec (its column sum and, through a shared-memory tile, its row sum),
+// against three FMAs per element of the full matrix and three passes over it
+// in cta_tridiag_col.  The trailing block is cut into 32 x 32 tiles, handled
+// by ntw warps in a fixed order; their partial sums go to gpart and are added
+// in a fixed order, so the result is deterministic.
+// Outputs as cta_tridiag_col: d, e, tau, and reflector k in row k to the right
+// of the diagonal (A[k][k+1+t] = v_t, v_0 = 1).
+// sm: 4 n + 64 doubles (vp, wp, vk, p, red) + ntw * 32 * 33 doubles of tiles;
+// gpart: nb (nb + 1) / 2 * 64 doubles, nb = ceil((n - 1) / 32).
+template <int NTH>
+__device__ inline void cta_tridiag_sym(double* A, int n, int lda, double* d, double* e, double* tau, double* sm,
+                                       int ntw, double* gpart) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* vp = sm;            // previous reflector v_{k-1}, by global index (0 outside its range)
+  double* wp = vp + n;        // previous w_{k-1}
+  double* vk = wp + n;        // current reflector v_k
+  double* p = vk + n;         // A_k v_k, then w_k
+  double* red = p + n;        // 64
+  double* tiles = red + 64;   // ntw x 32 x 33
+  __shared__ double s_tc, s_sc;
+  for (int t = tid; t < n; t += NTH) { vp[t] = 0.0; wp[t] = 0.0; }
+  __syncthreads();
+  for (int k = 0; k + 2 < n; k++) {
+    const int L = n - k - 1, k1 = k + 1;
+    // (a) column k (rows k..n-1) receives the previous update
+    double part = 0.0;
+    for (int r = k + tid; r < n; r += NTH) {
+      double a = A[(size_t)r * lda + k];
+      if (k > 0) a = fma(-wp[r], vp[k], fma(-vp[r], wp[k], a));
+      if (r == k) d[k] = a;
+      else {
+        vk[r] = a;
+        if (r > k1) part += a * a;
+      }
+    }
+    // (b) Householder reflector of column k below the diagonal
+    const double sigma = cta_sum(part, red);
+    if (tid == 0) {
+      const double alpha = vk[k1];
+      double tu = 0.0, beta = alpha, sc = 0.0;
+      if (sigma > 0.0) {
+        const double mu = sqrt(alpha * alpha + sigma);
+        beta = alpha <= 0.0 ? mu : -mu;
+        tu = (beta - alpha) / beta;
+        sc = 1.0 / (alpha - beta);
+      }
+      s_tc = tu;
+      s_sc = sc;
+      e[k] = beta;
+      tau[k] = tu;
+    }
+    __syncthreads();
+    const double tk = s_tc, sc = s_sc;
+    for (int r = k1 + tid; r < n; r += NTH) {
+      const double v = (r == k1) ? 1.0 : vk[r] * sc;
+      vk[r] = (tk != 0.0) ? v : 0.0;
+      A[(size_t)k * lda + r] = v;                 // reflector, row storage
+    }
+    for (int t = tid; t < k1; t += NTH) vk[t] = 0.0;
+    __syncthreads();
+    // (c) fused sweep over the lower triangle of the trailing block
+    const int nb = (L + 31) >> 5;
+    const int ntile = nb * (nb + 1) / 2;
+    if (warp < ntw) {
+      double* tb = tiles + (size_t)warp * 32 * 33;
+      for (int tl = warp; tl < ntile; tl += ntw) {
+        int bi = 0;
+        while ((bi + 1) * (bi + 2) / 2 <= tl) bi++;
+        const int bj = tl - bi * (bi + 1) / 2;
+        const int r0 = k1 + 32 * bi, c0 = k1 + 32 * bj;
+        const int c = c0 + lane;
+        const bool cin = c < n;
+        const double vpc = cin ? vp[c] : 0.0, wpc = cin ? wp[c] : 0.0;
+        double colsum = 0.0;
+        for (int i = 0; i < 32; i++) {
+          const int r = r0 + i;
+          double a = 0.0;
+          if (cin && r < n && r >= c) {
+            double* ap = A + (size_t)r * lda + c;
+            a = *ap;
+            if (k > 0) {
+              a = fma(-wp[r], vpc, fma(-vp[r], wpc, a));
+              *ap = a;
+            }
+            colsum = fma(a, vk[r], colsum);
+          }
+          tb[i * 33 + lane] = (r > c) ? a : 0.0;   // the row sums take the strictly lower part
+        }
+        __syncwarp();
+        double rowsum = 0.0;
+        for (int j = 0; j < 32; j++) rowsum = fma(tb[lane * 33 + j], vk[min(c0 + j, n - 1)], rowsum);   // tb = 0 past n
+        double* gp = gpart + (size_t)tl * 64;
+        gp[lane] = colsum;
+        gp[32 + lane] = rowsum;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // (d) p = A_k v_k from the partial sums (fixed order), then w_k
+    double pv = 0.0;
+    for (int c = k1 + tid; c < n; c += NTH) {
+      const int b = (c - k1) >> 5, o = (c - k1) & 31;
+      double s = 0.0;
+      for (int bi = b; bi < nb; bi++) s += gpart[(size_t)(bi * (bi + 1) / 2 + b) * 64 + o];        // column sums
+      for (int bj = 0; bj <= b; bj++) s += gpart[(size_t)(b * (b + 1) / 2 + bj) * 64 + 32 + o];   // row sums
+      s *= tk;
+      p[c] = s;
+      pv += s * vk[c];
+    }
+    const double Kc = 0.5 * tk * cta_sum(pv, red);
+    for (int c = tid; c < n; c += NTH) {
+      const double w = (c >= k1) ? p[c] - Kc * vk[c] : 0.0;
+      wp[c] = w;
+      vp[c] = vk[c];
+    }
+    __syncthreads();
+  }
+  // the trailing 2 x 2 block receives the last update
+  if (tid == 0) {
+    if (n >= 2) {
+      const int a0 = n - 2, a1 = n - 1;
+      double x00 = A[(size_t)a0 * lda + a0], x10 = A[(size_t)a1 * lda + a0], x11 = A[(size_t)a1 * lda + a1];
+      if (n >= 3) {
+        x00 -= 2.0 * vp[a0] * wp[a0];
+        x10 -= vp[a1] * wp[a0] + wp[a1] * vp[a0];
+        x11 -= 2.0 * vp[a1] * wp[a1];
+        tau[n - 2] = 0.0;
+      }
+      d[a0] = x00;
+      e[a0] = x10;
+      d[a1] = x11;
+    } else {
+      d[0] = A[0];
+    }
+    tau[n - 1] = 0.0;
+  }
+  __syncthreads();
+}
+
 // Z (n x n, row-major, ldz) = H_0 H_1 ... H_{n-3} from the reflectors left in A.
 // y, vs: shared scratch of n doubles each.
 template <int NTH = NT>

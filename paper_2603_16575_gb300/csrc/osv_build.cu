@@ -134,7 +134,7 @@ __device__ void eig_full_select(double* A, int n, double thr, int kmax, double* 
 // sequence, multisection for the kept eigenvalues, inverse iteration with
 // Gram-Schmidt inside clusters of close eigenvalues, back-transformation.
 __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, double* w, int* kout,
-                         double* scr, int* err, double* sm, int vpp) {
+                         double* scr, int* err, double* sm, int ntw) {
   double* d = scr;
   double* e = scr + n;
   double* tau = scr + 2 * n;
@@ -144,7 +144,8 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   double* red = sm + 2 * n;
   __shared__ int s_k, s_nclu;
   __shared__ double s_lo, s_hi, s_piv, s_norm;
-  cta_tridiag_col<NT_EIG>(A, n, n, d, e, tau, v, p, red);
+  if (ntw >= 2) cta_tridiag_sym<NT_EIG>(A, n, n, d, e, tau, sm, ntw, scr + 3 * n);   // partial sums in the Z room
+  else cta_tridiag_col<NT_EIG>(A, n, n, d, e, tau, v, p, red);
   // Gershgorin bounds and a pivot floor
   double glo = 1e300, ghi = -1e300, nrm = 0.0, emax = 0.0;
   for (int t = threadIdx.x; t < n; t += NT_EIG) {
@@ -231,55 +232,28 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   __syncthreads();
   // back-transformation V <- H_0 ... H_{n-3} V: eigenvectors are independent, so
   // each warp applies every reflector (stored contiguously in row kk of A) to
-  // its own vector, held in shared memory (vpp vectors per pass), with no
-  // CTA-wide barrier inside a pass.
-  double* xsm = sm + 4 * n + 64;
-  if (vpp == 0) {   // no room in shared memory: the vectors stay in global memory
-    for (int t = warp; t < k; t += NT_EIG / 32) {
-      double* x = V + (size_t)t * n;
-      for (int kk = n - 3; kk >= 0; kk--) {
-        const double tk = tau[kk];
-        if (tk == 0.0) continue;
-        const int L = n - kk - 1;
-        const double* vr = A + (size_t)kk * n + kk + 1;
-        double* xs = x + kk + 1;
-        double s = 0.0;
-        for (int r = lane; r < L; r += 32) s = fma(vr[r], xs[r], s);
-        s = tk * warp_sum(s);
-        for (int r = lane; r < L; r += 32) xs[r] = fma(-vr[r], s, xs[r]);
-        __syncwarp();
-      }
+  // its own vectors, with no CTA-wide barrier.
+  for (int t = warp; t < k; t += NT_EIG / 32) {
+    double* x = V + (size_t)t * n;
+    for (int kk = n - 3; kk >= 0; kk--) {
+      const double tk = tau[kk];
+      if (tk == 0.0) continue;
+      const int L = n - kk - 1;
+      const double* vr = A + (size_t)kk * n + kk + 1;
+      double* xs = x + kk + 1;
+      double s = 0.0;
+      for (int r = lane; r < L; r += 32) s = fma(vr[r], xs[r], s);
+      s = tk * warp_sum(s);
+      for (int r = lane; r < L; r += 32) xs[r] = fma(-vr[r], s, xs[r]);
+      __syncwarp();
     }
-    __syncthreads();
   }
-  for (int t0 = 0; vpp > 0 && t0 < k; t0 += vpp) {
-    const int nvp = min(vpp, k - t0);
-    for (int idx = threadIdx.x; idx < nvp * n; idx += NT_EIG) xsm[idx] = V[(size_t)t0 * n + idx];
-    __syncthreads();
-    for (int u = warp; u < nvp; u += NT_EIG / 32) {
-      double* x = xsm + (size_t)u * n;
-      for (int kk = n - 3; kk >= 0; kk--) {
-        const double tk = tau[kk];
-        if (tk == 0.0) continue;
-        const int L = n - kk - 1;
-        const double* vr = A + (size_t)kk * n + kk + 1;
-        double* xs = x + kk + 1;
-        double s = 0.0;
-        for (int r = lane; r < L; r += 32) s = fma(vr[r], xs[r], s);
-        s = tk * warp_sum(s);
-        for (int r = lane; r < L; r += 32) xs[r] = fma(-vr[r], s, xs[r]);
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nvp * n; idx += NT_EIG) V[(size_t)t0 * n + idx] = xsm[idx];
-    __syncthreads();
-  }
+  __syncthreads();
   sign_vectors(V, n, k);
 }
 
 __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double thr, int kmax, double* V, double* w,
-                                                int* kout, double* scratch, int* err, int zsmem, int vpp) {
+                                                int* kout, double* scratch, int* err, int zsmem, int ntw) {
   extern __shared__ double dyn[];
   const int b = blockIdx.x;
   double* A = T + (size_t)b * nv * nv;
@@ -292,7 +266,7 @@ __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double th
     double* sm = dyn + (size_t)nv * ldz;
     eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zs, ldz, sm);
   } else if (thr > 0.0) {
-    eig_topk(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, dyn, vpp);
+    eig_topk(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, dyn, ntw);
   } else {
     double* Zg = scr + 3 * nv;
     eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zg, nv, dyn);
@@ -303,16 +277,15 @@ void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, 
                     double* scratch, int* err, cudaStream_t st) {
   const int zsmem = nv <= ZSMEM_MAX;
   size_t smem = (size_t)(4 * nv + 64) * sizeof(double);
-  int vpp = 0;
+  int ntw = 0;
   if (zsmem) smem += (size_t)nv * (nv + 1) * sizeof(double);
-  else if (thr > 0.0) {   // eigenvectors of the back-transformation in shared memory, one per warp and pass
-    const size_t cap = (size_t)200 * 1024;
-    const size_t avail = cap > smem ? cap - smem : 0;
-    vpp = (int)std::min<size_t>(NT_EIG / 32, avail / ((size_t)nv * sizeof(double)));
-    smem += (size_t)vpp * nv * sizeof(double);
+  else if (thr > 0.0) {   // tiles of the symmetric tridiagonalisation: one warp per 32 x 33 doubles that fit
+    const size_t cap = (size_t)224 * 1024 / sizeof(double), base = (size_t)4 * nv + 64, tile = 32 * 33;
+    ntw = cap > base ? (int)std::min<size_t>(NT_EIG / 32, (cap - base) / tile) : 0;
+    if (ntw >= 2) smem += (size_t)ntw * tile * sizeof(double);
   }
   cudaFuncSetAttribute(k_eig_osv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_eig_osv<<<nb, NT_EIG, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem, vpp);
+  k_eig_osv<<<nb, NT_EIG, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem, ntw);
   note_launch(1);
 }
 

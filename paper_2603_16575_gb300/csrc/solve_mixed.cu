@@ -16,10 +16,11 @@
 //
 // Precision: the coupling C_p carries the off-diagonal occupied Fock elements
 // (|c_t| ~ 1e-2 against |D| ~ 1), so the rounding of its FP32 products perturbs
-// Y by ~ eps_32 |c| / |D| ~ 1e-9 relative.  C_p and Sigma_pq are FP32 products
-// summed per k-tile in FP32 and across k-tiles in compensated FP32 (two-sum);
-// K~_p, D_p, C_p, Y_p
-// (master copy) and the energy <K~_p, 2Y_p - Y_p^T> are FP64.
+// Y by ~ eps_32 |c| / |D| ~ 1e-9 relative.  The coupling products are FP32 (K =
+// a pair order), Sigma_pq comes from the split-precision table, and C_p is
+// accumulated over its terms in a compensated FP32 pair (two-sum: no FP64
+// arithmetic, whose throughput is 1/64 of FP32 here).  K~_p, 1/D_p, Y_p (master
+// copy), the update and the energy <K~_p, 2Y_p - Y_p^T> are FP64.
 #include "pairview.cuh"
 
 namespace osv {
@@ -86,12 +87,14 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
   const size_t M2 = (size_t)max_m * max_m;
   double* base = scratch + (size_t)blockIdx.x * frag_mixed_scratch_doubles(max_m);
   double* Y64[6];
-  double* C64[6];
+  float* Chi[6];            // C_p as a compensated FP32 pair (Chi + Clo)
+  float* Clo[6];
   double* invD[6];
   float* Y32[6];
   for (int u = 0; u < 6; u++) {
     Y64[u] = base + u * M2;
-    C64[u] = base + (6 + u) * M2;
+    Chi[u] = reinterpret_cast<float*>(base + 6 * M2) + (size_t)u * M2;
+    Clo[u] = reinterpret_cast<float*>(base + 6 * M2) + (size_t)(6 + u) * M2;
     invD[u] = base + (12 + u) * M2;
   }
   float* fb = reinterpret_cast<float*>(base + 18 * M2);
@@ -99,6 +102,8 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
   float* W32 = fb + 6 * M2;
   float* A1 = fb + 7 * M2;
   float* A2 = fb + 8 * M2;
+  float* G0[6];              // e~_a - (f_ii + f_jj)/2 per pair (FP32)
+  for (int u = 0; u < 6; u++) G0[u] = fb + 9 * M2 + (size_t)u * max_m;
   const double* f = t.f_occ;
   const int n = t.n_occ;
   while (true) {
@@ -180,6 +185,7 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
         Y32[p][idx] = 0.f;
         invD[p][idx] = 1.0 / (fij - et[idx / rp] - et[idx % rp]);   // update denominators, once per fragment
       }
+      for (int a = threadIdx.x; a < rp; a += NT) G0[p][a] = (float)(et[a] - 0.5 * fij);
     }
     __syncthreads();
     double e_prev = 0.0, e = 0.0, um = 0.0;
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
       // C_p from the previous sweep's amplitudes (Jacobi)
       for (int p = 0; p < np; p++) {
         const int rp = pr[p];
-        for (int idx = threadIdx.x; idx < rp * rp; idx += NT) C64[p][idx] = 0.0;
+        for (int idx = threadIdx.x; idx < rp * rp; idx += NT) Chi[p][idx] = Clo[p][idx] = 0.f;
         __syncthreads();
         for (int u = 0; u < nterm[p] && sig_ok; u++) {
           const MTerm tm = terms[p][u];
@@ -196,26 +202,28 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
           const ViewF S{sig_ptr[tm.sig], sig_ld[tm.sig], sig_tr[tm.sig]};        // Sigma_pq   (r_p x r_q)
           const ViewF St{sig_ptr[tm.sig], sig_ld[tm.sig], !sig_tr[tm.sig]};      // Sigma_pq^T (r_q x r_p)
           cta_gemm_f32s<float>(rq, rp, rq, 1.0, ViewF{Y32[tm.q], rq, tm.tr}, St, 0.0, W32, rp, fsm);
-          cta_gemm_f32s<double>(rp, rp, rq, tm.coef, S, ViewF{W32, rp, 0}, 1.0, C64[p], rp, fsm);
+          cta_gemm_f32s_acc2(rp, rp, rq, (float)tm.coef, S, ViewF{W32, rp, 0}, Chi[p], Clo[p], rp, fsm);
         }
         // leftovers of an inexact preconditioner basis (S~ = 1 + Sh, G0 = diag(e~) - (f_ii+f_jj)/2):
         // P = Gh (Y S~) + (S~ Y) Gh + G0 (Y Sh) + (Sh Y) G0
         const float* Sh = t.Sh ? t.Sh[pid[p]] : nullptr;
         if (Sh) {
           const float* Gh = t.Gh[pid[p]];
-          const double* et = t.et[pid[p]];
-          const double fh = 0.5 * (f[orbs[pa[p]] * n + orbs[pa[p]]] + f[orbs[pb[p]] * n + orbs[pb[p]]]);
+          const float* g0 = G0[p];
           cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Y32[p], rp, 0}, ViewF{Sh, rp, 0}, 0.0, A1, rp, fsm);
           cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Sh, rp, 0}, ViewF{Y32[p], rp, 0}, 0.0, A2, rp, fsm);
           for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
             const int a = idx / rp, b = idx % rp;
-            C64[p][idx] += (et[a] - fh) * (double)A1[idx] + (et[b] - fh) * (double)A2[idx];
+            float s, e2;
+            two_sum_f(Chi[p][idx], g0[a] * A1[idx] + g0[b] * A2[idx], s, e2);
+            Chi[p][idx] = s;
+            Clo[p][idx] += e2;
             A1[idx] += Y32[p][idx];
             A2[idx] += Y32[p][idx];
           }
           __syncthreads();
-          cta_gemm_f32s<double>(rp, rp, rp, 1.0, ViewF{Gh, rp, 0}, ViewF{A1, rp, 0}, 1.0, C64[p], rp, fsm);
-          cta_gemm_f32s<double>(rp, rp, rp, 1.0, ViewF{A2, rp, 0}, ViewF{Gh, rp, 0}, 1.0, C64[p], rp, fsm);
+          cta_gemm_f32s_acc2(rp, rp, rp, 1.f, ViewF{Gh, rp, 0}, ViewF{A1, rp, 0}, Chi[p], Clo[p], rp, fsm);
+          cta_gemm_f32s_acc2(rp, rp, rp, 1.f, ViewF{A2, rp, 0}, ViewF{Gh, rp, 0}, Chi[p], Clo[p], rp, fsm);
         }
       }
       // Y_p <- (K~_p + C_p) / D_p in FP64; energy <K~_p, 2Y_p - Y_p^T>
@@ -226,8 +234,8 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
         const double* Kt = t.Kt[pid[p]];
         double du = 0.0;
         for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
-          const double y = (Kt[idx] + C64[p][idx]) * invD[p][idx];
-          du = fmax(du, fabs(y - Y64[p][idx]));
+          const double y = (Kt[idx] + ((double)Chi[p][idx] + (double)Clo[p][idx])) * invD[p][idx];
+          du = fmax(du, (double)fabsf((float)(y - Y64[p][idx])));
           Y64[p][idx] = y;
         }
         um = fmax(um, cta_max(du, red));
