@@ -189,7 +189,13 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
       if (!isfinite(w[t])) atomicOr(err, ERR_NONFINITE);
   }
   __syncthreads();
-  // inverse iteration: warp per cluster, vectors of a cluster in order
+  // inverse iteration, parallel over the kept vectors (warp per vector): two
+  // solves from a seeded start, Gram-Schmidt inside each cluster of close
+  // eigenvalues (warp per cluster, in order), then one more solve per vector
+  // and the Gram-Schmidt again.  With shifts accurate to ~eps ||T||, one solve
+  // leaves a vector contaminated by an eigenvector at distance g at ~eps ||T|| / g,
+  // so the vectors separate without orthogonalising between every solve; the
+  // passes take care of (near-)degenerate groups.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* u0 = wk + (size_t)warp * 7 * n;
   double* u1 = u0 + n;
@@ -198,26 +204,21 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   double* y = mu + n;
   int* piv = reinterpret_cast<int*>(y + n);   // n ints fit in 2n doubles' room
   const double small = 2.220446049250313e-16 * fmax(s_norm, 1e-300);
-  for (int c = warp; c < s_nclu; c += NT_EIG / 32) {
-    const int t0 = clu[c], t1 = clu[c + 1];
-    for (int t = t0; t < t1; t++) {
+  for (int pass = 0; pass < 2; pass++) {
+    for (int t = warp; t < k; t += NT_EIG / 32) {
       if (lane == 0) tri_factor(d, e, n, w[t], small, u0, u1, u2, mu, piv);
       for (int r = lane; r < n; r += 32) {
-        const uint64_t h = draw(0x5eedull + (uint64_t)t, (uint64_t)r);
-        y[r] = (double)(h >> 11) * 0x1p-53 - 0.5;
+        if (pass == 0) {
+          const uint64_t h = draw(0x5eedull + (uint64_t)t, (uint64_t)r);
+          y[r] = (double)(h >> 11) * 0x1p-53 - 0.5;
+        } else {
+          y[r] = V[(size_t)t * n + r];
+        }
       }
       __syncwarp();
-      for (int it = 0; it < 3; it++) {
+      for (int it = 0; it < 2 - pass; it++) {
         if (lane == 0) tri_solve(n, u0, u1, u2, mu, piv, y);
         __syncwarp();
-        for (int s = t0; s < t; s++) {          // Gram-Schmidt against the cluster's earlier vectors
-          const double* Vs = V + (size_t)s * n;
-          double dot = 0.0;
-          for (int r = lane; r < n; r += 32) dot += y[r] * Vs[r];
-          dot = warp_sum(dot);
-          for (int r = lane; r < n; r += 32) y[r] -= dot * Vs[r];
-          __syncwarp();
-        }
         double nn = 0.0;
         for (int r = lane; r < n; r += 32) nn += y[r] * y[r];
         nn = warp_sum(nn);
@@ -228,28 +229,73 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
       for (int r = lane; r < n; r += 32) V[(size_t)t * n + r] = y[r];
       __syncwarp();
     }
-  }
-  __syncthreads();
-  // back-transformation V <- H_0 ... H_{n-3} V: eigenvectors are independent, so
-  // each warp applies every reflector (stored contiguously in row kk of A) to
-  // its own vectors, with no CTA-wide barrier.
-  for (int t = warp; t < k; t += NT_EIG / 32) {
-    double* x = V + (size_t)t * n;
-    for (int kk = n - 3; kk >= 0; kk--) {
-      const double tk = tau[kk];
-      if (tk == 0.0) continue;
-      const int L = n - kk - 1;
-      const double* vr = A + (size_t)kk * n + kk + 1;
-      double* xs = x + kk + 1;
-      double s = 0.0;
-      for (int r = lane; r < L; r += 32) s = fma(vr[r], xs[r], s);
-      s = tk * warp_sum(s);
-      for (int r = lane; r < L; r += 32) xs[r] = fma(-vr[r], s, xs[r]);
-      __syncwarp();
+    __syncthreads();
+    for (int c = warp; c < s_nclu; c += NT_EIG / 32) {   // Gram-Schmidt within clusters
+      const int t0 = clu[c], t1 = clu[c + 1];
+      for (int t = t0; t < t1; t++) {
+        double* Vt = V + (size_t)t * n;
+        for (int s = t0; s < t; s++) {
+          const double* Vs = V + (size_t)s * n;
+          double dot = 0.0;
+          for (int r = lane; r < n; r += 32) dot += Vt[r] * Vs[r];
+          dot = warp_sum(dot);
+          for (int r = lane; r < n; r += 32) Vt[r] -= dot * Vs[r];
+          __syncwarp();
+        }
+        double nn = 0.0;
+        for (int r = lane; r < n; r += 32) nn += Vt[r] * Vt[r];
+        nn = warp_sum(nn);
+        const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+        for (int r = lane; r < n; r += 32) Vt[r] *= sc;
+        __syncwarp();
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
-  sign_vectors(V, n, k);
+  // the back-transformation to the virtual basis is k_eig_back
+}
+
+// Back-transformation of the kept eigenvectors of eig_topk, one warp per
+// (orbital, vector) over the whole GPU (the vectors are independent, and
+// orbitals keep different numbers of them): x <- H_0 ... H_{n-3} x with the
+// reflectors stored contiguously in the rows of A and tau in the scratch, then
+// the sign convention of sign_vectors.
+constexpr int EB_WARPS = 8;
+__global__ void __launch_bounds__(EB_WARPS * 32) k_eig_back(const double* T, int n, int kmax, double* V,
+                                                           const int* kout, const double* scratch,
+                                                           size_t scr_stride) {
+  const int b = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.y * EB_WARPS + warp;
+  if (t >= kout[b]) return;   // warp-uniform
+  const double* A = T + (size_t)b * n * n;
+  const double* tau = scratch + (size_t)b * scr_stride + 2 * n;
+  double* x = V + (size_t)b * n * kmax + (size_t)t * n;
+  for (int kk = n - 3; kk >= 0; kk--) {
+    const double tk = tau[kk];
+    if (tk == 0.0) continue;
+    const int L = n - kk - 1;
+    const double* vr = A + (size_t)kk * n + kk + 1;
+    double* xs = x + kk + 1;
+    double s = 0.0;
+    for (int r = lane; r < L; r += 32) s = fma(vr[r], xs[r], s);
+    s = tk * warp_sum(s);
+    for (int r = lane; r < L; r += 32) xs[r] = fma(-vr[r], s, xs[r]);
+    __syncwarp();
+  }
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int r = lane; r < n; r += 32) {
+    const double a = fabs(x[r]);
+    if (a > best) { best = a; bi = r; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (x[bi] < 0.0)
+    for (int r = lane; r < n; r += 32) x[r] = -x[r];
 }
 
 __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double thr, int kmax, double* V, double* w,
@@ -287,6 +333,11 @@ void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, 
   cudaFuncSetAttribute(k_eig_osv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_eig_osv<<<nb, NT_EIG, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem, ntw);
   note_launch(1);
+  if (!zsmem && thr > 0.0) {
+    dim3 grid(nb, (std::min(kmax, nv) + EB_WARPS - 1) / EB_WARPS);
+    k_eig_back<<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, eig_osv_scratch_doubles(nv, kmax));
+    note_launch(1);
+  }
 }
 
 __global__ void k_pack_q(const double* V, const double* w, int nv, int kmax, const int* k,
