@@ -2,6 +2,7 @@
 // FP64 tiled GEMM, deterministic CTA reductions and the device form of the
 // counter-based generator that regenerates the RI integrals B.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -228,7 +229,10 @@ __device__ void cta_gemm_f32r(int M, int N, int K, double alpha, const VA& A, co
           const int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
           if (r < M && c < N) {
             CT* cp = C + (size_t)r * ldc + c;
-            *cp = static_cast<CT>((beta == 0.0 ? 0.0 : beta * static_cast<double>(*cp)) + alpha * (double)acc[i][j]);
+            if constexpr (std::is_same<CT, float>::value)   // FP32 output: no FP64 work in the epilogue
+              *cp = (beta == 0.0 ? 0.f : (float)beta * *cp) + (float)alpha * acc[i][j];
+            else
+              *cp = static_cast<CT>((beta == 0.0 ? 0.0 : beta * static_cast<double>(*cp)) + alpha * (double)acc[i][j]);
           }
         }
     }

@@ -12,7 +12,11 @@
 // X^T F X = diag(e~) + Fh, see precond_mixed.cu) the pair-diagonal terms give
 // -D o Y_p + P_p(Y_p) with P = Gh (Y S~) + (S~ Y) Gh + G0 (Y Sh) + (Sh Y) G0,
 // Gh = Fh - (f_ii+f_jj)/2 Sh, G0 = diag(e~) - (f_ii+f_jj)/2; P is added to C_p,
-// so the fixed point is the exact one.  Sh and Gh are ~1e-7, their products FP32.
+// so the fixed point is the exact one.  Sh and Gh are ~1e-7, their products FP32;
+// P is linear in Y and that small, so it is re-formed only after the
+// amplitudes have moved by more than P_LAG of their scale (in practice the
+// first two or three sweeps), and the fixed point is exact up to P applied to
+// that lag.
 //
 // Precision: the coupling C_p carries the off-diagonal occupied Fock elements
 // (|c_t| ~ 1e-2 against |D| ~ 1), so the rounding of its FP32 products perturbs
@@ -48,12 +52,27 @@ void launch_ktilde(const Tables& t, const KtJob* jobs, int n_jobs, double* scrat
   note_launch(1);
 }
 
-struct MTerm {     // one coupling term of local pair p: coef * Sigma[sig] op(Y_q) Sigma[sig]^T
+struct MTerm {     // coupling of local pair p to stored pair q: Sigma[sig] (cn Y_q + ct Y_q^T) Sigma[sig]^T
   int q;           // local stored pair
-  int tr;          // op = transpose
   int sig;         // index of Sigma_(p,q) in the fragment's list
-  double coef;
+  double cn, ct;   // coefficients of Y_q and of Y_q^T (terms with the same q share one Sigma)
 };
+
+// cn Y + ct Y^T of a square FP32 block, read element by element by the GEMM tiles.
+struct ViewFmix {
+  const float* p;
+  int ld;
+  float cn, ct;
+  __device__ __forceinline__ float get(int r, int c) const {
+    return cn * p[(size_t)r * ld + c] + ct * p[(size_t)c * ld + r];
+  }
+};
+
+// P(Y) is refreshed once the amplitudes have moved by more than this fraction of
+// their scale (max |Y| after the first sweep) since it was last formed: P is
+// ~1e-7 of the pair-diagonal terms, so a lag of 1e-2 of Y leaves ~1e-9 of P's
+// own contribution.
+constexpr double P_LAG = 1e-2;
 
 constexpr int MAX_TERMS = 24;   // 6 pairs x 4 coupling terms (three-orbital fragments)
 
@@ -102,8 +121,10 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
   float* W32 = fb + 6 * M2;
   float* A1 = fb + 7 * M2;
   float* A2 = fb + 8 * M2;
+  float* Pp[6];              // P_p(Y_p), refreshed when the amplitudes have drifted (FP32)
+  for (int u = 0; u < 6; u++) Pp[u] = fb + (9 + u) * M2;
   float* G0[6];              // e~_a - (f_ii + f_jj)/2 per pair (FP32)
-  for (int u = 0; u < 6; u++) G0[u] = fb + 9 * M2 + (size_t)u * max_m;
+  for (int u = 0; u < 6; u++) G0[u] = fb + 15 * M2 + (size_t)u * max_m;
   const double* f = t.f_occ;
   const int n = t.n_occ;
   while (true) {
@@ -154,7 +175,12 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
             for (int u = 0; u < ns; u++)
               if (sig_p[u] == p && sig_q[u] == q) sg = u;
             if (sg < 0) { sg = ns; sig_p[ns] = p; sig_q[ns] = q; ns++; }
-            terms[p][nt++] = MTerm{q, x > y, sg, coef};
+            int tu = -1;   // terms on the same q (Y_q and Y_q^T, diagonal pairs) share one product
+            for (int u = 0; u < nt; u++)
+              if (terms[p][u].q == q) tu = u;
+            if (tu < 0) { tu = nt++; terms[p][tu] = MTerm{q, sg, 0.0, 0.0}; }
+            if (x > y) terms[p][tu].ct += coef;
+            else terms[p][tu].cn += coef;
           }
         }
         nterm[p] = nt;
@@ -183,47 +209,56 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
       for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
         Y64[p][idx] = 0.0;
         Y32[p][idx] = 0.f;
+        Pp[p][idx] = 0.f;
         invD[p][idx] = 1.0 / (fij - et[idx / rp] - et[idx % rp]);   // update denominators, once per fragment
       }
       for (int a = threadIdx.x; a < rp; a += NT) G0[p][a] = (float)(et[a] - 0.5 * fij);
     }
     __syncthreads();
     double e_prev = 0.0, e = 0.0, um = 0.0;
+    double y_scale = 0.0, drift = 0.0;   // max |Y| after the first sweep; max-norm moves since P was formed
     int status = ERR_NOCONV, iters = o.max_iter;
     for (int it = 1; it <= o.max_iter; it++) {
+      // the first sweep starts from Y = 0: C = P = 0
+      const bool refresh_P = it > 1 && drift > P_LAG * y_scale;
+      if (refresh_P) drift = 0.0;
       // C_p from the previous sweep's amplitudes (Jacobi)
       for (int p = 0; p < np; p++) {
         const int rp = pr[p];
         for (int idx = threadIdx.x; idx < rp * rp; idx += NT) Chi[p][idx] = Clo[p][idx] = 0.f;
         __syncthreads();
-        for (int u = 0; u < nterm[p] && sig_ok; u++) {
+        for (int u = 0; u < nterm[p] && sig_ok && it > 1; u++) {
           const MTerm tm = terms[p][u];
           const int rq = pr[tm.q];
           const ViewF S{sig_ptr[tm.sig], sig_ld[tm.sig], sig_tr[tm.sig]};        // Sigma_pq   (r_p x r_q)
           const ViewF St{sig_ptr[tm.sig], sig_ld[tm.sig], !sig_tr[tm.sig]};      // Sigma_pq^T (r_q x r_p)
-          cta_gemm_f32s<float>(rq, rp, rq, 1.0, ViewF{Y32[tm.q], rq, tm.tr}, St, 0.0, W32, rp, fsm);
-          cta_gemm_f32s_acc2(rp, rp, rq, (float)tm.coef, S, ViewF{W32, rp, 0}, Chi[p], Clo[p], rp, fsm);
+          // W = (cn Y_q + ct Y_q^T) Sigma_pq^T, C_p += Sigma_pq W
+          if (tm.ct == 0.0)
+            cta_gemm_f32s<float>(rq, rp, rq, tm.cn, ViewF{Y32[tm.q], rq, 0}, St, 0.0, W32, rp, fsm);
+          else if (tm.cn == 0.0)
+            cta_gemm_f32s<float>(rq, rp, rq, tm.ct, ViewF{Y32[tm.q], rq, 1}, St, 0.0, W32, rp, fsm);
+          else
+            cta_gemm_f32s<float>(rq, rp, rq, 1.0, ViewFmix{Y32[tm.q], rq, (float)tm.cn, (float)tm.ct}, St, 0.0,
+                                 W32, rp, fsm);
+          cta_gemm_f32s_acc2(rp, rp, rq, 1.f, S, ViewF{W32, rp, 0}, Chi[p], Clo[p], rp, fsm);
         }
         // leftovers of an inexact preconditioner basis (S~ = 1 + Sh, G0 = diag(e~) - (f_ii+f_jj)/2):
-        // P = Gh (Y S~) + (S~ Y) Gh + G0 (Y Sh) + (Sh Y) G0
+        // P = Gh (Y S~) + (S~ Y) Gh + G0 (Y Sh) + (Sh Y) G0, from the amplitudes of the last refresh
         const float* Sh = t.Sh ? t.Sh[pid[p]] : nullptr;
-        if (Sh) {
+        if (Sh && refresh_P) {
           const float* Gh = t.Gh[pid[p]];
           const float* g0 = G0[p];
           cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Y32[p], rp, 0}, ViewF{Sh, rp, 0}, 0.0, A1, rp, fsm);
           cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Sh, rp, 0}, ViewF{Y32[p], rp, 0}, 0.0, A2, rp, fsm);
           for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
             const int a = idx / rp, b = idx % rp;
-            float s, e2;
-            two_sum_f(Chi[p][idx], g0[a] * A1[idx] + g0[b] * A2[idx], s, e2);
-            Chi[p][idx] = s;
-            Clo[p][idx] += e2;
+            Pp[p][idx] = g0[a] * A1[idx] + g0[b] * A2[idx];
             A1[idx] += Y32[p][idx];
             A2[idx] += Y32[p][idx];
           }
           __syncthreads();
-          cta_gemm_f32s_acc2(rp, rp, rp, 1.f, ViewF{Gh, rp, 0}, ViewF{A1, rp, 0}, Chi[p], Clo[p], rp, fsm);
-          cta_gemm_f32s_acc2(rp, rp, rp, 1.f, ViewF{A2, rp, 0}, ViewF{Gh, rp, 0}, Chi[p], Clo[p], rp, fsm);
+          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Gh, rp, 0}, ViewF{A1, rp, 0}, 1.0, Pp[p], rp, fsm);
+          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{A2, rp, 0}, ViewF{Gh, rp, 0}, 1.0, Pp[p], rp, fsm);
         }
       }
       // Y_p <- (K~_p + C_p) / D_p in FP64; energy <K~_p, 2Y_p - Y_p^T>
@@ -234,7 +269,7 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
         const double* Kt = t.Kt[pid[p]];
         double du = 0.0;
         for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
-          const double y = (Kt[idx] + ((double)Chi[p][idx] + (double)Clo[p][idx])) * invD[p][idx];
+          const double y = (Kt[idx] + ((double)Chi[p][idx] + (double)(Clo[p][idx] + Pp[p][idx]))) * invD[p][idx];
           du = fmax(du, (double)fabsf((float)(y - Y64[p][idx])));
           Y64[p][idx] = y;
         }
@@ -249,6 +284,8 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
         e += (pa[p] == pb[p]) ? s : 2.0 * s;
       }
       if (!isfinite(e) || !isfinite(um)) { status = ERR_NONFINITE; iters = it; break; }
+      if (it == 1) y_scale = um;
+      drift += um;
       if (um < o.tol_update && fabs(e - e_prev) < fmax(o.tol_energy, 1e-11 * fabs(e))) {
         status = 0;
         iters = it;
