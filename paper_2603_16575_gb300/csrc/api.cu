@@ -648,26 +648,31 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   }
   const int n_cta = std::min<int>((int)pjb.size(), 2 * c->num_sms);
   const int n_warps = std::min<int>((int)pjb.size(), 16 * c->num_sms);
+  const int n_cta_pm = std::min<int>((int)pjb.size(), 3 * c->num_sms);
   const bool warp_pc = max_m <= PW_MAX_ORDER;
   TRY(tmp_alloc(c, scr, std::max({(size_t)n_cta * precond_scratch_doubles(max_m),
                                   warp_pc ? precond_w_scratch_doubles(max_m, n_warps) : (size_t)0,
-                                  mixed_pc ? precond_mixed_scratch_doubles(max_m, n_warps, n_cta) : (size_t)0}) *
+                                  mixed_pc ? precond_mixed_scratch_doubles(max_m, n_cta_pm) : (size_t)0}) *
                                      sizeof(double)));
-  Tmp pm_slots, pm_off, pm_m;
+  Tmp pm_slots, pm_off, pm_m, pm_order;
   if (mixed_pc) {
     std::vector<long long> off(pjb.size());
-    std::vector<int> md(pjb.size());
+    std::vector<int> md(pjb.size()), ord(pjb.size());
     long long tot = 0;
     for (size_t q = 0; q < pjb.size(); q++) {
       md[q] = pair_dim_h(c, pjb[q].i, pjb[q].j);
       off[q] = tot;
       tot += (long long)precond_mixed_slot_doubles(md[q]);
+      ord[q] = (int)q;
     }
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return md[a] > md[b]; });
     TRY(tmp_alloc(c, pm_slots, (size_t)tot * sizeof(double)));
     TRY(tmp_alloc(c, pm_off, off.size() * sizeof(long long)));
     TRY(tmp_alloc(c, pm_m, md.size() * sizeof(int)));
+    TRY(tmp_alloc(c, pm_order, ord.size() * sizeof(int)));
     CK(cudaMemcpyAsync(pm_off.p, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(pm_m.p, md.data(), md.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(pm_order.p, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
   }
   double f_pc = 0.0;
   for (auto& j : pjb) {
@@ -682,9 +687,9 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   }
   ph_begin(c, OSVMP2_PH_PRECOND);
   if (mixed_pc)
-    launch_precond_mixed(t, c->opts.tau_s, (const PJob*)jp.p, (int)pjb.size(), max_m, (double*)pm_slots.p,
-                         (const long long*)pm_off.p, (const int*)pm_m.p, (double*)scr.p, n_warps, n_cta, c->err_d,
-                         c->st);
+    launch_precond_mixed(t, c->opts.tau_s, (const PJob*)jp.p, (const int*)pm_order.p, (int)pjb.size(), max_m,
+                         (double*)pm_slots.p, (const long long*)pm_off.p, (const int*)pm_m.p, (double*)scr.p,
+                         n_cta_pm, c->err_d, c->st);
   else if (warp_pc)
     launch_precond_w(t, c->opts.tau_s, (const PJob*)jp.p, (int)pjb.size(), max_m, (double*)scr.p, n_warps, c->err_d,
                      c->st);

@@ -402,6 +402,20 @@ __device__ inline double cta_sum(double v, double* red) {
   __syncthreads();
   return red[32];
 }
+__device__ inline float cta_sum(float v, float* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int k = 0; k < nw; k++) s += red[k];
+    red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
 __device__ inline double cta_max(double v, double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = warp_max(v);

@@ -19,31 +19,31 @@ namespace osv {
 
 // Householder tridiagonalisation of the symmetric n x n matrix A (row-major,
 // lda; global or shared memory), in place.  Outputs d[n], e[n-1] (any memory)
-// and tau[n]; v and p are shared scratch of n doubles each, red >= 33 doubles.
-template <int NTH = NT>
-__device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double* e, double* tau,
-                                   double* v, double* p, double* red) {
+// and tau[n]; v and p are shared scratch of n elements each, red >= 33.
+// T = double or float.
+template <int NTH = NT, class T = double>
+__device__ inline void cta_tridiag(T* A, int n, int lda, T* d, T* e, T* tau, T* v, T* p, T* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = NTH / 32;
-  __shared__ double s_tau;
+  __shared__ T s_tau;
   for (int k = 0; k + 2 < n; k++) {
     const int L = n - k - 1;          // trailing block rows/cols k+1 .. n-1
-    double* Ak = A + (size_t)(k + 1) * lda + (k + 1);   // trailing block origin
-    double part = 0.0;
+    T* Ak = A + (size_t)(k + 1) * lda + (k + 1);   // trailing block origin
+    T part = T(0.0);
     for (int t = tid; t < L; t += NTH) {
-      const double x = A[(size_t)(k + 1 + t) * lda + k];
+      const T x = A[(size_t)(k + 1 + t) * lda + k];
       v[t] = x;
       if (t > 0) part += x * x;
     }
-    const double sigma = cta_sum(part, red);
+    const T sigma = cta_sum(part, red);
     if (tid == 0) {
-      const double alpha = v[0];
-      double tu = 0.0, beta = alpha;
-      if (sigma > 0.0) {
-        const double mu = sqrt(alpha * alpha + sigma);
-        beta = alpha <= 0.0 ? mu : -mu;
+      const T alpha = v[0];
+      T tu = T(0.0), beta = alpha;
+      if (sigma > T(0.0)) {
+        const T mu = sqrt(alpha * alpha + sigma);
+        beta = alpha <= T(0.0) ? mu : -mu;
         tu = (beta - alpha) / beta;
-        const double v0 = alpha - beta;
-        red[0] = 1.0 / v0;   // scale for v[1..]
+        const T v0 = alpha - beta;
+        red[0] = T(1.0) / v0;   // scale for v[1..]
       }
       s_tau = tu;
       d[k] = A[(size_t)k * lda + k];
@@ -51,40 +51,40 @@ __device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double*
       tau[k] = tu;
     }
     __syncthreads();
-    const double tk = s_tau;
-    if (tk != 0.0) {
-      const double sc = red[0];
-      for (int t = tid; t < L; t += NTH) v[t] = (t == 0) ? 1.0 : v[t] * sc;
+    const T tk = s_tau;
+    if (tk != T(0.0)) {
+      const T sc = red[0];
+      for (int t = tid; t < L; t += NTH) v[t] = (t == 0) ? T(1.0) : v[t] * sc;
       __syncthreads();
       // p = tau * A' v  (warp per row, lanes over columns)
       for (int r = warp; r < L; r += nwarp) {
-        const double* row = Ak + (size_t)r * lda;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        const T* row = Ak + (size_t)r * lda;
+        T s0 = T(0.0), s1 = T(0.0), s2 = T(0.0), s3 = T(0.0);
         int c = lane;
         for (; c + 96 < L; c += 128) {       // four independent loads in flight per lane
-          const double a0 = row[c], a1 = row[c + 32], a2 = row[c + 64], a3 = row[c + 96];
+          const T a0 = row[c], a1 = row[c + 32], a2 = row[c + 64], a3 = row[c + 96];
           s0 += a0 * v[c];
           s1 += a1 * v[c + 32];
           s2 += a2 * v[c + 64];
           s3 += a3 * v[c + 96];
         }
         for (; c < L; c += 32) s0 += row[c] * v[c];
-        const double s = warp_sum((s0 + s1) + (s2 + s3));
+        const T s = warp_sum((s0 + s1) + (s2 + s3));
         if (lane == 0) p[r] = tk * s;
       }
       __syncthreads();
-      double pv = 0.0;
+      T pv = T(0.0);
       for (int t = tid; t < L; t += NTH) pv += p[t] * v[t];
-      const double Kc = 0.5 * tk * cta_sum(pv, red);
+      const T Kc = T(0.5) * tk * cta_sum(pv, red);
       for (int t = tid; t < L; t += NTH) p[t] -= Kc * v[t];   // p becomes w
       __syncthreads();
       // A' -= v w^T + w v^T
       for (int r = warp; r < L; r += nwarp) {
-        double* row = Ak + (size_t)r * lda;
-        const double vr = v[r], wr = p[r];
+        T* row = Ak + (size_t)r * lda;
+        const T vr = v[r], wr = p[r];
         int c = lane;
         for (; c + 96 < L; c += 128) {
-          const double a0 = row[c], a1 = row[c + 32], a2 = row[c + 64], a3 = row[c + 96];
+          const T a0 = row[c], a1 = row[c + 32], a2 = row[c + 64], a3 = row[c + 96];
           row[c] = a0 - (vr * p[c] + wr * v[c]);
           row[c + 32] = a1 - (vr * p[c + 32] + wr * v[c + 32]);
           row[c + 64] = a2 - (vr * p[c + 64] + wr * v[c + 64]);
@@ -101,10 +101,10 @@ __device__ inline void cta_tridiag(double* A, int n, int lda, double* d, double*
     if (n >= 2) {
       d[n - 2] = A[(size_t)(n - 2) * lda + (n - 2)];
       e[n - 2] = A[(size_t)(n - 1) * lda + (n - 2)];
-      if (n >= 3) tau[n - 2] = 0.0;
+      if (n >= 3) tau[n - 2] = T(0.0);
     }
     d[n - 1] = A[(size_t)(n - 1) * lda + (n - 1)];
-    tau[n - 1] = 0.0;
+    tau[n - 1] = T(0.0);
   }
   __syncthreads();
 }
@@ -381,13 +381,15 @@ __device__ inline void cta_form_z(const double* A, int n, int lda, const double*
 // Implicit symmetric QR on the tridiagonal (d[n], e[n-1]) with rotations
 // accumulated into the columns of Z (n x n, row-major, ldz).  d, e must be in
 // shared or global memory visible to thread 0; cs is shared scratch of 2n
-// doubles.  Returns 0 on convergence (d holds the eigenvalues, columns of Z the
+// elements.  Returns 0 on convergence (d holds the eigenvalues, columns of Z the
 // eigenvectors), 1 otherwise.  Every thread returns the same value.
-template <int NTH = NT>
-__device__ inline int cta_tridiag_qr(double* d, double* e, int n, double* Z, int ldz, double* cs) {
+// ZCM: Z stored column-major (Z[r][c] at Z[c * ldz + r]), so that the threads,
+// one per row, rotate it with coalesced accesses.  T = double or float.
+template <int NTH = NT, bool ZCM = false, class T = double>
+__device__ inline int cta_tridiag_qr(T* d, T* e, int n, T* Z, int ldz, T* cs) {
   __shared__ int s_l, s_h, s_done;
   const int tid = threadIdx.x;
-  const double eps = 2.220446049250313e-16;
+  const T eps = sizeof(T) == 8 ? T(2.220446049250313e-16) : T(1.1920929e-07);
   int sweeps = 0;
   const int max_sweeps = 40 * n + 100;
   while (true) {
@@ -395,30 +397,30 @@ __device__ inline int cta_tridiag_qr(double* d, double* e, int n, double* Z, int
       int h = n - 1, l = 0, done = 0;
       // deflate negligible couplings from the bottom
       while (h > 0) {
-        if (fabs(e[h - 1]) <= eps * (fabs(d[h - 1]) + fabs(d[h]))) { e[h - 1] = 0.0; h--; }
+        if (fabs(e[h - 1]) <= eps * (fabs(d[h - 1]) + fabs(d[h]))) { e[h - 1] = T(0.0); h--; }
         else break;
       }
       if (h == 0) done = 1;
       else {
         l = h - 1;
         while (l > 0) {
-          if (fabs(e[l - 1]) <= eps * (fabs(d[l - 1]) + fabs(d[l]))) { e[l - 1] = 0.0; break; }
+          if (fabs(e[l - 1]) <= eps * (fabs(d[l - 1]) + fabs(d[l]))) { e[l - 1] = T(0.0); break; }
           l--;
         }
         // Wilkinson shift from the trailing 2x2 of the unreduced block [l, h]
-        const double delta = 0.5 * (d[h - 1] - d[h]);
-        const double eh = e[h - 1];
-        const double den = delta + copysign(hypot(delta, eh), delta);
-        const double mu = d[h] - (den != 0.0 ? eh * eh / den : 0.0);
-        double x = d[l] - mu, z = e[l];
+        const T delta = T(0.5) * (d[h - 1] - d[h]);
+        const T eh = e[h - 1];
+        const T den = delta + copysign(hypot(delta, eh), delta);
+        const T mu = d[h] - (den != T(0.0) ? eh * eh / den : T(0.0));
+        T x = d[l] - mu, z = e[l];
         for (int k = l; k < h; k++) {
-          const double r = hypot(x, z);
-          double c = 1.0, s = 0.0;
-          if (r != 0.0) { c = x / r; s = z / r; }
+          const T r = hypot(x, z);
+          T c = T(1.0), s = T(0.0);
+          if (r != T(0.0)) { c = x / r; s = z / r; }
           if (k > l) e[k - 1] = r;
-          const double a = d[k], b = e[k], cc = d[k + 1];
-          d[k] = c * c * a + 2.0 * c * s * b + s * s * cc;
-          d[k + 1] = s * s * a - 2.0 * c * s * b + c * c * cc;
+          const T a = d[k], b = e[k], cc = d[k + 1];
+          d[k] = c * c * a + T(2.0) * c * s * b + s * s * cc;
+          d[k + 1] = s * s * a - T(2.0) * c * s * b + c * c * cc;
           e[k] = c * s * (cc - a) + (c * c - s * s) * b;
           if (k + 1 < h) {
             x = e[k];
@@ -437,15 +439,16 @@ __device__ inline int cta_tridiag_qr(double* d, double* e, int n, double* Z, int
     const int l = s_l, h = s_h;
     // Z <- Z R_l^T R_{l+1}^T ... : column pair (k, k+1) rotated for k = l..h-1
     for (int row = tid; row < n; row += NTH) {
-      double* zr = Z + (size_t)row * ldz;
-      double carry = zr[l];
+      T* zr = ZCM ? Z + row : Z + (size_t)row * ldz;
+      const size_t zs = ZCM ? (size_t)ldz : 1;   // stride between the columns of one row
+      T carry = zr[l * zs];
       for (int k = l; k < h; k++) {
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        const double y = zr[k + 1];
-        zr[k] = c * carry + s * y;
+        const T c = cs[2 * k], s = cs[2 * k + 1];
+        const T y = zr[(k + 1) * zs];
+        zr[k * zs] = c * carry + s * y;
         carry = -s * carry + c * y;
       }
-      zr[h] = carry;
+      zr[h * zs] = carry;
     }
     __syncthreads();
   }
@@ -476,6 +479,68 @@ __device__ inline int cta_syev(double* A, int n, int lda, double* w, double* Z, 
   }
   __syncthreads();
   const int rc = cta_tridiag_qr<NTH>(v, p, n, Z, ldz, cs);
+  for (int t = threadIdx.x; t < n; t += NTH) w[t] = v[t];
+  __syncthreads();
+  return rc;
+}
+
+// Z = H_0 H_1 ... H_{n-3} from the reflectors left in A, stored column-major
+// (Z[r][c] at Z[c * ldz + r]); a warp per column forms the dot products along
+// contiguous memory.  y, vs: shared scratch of n elements each.
+// T = double or float.
+template <int NTH = NT, class T>
+__device__ inline void cta_form_z_cm(const T* A, int n, int lda, const T* tau, T* Z, int ldz, T* y, T* vs) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NTH / 32;
+  for (int t = tid; t < n * n; t += NTH) Z[(size_t)(t / n) * ldz + (t % n)] = (t / n == t % n) ? T(1.0) : T(0.0);
+  __syncthreads();
+  for (int k = n - 3; k >= 0; k--) {
+    const T tk = tau[k];
+    if (tk == T(0.0)) continue;
+    const int L = n - k - 1;
+    for (int r = tid; r < L; r += NTH) vs[r] = (r == 0) ? T(1.0) : A[(size_t)(k + 1 + r) * lda + k];
+    __syncthreads();
+    // y_c = tau * sum_r v_r Z[k+1+r][k+1+c]: column k+1+c is contiguous
+    for (int c = warp; c < L; c += NW) {
+      const T* zc = Z + (size_t)(k + 1 + c) * ldz + (k + 1);
+      T s = T(0.0);
+      for (int r = lane; r < L; r += 32) s = fma(vs[r], zc[r], s);
+      s = warp_sum(s);
+      if (lane == 0) y[c] = tk * s;
+    }
+    __syncthreads();
+    for (int t = tid; t < L * L; t += NTH) {
+      const int c = t / L, r = t % L;
+      Z[(size_t)(k + 1 + c) * ldz + (k + 1 + r)] -= vs[r] * y[c];
+    }
+    __syncthreads();
+  }
+}
+
+// Full symmetric eigen-decomposition as cta_syev with Z column-major: on
+// return w[0..n) holds the eigenvalues and Z[t * ldz + a] is component a of
+// the eigenvector of w[t] (unordered).  A (row-major, lda) is destroyed; e,
+// tau: n elements each (any memory visible to the CTA); sm: shared scratch of
+// >= 4n + 33 elements.  Returns 0 on success.  T = double or float.
+template <int NTH = NT, class T>
+__device__ inline int cta_syev_cm(T* A, int n, int lda, T* w, T* Z, int ldz, T* e, T* tau, T* sm) {
+  T* v = sm;
+  T* p = sm + n;
+  T* cs = sm + 2 * n;      // 2n
+  T* red = sm + 4 * n;     // 33
+  if (n == 1) {
+    if (threadIdx.x == 0) { w[0] = A[0]; Z[0] = T(1.0); }
+    __syncthreads();
+    return 0;
+  }
+  cta_tridiag<NTH>(A, n, lda, w, e, tau, v, p, red);
+  cta_form_z_cm<NTH>(A, n, lda, tau, Z, ldz, v, p);
+  for (int t = threadIdx.x; t < n; t += NTH) {   // the bulge chase runs on shared copies of d and e
+    v[t] = w[t];
+    p[t] = (t + 1 < n) ? e[t] : T(0.0);
+  }
+  __syncthreads();
+  const int rc = cta_tridiag_qr<NTH, true>(v, p, n, Z, ldz, cs);
   for (int t = threadIdx.x; t < n; t += NTH) w[t] = v[t];
   __syncthreads();
   return rc;

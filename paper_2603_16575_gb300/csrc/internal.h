@@ -114,11 +114,12 @@ int launch_precond_w(const Tables& t, double tau_s, const PJob* jobs, int n_jobs
 // Mixed form (precond_mixed.cu): block-structured canonical orthogonalisation in
 // FP64, F' diagonalised in FP32, exact leftovers Sh/Gh; -1 if max_m is too large.
 // Per-pair intermediates: one slot of precond_mixed_slot_doubles(m) at slots + off[job];
-// mdim[job] = pair order m.
+// mdim[job] = pair order m; order: the jobs in the order the CTAs take them
+// (grid-stride; descending m balances the launch).
 size_t precond_mixed_slot_doubles(int m);
-size_t precond_mixed_scratch_doubles(int max_m, int n_warps, int n_cta);
-int launch_precond_mixed(const Tables& t, double tau_s, const PJob* jobs, int n_jobs, int max_m, double* slots,
-                         const long long* off, const int* mdim, double* scratch, int n_warps, int n_cta, int* err,
+size_t precond_mixed_scratch_doubles(int max_m, int n_cta);
+int launch_precond_mixed(const Tables& t, double tau_s, const PJob* jobs, const int* order, int n_jobs, int max_m,
+                         double* slots, const long long* off, const int* mdim, double* scratch, int n_cta, int* err,
                          cudaStream_t st);
 
 // ---- A4-A5 (solve.cu)

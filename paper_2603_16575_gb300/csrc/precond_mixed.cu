@@ -17,26 +17,28 @@
 // diagonalised in FP32 (F' = W diag(e~) W^T) and X = Y W.  A diagonal pair has
 // S_(ii,ii) = Q_i^T Q_i = 1: Y = 1, F' = F_(i,i).
 //
-// Four launches: (1) one warp per pair: 1 - M^T M, its FP64 eigen-decomposition,
-// Y and Z^T C Z; (2) one CTA per pair: F' = Y^T F Y (tiled FP64 GEMMs);
-// (3) one warp per pair: FP32 eigen-decomposition of F'; (4) one CTA per pair:
-// X = Y W and the leftovers (tiled FP64 GEMMs).  Per-pair intermediates live in
-// a scratch slot: Y [m][r], F' [r][r], W [r][r], Z^T C Z [nk][nk], e~ [r].
+// Four launches, each with one CTA per pair (grid-stride over the pairs in
+// descending order, so the largest start first): (1) 1 - M^T M, its FP64
+// eigen-decomposition, Y and Z^T C Z; (2) F' = Y^T F Y (tiled FP64 GEMMs);
+// (3) FP32 eigen-decomposition of F'; (4) X = Y W and the leftovers (tiled FP64
+// GEMMs).  The eigen-solvers (eig.cuh, Householder + implicit QR) keep the
+// eigenvectors column-major so that the rotations of the QR sweeps, one thread
+// per row, are coalesced.  Per-pair intermediates live in a scratch slot:
+// Y [m][r], F' [r][r], W [r][r], Z^T C Z [nk][nk], e~ [r].
 #include <algorithm>
 
+#include "eig.cuh"
 #include "pairview.cuh"
-#include "warp_eig.cuh"
 
 namespace osv {
 
-constexpr int PM_WARPS = 4;
+constexpr int PM_MAXN = 192;   // largest pair order (static shared scratch of the eigen-solvers)
 
 __host__ __device__ inline size_t pm_slot_doubles(int m) { return 4 * (size_t)m * m + (size_t)m + 8; }
-
-union PmSm {
-  WarpSmT<double> d;
-  WarpSmT<float> f;
-};
+// per-CTA scratch: (1) C, C0, V [3][max_m^2] + mu, e, tau; (2) F Y; (3) FP32 A, Z, e~, e, tau; (4) 3 blocks
+__host__ __device__ inline size_t pm_cta_doubles(int max_m) {
+  return 3 * (size_t)max_m * max_m + 3 * (size_t)max_m;
+}
 
 struct PmPair {              // per-pair view of the scratch slot
   double* Y;                 // [m][r]
@@ -52,78 +54,81 @@ __device__ __forceinline__ PmPair pm_pair(double* slots, const long long* off, i
 }
 
 // (1) S part: C = 1 - M^T M, eig(C) (FP64), kept directions, Y, Z^T C Z, r
-__global__ void __launch_bounds__(PM_WARPS * 32) k_pm_overlap(Tables t, double tau_s, const PJob* __restrict__ jobs,
-                                                              int n_jobs, double* slots, const long long* off,
-                                                              int max_m, double* scratch, int* err) {
-  __shared__ PmSm wsm[PM_WARPS];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * PM_WARPS + warp, nw = gridDim.x * PM_WARPS;
+__global__ void __launch_bounds__(NT, 3) k_pm_overlap(Tables t, double tau_s, const PJob* __restrict__ jobs,
+                                                      const int* __restrict__ order, int n_jobs, double* slots,
+                                                      const long long* off, int max_m, double* scratch, int* err) {
+  __shared__ double gsm[GEMM_SMEM_DOUBLES];
+  __shared__ double esm[4 * PM_MAXN + 33];
+  __shared__ int keep[PM_MAXN];
+  __shared__ int s_nk;
   const size_t M2 = (size_t)max_m * max_m;
-  double* Cw = scratch + (size_t)gw * (3 * M2 + 2 * (size_t)max_m);
+  double* Cw = scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m);
   double* C0 = Cw + M2;
-  double* V = C0 + M2;
+  double* V = C0 + M2;          // eigenvector k of C at V[k * nj ..]
   double* mu = V + M2;
-  double* tau = mu + max_m;
+  double* e = mu + max_m;
+  double* tau = e + max_m;
   const int n = t.n_occ;
-  for (int jid = gw; jid < n_jobs; jid += nw) {
+  for (int q = blockIdx.x; q < n_jobs; q += gridDim.x) {
+    const int jid = order[q];
     const PJob jb = jobs[jid];
     const int i = jb.i, j = jb.j;
     const int ni = t.n_osv[i], nj = (i == j) ? 0 : t.n_osv[j];
     const int m = ni + nj;
     const PmPair pp = pm_pair(slots, off, jid, m);
     if (i == j) {
-      if (lane == 0) *jb.r = ni;
-      __syncwarp();
+      if (threadIdx.x == 0) *jb.r = ni;
       continue;
     }
     const View Mv = dense_view(t.S[t.sf_id[i * n + j]], ni, nj, nj);
-    warp_gemm(nj, nj, ni, -1.0, transpose(Mv), Mv, 0.0, Cw, nj);
-    for (int c = lane; c < nj; c += 32) Cw[(size_t)c * nj + c] += 1.0;
-    __syncwarp();
-    for (int idx = lane; idx < nj * nj; idx += 32) C0[idx] = Cw[idx];
-    __syncwarp();
-    const int rc = warp_syev(Cw, nj, mu, V, tau, wsm[warp].d);
-    int nk = 0;
-    if (lane == 0) {
+    cta_gemm(nj, nj, ni, -1.0, transpose(Mv), Mv, 0.0, Cw, nj, gsm);
+    for (int c = threadIdx.x; c < nj; c += NT) Cw[(size_t)c * nj + c] += 1.0;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nj * nj; idx += NT) C0[idx] = Cw[idx];
+    __syncthreads();
+    const int rc = cta_syev_cm(Cw, nj, nj, mu, V, nj, e, tau, esm);
+    if (threadIdx.x == 0) {
       if (rc) atomicOr(err, ERR_EIG);
       double mumin = 1.0;
       for (int k = 0; k < nj; k++) mumin = fmin(mumin, mu[k]);
       const double smax = 1.0 + sqrt(fmax(0.0, 1.0 - mumin));
+      int nk = 0;
       for (int k = 0; k < nj; k++) {
         const double lam = mu[k] / (1.0 + sqrt(fmax(0.0, 1.0 - mu[k])));
-        if (mu[k] > 0.0 && lam > tau_s * smax) wsm[warp].d.keep[nk++] = k;
+        if (mu[k] > 0.0 && lam > tau_s * smax) keep[nk++] = k;
       }
+      s_nk = nk;
     }
-    nk = __shfl_sync(0xffffffffu, nk, 0);
-    __syncwarp();
-    const int r = ni + nk;
+    __syncthreads();
+    const int nk = s_nk, r = ni + nk;
     double* Y = pp.Y;
-    for (int idx = lane; idx < m * r; idx += 32) {
+    for (int idx = threadIdx.x; idx < m * r; idx += NT) {
       const int a = idx / r, b = idx % r;
       double y = 0.0;
       if (a < ni) y = (b == a) ? 1.0 : 0.0;
       else if (b >= ni) {
-        const int k = wsm[warp].d.keep[b - ni];
-        y = V[(size_t)(a - ni) * nj + k] / sqrt(mu[k]);
+        const int k = keep[b - ni];
+        y = V[(size_t)k * nj + (a - ni)] / sqrt(mu[k]);
       }
       Y[idx] = y;
     }
-    __syncwarp();
+    __syncthreads();
     const View Zv = dense_view(Y + (size_t)ni * r + ni, nj, nk, r);
-    warp_gemm(ni, nk, nj, -1.0, Mv, Zv, 0.0, Y + ni, r);                                     // -M Z
-    warp_gemm(nj, nk, nj, 1.0, dense_view(C0, nj, nj, nj), Zv, 0.0, Cw, nk);                // C Z
-    warp_gemm(nk, nk, nj, 1.0, transpose(Zv), dense_view(Cw, nj, nk, nk), 0.0, pp.ZCZ, nk);  // Z^T C Z
-    if (lane == 0) *jb.r = r;
-    __syncwarp();
+    cta_gemm(ni, nk, nj, -1.0, Mv, Zv, 0.0, Y + ni, r, gsm);                                     // -M Z
+    cta_gemm(nj, nk, nj, 1.0, dense_view(C0, nj, nj, nj), Zv, 0.0, Cw, nk, gsm);                // C Z
+    cta_gemm(nk, nk, nj, 1.0, transpose(Zv), dense_view(Cw, nj, nk, nk), 0.0, pp.ZCZ, nk, gsm);  // Z^T C Z
+    if (threadIdx.x == 0) *jb.r = r;
   }
 }
 
-// (2) F' = Y^T F Y, one CTA per pair (grid-stride)
-__global__ void __launch_bounds__(NT) k_pm_fprime(Tables t, const PJob* __restrict__ jobs, int n_jobs, double* slots,
+// (2) F' = Y^T F Y
+__global__ void __launch_bounds__(NT) k_pm_fprime(Tables t, const PJob* __restrict__ jobs,
+                                                  const int* __restrict__ order, int n_jobs, double* slots,
                                                   const long long* off, int max_m, double* scratch) {
   __shared__ double sm[GEMM_SMEM_DOUBLES];
-  double* FY = scratch + (size_t)blockIdx.x * max_m * max_m;
-  for (int jid = blockIdx.x; jid < n_jobs; jid += gridDim.x) {
+  double* FY = scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m);
+  for (int q = blockIdx.x; q < n_jobs; q += gridDim.x) {
+    const int jid = order[q];
     const PJob jb = jobs[jid];
     const int i = jb.i, j = jb.j;
     const int ni = t.n_osv[i], nj = (i == j) ? 0 : t.n_osv[j];
@@ -143,45 +148,50 @@ __global__ void __launch_bounds__(NT) k_pm_fprime(Tables t, const PJob* __restri
   }
 }
 
-// (3) FP32 eigen-decomposition of F' (symmetrised), one warp per pair: W, e~
-__global__ void __launch_bounds__(PM_WARPS * 32) k_pm_eig32(const PJob* __restrict__ jobs, int n_jobs, double* slots,
-                                                            const long long* off, const int* mdim, int max_m,
-                                                            float* scratch, int* err) {
-  __shared__ PmSm wsm[PM_WARPS];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * PM_WARPS + warp, nw = gridDim.x * PM_WARPS;
+// (3) FP32 eigen-decomposition of F' (symmetrised): W, e~
+__global__ void __launch_bounds__(NT, 3) k_pm_eig32(const PJob* __restrict__ jobs, const int* __restrict__ order,
+                                                    int n_jobs, double* slots, const long long* off,
+                                                    const int* mdim, int max_m, double* scratch, int* err) {
+  __shared__ float esm[4 * PM_MAXN + 33];
   const size_t M2 = (size_t)max_m * max_m;
-  float* A32 = scratch + (size_t)gw * (2 * M2 + 2 * (size_t)max_m);
-  float* Z32 = A32 + M2;
+  float* A32 = reinterpret_cast<float*>(scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m));
+  float* Z32 = A32 + M2;        // eigenvector t at Z32[t * r ..]
   float* e32 = Z32 + M2;
-  float* tau32 = e32 + max_m;
-  for (int jid = gw; jid < n_jobs; jid += nw) {
+  float* eb = e32 + max_m;
+  float* tau32 = eb + max_m;
+  for (int q = blockIdx.x; q < n_jobs; q += gridDim.x) {
+    const int jid = order[q];
     const PJob jb = jobs[jid];
     const int m = mdim[jid], r = *jb.r;
     const PmPair pp = pm_pair(slots, off, jid, m);
-    for (int idx = lane; idx < r * r; idx += 32) {
+    for (int idx = threadIdx.x; idx < r * r; idx += NT) {
       const int a = idx / r, b = idx % r;
       A32[idx] = (float)(0.5 * (pp.Fp[idx] + pp.Fp[(size_t)b * r + a]));
     }
-    __syncwarp();
-    const int rc = warp_syev(A32, r, e32, Z32, tau32, wsm[warp].f);
-    if (lane == 0 && rc) atomicOr(err, ERR_EIG);
-    for (int idx = lane; idx < r * r; idx += 32) pp.W[idx] = (double)Z32[idx];
-    for (int c = lane; c < r; c += 32) pp.et[c] = (double)e32[c];
-    __syncwarp();
+    __syncthreads();
+    const int rc = cta_syev_cm(A32, r, r, e32, Z32, r, eb, tau32, esm);
+    if (threadIdx.x == 0 && rc) atomicOr(err, ERR_EIG);
+    for (int idx = threadIdx.x; idx < r * r; idx += NT) {   // W[a][t] = component a of eigenvector t
+      const int tv = idx / r, a = idx % r;
+      pp.W[(size_t)a * r + tv] = (double)Z32[idx];
+    }
+    for (int c = threadIdx.x; c < r; c += NT) pp.et[c] = (double)e32[c];
+    __syncthreads();
   }
 }
 
-// (4) X = Y W; S~ = W^T (Y^T S Y) W; F~ = W^T F' W; leftovers.  One CTA per pair.
-__global__ void __launch_bounds__(NT) k_pm_final(Tables t, const PJob* __restrict__ jobs, int n_jobs, double* slots,
+// (4) X = Y W; S~ = W^T (Y^T S Y) W; F~ = W^T F' W; leftovers
+__global__ void __launch_bounds__(NT) k_pm_final(Tables t, const PJob* __restrict__ jobs,
+                                                 const int* __restrict__ order, int n_jobs, double* slots,
                                                  const long long* off, int max_m, double* scratch, int* err) {
   __shared__ double sm[GEMM_SMEM_DOUBLES];
   const size_t M2 = (size_t)max_m * max_m;
-  double* T1 = scratch + (size_t)blockIdx.x * 3 * M2;
+  double* T1 = scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m);
   double* St = T1 + M2;
   double* Ft = St + M2;
   const int n = t.n_occ;
-  for (int jid = blockIdx.x; jid < n_jobs; jid += gridDim.x) {
+  for (int q = blockIdx.x; q < n_jobs; q += gridDim.x) {
+    const int jid = order[q];
     const PJob jb = jobs[jid];
     const int i = jb.i, j = jb.j;
     const int ni = t.n_osv[i], nj = (i == j) ? 0 : t.n_osv[j];
@@ -216,24 +226,17 @@ __global__ void __launch_bounds__(NT) k_pm_final(Tables t, const PJob* __restric
 
 size_t precond_mixed_slot_doubles(int m) { return pm_slot_doubles(m); }
 
-size_t precond_mixed_scratch_doubles(int max_m, int n_warps, int n_cta) {
-  const size_t M2 = (size_t)max_m * max_m;
-  const size_t w = (size_t)n_warps * (3 * M2 + 2 * (size_t)max_m);     // (1), and (3) as floats
-  const size_t c = (size_t)n_cta * 3 * M2;                              // (2) uses M2 of it, (4) 3 M2
-  return std::max(w, c);
-}
+size_t precond_mixed_scratch_doubles(int max_m, int n_cta) { return (size_t)n_cta * pm_cta_doubles(max_m); }
 
-int launch_precond_mixed(const Tables& t, double tau_s, const PJob* jobs, int n_jobs, int max_m, double* slots,
-                         const long long* off, const int* mdim, double* scratch, int n_warps, int n_cta, int* err,
+int launch_precond_mixed(const Tables& t, double tau_s, const PJob* jobs, const int* order, int n_jobs, int max_m,
+                         double* slots, const long long* off, const int* mdim, double* scratch, int n_cta, int* err,
                          cudaStream_t st) {
   if (!n_jobs) return 0;
-  if (max_m > PW_MAXN) return -1;
-  const int n_wcta = (n_warps + PM_WARPS - 1) / PM_WARPS;
-  k_pm_overlap<<<n_wcta, PM_WARPS * 32, 0, st>>>(t, tau_s, jobs, n_jobs, slots, off, max_m, scratch, err);
-  k_pm_fprime<<<n_cta, NT, 0, st>>>(t, jobs, n_jobs, slots, off, max_m, scratch);
-  k_pm_eig32<<<n_wcta, PM_WARPS * 32, 0, st>>>(jobs, n_jobs, slots, off, mdim, max_m,
-                                                reinterpret_cast<float*>(scratch), err);
-  k_pm_final<<<n_cta, NT, 0, st>>>(t, jobs, n_jobs, slots, off, max_m, scratch, err);
+  if (max_m > PM_MAXN) return -1;
+  k_pm_overlap<<<n_cta, NT, 0, st>>>(t, tau_s, jobs, order, n_jobs, slots, off, max_m, scratch, err);
+  k_pm_fprime<<<n_cta, NT, 0, st>>>(t, jobs, order, n_jobs, slots, off, max_m, scratch);
+  k_pm_eig32<<<n_cta, NT, 0, st>>>(jobs, order, n_jobs, slots, off, mdim, max_m, scratch, err);
+  k_pm_final<<<n_cta, NT, 0, st>>>(t, jobs, order, n_jobs, slots, off, max_m, scratch, err);
   note_launch(4);
   return 0;
 }
