@@ -407,7 +407,7 @@ double fragment_mixed_flops(const osvmp2_ctx* c, const Frag& f, int iters) {
 // within a batch the tiles are ordered by (x, aux tile, pair) so that the
 // pairs sharing an aux tile of B_x read it while it is resident in L2.
 int gproj_tensor(osvmp2_ctx* c, const std::vector<GJob>& gj, const std::vector<long long>& usrow, const float* Us,
-                 long long us_rows, int ldv) {
+                 long long us_rows, int ldv, const std::vector<int>& gsrow, float* Gs, int ldg) {
   const int nv = c->sys.n_vir, nx = c->sys.n_aux, n = c->sys.n_occ;
   if (us_rows + tc::BN >= (long long)INT32_MAX)
     return fail(c, OSVMP2_E_ARG, "U slice store exceeds the tensor-map row range");
@@ -449,6 +449,8 @@ int gproj_tensor(osvmp2_ctx* c, const std::vector<GJob>& gj, const std::vector<l
             jb.m0 = mt * tc::BM;
             jb.n0 = n0;
             jb.s = 0.0;
+            jb.x_row = gsrow[q];
+            jb.x_sstride = g.r;
             jobs.push_back(jb);
           }
         }
@@ -456,7 +458,7 @@ int gproj_tensor(osvmp2_ctx* c, const std::vector<GJob>& gj, const std::vector<l
     TRY(tmp_alloc(c, jd, jobs.size() * sizeof(tc::Job)));
     CK(cudaMemcpyAsync(jd.p, jobs.data(), jobs.size() * sizeof(tc::Job), cudaMemcpyHostToDevice, c->st));
     if (launch_gproj_tc((const float*)bs.p, (long long)nb * tc::NSL * nx, Us, us_rows, nv, ldv, (const tc::Job*)jd.p,
-                        (int)jobs.size(), c->err_d, c->st))
+                        (int)jobs.size(), Gs, ldg, c->err_d, c->st))
       return fail(c, OSVMP2_E_CUDA, "tensor-map encoding for the G projection failed");
     CK(cudaGetLastError());
   }
@@ -709,7 +711,10 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
     std::vector<UJob> uj;
     std::vector<GJob> gj;
     std::vector<long long> g_usrow;    // row of slice 0 of U_p^T in Us, per G job
-    std::vector<KgJob> kgj;
+    std::vector<int> g_gsrow;          // row of slice 0 of G_p,x^T in Gs, per G job
+    std::vector<tc::Job> ktj;          // K~ tiles from the slices of G
+    const int ldg = (nx + 3) & ~3;
+    long long gs_rows = 0;
     for (auto& p : newp) {
       const int pid = c->pair_id[(size_t)p.first * n + p.second];
       const int r = c->r_h[pid];
@@ -748,40 +753,65 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
       go += (size_t)r * nx;
       gj.push_back(GJob{i, r, U, Gi});
       g_usrow.push_back((long long)urow);
+      const long long gi_row = gs_rows;
+      g_gsrow.push_back((int)gs_rows);
+      gs_rows += tc::NSL * (long long)r;
       float* Gj = Gi;
+      long long gj_row = gi_row;
       if (i != j) {
         Gj = gmem + go;
         go += (size_t)r * nx;
         gj.push_back(GJob{j, r, U, Gj});
         g_usrow.push_back((long long)urow);
+        gj_row = gs_rows;
+        g_gsrow.push_back((int)gs_rows);
+        gs_rows += tc::NSL * (long long)r;
       }
       urow += tc::NSL * (size_t)r;
       f_g += (i != j ? 2.0 : 1.0) * 2.0 * r * (double)nv * nx;
       c->Gi_h[pid] = Gi;
       c->Gj_h[pid] = Gj;
-      kgj.push_back(KgJob{r, Gi, Gj, c->Kt_h[pid]});
+      for (int m0 = 0; m0 < r; m0 += tc::BM)
+        for (int n0 = 0; n0 < r; n0 += tc::BN) {
+          tc::Job jb;
+          jb.a_row = (int)(gi_row + m0);
+          jb.a_sstride = r;
+          jb.b_row = (int)(gj_row + n0);
+          jb.b_sstride = r;
+          jb.m_valid = std::min(tc::BM, r - m0);
+          jb.n_valid = std::min(tc::BN, r - n0);
+          jb.out = c->Kt_h[pid] + (size_t)m0 * r + n0;
+          jb.ld_out = r;
+          jb.m0 = m0;
+          jb.n0 = n0;
+          jb.s = 0.0;
+          jb.x_row = jb.x_sstride = 0;
+          ktj.push_back(jb);
+        }
       f_kg += 2.0 * (double)r * r * nx;
     }
     std::vector<float*> uall(c->K_h.size(), nullptr);
     for (size_t q = 0; q < c->U_h.size(); q++) uall[q] = c->U_h[q];
     CK(cudaMemcpyAsync(c->U_d, uall.data(), uall.size() * sizeof(float*), cudaMemcpyHostToDevice, c->st));
-    Tmp ju, jg, jkg;
+    if (gs_rows + tc::BM >= (long long)INT32_MAX)
+      return fail(c, OSVMP2_E_ARG, "G slice store exceeds the tensor-map row range");
+    Tmp ju, jkt, gsl;
     TRY(tmp_alloc(c, ju, uj.size() * sizeof(UJob)));
-    TRY(tmp_alloc(c, jg, gj.size() * sizeof(GJob)));
-    TRY(tmp_alloc(c, jkg, kgj.size() * sizeof(KgJob)));
+    TRY(tmp_alloc(c, jkt, ktj.size() * sizeof(tc::Job)));
+    TRY(tmp_alloc(c, gsl, (size_t)gs_rows * ldg * sizeof(float)));
     CK(cudaMemcpyAsync(ju.p, uj.data(), uj.size() * sizeof(UJob), cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(jg.p, gj.data(), gj.size() * sizeof(GJob), cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(jkg.p, kgj.data(), kgj.size() * sizeof(KgJob), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(jkt.p, ktj.data(), ktj.size() * sizeof(tc::Job), cudaMemcpyHostToDevice, c->st));
     Tmp uscr;
     TRY(tmp_alloc(c, uscr, (size_t)n_cta * nv * std::max(max_r, 1) * sizeof(double)));
     ph_begin(c, OSVMP2_PH_PROJECT);
     launch_ubasis(t, (const UJob*)ju.p, (int)uj.size(), n_cta, (double*)uscr.p, max_r, c->st);
     CK(cudaGetLastError());
-    TRY(gproj_tensor(c, gj, g_usrow, usmem, (long long)us_rows, ldv));
+    TRY(gproj_tensor(c, gj, g_usrow, usmem, (long long)us_rows, ldv, g_gsrow, (float*)gsl.p, ldg));
     ph_end(c, OSVMP2_PH_PROJECT, f_u + f_g, c->sys.B ? 8.0 * (double)gj.size() * nx * nv : 0.0);
     CK(cudaGetLastError());
     ph_begin(c, OSVMP2_PH_EXCHANGE);
-    launch_ktilde_g(nx, (const KgJob*)jkg.p, (int)kgj.size(), max_r, c->st);
+    if (launch_kt_tc((const float*)gsl.p, gs_rows, nx, ldg, (const tc::Job*)jkt.p, (int)ktj.size(), c->err_d, c->st))
+      return fail(c, OSVMP2_E_CUDA, "tensor-map encoding for K~ failed");
     ph_end(c, OSVMP2_PH_EXCHANGE, f_kg);
     CK(cudaGetLastError());
     TRY(check_err_flag(c, "mixed pair build"));

@@ -11,7 +11,7 @@ namespace osv {
 constexpr int NT = 256;          // threads of every CTA that calls the CTA routines
 constexpr int TM = 64, TN = 64, TK = 16;
 constexpr int GEMM_SMEM_DOUBLES = TK * (TM + TN);
-constexpr int GEMM_SMEM_F32 = TK * 2 * 96;   // floats: the 96 x 96 tiles of cta_gemm_f32x64
+constexpr int GEMM_SMEM_F32 = TK * 2 * 96;   // floats: the 96 x 96 tiles of cta_gemm_f32s
 
 // ---------------------------------------------------------------- views
 // One dense block: element (r,c) at p[r*ld + c], or at p[c*ld + r] when tr.
@@ -101,70 +101,6 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   s = a + b;
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
-}
-
-// As tile_mma_t<float>, but each k-tile's sixteen FP32 products are summed in
-// FP32 and the tile sums are accumulated in a compensated (hi, lo) FP32 pair
-// (two-sum), added to acc in FP64 at the end: the rounding of long FP32
-// accumulations (which grows with K) is confined to sixteen terms, and the
-// accumulation across k-tiles costs FP32 operations only (FP64 throughput is
-// 1/64 of FP32 on this part).
-template <class VA, class VB>
-__device__ __forceinline__ void tile_mma_f32x64(int M, int N, int K, int m0, int n0, const VA& A, const VB& B,
-                                                double acc[4][4], float* sm) {
-  float* As = sm;
-  float* Bs = sm + TK * TM;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float hi[4][4], lo[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++) hi[i][j] = lo[i][j] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += TK) {
-#pragma unroll
-    for (int t = 0; t < TM * TK / NT; t++) {
-      const int e = tid + t * NT, m = e % TM, k = e / TM;
-      const int gm = m0 + m, gk = k0 + k;
-      As[k * TM + m] = (gm < M && gk < K) ? static_cast<float>(A.get(gm, gk)) : 0.f;
-    }
-#pragma unroll
-    for (int t = 0; t < TN * TK / NT; t++) {
-      const int e = tid + t * NT, n = e % TN, k = e / TN;
-      const int gn = n0 + n, gk = k0 + k;
-      Bs[k * TN + n] = (gn < N && gk < K) ? static_cast<float>(B.get(gk, gn)) : 0.f;
-    }
-    __syncthreads();
-    float part[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-      for (int j = 0; j < 4; j++) part[i][j] = 0.f;
-#pragma unroll
-    for (int k = 0; k < TK; k++) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; i++) a[i] = As[k * TM + ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; j++) b[j] = Bs[k * TN + tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) part[i][j] = fmaf(a[i], b[j], part[i][j]);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        float e;
-        two_sum_f(hi[i][j], part[i][j], hi[i][j], e);
-        lo[i][j] += e;
-      }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++) acc[i][j] += (double)hi[i][j] + (double)lo[i][j];
 }
 
 // FP32 tile of (16 R) x (16 R) outputs, R x R per thread (thread (ty, tx) owns
@@ -292,34 +228,6 @@ __device__ void cta_gemm_f32s(int M, int N, int K, double alpha, const VA& A, co
     cta_gemm_f32r<4>(M, N, K, alpha, A, B, beta, C, ldc, sm);
 }
 
-// C[MxN] (ld ldc, element type CT) = beta*C + alpha*A*B with FP32 products
-// accumulated per k-tile in FP32 and across k-tiles in compensated FP32
-// (tile_mma_f32x64); the final scaling and the update of C are FP64.
-template <class CT, class VA, class VB>
-__device__ void cta_gemm_f32x64(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, CT* C,
-                                int ldc, float* sm) {
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int m0 = 0; m0 < M; m0 += TM)
-    for (int n0 = 0; n0 < N; n0 += TN) {
-      double acc[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
-      tile_mma_f32x64(M, N, K, m0, n0, A, B, acc, sm);
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-          const int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
-          if (r < M && c < N) {
-            CT* cp = C + (size_t)r * ldc + c;
-            *cp = static_cast<CT>((beta == 0.0 ? 0.0 : beta * static_cast<double>(*cp)) + alpha * acc[i][j]);
-          }
-        }
-    }
-  __syncthreads();
-}
 
 template <class VA, class VB>
 __device__ __forceinline__ void tile_mma(int M, int N, int K, int m0, int n0, const VA& A, const VB& B,
@@ -358,6 +266,79 @@ template <class VA, class VB>
 __device__ void cta_gemm(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, double* C,
                          int ldc, double* sm) {
   cta_gemm_t<double, double>(M, N, K, alpha, A, B, beta, C, ldc, sm);
+}
+
+// FP64 GEMM with (16 R) x (16 R) output tiles, R x R per thread (thread (ty, tx)
+// owns rows m0 + ty + 16 i and columns n0 + tx + 16 j); the K order of every
+// output's FMAs is that of cta_gemm, so the results are the same.  sm: 2 TK 16R.
+template <int R, class VA, class VB>
+__device__ void cta_gemm_r(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, double* C,
+                           int ldc, double* sm) {
+  constexpr int TMR = 16 * R;
+  double* As = sm;
+  double* Bs = sm + TK * TMR;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += TMR)
+    for (int n0 = 0; n0 < N; n0 += TMR) {
+      double acc[R][R];
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int j = 0; j < R; j++) acc[i][j] = 0.0;
+      for (int k0 = 0; k0 < K; k0 += TK) {
+#pragma unroll
+        for (int t = 0; t < TMR * TK / NT; t++) {
+          const int e = tid + t * NT, m = e % TMR, k = e / TMR;
+          const int gm = m0 + m, gk = k0 + k;
+          As[k * TMR + m] = (gm < M && gk < K) ? static_cast<double>(A.get(gm, gk)) : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < TMR * TK / NT; t++) {
+          const int e = tid + t * NT, n = e % TMR, k = e / TMR;
+          const int gn = n0 + n, gk = k0 + k;
+          Bs[k * TMR + n] = (gn < N && gk < K) ? static_cast<double>(B.get(gk, gn)) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < TK; k++) {
+          double a[R], b[R];
+#pragma unroll
+          for (int i = 0; i < R; i++) a[i] = As[k * TMR + ty + 16 * i];
+#pragma unroll
+          for (int j = 0; j < R; j++) b[j] = Bs[k * TMR + tx + 16 * j];
+#pragma unroll
+          for (int i = 0; i < R; i++)
+#pragma unroll
+            for (int j = 0; j < R; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+          const int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
+          if (r < M && c < N) {
+            double* cp = C + (size_t)r * ldc + c;
+            *cp = (beta == 0.0 ? 0.0 : beta * *cp) + alpha * acc[i][j];
+          }
+        }
+    }
+  __syncthreads();
+}
+
+// cta_gemm with 96 x 96 tiles where they pad less than 64 x 64 ones (pair
+// orders 65..96 fit one tile instead of four); sm holds GEMM_SMEM_WIDE doubles.
+constexpr int GEMM_SMEM_WIDE = TK * 2 * 96;
+template <class VA, class VB>
+__device__ void cta_gemm_a(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, double* C,
+                           int ldc, double* sm) {
+  const long long p64 = (long long)((M + 63) / 64) * ((N + 63) / 64) * 4096;
+  const long long p96 = (long long)((M + 95) / 96) * ((N + 95) / 96) * 9216;
+  if (p96 < p64)
+    cta_gemm_r<6>(M, N, K, alpha, A, B, beta, C, ldc, sm);
+  else
+    cta_gemm_r<4>(M, N, K, alpha, A, B, beta, C, ldc, sm);
 }
 
 // Dense float matrix view (element (r,c) at p[r*ld+c], or p[c*ld+r] when tr).

@@ -546,6 +546,133 @@ __device__ inline int cta_syev_cm(T* A, int n, int lda, T* w, T* Z, int ldz, T* 
   return rc;
 }
 
+// ---------------------------------------------------------------- batched QR
+// The bulge chase of the implicit QR (as cta_tridiag_qr) is sequential; run by
+// one thread of a CTA it leaves the rest of the CTA idle and, in FP64, uses a
+// thirty-second of the FP64 pipe for every instruction.  These two routines
+// split cta_tridiag_qr into (a) the chase of one tridiagonal per THREAD, many
+// problems per warp, recording the sweeps (l, h) and their rotations, and (b)
+// the application of the recorded rotations to the rows of Z by a CTA.  The
+// sweeps are those of cta_tridiag_qr; the rotations are formed with fewer
+// FP64 operations (chase_rotation).
+
+// (a) One thread: chase (d[n], e[n-1]) to diagonal form, appending each sweep
+// to swp (l, h pairs, capacity cap_s sweeps) and its rotations (c, s pairs,
+// capacity cap_r) to rot.  Returns 0 on convergence (*n_sw sweeps recorded, d
+// holds the eigenvalues), 1 if the sweep limit was reached, 2 if a record
+// would overflow.
+// Givens rotation (c, s) with c x + s z = r >= 0, -s x + c z = 0.  FP64: one
+// reciprocal square root; FP32: a correctly rounded square root and one
+// division (unbiased rounding, so the accumulated rotations stay orthogonal
+// to the FP32 rounding level).  hypot and two divisions where x^2 + z^2 could
+// leave the normal range.
+__device__ __forceinline__ void chase_rotation(double x, double z, double& c, double& s, double& r) {
+  const double q = x * x + z * z;
+  if (q > 1e-280 && q < 1e280) {
+    const double inv = rsqrt(q);
+    c = x * inv;
+    s = z * inv;
+    r = q * inv;
+  } else {
+    r = hypot(x, z);
+    c = 1.0;
+    s = 0.0;
+    if (r != 0.0) { c = x / r; s = z / r; }
+  }
+}
+__device__ __forceinline__ void chase_rotation(float x, float z, float& c, float& s, float& r) {
+  const float q = x * x + z * z;
+  if (q > 1e-36f && q < 1e36f) {
+    r = sqrtf(q);
+    const float inv = 1.f / r;
+    c = x * inv;
+    s = z * inv;
+  } else {
+    r = hypotf(x, z);
+    c = 1.f;
+    s = 0.f;
+    if (r != 0.f) { c = x / r; s = z / r; }
+  }
+}
+
+template <class T>
+__device__ inline int tridiag_qr_record(T* __restrict__ d, T* __restrict__ e, int n, int* __restrict__ swp, int cap_s,
+                                        T* __restrict__ rot, int cap_r, int* n_sw) {
+  const T eps = sizeof(T) == 8 ? T(2.220446049250313e-16) : T(1.1920929e-07);
+  const int max_sweeps = 40 * n + 100;
+  int ns = 0, nr = 0;
+  *n_sw = 0;
+  for (int sweeps = 0;; sweeps++) {
+    int h = n - 1;
+    while (h > 0) {
+      if (fabs(e[h - 1]) <= eps * (fabs(d[h - 1]) + fabs(d[h]))) { e[h - 1] = T(0.0); h--; }
+      else break;
+    }
+    if (h == 0) { *n_sw = ns; return 0; }
+    if (sweeps >= max_sweeps) return 1;
+    int l = h - 1;
+    while (l > 0) {
+      if (fabs(e[l - 1]) <= eps * (fabs(d[l - 1]) + fabs(d[l]))) { e[l - 1] = T(0.0); break; }
+      l--;
+    }
+    if (ns >= cap_s || nr + (h - l) > cap_r) return 2;
+    swp[2 * ns] = l;
+    swp[2 * ns + 1] = h;
+    ns++;
+    T* cs = rot + 2 * (size_t)nr;
+    nr += h - l;
+    const T delta = T(0.5) * (d[h - 1] - d[h]);
+    const T eh = e[h - 1];
+    const T den = delta + copysign(hypot(delta, eh), delta);
+    const T mu = d[h] - (den != T(0.0) ? eh * eh / den : T(0.0));
+    // d[k] and e[k] as updated by the previous rotation stay in registers
+    T dk = d[l], ek = e[l];
+    T x = dk - mu, z = ek;
+    for (int k = l; k < h; k++) {
+      const T cc = d[k + 1];
+      const T en = (k + 1 < h) ? e[k + 1] : T(0.0);
+      T c, s, r;
+      chase_rotation(x, z, c, s, r);
+      if (k > l) e[k - 1] = r;
+      const T a = dk, b = ek;
+      d[k] = c * c * a + T(2.0) * c * s * b + s * s * cc;
+      dk = s * s * a - T(2.0) * c * s * b + c * c * cc;
+      const T ekn = c * s * (cc - a) + (c * c - s * s) * b;
+      e[k] = ekn;
+      if (k + 1 < h) {
+        x = ekn;
+        z = s * en;
+        ek = c * en;
+      }
+      cs[2 * (k - l)] = c;
+      cs[2 * (k - l) + 1] = s;
+    }
+    d[h] = dk;
+  }
+}
+
+// (b) The CTA: apply the n_sw recorded sweeps to Z (n x n, column-major, ldz;
+// a thread per row, coalesced).
+template <int NTH = NT, class T>
+__device__ inline void apply_qr_record_cm(T* Z, int ldz, int n, const int* swp, int n_sw, const T* rot) {
+  for (int row = threadIdx.x; row < n; row += NTH) {
+    T* zr = Z + row;
+    const T* cs = rot;
+    for (int q = 0; q < n_sw; q++) {
+      const int l = swp[2 * q], h = swp[2 * q + 1];
+      T carry = zr[(size_t)l * ldz];
+      for (int k = l; k < h; k++, cs += 2) {
+        const T c = cs[0], s = cs[1];
+        const T y = zr[(size_t)(k + 1) * ldz];
+        zr[(size_t)k * ldz] = c * carry + s * y;
+        carry = -s * carry + c * y;
+      }
+      zr[(size_t)h * ldz] = carry;
+    }
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- top-k
 // Number of eigenvalues of the tridiagonal (d, e) strictly below x
 // (Sturm sequence of the LDL^T pivots).

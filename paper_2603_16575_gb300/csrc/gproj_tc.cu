@@ -11,6 +11,15 @@
 // The tile M dimension is the aux index (128 per tile), N the pair-basis
 // index mu (<= 64 per tile), so the output G[mu][P] is stored with the TMEM
 // lane (aux) as the contiguous index.
+//
+// The epilogue also cuts G (hi + lo, before its rounding to FP32) into the
+// fixed-point slices of G^T along the aux index: the 32 lanes of a drain warp
+// hold 32 consecutive aux rows of one column, i.e. one k-chunk of the next
+// contraction K~_p = G_p,i G_p,j^T (Eq. osv_close_k in the orthonormal pair
+// basis), which then runs on the tensor cores with the same split-precision
+// kernel: exact slice products and ~35 bits in K~, where FP32 products of the
+// rounded G would leave a relative error of ~1e-8 in every pair energy.
+//   Gs  [G job][slice][r][ldg]      G_p,x slices, K = n_aux innermost
 #include "internal.h"
 #include "tc_tf32x3.cuh"
 
@@ -54,17 +63,46 @@ void launch_bslices(const BSrc& src, const int* xs, int n_x, float* Bs, int ldv,
   note_launch(1);
 }
 
-// G[mu][P] = hi + lo (TMEM lane = aux row P, column = mu)
-struct EpiG {
-  __device__ __forceinline__ void operator()(const tc::Job& jb, int r, int c, float h, float l) const {
-    static_cast<float*>(jb.out)[(size_t)c * jb.ld_out + r] = h + l;
+// G[mu][P] = hi + lo (TMEM lane = aux row P, column = mu), and the slices of
+// G^T: slice s of row mu at Gs[(x_row + s x_sstride + mu) ldg + P]
+struct EpiGS {
+  static constexpr bool kWarp = true;
+  float* gs;
+  int ldg;
+  __device__ __forceinline__ void warp(const tc::Job& jb, int row, int n0, const uint32_t* h,
+                                       const uint32_t* l) const {
+    const bool ok = row < jb.m_valid;
+    const int P = jb.m0 + row;
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const int c = n0 + u;
+      if (c >= jb.n_valid) break;   // warp-uniform
+      const float hf = __uint_as_float(h[u]), lf = __uint_as_float(l[u]);
+      float v[tc::NSL];
+      tc::warp_fixed_slices(ok ? (double)hf + (double)lf : 0.0, v);
+      if (ok) {
+        static_cast<float*>(jb.out)[(size_t)c * jb.ld_out + row] = hf + lf;
+        const int mu = jb.n0 + c;
+#pragma unroll
+        for (int s = 0; s < tc::NSL; s++) gs[(size_t)(jb.x_row + s * jb.x_sstride + mu) * ldg + P] = v[s];
+      }
+    }
   }
 };
 
 // out[row][col] = hi + lo (row-major)
 struct EpiRow {
+  static constexpr bool kWarp = false;
   __device__ __forceinline__ void operator()(const tc::Job& jb, int r, int c, float h, float l) const {
     static_cast<float*>(jb.out)[(size_t)r * jb.ld_out + c] = h + l;
+  }
+};
+
+// out[row][col] = hi + lo in FP64 (row-major): K~ from the slices of G
+struct EpiRow64 {
+  static constexpr bool kWarp = false;
+  __device__ __forceinline__ void operator()(const tc::Job& jb, int r, int c, float h, float l) const {
+    static_cast<double*>(jb.out)[(size_t)r * jb.ld_out + c] = (double)h + (double)l;
   }
 };
 
@@ -97,14 +135,29 @@ bool make_slice_map(CUtensorMap* m, const float* base, int n_k, int ldk, long lo
 }
 
 int launch_gproj_tc(const float* Bs, long long a_rows, const float* Us, long long b_rows, int n_vir, int ldv,
-                    const tc::Job* jobs, int n_jobs, int* err, cudaStream_t st) {
+                    const tc::Job* jobs, int n_jobs, float* Gs, int ldg, int* err, cudaStream_t st) {
   if (!n_jobs) return 0;
-  if (cudaFuncSetAttribute(tc::k_tf32x3<EpiG>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess)
+  if (cudaFuncSetAttribute(tc::k_tf32x3<EpiGS>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) !=
+      cudaSuccess)
     return -1;
   CUtensorMap ma, mb;
   if (!make_slice_map(&ma, Bs, n_vir, ldv, a_rows, tc::BM) || !make_slice_map(&mb, Us, n_vir, ldv, b_rows, tc::BROWS))
     return -1;
-  tc::k_tf32x3<EpiG><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_vir, err, EpiG{});
+  tc::k_tf32x3<EpiGS><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_vir, err, EpiGS{Gs, ldg});
+  note_launch(1);
+  return 0;
+}
+
+int launch_kt_tc(const float* Gs, long long rows, int n_aux, int ldg, const tc::Job* jobs, int n_jobs, int* err,
+                 cudaStream_t st) {
+  if (!n_jobs) return 0;
+  if (cudaFuncSetAttribute(tc::k_tf32x3<EpiRow64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) !=
+      cudaSuccess)
+    return -1;
+  CUtensorMap ma, mb;
+  if (!make_slice_map(&ma, Gs, n_aux, ldg, rows, tc::BM) || !make_slice_map(&mb, Gs, n_aux, ldg, rows, tc::BROWS))
+    return -1;
+  tc::k_tf32x3<EpiRow64><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_aux, err, EpiRow64{});
   note_launch(1);
   return 0;
 }

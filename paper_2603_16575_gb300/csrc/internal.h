@@ -143,23 +143,19 @@ struct GJob {          // G = U^T B_x  [r][n_aux]
   const float* U;
   float* G;
 };
-struct KgJob {         // K~ = G_i G_j^T  [r][r]
-  int r;
-  const float* Gi;
-  const float* Gj;
-  double* Kt;
-};
 void launch_ubasis(const Tables& t, const UJob* jobs, int n_jobs, int n_cta, double* scratch, int max_r,
                    cudaStream_t st);
-void launch_gproj(const BSrc& src, const GJob* jobs, int n_jobs, int max_r, cudaStream_t st);
 // B_x for the orbitals xs[0..n_x) as TF32 slices (tf32_split.cuh), transposed:
 // slot u, slice s, row P at Bs + ((u * tc::NSL + s) * n_aux + P) * ldv
 void launch_bslices(const BSrc& src, const int* xs, int n_x, float* Bs, int ldv, cudaStream_t st);
-// G tiles with the split-TF32 tensor-core kernel: A = Bs (rows a_rows), B = Us (rows b_rows), K = n_vir.
-// Returns 0, or -1 if a tensor map could not be encoded.
+// G tiles with the split-TF32 tensor-core kernel: A = Bs (rows a_rows), B = Us (rows b_rows), K = n_vir;
+// each job also writes the slices of its G^T to Gs [rows][ldg] (slice s of row mu at row
+// job.x_row + s * job.x_sstride + mu).  Returns 0, or -1 if a tensor map could not be encoded.
 int launch_gproj_tc(const float* Bs, long long a_rows, const float* Us, long long b_rows, int n_vir, int ldv,
-                    const tc::Job* jobs, int n_jobs, int* err, cudaStream_t st);
-void launch_ktilde_g(int n_aux, const KgJob* jobs, int n_jobs, int max_r, cudaStream_t st);
+                    const tc::Job* jobs, int n_jobs, float* Gs, int ldg, int* err, cudaStream_t st);
+// K~ = G_i G_j^T tiles from the slices in Gs (rows in total, K = n_aux), FP64 row-major output.
+int launch_kt_tc(const float* Gs, long long rows, int n_aux, int ldg, const tc::Job* jobs, int n_jobs, int* err,
+                 cudaStream_t st);
 // 2-D FP32 tensor map over rows x n_k (row stride ldk floats, a multiple of 4),
 // 128-byte swizzle, box tc::BK x box_rows; false if the driver rejects it.
 bool make_slice_map(CUtensorMap* m, const float* base, int n_k, int ldk, long long rows, int box_rows);

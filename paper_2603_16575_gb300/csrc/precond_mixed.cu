@@ -17,14 +17,20 @@
 // diagonalised in FP32 (F' = W diag(e~) W^T) and X = Y W.  A diagonal pair has
 // S_(ii,ii) = Q_i^T Q_i = 1: Y = 1, F' = F_(i,i).
 //
-// Four launches, each with one CTA per pair (grid-stride over the pairs in
-// descending order, so the largest start first): (1) 1 - M^T M, its FP64
-// eigen-decomposition, Y and Z^T C Z; (2) F' = Y^T F Y (tiled FP64 GEMMs);
-// (3) FP32 eigen-decomposition of F'; (4) X = Y W and the leftovers (tiled FP64
-// GEMMs).  The eigen-solvers (eig.cuh, Householder + implicit QR) keep the
-// eigenvectors column-major so that the rotations of the QR sweeps, one thread
-// per row, are coalesced.  Per-pair intermediates live in a scratch slot:
-// Y [m][r], F' [r][r], W [r][r], Z^T C Z [nk][nk], e~ [r].
+// Launches (CTA kernels take one pair per CTA, grid-stride over the pairs in
+// descending order, so the largest start first):
+//   (1a) C = 1 - M^T M, Householder tridiagonalisation and Z (FP64, CTA);
+//   (1b) the QR bulge chase of every C, one pair per thread (FP64);
+//   (1c) recorded rotations applied to Z, kept directions, Y, Z^T C Z (CTA);
+//   (2)  F' = Y^T F Y (tiled FP64 GEMMs, CTA);
+//   (3a-c) the same three steps for the FP32 eigen-decomposition of F';
+//   (4)  X = Y W and the leftovers (tiled FP64 GEMMs, CTA).
+// The eigen-solver is Householder + implicit QR (eig.cuh) with the chase run
+// per thread over many pairs at once and its rotations recorded, then applied
+// to the eigenvectors (kept column-major, so the rotations are coalesced) by a
+// CTA; a pair whose record overflows is redone by the in-CTA solver.
+// Per-pair intermediates live in a scratch slot: Y [m][r], F' [r][r], W [r][r],
+// Z^T C Z [nk][nk], e~ [r], and the eigen-solver's work area.
 #include <algorithm>
 
 #include "eig.cuh"
@@ -34,7 +40,17 @@ namespace osv {
 
 constexpr int PM_MAXN = 192;   // largest pair order (static shared scratch of the eigen-solvers)
 
-__host__ __device__ inline size_t pm_slot_doubles(int m) { return 4 * (size_t)m * m + (size_t)m + 8; }
+// eigen-solver work area of a pair of order m: status and sweep count, Z (m x m),
+// d and e (m each), the sweep record (cap_s (l, h) pairs) and the rotation
+// record (cap_r (c, s) pairs); typed FP64 or FP32 by the step that uses it
+__host__ __device__ inline int pm_cap_s(int m) { return 4 * m + 64; }
+__host__ __device__ inline int pm_cap_r(int m) { return 2 * m * m + 64; }
+__host__ __device__ inline size_t pm_work_doubles(int m) {
+  return 2 + (size_t)m * m + 2 * (size_t)m + (size_t)pm_cap_s(m) + 2 * (size_t)pm_cap_r(m);
+}
+__host__ __device__ inline size_t pm_slot_doubles(int m) {
+  return 4 * (size_t)m * m + (size_t)m + 8 + pm_work_doubles(m);
+}
 // per-CTA scratch: (1) C, C0, V [3][max_m^2] + mu, e, tau; (2) F Y; (3) FP32 A, Z, e~, e, tau; (4) 3 blocks
 __host__ __device__ inline size_t pm_cta_doubles(int max_m) {
   return 3 * (size_t)max_m * max_m + 3 * (size_t)max_m;
@@ -46,28 +62,112 @@ struct PmPair {              // per-pair view of the scratch slot
   double* W;                 // [r][r]
   double* ZCZ;               // [nk][nk]
   double* et;                // [r]
+  double* wk;                // eigen-solver work area
 };
 __device__ __forceinline__ PmPair pm_pair(double* slots, const long long* off, int jid, int m) {
   double* b = slots + off[jid];
   const size_t M2 = (size_t)m * m;
-  return PmPair{b, b + M2, b + 2 * M2, b + 3 * M2, b + 4 * M2};
+  return PmPair{b, b + M2, b + 2 * M2, b + 3 * M2, b + 4 * M2, b + 4 * M2 + m + 8};
 }
 
-// (1) S part: C = 1 - M^T M, eig(C) (FP64), kept directions, Y, Z^T C Z, r
-__global__ void __launch_bounds__(NT, 3) k_pm_overlap(Tables t, double tau_s, const PJob* __restrict__ jobs,
-                                                      const int* __restrict__ order, int n_jobs, double* slots,
-                                                      const long long* off, int max_m, double* scratch, int* err) {
+template <class T>
+struct PmEig {               // typed view of a pair's eigen-solver work area
+  int* hdr;                  // [0] status of the chase (0, 1 no convergence, 2 record overflow), [1] sweeps
+  T* Z;                      // eigenvector t at Z[t * n ..] (column-major eigenvector matrix)
+  T* d;                      // eigenvalues after the chase
+  T* e;
+  int* swp;
+  T* rot;
+};
+template <class T>
+__device__ __forceinline__ PmEig<T> pm_eig(double* wk, int m) {
+  const size_t M2 = (size_t)m * m;
+  PmEig<T> w;
+  w.hdr = reinterpret_cast<int*>(wk);
+  w.Z = reinterpret_cast<T*>(wk + 2);
+  w.d = reinterpret_cast<T*>(wk + 2 + M2);
+  w.e = reinterpret_cast<T*>(wk + 2 + M2 + m);
+  w.swp = reinterpret_cast<int*>(wk + 2 + M2 + 2 * m);
+  w.rot = reinterpret_cast<T*>(wk + 2 + M2 + 2 * m + pm_cap_s(m));
+  return w;
+}
+
+// Householder tridiagonalisation of A (order n, destroyed) and the column-major
+// Z of its reflectors into the work area (CTA); tau: n elements, sm: 4n + 33.
+template <class T>
+__device__ void pm_tridiag(T* A, int n, const PmEig<T>& w, T* tau, T* sm) {
+  if (n == 1) {
+    if (threadIdx.x == 0) { w.d[0] = A[0]; w.e[0] = T(0.0); w.Z[0] = T(1.0); }
+    __syncthreads();
+    return;
+  }
+  cta_tridiag(A, n, n, w.d, w.e, tau, sm, sm + n, sm + 4 * n);
+  cta_form_z_cm(A, n, n, tau, w.Z, n, sm, sm + n);
+  if (threadIdx.x == 0) w.e[n - 1] = T(0.0);
+  __syncthreads();
+}
+
+// (1b) / (3b): the QR chase of one pair per thread; which = 0: C (order n_j),
+// 1: F' (order r).  Pairs in the order array, so a warp holds pairs of similar size.
+template <class T>
+__global__ void __launch_bounds__(32) k_pm_chase(Tables t, const PJob* __restrict__ jobs,
+                                                 const int* __restrict__ order, int n_jobs, double* slots,
+                                                 const long long* off, const int* mdim, int which, int* err) {
+  const int q = blockIdx.x * 32 + threadIdx.x;
+  if (q >= n_jobs) return;
+  const int jid = order[q];
+  const PJob jb = jobs[jid];
+  const int m = mdim[jid];
+  const int ne = which == 0 ? (jb.i == jb.j ? 0 : t.n_osv[jb.j]) : *jb.r;
+  if (ne == 0) return;
+  const PmEig<T> w = pm_eig<T>(pm_pair(slots, off, jid, m).wk, m);
+  int ns = 0;
+  const int rc = tridiag_qr_record(w.d, w.e, ne, w.swp, pm_cap_s(m), w.rot, pm_cap_r(m), &ns);
+  w.hdr[0] = rc;
+  w.hdr[1] = ns;
+  if (rc == 1) atomicOr(err, ERR_EIG);
+}
+
+// (1a) C = 1 - M^T M, tridiagonalised, Z of the reflectors
+__global__ void __launch_bounds__(NT, 3) k_pm_overlap_a(Tables t, const PJob* __restrict__ jobs,
+                                                        const int* __restrict__ order, int n_jobs, double* slots,
+                                                        const long long* off, int max_m, double* scratch) {
+  __shared__ double gsm[GEMM_SMEM_DOUBLES];
+  __shared__ double esm[4 * PM_MAXN + 33];
+  const size_t M2 = (size_t)max_m * max_m;
+  double* Cw = scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m);
+  double* tau = Cw + M2;
+  const int n = t.n_occ;
+  for (int q = blockIdx.x; q < n_jobs; q += gridDim.x) {
+    const int jid = order[q];
+    const PJob jb = jobs[jid];
+    const int i = jb.i, j = jb.j;
+    if (i == j) continue;
+    const int ni = t.n_osv[i], nj = t.n_osv[j], m = ni + nj;
+    const View Mv = dense_view(t.S[t.sf_id[i * n + j]], ni, nj, nj);
+    cta_gemm(nj, nj, ni, -1.0, transpose(Mv), Mv, 0.0, Cw, nj, gsm);
+    for (int c = threadIdx.x; c < nj; c += NT) Cw[(size_t)c * nj + c] += 1.0;
+    __syncthreads();
+    pm_tridiag(Cw, nj, pm_eig<double>(pm_pair(slots, off, jid, m).wk, m), tau, esm);
+  }
+}
+
+// (1c) eig(C) completed (mu, V), kept directions, Y, Z^T C Z, r
+__global__ void __launch_bounds__(NT, 3) k_pm_overlap_c(Tables t, double tau_s, const PJob* __restrict__ jobs,
+                                                        const int* __restrict__ order, int n_jobs, double* slots,
+                                                        const long long* off, int max_m, double* scratch,
+                                                        int* err) {
   __shared__ double gsm[GEMM_SMEM_DOUBLES];
   __shared__ double esm[4 * PM_MAXN + 33];
   __shared__ int keep[PM_MAXN];
   __shared__ int s_nk;
   const size_t M2 = (size_t)max_m * max_m;
-  double* Cw = scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m);
-  double* C0 = Cw + M2;
-  double* V = C0 + M2;          // eigenvector k of C at V[k * nj ..]
-  double* mu = V + M2;
-  double* e = mu + max_m;
-  double* tau = e + max_m;
+  double* C0 = scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m);
+  double* CZ = C0 + M2;
+  double* Af = CZ + M2;         // in-CTA solve of a pair whose chase record overflowed
+  double* muf = Af + M2;
+  double* ef = muf + max_m;
+  double* tauf = ef + max_m;
   const int n = t.n_occ;
   for (int q = blockIdx.x; q < n_jobs; q += gridDim.x) {
     const int jid = order[q];
@@ -81,14 +181,21 @@ __global__ void __launch_bounds__(NT, 3) k_pm_overlap(Tables t, double tau_s, co
       continue;
     }
     const View Mv = dense_view(t.S[t.sf_id[i * n + j]], ni, nj, nj);
-    cta_gemm(nj, nj, ni, -1.0, transpose(Mv), Mv, 0.0, Cw, nj, gsm);
-    for (int c = threadIdx.x; c < nj; c += NT) Cw[(size_t)c * nj + c] += 1.0;
+    cta_gemm(nj, nj, ni, -1.0, transpose(Mv), Mv, 0.0, C0, nj, gsm);
+    for (int c = threadIdx.x; c < nj; c += NT) C0[(size_t)c * nj + c] += 1.0;
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nj * nj; idx += NT) C0[idx] = Cw[idx];
-    __syncthreads();
-    const int rc = cta_syev_cm(Cw, nj, nj, mu, V, nj, e, tau, esm);
+    const PmEig<double> w = pm_eig<double>(pp.wk, m);
+    const double* mu = w.d;
+    const double* V = w.Z;      // eigenvector k of C at V[k * nj ..]
+    if (w.hdr[0] == 2) {
+      for (int idx = threadIdx.x; idx < nj * nj; idx += NT) Af[idx] = C0[idx];
+      __syncthreads();
+      if (cta_syev_cm(Af, nj, nj, muf, w.Z, nj, ef, tauf, esm) && threadIdx.x == 0) atomicOr(err, ERR_EIG);
+      mu = muf;
+    } else {
+      apply_qr_record_cm(w.Z, nj, nj, w.swp, w.hdr[1], w.rot);
+    }
     if (threadIdx.x == 0) {
-      if (rc) atomicOr(err, ERR_EIG);
       double mumin = 1.0;
       for (int k = 0; k < nj; k++) mumin = fmin(mumin, mu[k]);
       const double smax = 1.0 + sqrt(fmax(0.0, 1.0 - mumin));
@@ -115,17 +222,17 @@ __global__ void __launch_bounds__(NT, 3) k_pm_overlap(Tables t, double tau_s, co
     __syncthreads();
     const View Zv = dense_view(Y + (size_t)ni * r + ni, nj, nk, r);
     cta_gemm(ni, nk, nj, -1.0, Mv, Zv, 0.0, Y + ni, r, gsm);                                     // -M Z
-    cta_gemm(nj, nk, nj, 1.0, dense_view(C0, nj, nj, nj), Zv, 0.0, Cw, nk, gsm);                // C Z
-    cta_gemm(nk, nk, nj, 1.0, transpose(Zv), dense_view(Cw, nj, nk, nk), 0.0, pp.ZCZ, nk, gsm);  // Z^T C Z
+    cta_gemm(nj, nk, nj, 1.0, dense_view(C0, nj, nj, nj), Zv, 0.0, CZ, nk, gsm);                // C Z
+    cta_gemm(nk, nk, nj, 1.0, transpose(Zv), dense_view(CZ, nj, nk, nk), 0.0, pp.ZCZ, nk, gsm);  // Z^T C Z
     if (threadIdx.x == 0) *jb.r = r;
   }
 }
 
 // (2) F' = Y^T F Y
-__global__ void __launch_bounds__(NT) k_pm_fprime(Tables t, const PJob* __restrict__ jobs,
+__global__ void __launch_bounds__(NT, 2) k_pm_fprime(Tables t, const PJob* __restrict__ jobs,
                                                   const int* __restrict__ order, int n_jobs, double* slots,
                                                   const long long* off, int max_m, double* scratch) {
-  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  __shared__ double sm[GEMM_SMEM_WIDE];
   double* FY = scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m);
   for (int q = blockIdx.x; q < n_jobs; q += gridDim.x) {
     const int jid = order[q];
@@ -143,22 +250,19 @@ __global__ void __launch_bounds__(NT) k_pm_fprime(Tables t, const PJob* __restri
     // F Y: the first ni columns of Y are unit vectors
     for (int idx = threadIdx.x; idx < m * ni; idx += NT)
       FY[(size_t)(idx / ni) * r + idx % ni] = Fv.get(idx / ni, idx % ni);
-    cta_gemm(m, nk, m, 1.0, Fv, dense_view(pp.Y + ni, m, nk, r), 0.0, FY + ni, r, sm);
-    cta_gemm(r, r, m, 1.0, transpose(dense_view(pp.Y, m, r, r)), dense_view(FY, m, r, r), 0.0, pp.Fp, r, sm);
+    cta_gemm_a(m, nk, m, 1.0, Fv, dense_view(pp.Y + ni, m, nk, r), 0.0, FY + ni, r, sm);
+    cta_gemm_a(r, r, m, 1.0, transpose(dense_view(pp.Y, m, r, r)), dense_view(FY, m, r, r), 0.0, pp.Fp, r, sm);
   }
 }
 
-// (3) FP32 eigen-decomposition of F' (symmetrised): W, e~
-__global__ void __launch_bounds__(NT, 3) k_pm_eig32(const PJob* __restrict__ jobs, const int* __restrict__ order,
-                                                    int n_jobs, double* slots, const long long* off,
-                                                    const int* mdim, int max_m, double* scratch, int* err) {
+// (3a) F' symmetrised in FP32, tridiagonalised, Z of the reflectors
+__global__ void __launch_bounds__(NT, 3) k_pm_eig32_a(const PJob* __restrict__ jobs, const int* __restrict__ order,
+                                                      int n_jobs, double* slots, const long long* off,
+                                                      const int* mdim, int max_m, double* scratch) {
   __shared__ float esm[4 * PM_MAXN + 33];
   const size_t M2 = (size_t)max_m * max_m;
   float* A32 = reinterpret_cast<float*>(scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m));
-  float* Z32 = A32 + M2;        // eigenvector t at Z32[t * r ..]
-  float* e32 = Z32 + M2;
-  float* eb = e32 + max_m;
-  float* tau32 = eb + max_m;
+  float* tau32 = A32 + M2;
   for (int q = blockIdx.x; q < n_jobs; q += gridDim.x) {
     const int jid = order[q];
     const PJob jb = jobs[jid];
@@ -169,22 +273,52 @@ __global__ void __launch_bounds__(NT, 3) k_pm_eig32(const PJob* __restrict__ job
       A32[idx] = (float)(0.5 * (pp.Fp[idx] + pp.Fp[(size_t)b * r + a]));
     }
     __syncthreads();
-    const int rc = cta_syev_cm(A32, r, r, e32, Z32, r, eb, tau32, esm);
-    if (threadIdx.x == 0 && rc) atomicOr(err, ERR_EIG);
+    pm_tridiag(A32, r, pm_eig<float>(pp.wk, m), tau32, esm);
+  }
+}
+
+// (3c) eig(F') completed: W, e~
+__global__ void __launch_bounds__(NT, 3) k_pm_eig32_c(const PJob* __restrict__ jobs, const int* __restrict__ order,
+                                                      int n_jobs, double* slots, const long long* off,
+                                                      const int* mdim, int max_m, double* scratch, int* err) {
+  __shared__ float esm[4 * PM_MAXN + 33];
+  const size_t M2 = (size_t)max_m * max_m;
+  float* A32 = reinterpret_cast<float*>(scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m));
+  float* e32 = A32 + M2;        // in-CTA solve of a pair whose chase record overflowed
+  float* eb = e32 + max_m;
+  float* tau32 = eb + max_m;
+  for (int q = blockIdx.x; q < n_jobs; q += gridDim.x) {
+    const int jid = order[q];
+    const PJob jb = jobs[jid];
+    const int m = mdim[jid], r = *jb.r;
+    const PmPair pp = pm_pair(slots, off, jid, m);
+    const PmEig<float> w = pm_eig<float>(pp.wk, m);
+    const float* ev = w.d;
+    if (w.hdr[0] == 2) {
+      for (int idx = threadIdx.x; idx < r * r; idx += NT) {
+        const int a = idx / r, b = idx % r;
+        A32[idx] = (float)(0.5 * (pp.Fp[idx] + pp.Fp[(size_t)b * r + a]));
+      }
+      __syncthreads();
+      if (cta_syev_cm(A32, r, r, e32, w.Z, r, eb, tau32, esm) && threadIdx.x == 0) atomicOr(err, ERR_EIG);
+      ev = e32;
+    } else {
+      apply_qr_record_cm(w.Z, r, r, w.swp, w.hdr[1], w.rot);
+    }
     for (int idx = threadIdx.x; idx < r * r; idx += NT) {   // W[a][t] = component a of eigenvector t
       const int tv = idx / r, a = idx % r;
-      pp.W[(size_t)a * r + tv] = (double)Z32[idx];
+      pp.W[(size_t)a * r + tv] = (double)w.Z[idx];
     }
-    for (int c = threadIdx.x; c < r; c += NT) pp.et[c] = (double)e32[c];
+    for (int c = threadIdx.x; c < r; c += NT) pp.et[c] = (double)ev[c];
     __syncthreads();
   }
 }
 
 // (4) X = Y W; S~ = W^T (Y^T S Y) W; F~ = W^T F' W; leftovers
-__global__ void __launch_bounds__(NT) k_pm_final(Tables t, const PJob* __restrict__ jobs,
+__global__ void __launch_bounds__(NT, 2) k_pm_final(Tables t, const PJob* __restrict__ jobs,
                                                  const int* __restrict__ order, int n_jobs, double* slots,
                                                  const long long* off, int max_m, double* scratch, int* err) {
-  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  __shared__ double sm[GEMM_SMEM_WIDE];
   const size_t M2 = (size_t)max_m * max_m;
   double* T1 = scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m);
   double* St = T1 + M2;
@@ -199,17 +333,17 @@ __global__ void __launch_bounds__(NT) k_pm_final(Tables t, const PJob* __restric
     const PmPair pp = pm_pair(slots, off, jid, m);
     const View Wv = dense_view(pp.W, r, r, r);
     if (i != j) {
-      cta_gemm(m, r, r, 1.0, dense_view(pp.Y, m, r, r), Wv, 0.0, jb.X, m, sm);       // X = Y W
+      cta_gemm_a(m, r, r, 1.0, dense_view(pp.Y, m, r, r), Wv, 0.0, jb.X, m, sm);       // X = Y W
       for (int idx = threadIdx.x; idx < ni * r; idx += NT) T1[idx] = pp.W[idx];        // (Y^T S Y) W, top rows
-      cta_gemm(nk, r, nk, 1.0, dense_view(pp.ZCZ, nk, nk, nk), dense_view(pp.W + (size_t)ni * r, nk, r, r), 0.0,
+      cta_gemm_a(nk, r, nk, 1.0, dense_view(pp.ZCZ, nk, nk, nk), dense_view(pp.W + (size_t)ni * r, nk, r, r), 0.0,
                T1 + (size_t)ni * r, r, sm);
     } else {
       for (int idx = threadIdx.x; idx < m * r; idx += NT) jb.X[(size_t)(idx / r) * m + idx % r] = pp.W[idx];
-      cta_gemm(r, r, r, 1.0, dense_view(t.S[t.sf_id[i * n + i]], ni, ni, ni), Wv, 0.0, T1, r, sm);
+      cta_gemm_a(r, r, r, 1.0, dense_view(t.S[t.sf_id[i * n + i]], ni, ni, ni), Wv, 0.0, T1, r, sm);
     }
-    cta_gemm(r, r, r, 1.0, transpose(Wv), dense_view(T1, r, r, r), 0.0, St, r, sm);      // S~
-    cta_gemm(r, r, r, 1.0, dense_view(pp.Fp, r, r, r), Wv, 0.0, T1, r, sm);
-    cta_gemm(r, r, r, 1.0, transpose(Wv), dense_view(T1, r, r, r), 0.0, Ft, r, sm);      // F~
+    cta_gemm_a(r, r, r, 1.0, transpose(Wv), dense_view(T1, r, r, r), 0.0, St, r, sm);      // S~
+    cta_gemm_a(r, r, r, 1.0, dense_view(pp.Fp, r, r, r), Wv, 0.0, T1, r, sm);
+    cta_gemm_a(r, r, r, 1.0, transpose(Wv), dense_view(T1, r, r, r), 0.0, Ft, r, sm);      // F~
     const double fh = 0.5 * (t.f_occ[i * n + i] + t.f_occ[j * n + j]);
     for (int idx = threadIdx.x; idx < r * r; idx += NT) {
       const int a = idx / r, b = idx % r;
@@ -233,11 +367,16 @@ int launch_precond_mixed(const Tables& t, double tau_s, const PJob* jobs, const 
                          cudaStream_t st) {
   if (!n_jobs) return 0;
   if (max_m > PM_MAXN) return -1;
-  k_pm_overlap<<<n_cta, NT, 0, st>>>(t, tau_s, jobs, order, n_jobs, slots, off, max_m, scratch, err);
+  const int n_chase = (n_jobs + 31) / 32;
+  k_pm_overlap_a<<<n_cta, NT, 0, st>>>(t, jobs, order, n_jobs, slots, off, max_m, scratch);
+  k_pm_chase<double><<<n_chase, 32, 0, st>>>(t, jobs, order, n_jobs, slots, off, mdim, 0, err);
+  k_pm_overlap_c<<<n_cta, NT, 0, st>>>(t, tau_s, jobs, order, n_jobs, slots, off, max_m, scratch, err);
   k_pm_fprime<<<n_cta, NT, 0, st>>>(t, jobs, order, n_jobs, slots, off, max_m, scratch);
-  k_pm_eig32<<<n_cta, NT, 0, st>>>(jobs, order, n_jobs, slots, off, mdim, max_m, scratch, err);
+  k_pm_eig32_a<<<n_cta, NT, 0, st>>>(jobs, order, n_jobs, slots, off, mdim, max_m, scratch);
+  k_pm_chase<float><<<n_chase, 32, 0, st>>>(t, jobs, order, n_jobs, slots, off, mdim, 1, err);
+  k_pm_eig32_c<<<n_cta, NT, 0, st>>>(jobs, order, n_jobs, slots, off, mdim, max_m, scratch, err);
   k_pm_final<<<n_cta, NT, 0, st>>>(t, jobs, order, n_jobs, slots, off, max_m, scratch, err);
-  note_launch(4);
+  note_launch(8);
   return 0;
 }
 

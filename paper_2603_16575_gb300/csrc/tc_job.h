@@ -17,6 +17,7 @@ struct Job {
   int ld_out;
   int m0, n0;              // global row / column of the tile's first element
   double s;                // epilogue scalar
+  int x_row, x_sstride;    // slice-writing epilogues: row of slice 0 of the output, rows per slice
 };
 
 }  // namespace tc

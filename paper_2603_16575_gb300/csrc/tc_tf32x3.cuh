@@ -106,7 +106,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
                "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]))
 
 // Epi: functor epi(job, row, col, hi, lo) storing the tile element (row < m_valid,
-// col < n_valid) whose value is hi + lo.
+// col < n_valid) whose value is hi + lo; or, when Epi::kWarp, epi.warp(job, row,
+// col0, hi[16], lo[16]) called by every lane of a drain warp (row = its TMEM lane,
+// rows past m_valid included) for the columns col0 .. col0 + 15, for epilogues
+// that combine the 32 rows of a warp (fixed-point slicing along the rows).
 template <class Epi>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -240,10 +243,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       OSV_TMEM_LD16(lrow + COL_HI + n0, h);
       OSV_TMEM_LD16(lrow + COL_LO + n0, l);
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (row < jb.m_valid)
+      if constexpr (Epi::kWarp) {
+        epi.warp(jb, row, n0, h, l);
+      } else if (row < jb.m_valid) {
 #pragma unroll
         for (int u = 0; u < 16; u++)
           if (n0 + u < jb.n_valid) epi(jb, row, n0 + u, __uint_as_float(h[u]), __uint_as_float(l[u]));
+      }
     }
   }
   if (!ok) atomicOr(err, ERR_TC_TIMEOUT);

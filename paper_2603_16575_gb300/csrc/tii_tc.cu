@@ -40,6 +40,7 @@ void launch_rslices(const BSrc& src, int i0, int nb, float* Bt, int ldx, cudaStr
 
 // T[a][b] = T[b][a] = (hi + lo) / (e_a + e_b - s) for a >= b; out = T_i, s = 2 f_ii.
 struct EpiT {
+  static constexpr bool kWarp = false;
   const double* e_vir;
   __device__ __forceinline__ void operator()(const tc::Job& jb, int r, int c, float h, float l) const {
     const int a = jb.m0 + r, b = jb.n0 + c;
