@@ -689,13 +689,29 @@ __device__ inline int sturm_count(const double* d, const double* e, int n, doubl
   return cnt;
 }
 
+// sturm_count with the squared off-diagonal e2[i] = e[i]^2 given.
+__device__ inline int sturm_count_sq(const double* d, const double* e2, int n, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int i = 1; i < n; i++) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
 // Eigenvalues with ascending indices n-1-t, t < k, of (d, e) by multisection
 // on the Sturm count, called by one warp that handles t = t0, t0 + tstride, ...:
 // g = lane / L lanes per eigenvalue split its interval at L points per step
-// (log2(L+1) bits per Sturm sequence instead of one).  w[t] receives the
-// eigenvalue.
-__device__ inline void multisect_eigs(const double* d, const double* e, int n, int k, int t0, int tstride,
-                                      double lo0, double hi0, double pivmin, double* w) {
+// (log2(L+1) bits per Sturm sequence instead of one), until the interval is
+// below 2 eps |lambda| or atol (the eigenvalues of the tridiagonal are only
+// determined to ~eps ||T|| by its rounding).  e2 holds the squared
+// off-diagonal.  w[t] receives the eigenvalue.
+__device__ inline void multisect_eigs(const double* d, const double* e2, int n, int k, int t0, int tstride,
+                                      double lo0, double hi0, double pivmin, double atol, double* w) {
   const int lane = threadIdx.x & 31;
   const int ng = (k - t0 + tstride - 1) / tstride;          // eigenvalues of this warp
   if (ng <= 0) return;
@@ -713,7 +729,7 @@ __device__ inline void multisect_eigs(const double* d, const double* e, int n, i
       if (!__any_sync(0xffffffffu, !done)) break;
       const double x = lo + (hi - lo) * (double)(q + 1) / (double)(L + 1);
       bool above = false;   // more than j eigenvalues below x: eigenvalue j lies below x
-      if (!done) above = sturm_count(d, e, n, x, pivmin) > j;
+      if (!done) above = sturm_count_sq(d, e2, n, x, pivmin) > j;
       const unsigned bal = __ballot_sync(0xffffffffu, above);
       if (!done) {
         const unsigned bits = (bal >> ((lane / L) * L)) & ((L == 32) ? 0xffffffffu : ((1u << L) - 1u));
@@ -723,7 +739,7 @@ __device__ inline void multisect_eigs(const double* d, const double* e, int n, i
         if (!(nlo > lo || nhi < hi)) done = true;           // no progress at this precision
         lo = nlo;
         hi = nhi;
-        if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin) done = true;
+        if (hi - lo <= fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), atol) + pivmin) done = true;
       }
     }
     if (mine && q == 0) w[t] = 0.5 * (lo + hi);
@@ -767,6 +783,52 @@ __device__ inline void tri_solve(int n, const double* u0, const double* u1, cons
     if (i + 1 < n) s -= u1[i] * y[i + 1];
     if (i + 2 < n) s -= u2[i] * y[i + 2];
     y[i] = s / u0[i];
+  }
+}
+
+// The same factorisation and solve for many shifts at once, one per lane of a
+// warp: element i of a lane's arrays at [i * 32] from the lane's base pointer,
+// so a warp's accesses are coalesced.  Branch-free, one division per row
+// (the inverse pivot ui = 1 / u0 is kept), so the lanes do not diverge.
+__device__ inline void tri_factor_lanes(const double* d, const double* e, int n, double lam, double small,
+                                        double* ui, double* u1, double* u2, double* mul, int* piv) {
+  double wa = d[0] - lam, wb = (n > 1) ? e[0] : 0.0;
+  for (int i = 0; i + 1 < n; i++) {
+    const double c = e[i], a1 = d[i + 1] - lam, b1 = (i + 2 < n) ? e[i + 1] : 0.0;
+    const bool keep = fabs(wa) >= fabs(c);
+    const double a = keep ? (wa == 0.0 ? small : wa) : c;
+    const double inv = 1.0 / a;
+    const double m = (keep ? c : wa) * inv;
+    ui[32 * i] = inv;
+    u1[32 * i] = keep ? wb : a1;
+    u2[32 * i] = keep ? 0.0 : b1;
+    mul[32 * i] = m;
+    piv[32 * i] = keep ? 0 : 1;
+    const double na = keep ? a1 - m * wb : wb - m * a1;
+    wb = keep ? b1 : -m * b1;
+    wa = na;
+  }
+  ui[32 * (n - 1)] = 1.0 / ((wa == 0.0) ? small : wa);
+  u1[32 * (n - 1)] = 0.0;
+  u2[32 * (n - 1)] = 0.0;
+}
+__device__ inline void tri_solve_lanes(int n, const double* ui, const double* u1, const double* u2,
+                                       const double* mul, const int* piv, double* y) {
+  double cur = y[0];
+  for (int i = 0; i + 1 < n; i++) {
+    const double nx = y[32 * (i + 1)];
+    const bool sw = piv[32 * i] != 0;
+    const double lo = sw ? nx : cur, hi = sw ? cur : nx;
+    y[32 * i] = lo;
+    cur = hi - mul[32 * i] * lo;
+  }
+  y[32 * (n - 1)] = cur;
+  double y1 = 0.0, y2 = 0.0;   // x[i + 1], x[i + 2]
+  for (int i = n - 1; i >= 0; i--) {
+    const double x = (y[32 * i] - u1[32 * i] * y1 - u2[32 * i] * y2) * ui[32 * i];
+    y[32 * i] = x;
+    y2 = y1;
+    y1 = x;
   }
 }
 

@@ -58,10 +58,12 @@ int launch_tii_tc(const float* Bt, long long rows, int n_aux, int ldx, const tc:
                   const double* e_vir, int* err, cudaStream_t st);
 // Eigen-decomposition of each T[b] and selection omega >= thr (all if thr <= 0),
 // at most kmax per orbital: V [nb][kmax][nv] (eigenvector-major), w [nb][kmax], k [nb], err |= ERR_*.
-// e, tau, w (3 nv) + Z (nv*nv, global path) + 32 warps x 7 nv (inverse iteration)
+// d, e, tau (3 nv) + Z (nv*nv, full path) or the tridiagonalisation's partial sums,
+// then 4 groups x 176 nv of lane-batched inverse iteration (top-k path)
 __host__ __device__ inline size_t eig_osv_scratch_doubles(int nv, int kmax) {
   (void)kmax;
-  return (size_t)3 * nv + (size_t)nv * nv + (size_t)32 * 7 * nv + 64;
+  const size_t work = (size_t)nv * nv > (size_t)4 * 176 * nv ? (size_t)nv * nv : (size_t)4 * 176 * nv;
+  return (size_t)3 * nv + work + 64;
 }
 void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, double* w, int* k,
                     double* scratch, int* err, cudaStream_t st);

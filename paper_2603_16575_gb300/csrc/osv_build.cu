@@ -65,6 +65,7 @@ void launch_tii(const BSrc& src, const double* e_vir, const double* f_occ, int n
 // ---------------------------------------------------------------- eigen
 constexpr int ZSMEM_MAX = 160;   // Z kept in shared memory up to this order
 constexpr int NT_EIG = 1024;     // threads of the OSV eigen kernel (more loads in flight)
+constexpr int INV_GROUPS = 4;    // warps running the lane-batched inverse iteration (176 n doubles each)
 
 // Sign eigenvector t (V[t][0..n), eigenvector-major) so that its largest-magnitude
 // entry (lowest index on ties) is positive.  One warp per vector.
@@ -138,7 +139,6 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   double* d = scr;
   double* e = scr + n;
   double* tau = scr + 2 * n;
-  double* wk = scr + 3 * n + (size_t)n * n;   // per-warp inverse-iteration scratch (7n each)
   double* v = sm;
   double* p = sm + n;
   double* red = sm + 2 * n;
@@ -176,7 +176,16 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   const int k = s_k;
   // kept eigenvalues by multisection: warps 0-3 (one per SM sub-partition, whose
   // FP64 pipes work in parallel), several lanes per eigenvalue
-  if ((threadIdx.x >> 5) < 4) multisect_eigs(d, e, n, k, threadIdx.x >> 5, 4, s_lo, s_hi, s_piv, w);
+  // (shared copies of d and e^2)
+  double* ds = p;
+  double* e2s = v;
+  for (int t = threadIdx.x; t < n; t += NT_EIG) {
+    ds[t] = d[t];
+    e2s[t] = (t + 1 < n) ? e[t] * e[t] : 0.0;
+  }
+  __syncthreads();
+  if ((threadIdx.x >> 5) < 4)
+    multisect_eigs(ds, e2s, n, k, threadIdx.x >> 5, 4, s_lo, s_hi, s_piv, 4.0 * 2.220446049250313e-16 * s_norm, w);
   __syncthreads();
   if (threadIdx.x == 0) {
     const double ortol = 1e-3 * s_norm;
@@ -189,45 +198,50 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
       if (!isfinite(w[t])) atomicOr(err, ERR_NONFINITE);
   }
   __syncthreads();
-  // inverse iteration, parallel over the kept vectors (warp per vector): two
-  // solves from a seeded start, Gram-Schmidt inside each cluster of close
-  // eigenvalues (warp per cluster, in order), then one more solve per vector
-  // and the Gram-Schmidt again.  With shifts accurate to ~eps ||T||, one solve
-  // leaves a vector contaminated by an eigenvector at distance g at ~eps ||T|| / g,
-  // so the vectors separate without orthogonalising between every solve; the
-  // passes take care of (near-)degenerate groups.
+  // inverse iteration, parallel over the kept vectors, one vector per LANE
+  // (lane-interleaved factorisations, so every FP64 instruction of a warp works
+  // for 32 vectors): two solves from a seeded start, Gram-Schmidt inside each
+  // cluster of close eigenvalues (warp per cluster, in order), then one more
+  // solve per vector and the Gram-Schmidt again.  With shifts accurate to
+  // ~eps ||T||, one solve leaves a vector contaminated by an eigenvector at
+  // distance g at ~eps ||T|| / g, so the vectors separate without
+  // orthogonalising between every solve; the passes take care of
+  // (near-)degenerate groups.  Warps 0-3 (one per SM sub-partition) take the
+  // groups of 32 vectors; group slot w uses 176 n doubles of the scratch from
+  // scr + 3n (the tridiagonalisation's partial sums are no longer needed).
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* u0 = wk + (size_t)warp * 7 * n;
-  double* u1 = u0 + n;
-  double* u2 = u1 + n;
-  double* mu = u2 + n;
-  double* y = mu + n;
-  int* piv = reinterpret_cast<int*>(y + n);   // n ints fit in 2n doubles' room
   const double small = 2.220446049250313e-16 * fmax(s_norm, 1e-300);
   for (int pass = 0; pass < 2; pass++) {
-    for (int t = warp; t < k; t += NT_EIG / 32) {
-      if (lane == 0) tri_factor(d, e, n, w[t], small, u0, u1, u2, mu, piv);
-      for (int r = lane; r < n; r += 32) {
-        if (pass == 0) {
-          const uint64_t h = draw(0x5eedull + (uint64_t)t, (uint64_t)r);
-          y[r] = (double)(h >> 11) * 0x1p-53 - 0.5;
-        } else {
-          y[r] = V[(size_t)t * n + r];
+    if (warp < INV_GROUPS) {
+      double* base = scr + 3 * n + (size_t)warp * 176 * n;
+      double* ui = base + lane;
+      double* u1 = base + 32 * (size_t)n + lane;
+      double* u2 = base + 64 * (size_t)n + lane;
+      double* mul = base + 96 * (size_t)n + lane;
+      double* y = base + 128 * (size_t)n + lane;
+      int* piv = reinterpret_cast<int*>(base + 160 * (size_t)n) + lane;
+      for (int g = warp; 32 * g < k; g += INV_GROUPS) {
+        const int t = 32 * g + lane;
+        if (t < k) {
+          tri_factor_lanes(d, e, n, w[t], small, ui, u1, u2, mul, piv);
+          for (int r = 0; r < n; r++) {
+            if (pass == 0) {
+              const uint64_t h = draw(0x5eedull + (uint64_t)t, (uint64_t)r);
+              y[32 * r] = (double)(h >> 11) * 0x1p-53 - 0.5;
+            } else {
+              y[32 * r] = V[(size_t)t * n + r];
+            }
+          }
+          for (int it = 0; it < 2 - pass; it++) {
+            tri_solve_lanes(n, ui, u1, u2, mul, piv, y);
+            double nn = 0.0;
+            for (int r = 0; r < n; r++) nn += y[32 * r] * y[32 * r];
+            const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+            for (int r = 0; r < n; r++) y[32 * r] *= sc;
+          }
+          for (int r = 0; r < n; r++) V[(size_t)t * n + r] = y[32 * r];
         }
       }
-      __syncwarp();
-      for (int it = 0; it < 2 - pass; it++) {
-        if (lane == 0) tri_solve(n, u0, u1, u2, mu, piv, y);
-        __syncwarp();
-        double nn = 0.0;
-        for (int r = lane; r < n; r += 32) nn += y[r] * y[r];
-        nn = warp_sum(nn);
-        const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-        for (int r = lane; r < n; r += 32) y[r] *= sc;
-        __syncwarp();
-      }
-      for (int r = lane; r < n; r += 32) V[(size_t)t * n + r] = y[r];
-      __syncwarp();
     }
     __syncthreads();
     for (int c = warp; c < s_nclu; c += NT_EIG / 32) {   // Gram-Schmidt within clusters
