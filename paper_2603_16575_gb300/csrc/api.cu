@@ -9,6 +9,7 @@
 #include <cstring>
 #include <cstdint>
 #include <map>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -38,7 +39,22 @@ struct Frag {
 
 }  // namespace
 
+// Device-memory cache of a ctx.  Blocks released by the temporaries of a call
+// and by the pair store go to a free list and are handed out again to later
+// requests of similar size, so a repeated call (one energy step after another)
+// allocates nothing from the driver and never waits in cudaFree.  All work of
+// a ctx runs on its one stream, so a reused block is only touched by work
+// enqueued after the last use by its previous owner.  Sizes are rounded up
+// (256-byte granules below 1 MiB, 1 MiB granules above); a free block serves a
+// request when it is at most an eighth (plus one granule) larger; a failed
+// cudaMalloc first returns every cached block to the driver.
+struct DevPool {
+  std::multimap<size_t, void*> free_blocks;   // size -> block
+  std::unordered_map<void*, size_t> size_of;  // every block the pool handed out
+};
+
 struct osvmp2_ctx {
+  DevPool pool;
   int device = 0;
   cudaStream_t st = nullptr;
   osvmp2_opts opts{};
@@ -141,18 +157,67 @@ int dalloc_t(osvmp2_ctx* c, T** p, size_t n) {
   return dalloc(c, reinterpret_cast<void**>(p), n * sizeof(T));
 }
 
-// Temporary device buffer freed at scope exit.
+size_t pool_round(size_t b) {
+  constexpr size_t MiB = (size_t)1 << 20;
+  if (b < MiB) return (std::max<size_t>(b, 16) + 255) & ~(size_t)255;
+  return (b + MiB - 1) & ~(MiB - 1);
+}
+// Return every cached block to the driver.
+void pool_trim(osvmp2_ctx* c) {
+  if (c->pool.free_blocks.empty()) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (auto& kv : c->pool.free_blocks) {
+    c->pool.size_of.erase(kv.second);
+    cudaFree(kv.second);
+  }
+  c->pool.free_blocks.clear();
+}
+cudaError_t pool_get(osvmp2_ctx* c, void** p, size_t bytes) {
+  const size_t r = pool_round(bytes);
+  const size_t slack = r / 8 + (r < ((size_t)1 << 20) ? 256 : ((size_t)1 << 20));
+  auto it = c->pool.free_blocks.lower_bound(r);
+  if (it != c->pool.free_blocks.end() && it->first <= r + slack) {
+    *p = it->second;
+    c->pool.free_blocks.erase(it);
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaMalloc(p, r);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pool_trim(c);
+    e = cudaMalloc(p, r);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return e;
+  }
+  c->pool.size_of[*p] = r;
+  return cudaSuccess;
+}
+void pool_put(osvmp2_ctx* c, void* p) {
+  if (!p) return;
+  auto s = c->pool.size_of.find(p);
+  if (s == c->pool.size_of.end()) {
+    cudaFree(p);
+    return;
+  }
+  c->pool.free_blocks.emplace(s->second, p);
+}
+
+// Temporary device buffer returned to the ctx's cache at scope exit.
 struct Tmp {
   void* p = nullptr;
+  osvmp2_ctx* c = nullptr;
   ~Tmp() {
-    if (p) cudaFree(p);
+    if (p) pool_put(c, p);
   }
 };
 int tmp_alloc(osvmp2_ctx* c, Tmp& t, size_t bytes) {
-  if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&t.p, bytes);
+  if (t.p) pool_put(t.c, t.p);
+  t.c = c;
+  cudaError_t e = pool_get(c, &t.p, bytes);
   if (e != cudaSuccess) {
-    cudaGetLastError();
     t.p = nullptr;
     return fail(c, OSVMP2_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
   }
@@ -163,7 +228,7 @@ void free_system(osvmp2_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   for (void* p : c->sys_allocs) cudaFree(p);
   c->sys_allocs.clear();
-  for (void* p : c->pair_allocs) cudaFree(p);
+  for (void* p : c->pair_allocs) pool_put(c, p);
   c->pair_allocs.clear();
   c->pair_prec = -1;
   c->have_sys = c->have_osv = false;
@@ -300,11 +365,9 @@ int pair_dim_h(const osvmp2_ctx* c, int i, int j) { return c->n_osv[i] + (i != j
 int palloc(osvmp2_ctx* c, double** p, size_t n) {
   *p = nullptr;
   const size_t bytes = std::max<size_t>(16, n * sizeof(double));
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
+  cudaError_t e = pool_get(c, reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess)
     return fail(c, OSVMP2_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
-  }
   c->pair_allocs.push_back(*p);
   return 0;
 }
@@ -312,7 +375,7 @@ int palloc(osvmp2_ctx* c, double** p, size_t n) {
 // Drop every built pair (blocks, projections, K, preconditioners).
 int reset_pairs(osvmp2_ctx* c) {
   CK(cudaStreamSynchronize(c->st));
-  for (void* p : c->pair_allocs) cudaFree(p);
+  for (void* p : c->pair_allocs) pool_put(c, p);
   c->pair_allocs.clear();
   const size_t nn = (size_t)c->sys.n_occ * c->sys.n_occ;
   c->sf_id.assign(nn, -1);
@@ -893,6 +956,7 @@ void osvmp2_destroy(osvmp2_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   free_system(c);
+  pool_trim(c);
   if (c->err_d) cudaFree(c->err_d);
   if (c->scal_d) cudaFree(c->scal_d);
   for (int ph = 0; ph < OSVMP2_NPHASE; ph++) {
