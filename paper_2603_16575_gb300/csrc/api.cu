@@ -621,8 +621,8 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
   std::vector<KJob> kj;
   std::vector<PJob> pjb;
   std::vector<int> new_ids;
-  // mixed form with the warp preconditioner: leftovers Sh, Gh (m^2 floats each per pair)
-  const bool mixed_pc = mixed && max_m <= PW_MAX_ORDER;
+  // mixed form: leftovers Sh, Gh of the preconditioner basis (m^2 floats each per pair)
+  const bool mixed_pc = mixed;
   float* shmem = nullptr;
   if (mixed_pc) {
     size_t shf = 0;
@@ -751,11 +751,12 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
     }
   }
   ph_begin(c, OSVMP2_PH_PRECOND);
-  if (mixed_pc)
-    launch_precond_mixed(t, c->opts.tau_s, (const PJob*)jp.p, (const int*)pm_order.p, (int)pjb.size(), max_m,
-                         (double*)pm_slots.p, (const long long*)pm_off.p, (const int*)pm_m.p, (double*)scr.p,
-                         n_cta_pm, c->err_d, c->st);
-  else if (warp_pc)
+  if (mixed_pc) {
+    if (launch_precond_mixed(t, c->opts.tau_s, (const PJob*)jp.p, (const int*)pm_order.p, (int)pjb.size(), max_m,
+                             (double*)pm_slots.p, (const long long*)pm_off.p, (const int*)pm_m.p, (double*)scr.p,
+                             n_cta_pm, c->err_d, c->st))
+      return fail(c, OSVMP2_E_ARG, "pair order %d exceeds the mixed preconditioner's shared scratch", max_m);
+  } else if (warp_pc)
     launch_precond_w(t, c->opts.tau_s, (const PJob*)jp.p, (int)pjb.size(), max_m, (double*)scr.p, n_warps, c->err_d,
                      c->st);
   else

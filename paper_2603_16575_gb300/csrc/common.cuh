@@ -11,7 +11,7 @@ namespace osv {
 constexpr int NT = 256;          // threads of every CTA that calls the CTA routines
 constexpr int TM = 64, TN = 64, TK = 16;
 constexpr int GEMM_SMEM_DOUBLES = TK * (TM + TN);
-constexpr int GEMM_SMEM_F32 = TK * 2 * 96;   // floats: the 96 x 96 tiles of cta_gemm_f32s
+constexpr int GEMM_SMEM_F32 = TK * 2 * 97;   // floats: the (padded) 96 x 96 tiles of cta_gemm_f32s
 
 // ---------------------------------------------------------------- views
 // One dense block: element (r,c) at p[r*ld + c], or at p[c*ld + r] when tr.
@@ -107,35 +107,54 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
 // rows m0 + ty + 16 i and columns n0 + tx + 16 j), accumulated in FP32 over
 // the whole K: for the short contractions (K ~ a pair order) of the coupling
 // terms, whose FP32 rounding is scaled down by the off-diagonal Fock
-// elements.  sm: 2 TK 16R floats.
+// elements.  Each operand's k-tile is read along its contiguous direction
+// (views report it through row_major()), and the next k-tile is loaded into
+// registers while the current one is multiplied.  sm: 2 TK (16R + 1) floats.
 template <int R, class VA, class VB>
 __device__ __forceinline__ void tile_mma_f32r(int M, int N, int K, int m0, int n0, const VA& A, const VB& B,
                                               float acc[R][R], float* sm) {
-  constexpr int TMR = 16 * R;
-  float* As = sm;
-  float* Bs = sm + TK * TMR;
+  constexpr int TMR = 16 * R, LDT = TMR + 1, LPT = TMR * TK / NT;
+  float* As = sm;             // [TK][LDT]
+  float* Bs = sm + TK * LDT;  // [TK][LDT]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const bool a_kf = A.row_major();   // A(m, k), A(m, k + 1) adjacent: walk k fastest
+  const bool b_kf = !B.row_major();  // B(k, n), B(k + 1, n) adjacent: walk k fastest
+  float ra[LPT], rb[LPT];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int t = 0; t < LPT; t++) {
+      const int e = tid + t * NT;
+      const int m = a_kf ? e / TK : e % TMR, k = a_kf ? e % TK : e / TMR;
+      const int gm = m0 + m, gk = k0 + k;
+      ra[t] = (gm < M && gk < K) ? static_cast<float>(A.get(gm, gk)) : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < LPT; t++) {
+      const int e = tid + t * NT;
+      const int n = b_kf ? e / TK : e % TMR, k = b_kf ? e % TK : e / TMR;
+      const int gn = n0 + n, gk = k0 + k;
+      rb[t] = (gn < N && gk < K) ? static_cast<float>(B.get(gk, gn)) : 0.f;
+    }
+  };
+  load(0);
   for (int k0 = 0; k0 < K; k0 += TK) {
 #pragma unroll
-    for (int t = 0; t < TMR * TK / NT; t++) {
-      const int e = tid + t * NT, m = e % TMR, k = e / TMR;
-      const int gm = m0 + m, gk = k0 + k;
-      As[k * TMR + m] = (gm < M && gk < K) ? static_cast<float>(A.get(gm, gk)) : 0.f;
-    }
-#pragma unroll
-    for (int t = 0; t < TMR * TK / NT; t++) {
-      const int e = tid + t * NT, n = e % TMR, k = e / TMR;
-      const int gn = n0 + n, gk = k0 + k;
-      Bs[k * TMR + n] = (gn < N && gk < K) ? static_cast<float>(B.get(gk, gn)) : 0.f;
+    for (int t = 0; t < LPT; t++) {
+      const int e = tid + t * NT;
+      const int m = a_kf ? e / TK : e % TMR, k = a_kf ? e % TK : e / TMR;
+      As[k * LDT + m] = ra[t];
+      const int n = b_kf ? e / TK : e % TMR, kb = b_kf ? e % TK : e / TMR;
+      Bs[kb * LDT + n] = rb[t];
     }
     __syncthreads();
+    if (k0 + TK < K) load(k0 + TK);   // in flight during the products below
 #pragma unroll
     for (int k = 0; k < TK; k++) {
       float a[R], b[R];
 #pragma unroll
-      for (int i = 0; i < R; i++) a[i] = As[k * TMR + ty + 16 * i];
+      for (int i = 0; i < R; i++) a[i] = As[k * LDT + ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < R; j++) b[j] = Bs[k * TMR + tx + 16 * j];
+      for (int j = 0; j < R; j++) b[j] = Bs[k * LDT + tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < R; i++)
 #pragma unroll
@@ -349,6 +368,7 @@ struct ViewF {
   __device__ __forceinline__ float get(int r, int c) const {
     return tr ? p[(size_t)c * ld + r] : p[(size_t)r * ld + c];
   }
+  __device__ __forceinline__ bool row_major() const { return !tr; }   // (r, c), (r, c + 1) adjacent
 };
 
 // ---------------------------------------------------------------- reductions

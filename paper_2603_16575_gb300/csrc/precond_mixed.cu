@@ -38,7 +38,6 @@
 
 namespace osv {
 
-constexpr int PM_MAXN = 192;   // largest pair order (static shared scratch of the eigen-solvers)
 
 // eigen-solver work area of a pair of order m: status and sweep count, Z (m x m),
 // d and e (m each), the sweep record (cap_s (l, h) pairs) and the rotation
@@ -133,7 +132,7 @@ __global__ void __launch_bounds__(NT, 3) k_pm_overlap_a(Tables t, const PJob* __
                                                         const int* __restrict__ order, int n_jobs, double* slots,
                                                         const long long* off, int max_m, double* scratch) {
   __shared__ double gsm[GEMM_SMEM_DOUBLES];
-  __shared__ double esm[4 * PM_MAXN + 33];
+  extern __shared__ double esm[];   // eigen-solver scratch: 4 max_m + 33 doubles
   const size_t M2 = (size_t)max_m * max_m;
   double* Cw = scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m);
   double* tau = Cw + M2;
@@ -158,8 +157,8 @@ __global__ void __launch_bounds__(NT, 3) k_pm_overlap_c(Tables t, double tau_s, 
                                                         const long long* off, int max_m, double* scratch,
                                                         int* err) {
   __shared__ double gsm[GEMM_SMEM_DOUBLES];
-  __shared__ double esm[4 * PM_MAXN + 33];
-  __shared__ int keep[PM_MAXN];
+  extern __shared__ double esm[];   // eigen-solver scratch: 4 max_m + 33 doubles, then keep [max_m]
+  int* keep = reinterpret_cast<int*>(esm + 4 * max_m + 33);
   __shared__ int s_nk;
   const size_t M2 = (size_t)max_m * max_m;
   double* C0 = scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m);
@@ -259,7 +258,8 @@ __global__ void __launch_bounds__(NT, 2) k_pm_fprime(Tables t, const PJob* __res
 __global__ void __launch_bounds__(NT, 3) k_pm_eig32_a(const PJob* __restrict__ jobs, const int* __restrict__ order,
                                                       int n_jobs, double* slots, const long long* off,
                                                       const int* mdim, int max_m, double* scratch) {
-  __shared__ float esm[4 * PM_MAXN + 33];
+  extern __shared__ float esmf[];   // eigen-solver scratch: 4 max_m + 33 floats
+  float* esm = esmf;
   const size_t M2 = (size_t)max_m * max_m;
   float* A32 = reinterpret_cast<float*>(scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m));
   float* tau32 = A32 + M2;
@@ -281,7 +281,8 @@ __global__ void __launch_bounds__(NT, 3) k_pm_eig32_a(const PJob* __restrict__ j
 __global__ void __launch_bounds__(NT, 3) k_pm_eig32_c(const PJob* __restrict__ jobs, const int* __restrict__ order,
                                                       int n_jobs, double* slots, const long long* off,
                                                       const int* mdim, int max_m, double* scratch, int* err) {
-  __shared__ float esm[4 * PM_MAXN + 33];
+  extern __shared__ float esmf[];   // eigen-solver scratch: 4 max_m + 33 floats
+  float* esm = esmf;
   const size_t M2 = (size_t)max_m * max_m;
   float* A32 = reinterpret_cast<float*>(scratch + (size_t)blockIdx.x * pm_cta_doubles(max_m));
   float* e32 = A32 + M2;        // in-CTA solve of a pair whose chase record overflowed
@@ -366,15 +367,22 @@ int launch_precond_mixed(const Tables& t, double tau_s, const PJob* jobs, const 
                          double* slots, const long long* off, const int* mdim, double* scratch, int n_cta, int* err,
                          cudaStream_t st) {
   if (!n_jobs) return 0;
-  if (max_m > PM_MAXN) return -1;
+  const size_t sm_d = ((size_t)4 * max_m + 33) * sizeof(double) + (size_t)max_m * sizeof(int);
+  const size_t sm_f = ((size_t)4 * max_m + 33) * sizeof(float);
+  if (sm_d > 160 * 1024) return -1;
+  if (cudaFuncSetAttribute(k_pm_overlap_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_d) != cudaSuccess ||
+      cudaFuncSetAttribute(k_pm_overlap_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_d) != cudaSuccess ||
+      cudaFuncSetAttribute(k_pm_eig32_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_f) != cudaSuccess ||
+      cudaFuncSetAttribute(k_pm_eig32_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_f) != cudaSuccess)
+    return -1;
   const int n_chase = (n_jobs + 31) / 32;
-  k_pm_overlap_a<<<n_cta, NT, 0, st>>>(t, jobs, order, n_jobs, slots, off, max_m, scratch);
+  k_pm_overlap_a<<<n_cta, NT, sm_d, st>>>(t, jobs, order, n_jobs, slots, off, max_m, scratch);
   k_pm_chase<double><<<n_chase, 32, 0, st>>>(t, jobs, order, n_jobs, slots, off, mdim, 0, err);
-  k_pm_overlap_c<<<n_cta, NT, 0, st>>>(t, tau_s, jobs, order, n_jobs, slots, off, max_m, scratch, err);
+  k_pm_overlap_c<<<n_cta, NT, sm_d, st>>>(t, tau_s, jobs, order, n_jobs, slots, off, max_m, scratch, err);
   k_pm_fprime<<<n_cta, NT, 0, st>>>(t, jobs, order, n_jobs, slots, off, max_m, scratch);
-  k_pm_eig32_a<<<n_cta, NT, 0, st>>>(jobs, order, n_jobs, slots, off, mdim, max_m, scratch);
+  k_pm_eig32_a<<<n_cta, NT, sm_f, st>>>(jobs, order, n_jobs, slots, off, mdim, max_m, scratch);
   k_pm_chase<float><<<n_chase, 32, 0, st>>>(t, jobs, order, n_jobs, slots, off, mdim, 1, err);
-  k_pm_eig32_c<<<n_cta, NT, 0, st>>>(jobs, order, n_jobs, slots, off, mdim, max_m, scratch, err);
+  k_pm_eig32_c<<<n_cta, NT, sm_f, st>>>(jobs, order, n_jobs, slots, off, mdim, max_m, scratch, err);
   k_pm_final<<<n_cta, NT, 0, st>>>(t, jobs, order, n_jobs, slots, off, max_m, scratch, err);
   note_launch(8);
   return 0;

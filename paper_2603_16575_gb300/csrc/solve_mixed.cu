@@ -66,6 +66,7 @@ struct ViewFmix {
   __device__ __forceinline__ float get(int r, int c) const {
     return cn * p[(size_t)r * ld + c] + ct * p[(size_t)c * ld + r];
   }
+  __device__ __forceinline__ bool row_major() const { return true; }
 };
 
 // P(Y) is refreshed once the amplitudes have moved by more than this fraction of
