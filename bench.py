@@ -167,6 +167,7 @@ def run_gpu(args):
             torch.distributed.barrier()
     launches = pkg.osvmp2.kernel_launches() - launches0
     prof = ctx.profile(reset=True)
+    plan = ctx.solve_plan() if args.prec == "mixed" else None
     a0_ms = sum(prof.get(k, (0.0,))[0] for k in ("tii", "eig")) / args.steps
     err = None
     if args.prec == "mixed":
@@ -267,7 +268,8 @@ def run_gpu(args):
                    "prec": args.prec, "b_mode": args.b_mode, "grad": bool(args.grad),
                    "fragments": n_frag, "n_single": int(st["n_single"]), "n_pair": int(st["n_pair"]),
                    "n_triple": int(st["n_triple"]), "n_osv_mean": float(np.mean(n_osv)),
-                   "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
+                   "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{world}",
+                   "solve_plan": plan},
         "energy": E,
         "energy_vs_fp64_form": err,
         "fragments_per_s_excl_osv_build": world * n_frag / max(1e-9, t_tot / args.steps - a0_ms / 1e3),

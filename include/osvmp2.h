@@ -74,7 +74,11 @@ typedef struct {
                          the tensor cores with split-precision operands (~35 significant
                          bits); the eigen-decomposition stays FP64 in both.  Library
                          extension: the paper forms T_ii in one precision only. */
-  int32_t reserved[6];
+  int32_t no_autotune; /* 0 (default): the first osvmp2_mbe3_energy for a given fragment count and
+                          largest pair order times the candidate launch shapes of the mixed
+                          fragment solve and keeps the fastest (osvmp2_get_solve_plan); 1: fixed
+                          default shape.  The energies are identical either way. */
+  int32_t reserved[5];
 } osvmp2_opts;
 
 /* Synthetic or caller-supplied system.  All arrays are read by the kernels. */
@@ -115,6 +119,12 @@ void osvmp2_default_opts(osvmp2_opts *opts);
  * unchanged).  Takes effect for the next call; built OSVs and pair blocks are
  * kept. */
 int osvmp2_set_opts(osvmp2_ctx *ctx, const osvmp2_opts *opts);
+/* Launch shape of the last mixed MBE(3) fragment solve: out[0] CTAs per SM, out[1] tile set
+ * of its FP32 contractions (0: 64/96-wide tiles, 1: also 80-wide), out[2] 1 if chosen by the
+ * autotuner, out[3] number of tuned (fragment count, largest pair order) keys.  out: 4 ints
+ * (host).  The solve and the MBE(3) sum run as one CUDA graph, replayed with updated
+ * arguments on later calls.  Library extension (the paper does not batch this way). */
+int osvmp2_get_solve_plan(const osvmp2_ctx *ctx, int32_t *out);
 /* Number of CUDA kernels this library has launched in this process (all ctxs). */
 int64_t osvmp2_kernel_launches(void);
 

@@ -53,8 +53,23 @@ struct DevPool {
   std::unordered_map<void*, size_t> size_of;  // every block the pool handed out
 };
 
+// Launch shape of the mixed fragment solve, chosen per (fragment count, largest
+// pair order) by the autotuner of mbe3_core: CTAs per SM and the tile set of
+// the solver's FP32 contractions.  Every candidate computes the same numbers
+// (one CTA per fragment, the same FMA order), so the choice changes time only.
+struct SolvePlan {
+  int ctas_per_sm = 2;
+  int tiles = 0;
+  bool tuned = false;
+  float ms = 0.f;      // measured time of the chosen plan (autotuned plans)
+};
+
 struct osvmp2_ctx {
   DevPool pool;
+  std::map<std::pair<int, int>, SolvePlan> plans;   // mixed solve plans by (n_frag, max_m)
+  SolvePlan last_plan;
+  cudaStream_t cap_st = nullptr;      // private stream used only to record the solve graph
+  cudaGraphExec_t solve_exec = nullptr;
   int device = 0;
   cudaStream_t st = nullptr;
   osvmp2_opts opts{};
@@ -913,7 +928,16 @@ void osvmp2_default_opts(osvmp2_opts* o) {
 
 static bool opts_valid(const osvmp2_opts& o) {
   return o.max_iter > 0 && o.tau_s >= 0 && o.tol_update > 0 && o.tol_energy > 0 &&
-         (o.osv_prec == OSVMP2_FP64 || o.osv_prec == OSVMP2_MIXED);
+         (o.osv_prec == OSVMP2_FP64 || o.osv_prec == OSVMP2_MIXED) && (o.no_autotune == 0 || o.no_autotune == 1);
+}
+
+int osvmp2_get_solve_plan(const osvmp2_ctx* c, int32_t* out) {
+  if (!c || !out) return OSVMP2_E_ARG;
+  out[0] = c->last_plan.ctas_per_sm;
+  out[1] = c->last_plan.tiles;
+  out[2] = c->last_plan.tuned ? 1 : 0;
+  out[3] = (int32_t)c->plans.size();
+  return OSVMP2_OK;
 }
 
 int osvmp2_set_opts(osvmp2_ctx* c, const osvmp2_opts* opts) {
@@ -958,6 +982,8 @@ void osvmp2_destroy(osvmp2_ctx* c) {
   cudaSetDevice(c->device);
   free_system(c);
   pool_trim(c);
+  if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   if (c->err_d) cudaFree(c->err_d);
   if (c->scal_d) cudaFree(c->scal_d);
   for (int ph = 0; ph < OSVMP2_NPHASE; ph++) {
@@ -1439,7 +1465,7 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
     for (int u = 0; u < 3; u++) orbs_h[3 * f + u] = c->frags[f].orbs[u];
     w_h[f] = c->frags[f].weight;
   }
-  const int n_cta = std::max(1, std::min(nf, 2 * c->num_sms));
+  int n_cta = std::max(1, std::min(nf, 2 * c->num_sms));   // scratch sized for the largest launch
   Tmp d_orbs, d_order, d_w, d_out, d_cnt, d_scr;
   TRY(tmp_alloc(c, d_orbs, orbs_h.size() * sizeof(int)));
   TRY(tmp_alloc(c, d_order, nf * sizeof(int)));
@@ -1477,18 +1503,91 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
   if (prec == OSVMP2_MIXED) {
     CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
     TRY(build_sigma_table(c, sig));
-    launch_frag_solve_mixed(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, sig.tab,
-                            (double*)d_scr.p, n_cta, (int*)d_cnt.p, (FragOut*)d_out.p, tdst,
-                            (const long long*)d_toff.p, c->err_d, c->st);
-  } else
+    const Tables tb = tables(c);
+    auto solve = [&](const SolvePlan& pl, cudaStream_t st) {
+      SolveOpts o = so;
+      o.tiles = pl.tiles;
+      const int nc = std::max(1, std::min(nf, pl.ctas_per_sm * c->num_sms));
+      launch_frag_solve_mixed(tb, (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, o, sig.tab,
+                              (double*)d_scr.p, nc, (int*)d_cnt.p, (FragOut*)d_out.p, tdst,
+                              (const long long*)d_toff.p, c->err_d, st);
+    };
+    // autotuner: the first call for a (fragment count, largest pair order) times
+    // every candidate plan on the full solve and keeps the fastest
+    const std::pair<int, int> key{nf, max_m};
+    auto it = c->plans.find(key);
+    if (it == c->plans.end()) {
+      SolvePlan best;
+      if (!c->opts.no_autotune) {
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        for (int cps = 1; cps <= 2; cps++)
+          for (int tl = 0; tl <= 1; tl++) {
+            SolvePlan pl;
+            pl.ctas_per_sm = cps;
+            pl.tiles = tl;
+            CK(cudaEventRecord(e0, c->st));
+            solve(pl, c->st);
+            CK(cudaEventRecord(e1, c->st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+              best_ms = ms;
+              best = pl;
+            }
+          }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        best.tuned = true;
+        best.ms = best_ms;
+        CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
+      }
+      it = c->plans.emplace(key, best).first;
+    }
+    c->last_plan = it->second;
+    // the solve and the MBE(3) sum replayed as one CUDA graph (recorded on a
+    // private stream, launched on the ctx stream; an instantiated graph is
+    // updated in place when only its arguments changed)
+    bool graphed = false;
+    if (!c->cap_st) cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking);
+    if (c->cap_st && cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      solve(it->second, c->cap_st);
+      launch_weighted_sum((const FragOut*)d_out.p, (const int*)d_w.p, nf, c->scal_d, c->cap_st);
+      cudaGraph_t g = nullptr;
+      if (cudaStreamEndCapture(c->cap_st, &g) == cudaSuccess && g) {
+        if (c->solve_exec) {
+          cudaGraphExecUpdateResultInfo info;
+          if (cudaGraphExecUpdate(c->solve_exec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(c->solve_exec);
+            c->solve_exec = nullptr;
+          }
+        }
+        if (!c->solve_exec && cudaGraphInstantiate(&c->solve_exec, g, 0) != cudaSuccess) {
+          cudaGetLastError();
+          c->solve_exec = nullptr;
+        }
+        if (c->solve_exec && cudaGraphLaunch(c->solve_exec, c->st) == cudaSuccess) graphed = true;
+        cudaGraphDestroy(g);
+      }
+      cudaGetLastError();
+    }
+    if (!graphed) {
+      solve(it->second, c->st);
+      launch_weighted_sum((const FragOut*)d_out.p, (const int*)d_w.p, nf, c->scal_d, c->st);
+    }
+  } else {
     launch_frag_solve(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, (double*)d_scr.p, n_cta,
                       (int*)d_cnt.p, (FragOut*)d_out.p, tdst, (const long long*)d_toff.p, c->st);
+    launch_weighted_sum((const FragOut*)d_out.p, (const int*)d_w.p, nf, c->scal_d, c->st);
+  }
   CK(cudaGetLastError());
   ph_end(c, OSVMP2_PH_SOLVE, 0.0);
-  ph_begin(c, OSVMP2_PH_MBE_SUM);
-  launch_weighted_sum((const FragOut*)d_out.p, (const int*)d_w.p, nf, c->scal_d, c->st);
+  ph_begin(c, OSVMP2_PH_MBE_SUM);   // (inside the solve phase: the sum is part of the same graph)
   ph_end(c, OSVMP2_PH_MBE_SUM, 2.0 * nf);
-  CK(cudaGetLastError());
   c->frag_out.resize(nf);
   CK(cudaMemcpyAsync(c->frag_out.data(), d_out.p, nf * sizeof(FragOut), cudaMemcpyDeviceToHost, c->st));
   CK(cudaMemcpyAsync(e_out, c->scal_d, sizeof(double), cudaMemcpyDeviceToHost, c->st));

@@ -226,13 +226,20 @@ __device__ void cta_gemm_f32r_acc2(int M, int N, int K, float alpha, const VA& A
     }
   __syncthreads();
 }
+// Tile set of the short FP32 contractions: 0 = 64 x 64 tiles up to 64 x 64
+// outputs and 96 x 96 above; 1 = also 80 x 80 tiles for outputs up to 80 x 80.
+// (A runtime choice of the solver's autotuner; the K order of every output's
+// FMAs, hence the result, is the same for every tile shape.)
 template <class VA, class VB>
 __device__ void cta_gemm_f32s_acc2(int M, int N, int K, float alpha, const VA& A, const VB& B, float* Chi, float* Clo,
-                                   int ldc, float* sm) {
-  if (M > TM || N > TN)
-    cta_gemm_f32r_acc2<6>(M, N, K, alpha, A, B, Chi, Clo, ldc, sm);
-  else
+                                   int ldc, float* sm, int tiles = 0) {
+  const int mx = max(M, N);
+  if (mx <= TM)
     cta_gemm_f32r_acc2<4>(M, N, K, alpha, A, B, Chi, Clo, ldc, sm);
+  else if (tiles == 1 && mx <= 80)
+    cta_gemm_f32r_acc2<5>(M, N, K, alpha, A, B, Chi, Clo, ldc, sm);
+  else
+    cta_gemm_f32r_acc2<6>(M, N, K, alpha, A, B, Chi, Clo, ldc, sm);
 }
 
 // C = beta C + alpha A B for short K (<= a few hundred) in FP32 (tile_mma_f32r),
@@ -240,11 +247,14 @@ __device__ void cta_gemm_f32s_acc2(int M, int N, int K, float alpha, const VA& A
 // the usual pair orders ~80) above; sm holds GEMM_SMEM_F32 floats.
 template <class CT, class VA, class VB>
 __device__ void cta_gemm_f32s(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, CT* C, int ldc,
-                              float* sm) {
-  if (M > TM || N > TN)
-    cta_gemm_f32r<6>(M, N, K, alpha, A, B, beta, C, ldc, sm);
-  else
+                              float* sm, int tiles = 0) {
+  const int mx = max(M, N);
+  if (mx <= TM)
     cta_gemm_f32r<4>(M, N, K, alpha, A, B, beta, C, ldc, sm);
+  else if (tiles == 1 && mx <= 80)
+    cta_gemm_f32r<5>(M, N, K, alpha, A, B, beta, C, ldc, sm);
+  else
+    cta_gemm_f32r<6>(M, N, K, alpha, A, B, beta, C, ldc, sm);
 }
 
 

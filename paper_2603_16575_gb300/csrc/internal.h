@@ -36,6 +36,7 @@ void note_launch(int n);
 struct SolveOpts {
   double tol_update, tol_energy;
   int max_iter;
+  int tiles;      // mixed solver: tile set of its FP32 contractions (cta_gemm_f32s)
 };
 
 // Per-fragment result record written by the solvers.

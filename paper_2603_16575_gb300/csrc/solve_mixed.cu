@@ -235,13 +235,13 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
           const ViewF St{sig_ptr[tm.sig], sig_ld[tm.sig], !sig_tr[tm.sig]};      // Sigma_pq^T (r_q x r_p)
           // W = (cn Y_q + ct Y_q^T) Sigma_pq^T, C_p += Sigma_pq W
           if (tm.ct == 0.0)
-            cta_gemm_f32s<float>(rq, rp, rq, tm.cn, ViewF{Y32[tm.q], rq, 0}, St, 0.0, W32, rp, fsm);
+            cta_gemm_f32s<float>(rq, rp, rq, tm.cn, ViewF{Y32[tm.q], rq, 0}, St, 0.0, W32, rp, fsm, o.tiles);
           else if (tm.cn == 0.0)
-            cta_gemm_f32s<float>(rq, rp, rq, tm.ct, ViewF{Y32[tm.q], rq, 1}, St, 0.0, W32, rp, fsm);
+            cta_gemm_f32s<float>(rq, rp, rq, tm.ct, ViewF{Y32[tm.q], rq, 1}, St, 0.0, W32, rp, fsm, o.tiles);
           else
             cta_gemm_f32s<float>(rq, rp, rq, 1.0, ViewFmix{Y32[tm.q], rq, (float)tm.cn, (float)tm.ct}, St, 0.0,
-                                 W32, rp, fsm);
-          cta_gemm_f32s_acc2(rp, rp, rq, 1.f, S, ViewF{W32, rp, 0}, Chi[p], Clo[p], rp, fsm);
+                                 W32, rp, fsm, o.tiles);
+          cta_gemm_f32s_acc2(rp, rp, rq, 1.f, S, ViewF{W32, rp, 0}, Chi[p], Clo[p], rp, fsm, o.tiles);
         }
         // leftovers of an inexact preconditioner basis (S~ = 1 + Sh, G0 = diag(e~) - (f_ii+f_jj)/2):
         // P = Gh (Y S~) + (S~ Y) Gh + G0 (Y Sh) + (Sh Y) G0, from the amplitudes of the last refresh
@@ -249,8 +249,8 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
         if (Sh && refresh_P) {
           const float* Gh = t.Gh[pid[p]];
           const float* g0 = G0[p];
-          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Y32[p], rp, 0}, ViewF{Sh, rp, 0}, 0.0, A1, rp, fsm);
-          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Sh, rp, 0}, ViewF{Y32[p], rp, 0}, 0.0, A2, rp, fsm);
+          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Y32[p], rp, 0}, ViewF{Sh, rp, 0}, 0.0, A1, rp, fsm, o.tiles);
+          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Sh, rp, 0}, ViewF{Y32[p], rp, 0}, 0.0, A2, rp, fsm, o.tiles);
           for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
             const int a = idx / rp, b = idx % rp;
             Pp[p][idx] = g0[a] * A1[idx] + g0[b] * A2[idx];
@@ -258,8 +258,8 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
             A2[idx] += Y32[p][idx];
           }
           __syncthreads();
-          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Gh, rp, 0}, ViewF{A1, rp, 0}, 1.0, Pp[p], rp, fsm);
-          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{A2, rp, 0}, ViewF{Gh, rp, 0}, 1.0, Pp[p], rp, fsm);
+          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{Gh, rp, 0}, ViewF{A1, rp, 0}, 1.0, Pp[p], rp, fsm, o.tiles);
+          cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{A2, rp, 0}, ViewF{Gh, rp, 0}, 1.0, Pp[p], rp, fsm, o.tiles);
         }
       }
       // Y_p <- (K~_p + C_p) / D_p in FP64; energy <K~_p, 2Y_p - Y_p^T>

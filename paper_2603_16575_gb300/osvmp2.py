@@ -26,7 +26,8 @@ STATUS_CODES = {v: k for k, v in STATUS.items()}
 
 class Opts(ctypes.Structure):
     _fields_ = [("tau_s", ctypes.c_double), ("tol_update", ctypes.c_double), ("tol_energy", ctypes.c_double),
-                ("max_iter", ctypes.c_int32), ("osv_prec", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("max_iter", ctypes.c_int32), ("osv_prec", ctypes.c_int32), ("no_autotune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class System(ctypes.Structure):
@@ -54,6 +55,7 @@ SIGNATURES = {
     "osvmp2_last_error": (ctypes.c_char_p, [_P]),
     "osvmp2_default_opts": (None, [ctypes.POINTER(Opts)]),
     "osvmp2_set_opts": (ctypes.c_int, [_P, ctypes.POINTER(Opts)]),
+    "osvmp2_get_solve_plan": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "osvmp2_kernel_launches": (ctypes.c_int64, []),
     "osvmp2_build_osv": (ctypes.c_int, [_P, ctypes.POINTER(System), _D, _P]),
     "osvmp2_get_osv": (ctypes.c_int, [_P, _I32, _P, _P]),
@@ -201,6 +203,12 @@ class Context:
         _apply_opts(o, kw)
         self._check("osvmp2_set_opts", lib().osvmp2_set_opts(self._h, ctypes.byref(o)))
         self.opts = o
+
+    def solve_plan(self):
+        """Launch shape of the last mixed MBE(3) solve: dict(ctas_per_sm, tiles, tuned, n_keys)."""
+        out = (ctypes.c_int32 * 4)()
+        self._check("osvmp2_get_solve_plan", lib().osvmp2_get_solve_plan(self._h, out))
+        return {"ctas_per_sm": out[0], "tiles": out[1], "tuned": bool(out[2]), "n_keys": out[3]}
 
     def close(self):
         if getattr(self, "_h", None):

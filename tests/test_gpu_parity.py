@@ -261,3 +261,25 @@ def test_mixed_gradient_close_to_oracle():
         g = g.cpu().numpy()
         assert np.abs(g - r).max() < 1e-6 * np.abs(r).max()
     ctx.close()
+
+
+def test_mixed_autotuned_graph_replay_is_exact():
+    """The autotuned launch shape and the CUDA-graph replay of the mixed fragment solve
+    change time only: the same energy bit for bit as the fixed default shape, on the
+    first (tuning) call, on graph replays, and after the fragment list changes."""
+    s = synth.make_system(14, 60, 120, seed=43, lam=1.2)
+    energies = []
+    for no_tune in (1, 0):
+        ctx = _ctx(no_autotune=no_tune)
+        _build(ctx, s, 1e-4)
+        runs = [ctx.mbe3_energy(4.5, 3.8, "mixed")[0] for _ in range(3)]
+        plan = ctx.solve_plan()
+        assert plan["tuned"] == (no_tune == 0) and plan["n_keys"] == 1
+        assert runs[0] == runs[1] == runs[2]
+        other = ctx.mbe3_energy(4.0, 3.5, "mixed")[0]   # a different fragment list: new key, new graph
+        assert ctx.solve_plan()["n_keys"] == 2
+        again = ctx.mbe3_energy(4.5, 3.8, "mixed")[0]
+        assert again == runs[0]
+        energies.append((runs[0], other))
+        ctx.close()
+    assert energies[0] == energies[1]
