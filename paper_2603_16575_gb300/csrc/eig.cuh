@@ -704,16 +704,17 @@ __device__ inline int sturm_count_sq(const double* d, const double* e2, int n, d
 }
 
 // Eigenvalues with ascending indices n-1-t, t < k, of (d, e) by multisection
-// on the Sturm count, called by one warp that handles t = t0, t0 + tstride, ...:
+// on the Sturm count, called by one warp that handles t = t0, t0 + tstride, ...
+// (at most tcount of them):
 // g = lane / L lanes per eigenvalue split its interval at L points per step
 // (log2(L+1) bits per Sturm sequence instead of one), until the interval is
 // below 2 eps |lambda| or atol (the eigenvalues of the tridiagonal are only
 // determined to ~eps ||T|| by its rounding).  e2 holds the squared
 // off-diagonal.  w[t] receives the eigenvalue.
 __device__ inline void multisect_eigs(const double* d, const double* e2, int n, int k, int t0, int tstride,
-                                      double lo0, double hi0, double pivmin, double atol, double* w) {
+                                      int tcount, double lo0, double hi0, double pivmin, double atol, double* w) {
   const int lane = threadIdx.x & 31;
-  const int ng = (k - t0 + tstride - 1) / tstride;          // eigenvalues of this warp
+  const int ng = min(tcount, (k - t0 + tstride - 1) / tstride);   // eigenvalues of this warp
   if (ng <= 0) return;
   const int L = max(1, 32 / ng);
   const int gmax = 32 / L;                                  // groups per pass

@@ -184,8 +184,16 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
     e2s[t] = (t + 1 < n) ? e[t] * e[t] : 0.0;
   }
   __syncthreads();
-  if ((threadIdx.x >> 5) < 4)
-    multisect_eigs(ds, e2s, n, k, threadIdx.x >> 5, 4, s_lo, s_hi, s_piv, 4.0 * 2.220446049250313e-16 * s_norm, w);
+  // Many kept eigenvalues (k >= 64): whole warps of one eigenvalue per lane (pure
+  // bisection, the fewest Sturm counts), so fewer warp instructions feed the FP64
+  // pipe; otherwise four warps, several lanes per eigenvalue.
+  const double atol = 4.0 * 2.220446049250313e-16 * s_norm;
+  if (k >= 64) {
+    const int wv = threadIdx.x >> 5;
+    if (32 * wv < k) multisect_eigs(ds, e2s, n, k, 32 * wv, 1, 32, s_lo, s_hi, s_piv, atol, w);
+  } else if ((threadIdx.x >> 5) < 4) {
+    multisect_eigs(ds, e2s, n, k, threadIdx.x >> 5, 4, k, s_lo, s_hi, s_piv, atol, w);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     const double ortol = 1e-3 * s_norm;
