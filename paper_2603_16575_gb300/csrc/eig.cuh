@@ -813,24 +813,68 @@ __device__ inline void tri_factor_lanes(const double* d, const double* e, int n,
   u1[32 * (n - 1)] = 0.0;
   u2[32 * (n - 1)] = 0.0;
 }
-__device__ inline void tri_solve_lanes(int n, const double* ui, const double* u1, const double* u2,
-                                       const double* mul, const int* piv, double* y) {
-  double cur = y[0];
-  for (int i = 0; i + 1 < n; i++) {
-    const double nx = y[32 * (i + 1)];
+// y <- (T - lam I)^{-1} (sc y) for each lane's vector, returning |x|^2 of the
+// result.  The element loads of each sweep are issued eight rows ahead of the
+// recurrence (the arrays live in L2), so their latency is not paid per row.
+__device__ inline double tri_solve_lanes(int n, double sc, const double* ui, const double* u1, const double* u2,
+                                         const double* mul, const int* piv, double* y) {
+  constexpr int U = 8;
+  double cur = sc * y[0];
+  int i = 0;
+  for (; i + U < n; i += U) {
+    double nx[U], mu[U];
+    int pv[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      nx[u] = y[32 * (i + 1 + u)];
+      mu[u] = mul[32 * (i + u)];
+      pv[u] = piv[32 * (i + u)];
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const double v = sc * nx[u];
+      const bool sw = pv[u] != 0;
+      const double lo = sw ? v : cur, hi = sw ? cur : v;
+      y[32 * (i + u)] = lo;
+      cur = hi - mu[u] * lo;
+    }
+  }
+  for (; i + 1 < n; i++) {
+    const double v = sc * y[32 * (i + 1)];
     const bool sw = piv[32 * i] != 0;
-    const double lo = sw ? nx : cur, hi = sw ? cur : nx;
+    const double lo = sw ? v : cur, hi = sw ? cur : v;
     y[32 * i] = lo;
     cur = hi - mul[32 * i] * lo;
   }
   y[32 * (n - 1)] = cur;
-  double y1 = 0.0, y2 = 0.0;   // x[i + 1], x[i + 2]
-  for (int i = n - 1; i >= 0; i--) {
+  double y1 = 0.0, y2 = 0.0, nn = 0.0;   // x[i + 1], x[i + 2]
+  i = n - 1;
+  for (; i - U + 1 >= 0; i -= U) {
+    double yv[U], a1[U], a2[U], iv[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      yv[u] = y[32 * (i - u)];
+      a1[u] = u1[32 * (i - u)];
+      a2[u] = u2[32 * (i - u)];
+      iv[u] = ui[32 * (i - u)];
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const double x = (yv[u] - a1[u] * y1 - a2[u] * y2) * iv[u];
+      y[32 * (i - u)] = x;
+      nn += x * x;
+      y2 = y1;
+      y1 = x;
+    }
+  }
+  for (; i >= 0; i--) {
     const double x = (y[32 * i] - u1[32 * i] * y1 - u2[32 * i] * y2) * ui[32 * i];
     y[32 * i] = x;
+    nn += x * x;
     y2 = y1;
     y1 = x;
   }
+  return nn;
 }
 
 }  // namespace osv

@@ -232,22 +232,23 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
         const int t = 32 * g + lane;
         if (t < k) {
           tri_factor_lanes(d, e, n, w[t], small, ui, u1, u2, mul, piv);
-          for (int r = 0; r < n; r++) {
-            if (pass == 0) {
+          if (pass == 0) {
+#pragma unroll 4
+            for (int r = 0; r < n; r++) {
               const uint64_t h = draw(0x5eedull + (uint64_t)t, (uint64_t)r);
               y[32 * r] = (double)(h >> 11) * 0x1p-53 - 0.5;
-            } else {
-              y[32 * r] = V[(size_t)t * n + r];
             }
+          } else {
+#pragma unroll 8
+            for (int r = 0; r < n; r++) y[32 * r] = V[(size_t)t * n + r];
           }
+          double sc = 1.0;   // normalisation of the previous solve, applied on the next read
           for (int it = 0; it < 2 - pass; it++) {
-            tri_solve_lanes(n, ui, u1, u2, mul, piv, y);
-            double nn = 0.0;
-            for (int r = 0; r < n; r++) nn += y[32 * r] * y[32 * r];
-            const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-            for (int r = 0; r < n; r++) y[32 * r] *= sc;
+            const double nn = tri_solve_lanes(n, sc, ui, u1, u2, mul, piv, y);
+            sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
           }
-          for (int r = 0; r < n; r++) V[(size_t)t * n + r] = y[32 * r];
+#pragma unroll 8
+          for (int r = 0; r < n; r++) V[(size_t)t * n + r] = sc * y[32 * r];
         }
       }
     }
