@@ -98,48 +98,86 @@ void launch_exchange(const Tables& t, int n_aux, const KJob* jobs, int n_jobs, i
   note_launch(1);
 }
 
-struct QtScaled {         // A(mu, a) = Q_x[a][mu] * (e ? e[a] : 1)
-  const double* q;
-  int ld;
-  const double* e;
-  __device__ __forceinline__ double get(int mu, int a) const {
-    const double v = q[(size_t)a * ld + mu];
-    return e ? v * e[a] : v;
-  }
-};
 
-// S_(x,y) = Q_x^T Q_y and F_(x,y) = Q_x^T diag(e) Q_y.  grid: (job, tile r, tile c, 2)
+// S_(x,y) = Q_x^T Q_y and F_(x,y) = Q_x^T diag(e) Q_y, both from the same
+// staged tiles of Q_x and Q_y, one CTA per block.  The output tile is the
+// smallest of 48, 64 and 80 wide that covers the block (OSV blocks are ~10-80
+// wide; a fixed 64-wide tile would mostly compute padding), 80-wide tiles in a
+// loop above that.  Every output's FMAs run in k order with the product
+// e_a Q_x[a][mu] rounded first, as in a plain GEMM of the scaled operand.
+constexpr int SF_TMAX = 80;
+template <int R>
+__device__ void sf_tiles(int nx, int ny, int nv, const double* __restrict__ qx, const double* __restrict__ qy,
+                         const double* __restrict__ e_vir, double* S, double* F, double* sm) {
+  constexpr int T = 16 * R;
+  double* As = sm;                 // [TK][T]
+  double* Bs = sm + TK * T;        // [TK][T]
+  double* es = sm + 2 * TK * T;    // [TK]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < nx; m0 += T)
+    for (int n0 = 0; n0 < ny; n0 += T) {
+      double aS[R][R], aF[R][R];
+#pragma unroll
+      for (int u = 0; u < R; u++)
+#pragma unroll
+        for (int v = 0; v < R; v++) aS[u][v] = aF[u][v] = 0.0;
+      for (int k0 = 0; k0 < nv; k0 += TK) {
+        for (int e = tid; e < TK * T; e += NT) {
+          const int k = e / T, m = e % T, gk = k0 + k;
+          As[e] = (gk < nv && m0 + m < nx) ? qx[(size_t)gk * nx + m0 + m] : 0.0;
+          Bs[e] = (gk < nv && n0 + m < ny) ? qy[(size_t)gk * ny + n0 + m] : 0.0;
+        }
+        if (tid < TK) es[tid] = (k0 + tid < nv) ? e_vir[k0 + tid] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < TK; k++) {
+          double a[R], ea[R], b[R];
+          const double ek = es[k];
+#pragma unroll
+          for (int u = 0; u < R; u++) {
+            a[u] = As[k * T + ty + 16 * u];
+            ea[u] = a[u] * ek;
+          }
+#pragma unroll
+          for (int v = 0; v < R; v++) b[v] = Bs[k * T + tx + 16 * v];
+#pragma unroll
+          for (int u = 0; u < R; u++)
+#pragma unroll
+            for (int v = 0; v < R; v++) {
+              aS[u][v] = fma(a[u], b[v], aS[u][v]);
+              aF[u][v] = fma(ea[u], b[v], aF[u][v]);
+            }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int u = 0; u < R; u++)
+#pragma unroll
+        for (int v = 0; v < R; v++) {
+          const int r = m0 + ty + 16 * u, c = n0 + tx + 16 * v;
+          if (r < nx && c < ny) {
+            S[(size_t)r * ny + c] = aS[u][v];
+            F[(size_t)r * ny + c] = aF[u][v];
+          }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(NT) k_sf(Tables t, const double* __restrict__ e_vir,
                                            const SFJob* __restrict__ jobs) {
-  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  __shared__ double sm[2 * TK * SF_TMAX + TK];
   const SFJob jb = jobs[blockIdx.x];
-  const int nx = t.n_osv[jb.x], ny = t.n_osv[jb.y];
-  const int m0 = blockIdx.y * TM, n0 = (blockIdx.z >> 1) * TN;
-  const int isF = blockIdx.z & 1;
-  if (m0 >= nx || n0 >= ny) return;
-  double acc[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; u++)
-#pragma unroll
-    for (int v = 0; v < 4; v++) acc[u][v] = 0.0;
-  tile_mma(nx, ny, t.n_vir, m0, n0, QtScaled{t.Q[jb.x], nx, isF ? e_vir : nullptr}, RowMajor{t.Q[jb.y], ny},
-           acc, sm);
-  double* out = isF ? jb.F : jb.S;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll
-  for (int u = 0; u < 4; u++)
-#pragma unroll
-    for (int v = 0; v < 4; v++) {
-      const int r = m0 + ty + 16 * u, c = n0 + tx + 16 * v;
-      if (r < nx && c < ny) out[(size_t)r * ny + c] = acc[u][v];
-    }
+  const int nx = t.n_osv[jb.x], ny = t.n_osv[jb.y], nv = t.n_vir;
+  const int w = max(nx, ny);
+  if (w <= 48) sf_tiles<3>(nx, ny, nv, t.Q[jb.x], t.Q[jb.y], e_vir, jb.S, jb.F, sm);
+  else if (w <= 64) sf_tiles<4>(nx, ny, nv, t.Q[jb.x], t.Q[jb.y], e_vir, jb.S, jb.F, sm);
+  else sf_tiles<5>(nx, ny, nv, t.Q[jb.x], t.Q[jb.y], e_vir, jb.S, jb.F, sm);
 }
 
 void launch_sf(const Tables& t, const double* e_vir, const SFJob* jobs, int n_jobs, int max_n, cudaStream_t st) {
   if (n_jobs == 0) return;
-  const int nt = (max_n + TM - 1) / TM;
-  dim3 grid(n_jobs, nt, 2 * nt);
-  k_sf<<<grid, NT, 0, st>>>(t, e_vir, jobs);
+  (void)max_n;
+  k_sf<<<n_jobs, NT, 0, st>>>(t, e_vir, jobs);
   note_launch(1);
 }
 
