@@ -163,7 +163,7 @@ __device__ void sf_tiles(int nx, int ny, int nv, const double* __restrict__ qx, 
     }
 }
 
-__global__ void __launch_bounds__(NT) k_sf(Tables t, const double* __restrict__ e_vir,
+__global__ void __launch_bounds__(NT, 2) k_sf(Tables t, const double* __restrict__ e_vir,
                                            const SFJob* __restrict__ jobs) {
   __shared__ double sm[2 * TK * SF_TMAX + TK];
   const SFJob jb = jobs[blockIdx.x];
