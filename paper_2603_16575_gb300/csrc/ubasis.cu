@@ -23,13 +23,18 @@
 
 namespace osv {
 
-// U_p = [Q_i Q_j] X_p in FP64 (per-CTA scratch [n_vir][max_r]), written as FP32
-// [n_vir][r] and as the TF32 slices of U_p^T.  One CTA per pair (grid-stride).
+// U_p = [Q_i Q_j] X_p in FP64, formed transposed (U_p^T [r][n_vir] in the
+// per-CTA scratch, so that the slices of U_p^T are cut from contiguous rows),
+// written as FP32 [n_vir][r] through a shared-memory transpose and as the TF32
+// slices of U_p^T.  One CTA per pair (grid-stride).
 __global__ void __launch_bounds__(NT) k_ubasis(Tables t, const UJob* __restrict__ jobs, int n_jobs,
                                                double* scratch, int max_r) {
-  __shared__ double sm[GEMM_SMEM_WIDE];
+  __shared__ double sm[GEMM_SMEM_WIDE];   // GEMM tiles, then the transpose tiles
+  constexpr int TW = (GEMM_SMEM_WIDE * 2) / (32 * 33);   // warps with a 32 x 33 float tile
+  float (*tr)[32][33] = reinterpret_cast<float (*)[32][33]>(sm);
   const int nv = t.n_vir;
-  double* W = scratch + (size_t)blockIdx.x * nv * max_r;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* Wt = scratch + (size_t)blockIdx.x * nv * max_r;
   for (int jid = blockIdx.x; jid < n_jobs; jid += gridDim.x) {
     const UJob jb = jobs[jid];
     const int ni = t.n_osv[jb.i], nj = (jb.i == jb.j) ? 0 : t.n_osv[jb.j];
@@ -40,19 +45,32 @@ __global__ void __launch_bounds__(NT) k_ubasis(Tables t, const UJob* __restrict_
     P.rows = nv; P.cols = m; P.rs = nv; P.cs = ni;
     P.b[0][0] = P.b[1][0] = Blk{t.Q[jb.i], ni, 0};
     P.b[0][1] = P.b[1][1] = Blk{nj ? t.Q[jb.j] : t.Q[jb.i], nj ? nj : ni, 0};
-    cta_gemm_a(nv, r, m, 1.0, P, dense_view(t.X[pid], m, r, m), 0.0, W, r, sm);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nv * r; idx += NT) jb.U[idx] = (float)W[idx];
+    cta_gemm_a(r, nv, m, 1.0, transpose(dense_view(t.X[pid], m, r, m)), transpose(P), 0.0, Wt, nv, sm);
     const size_t sl = (size_t)r * jb.ldv;
     const int nch = (nv + tc::CHUNK - 1) / tc::CHUNK;
-    const int lane = threadIdx.x & 31;
-    for (int w = threadIdx.x >> 5; w < r * nch; w += NT / 32) {   // one (mu, chunk) per warp step
+    // slices of U^T: one (mu, 32-virtual chunk) per warp step, lanes along the virtuals
+    for (int w = warp; w < r * nch; w += NT / 32) {
       const int mu = w / nch, a = (w - mu * nch) * tc::CHUNK + lane;
       float v[tc::NSL];
-      tc::warp_fixed_slices(a < nv ? W[(size_t)a * r + mu] : 0.0, v);
+      tc::warp_fixed_slices(a < nv ? Wt[(size_t)mu * nv + a] : 0.0, v);
       if (a < nv)
 #pragma unroll
         for (int s = 0; s < tc::NSL; s++) jb.Us[s * sl + (size_t)mu * jb.ldv + a] = v[s];
+    }
+    // U [a][mu] = U^T [mu][a], 32 x 32 tiles through shared memory (warps 0 .. TW-1)
+    const int nta = (nv + 31) / 32, ntm = (r + 31) / 32;
+    for (int tl = warp; warp < TW && tl < nta * ntm; tl += TW) {
+      const int a0 = (tl % nta) * 32, m0 = (tl / nta) * 32;
+      for (int q = 0; q < 32; q++) {
+        const int mu = m0 + q, a = a0 + lane;
+        tr[warp][q][lane] = (mu < r && a < nv) ? (float)Wt[(size_t)mu * nv + a] : 0.f;
+      }
+      __syncwarp();
+      for (int q = 0; q < 32; q++) {
+        const int a = a0 + q, mu = m0 + lane;
+        if (a < nv && mu < r) jb.U[(size_t)a * r + mu] = tr[warp][lane][q];
+      }
+      __syncwarp();
     }
     __syncthreads();
   }
