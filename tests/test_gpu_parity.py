@@ -283,3 +283,19 @@ def test_mixed_autotuned_graph_replay_is_exact():
         energies.append((runs[0], other))
         ctx.close()
     assert energies[0] == energies[1]
+
+
+def test_mixed_form_large_pair_orders():
+    """Pairs of order above 192 (more OSVs per orbital than the 128-orbital workload): the
+    mixed preconditioner (eigen-solver scratch sized at launch) and solver against the oracle."""
+    s = synth.make_system(5, 220, 300, seed=47, lam=1.2)    # 89-167 OSVs per orbital
+    ctx = _ctx()
+    n_osv = list(_build(ctx, s, 1e-4))
+    assert max(n_osv) * 2 > 192
+    E, st = ctx.mbe3_energy(8.0, 6.0, "mixed")
+    o = oracle.OSVSystem(s.B_block, 5, s.e_vir, s.f_occ, l_osv=1e-4)
+    assert [q.shape[1] for q in o.Q] == n_osv
+    E_ref, _ = o.mbe3_energy(s.r_occ, 8.0, 6.0)
+    assert st["n_unconverged"] == 0
+    assert abs(E - E_ref) < 1e-6
+    ctx.close()
