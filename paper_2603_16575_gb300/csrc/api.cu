@@ -1112,7 +1112,7 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
     CK(cudaGetLastError());
     ph_begin(c, OSVMP2_PH_EIG);
     launch_eig_osv((double*)Tm.p, b, nv, l_osv, kmax, (double*)Vm.p, (double*)wm.p, (int*)km.p, (double*)sm.p,
-                   c->err_d, c->st);
+                   c->err_d, tii_tc, c->st);
     {
       const double nd = nv;
       const bool full = (nv <= 160) || (l_osv <= 0.0);

@@ -349,6 +349,207 @@ __device__ inline void cta_tridiag_sym(double* A, int n, int lda, double* d, dou
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- double-float
+// Unevaluated sums hi + lo of two FP32 numbers (~48 significant bits), with the
+// error-free transformations of Knuth (two-sum) and Dekker (fast two-sum) and
+// the FMA-based exact product.  On this part FP32 runs at 64x the FP64 rate, so
+// an FMA in this arithmetic (~16 FP32 operations) costs a quarter of an FP64 FMA.
+struct dfl {
+  float h, l;
+};
+__device__ __forceinline__ dfl df_from(double x) {
+  const float h = (float)x;
+  return dfl{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ dfl df_fast2(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return dfl{s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float e = (a.h - (s - bb)) + (b.h - bb);
+  return df_fast2(s, e + (a.l + b.l));
+}
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_fast2(p, e);
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.h, -a.l}; }
+__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return df_add(df_mul(a, b), c); }   // a b + c
+__device__ __forceinline__ dfl df_shfl_xor(dfl a, int o) {
+  return dfl{__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+}
+// CTA sum in double-float (fixed order); red: >= 66 floats of shared memory.
+__device__ inline dfl cta_sum_df(dfl v, float* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  __syncthreads();
+  if (lane == 0) { red[2 * w] = v.h; red[2 * w + 1] = v.l; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dfl s{0.f, 0.f};
+    for (int k = 0; k < nw; k++) s = df_add(s, dfl{red[2 * k], red[2 * k + 1]});
+    red[64] = s.h;
+    red[65] = s.l;
+  }
+  __syncthreads();
+  return dfl{red[64], red[65]};
+}
+
+// cta_tridiag_sym in double-float arithmetic, for the mixed-form OSV build
+// (whose T_ii carries ~35 significant bits, so the ~48 bits here do not limit
+// it): the same fused sweep over the lower triangle, with A held as (hi, lo)
+// FP32 pairs in place of its FP64 elements (converted on the first step).
+// Outputs in FP64: d, e, tau, and reflector k in row k to the right of the
+// diagonal (A[k][k+1+t] = v_t, v_0 = 1), as cta_tridiag_sym.
+// sm: 4 n + 64 doubles (vp, wp, vk, p as pairs; reductions) + ntw * 32 * 33 doubles of tiles.
+template <int NTH>
+__device__ inline void cta_tridiag_sym_df(double* A, int n, int lda, double* d, double* e, double* tau, double* sm,
+                                          int ntw, double* gpart_d) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  dfl* vp = reinterpret_cast<dfl*>(sm);   // previous reflector v_{k-1}
+  dfl* wp = vp + n;                        // previous w_{k-1}
+  dfl* vk = wp + n;                        // current reflector v_k
+  dfl* p = vk + n;                         // A_k v_k, then w_k
+  float* red = reinterpret_cast<float*>(p + n);   // 64 doubles of room
+  dfl* tiles = reinterpret_cast<dfl*>(sm + 4 * n + 64);   // ntw x 32 x 33 pairs
+  dfl* gpart = reinterpret_cast<dfl*>(gpart_d);
+  dfl* Ad = reinterpret_cast<dfl*>(A);     // element (r, c) of the lower triangle at Ad[r * lda + c]
+  __shared__ double s_tc, s_sc;
+  // the lower triangle to (hi, lo) pairs, in place
+  for (int r = warp; r < n; r += NTH / 32)
+    for (int c = lane; c <= r; c += 32) Ad[(size_t)r * lda + c] = df_from(A[(size_t)r * lda + c]);
+  for (int t = tid; t < n; t += NTH) { vp[t] = dfl{0.f, 0.f}; wp[t] = dfl{0.f, 0.f}; }
+  __syncthreads();
+  for (int k = 0; k + 2 < n; k++) {
+    const int L = n - k - 1, k1 = k + 1;
+    // (a) column k (rows k..n-1) receives the previous update
+    dfl part{0.f, 0.f};
+    const dfl vpk = vp[k], wpk = wp[k];
+    for (int r = k + tid; r < n; r += NTH) {
+      dfl a = Ad[(size_t)r * lda + k];
+      if (k > 0) a = df_fma(df_neg(wp[r]), vpk, df_fma(df_neg(vp[r]), wpk, a));
+      if (r == k) d[k] = df_to(a);
+      else {
+        vk[r] = a;
+        if (r > k1) part = df_fma(a, a, part);
+      }
+    }
+    // (b) Householder reflector of column k below the diagonal (scalars in FP64)
+    const double sigma = df_to(cta_sum_df(part, red));
+    if (tid == 0) {
+      const double alpha = df_to(vk[k1]);
+      double tu = 0.0, beta = alpha, sc = 0.0;
+      if (sigma > 0.0) {
+        const double mu = sqrt(alpha * alpha + sigma);
+        beta = alpha <= 0.0 ? mu : -mu;
+        tu = (beta - alpha) / beta;
+        sc = 1.0 / (alpha - beta);
+      }
+      s_tc = tu;
+      s_sc = sc;
+      e[k] = beta;
+      tau[k] = tu;
+    }
+    __syncthreads();
+    const double tk = s_tc;
+    const dfl scd = df_from(s_sc);
+    for (int r = k1 + tid; r < n; r += NTH) {
+      const dfl v = (r == k1) ? dfl{1.f, 0.f} : df_mul(vk[r], scd);
+      vk[r] = (tk != 0.0) ? v : dfl{0.f, 0.f};
+      A[(size_t)k * lda + r] = df_to(v);          // reflector, row storage (FP64; not read again as a pair)
+    }
+    for (int t = tid; t < k1; t += NTH) vk[t] = dfl{0.f, 0.f};
+    __syncthreads();
+    // (c) fused sweep over the lower triangle of the trailing block
+    const int nb = (L + 31) >> 5;
+    const int ntile = nb * (nb + 1) / 2;
+    if (warp < ntw) {
+      dfl* tb = tiles + (size_t)warp * 32 * 33;
+      for (int tl = warp; tl < ntile; tl += ntw) {
+        int bi = 0;
+        while ((bi + 1) * (bi + 2) / 2 <= tl) bi++;
+        const int bj = tl - bi * (bi + 1) / 2;
+        const int r0 = k1 + 32 * bi, c0 = k1 + 32 * bj;
+        const int c = c0 + lane;
+        const bool cin = c < n;
+        const dfl nvpc = cin ? df_neg(vp[c]) : dfl{0.f, 0.f}, nwpc = cin ? df_neg(wp[c]) : dfl{0.f, 0.f};
+        dfl colsum{0.f, 0.f};
+        for (int i = 0; i < 32; i++) {
+          const int r = r0 + i;
+          dfl a{0.f, 0.f};
+          if (cin && r < n && r >= c) {
+            dfl* ap = Ad + (size_t)r * lda + c;
+            a = *ap;
+            if (k > 0) {
+              a = df_fma(wp[r], nvpc, df_fma(vp[r], nwpc, a));
+              *ap = a;
+            }
+            colsum = df_fma(a, vk[r], colsum);
+          }
+          tb[i * 33 + lane] = (r > c) ? a : dfl{0.f, 0.f};   // the row sums take the strictly lower part
+        }
+        __syncwarp();
+        dfl rowsum{0.f, 0.f};
+        for (int j = 0; j < 32; j++) rowsum = df_fma(tb[lane * 33 + j], vk[min(c0 + j, n - 1)], rowsum);
+        dfl* gp = gpart + (size_t)tl * 64;
+        gp[lane] = colsum;
+        gp[32 + lane] = rowsum;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // (d) p = A_k v_k from the partial sums (fixed order), then w_k
+    const dfl tkd = df_from(tk);
+    dfl pv{0.f, 0.f};
+    for (int c = k1 + tid; c < n; c += NTH) {
+      const int b = (c - k1) >> 5, o = (c - k1) & 31;
+      dfl s2{0.f, 0.f};
+      for (int bi = b; bi < nb; bi++) s2 = df_add(s2, gpart[(size_t)(bi * (bi + 1) / 2 + b) * 64 + o]);
+      for (int bj = 0; bj <= b; bj++) s2 = df_add(s2, gpart[(size_t)(b * (b + 1) / 2 + bj) * 64 + 32 + o]);
+      s2 = df_mul(s2, tkd);
+      p[c] = s2;
+      pv = df_fma(s2, vk[c], pv);
+    }
+    const dfl Kc = df_mul(df_from(0.5 * tk), cta_sum_df(pv, red));
+    const dfl nKc = df_neg(Kc);
+    for (int c = tid; c < n; c += NTH) {
+      const dfl w = (c >= k1) ? df_fma(nKc, vk[c], p[c]) : dfl{0.f, 0.f};
+      wp[c] = w;
+      vp[c] = vk[c];
+    }
+    __syncthreads();
+  }
+  // the trailing 2 x 2 block receives the last update
+  if (tid == 0) {
+    if (n >= 2) {
+      const int a0 = n - 2, a1 = n - 1;
+      double x00 = df_to(Ad[(size_t)a0 * lda + a0]), x10 = df_to(Ad[(size_t)a1 * lda + a0]);
+      double x11 = df_to(Ad[(size_t)a1 * lda + a1]);
+      if (n >= 3) {
+        const double v0 = df_to(vp[a0]), v1 = df_to(vp[a1]), w0 = df_to(wp[a0]), w1 = df_to(wp[a1]);
+        x00 -= 2.0 * v0 * w0;
+        x10 -= v1 * w0 + w1 * v0;
+        x11 -= 2.0 * v1 * w1;
+        tau[n - 2] = 0.0;
+      }
+      d[a0] = x00;
+      e[a0] = x10;
+      d[a1] = x11;
+    } else {
+      d[0] = df_to(Ad[0]);
+    }
+    tau[n - 1] = 0.0;
+  }
+  __syncthreads();
+}
+
 // Z (n x n, row-major, ldz) = H_0 H_1 ... H_{n-3} from the reflectors left in A.
 // y, vs: shared scratch of n doubles each.
 template <int NTH = NT>

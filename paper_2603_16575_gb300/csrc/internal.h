@@ -66,8 +66,10 @@ __host__ __device__ inline size_t eig_osv_scratch_doubles(int nv, int kmax) {
   const size_t work = (size_t)nv * nv > (size_t)4 * 176 * nv ? (size_t)nv * nv : (size_t)4 * 176 * nv;
   return (size_t)3 * nv + work + 64;
 }
+// dfl_tridiag: the top-k path tridiagonalises in double-float arithmetic (the
+// mixed-form OSV build, whose T_ii is a split-precision product).
 void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, double* w, int* k,
-                    double* scratch, int* err, cudaStream_t st);
+                    double* scratch, int* err, bool dfl_tridiag, cudaStream_t st);
 // Copy V[b][:, :k_b] into the packed Q store (Q[i0+b] as [nv][k]).
 void launch_pack_q(const double* V, const double* w, int nb, int nv, int kmax, const int* k,
                    double* const* Qdst, double* const* wdst, cudaStream_t st);

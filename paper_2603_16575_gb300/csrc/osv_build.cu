@@ -135,7 +135,7 @@ __device__ void eig_full_select(double* A, int n, double thr, int kmax, double* 
 // sequence, multisection for the kept eigenvalues, inverse iteration with
 // Gram-Schmidt inside clusters of close eigenvalues, back-transformation.
 __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, double* w, int* kout,
-                         double* scr, int* err, double* sm, int ntw) {
+                         double* scr, int* err, double* sm, int ntw, int dfl_tridiag) {
   double* d = scr;
   double* e = scr + n;
   double* tau = scr + 2 * n;
@@ -144,7 +144,10 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   double* red = sm + 2 * n;
   __shared__ int s_k, s_nclu;
   __shared__ double s_lo, s_hi, s_piv, s_norm;
-  if (ntw >= 2) cta_tridiag_sym<NT_EIG>(A, n, n, d, e, tau, sm, ntw, scr + 3 * n);   // partial sums in the Z room
+  if (ntw >= 2 && dfl_tridiag)
+    cta_tridiag_sym_df<NT_EIG>(A, n, n, d, e, tau, sm, ntw, scr + 3 * n);   // partial sums in the Z room
+  else if (ntw >= 2)
+    cta_tridiag_sym<NT_EIG>(A, n, n, d, e, tau, sm, ntw, scr + 3 * n);
   else cta_tridiag_col<NT_EIG>(A, n, n, d, e, tau, v, p, red);
   // Gershgorin bounds and a pivot floor
   double glo = 1e300, ghi = -1e300, nrm = 0.0, emax = 0.0;
@@ -322,7 +325,8 @@ __global__ void __launch_bounds__(EB_WARPS * 32) k_eig_back(const double* T, int
 }
 
 __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double thr, int kmax, double* V, double* w,
-                                                int* kout, double* scratch, int* err, int zsmem, int ntw) {
+                                                int* kout, double* scratch, int* err, int zsmem, int ntw,
+                                                int dfl_tridiag) {
   extern __shared__ double dyn[];
   const int b = blockIdx.x;
   double* A = T + (size_t)b * nv * nv;
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double th
     double* sm = dyn + (size_t)nv * ldz;
     eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zs, ldz, sm);
   } else if (thr > 0.0) {
-    eig_topk(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, dyn, ntw);
+    eig_topk(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, dyn, ntw, dfl_tridiag);
   } else {
     double* Zg = scr + 3 * nv;
     eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zg, nv, dyn);
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double th
 }
 
 void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, double* w, int* k,
-                    double* scratch, int* err, cudaStream_t st) {
+                    double* scratch, int* err, bool dfl_tridiag, cudaStream_t st) {
   const int zsmem = nv <= ZSMEM_MAX;
   size_t smem = (size_t)(4 * nv + 64) * sizeof(double);
   int ntw = 0;
@@ -354,7 +358,7 @@ void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, 
     if (ntw >= 2) smem += (size_t)ntw * tile * sizeof(double);
   }
   cudaFuncSetAttribute(k_eig_osv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_eig_osv<<<nb, NT_EIG, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem, ntw);
+  k_eig_osv<<<nb, NT_EIG, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem, ntw, dfl_tridiag ? 1 : 0);
   note_launch(1);
   if (!zsmem && thr > 0.0) {
     dim3 grid(nb, (std::min(kmax, nv) + EB_WARPS - 1) / EB_WARPS);
