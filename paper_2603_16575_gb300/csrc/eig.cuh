@@ -481,19 +481,27 @@ __device__ inline void cta_tridiag_sym_df(double* A, int n, int lda, double* d, 
         const bool cin = c < n;
         const dfl nvpc = cin ? df_neg(vp[c]) : dfl{0.f, 0.f}, nwpc = cin ? df_neg(wp[c]) : dfl{0.f, 0.f};
         dfl colsum{0.f, 0.f};
-        for (int i = 0; i < 32; i++) {
-          const int r = r0 + i;
-          dfl a{0.f, 0.f};
-          if (cin && r < n && r >= c) {
-            dfl* ap = Ad + (size_t)r * lda + c;
-            a = *ap;
-            if (k > 0) {
-              a = df_fma(wp[r], nvpc, df_fma(vp[r], nwpc, a));
-              *ap = a;
-            }
-            colsum = df_fma(a, vk[r], colsum);
+        for (int i0 = 0; i0 < 32; i0 += 8) {   // eight rows' loads in flight before their arithmetic
+          dfl av[8];
+#pragma unroll
+          for (int u = 0; u < 8; u++) {
+            const int r = r0 + i0 + u;
+            av[u] = (cin && r < n && r >= c) ? Ad[(size_t)r * lda + c] : dfl{0.f, 0.f};
           }
-          tb[i * 33 + lane] = (r > c) ? a : dfl{0.f, 0.f};   // the row sums take the strictly lower part
+#pragma unroll
+          for (int u = 0; u < 8; u++) {
+            const int r = r0 + i0 + u;
+            dfl a{0.f, 0.f};
+            if (cin && r < n && r >= c) {
+              a = av[u];
+              if (k > 0) {
+                a = df_fma(wp[r], nvpc, df_fma(vp[r], nwpc, a));
+                Ad[(size_t)r * lda + c] = a;
+              }
+              colsum = df_fma(a, vk[r], colsum);
+            }
+            tb[(i0 + u) * 33 + lane] = (r > c) ? a : dfl{0.f, 0.f};   // the row sums take the strictly lower part
+          }
         }
         __syncwarp();
         dfl rowsum{0.f, 0.f};
