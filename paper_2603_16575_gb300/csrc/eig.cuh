@@ -284,19 +284,27 @@ __device__ inline void cta_tridiag_sym(double* A, int n, int lda, double* d, dou
         const bool cin = c < n;
         const double vpc = cin ? vp[c] : 0.0, wpc = cin ? wp[c] : 0.0;
         double colsum = 0.0;
-        for (int i = 0; i < 32; i++) {
-          const int r = r0 + i;
-          double a = 0.0;
-          if (cin && r < n && r >= c) {
-            double* ap = A + (size_t)r * lda + c;
-            a = *ap;
-            if (k > 0) {
-              a = fma(-wp[r], vpc, fma(-vp[r], wpc, a));
-              *ap = a;
-            }
-            colsum = fma(a, vk[r], colsum);
+        for (int i0 = 0; i0 < 32; i0 += 8) {   // eight rows' loads in flight before their arithmetic
+          double av[8];
+#pragma unroll
+          for (int u = 0; u < 8; u++) {
+            const int r = r0 + i0 + u;
+            av[u] = (cin && r < n && r >= c) ? A[(size_t)r * lda + c] : 0.0;
           }
-          tb[i * 33 + lane] = (r > c) ? a : 0.0;   // the row sums take the strictly lower part
+#pragma unroll
+          for (int u = 0; u < 8; u++) {
+            const int r = r0 + i0 + u;
+            double a = 0.0;
+            if (cin && r < n && r >= c) {
+              a = av[u];
+              if (k > 0) {
+                a = fma(-wp[r], vpc, fma(-vp[r], wpc, a));
+                A[(size_t)r * lda + c] = a;
+              }
+              colsum = fma(a, vk[r], colsum);
+            }
+            tb[(i0 + u) * 33 + lane] = (r > c) ? a : 0.0;   // the row sums take the strictly lower part
+          }
         }
         __syncwarp();
         double rowsum = 0.0;
