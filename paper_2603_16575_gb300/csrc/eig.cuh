@@ -965,6 +965,70 @@ __device__ inline void multisect_eigs(const double* d, const double* e2, int n, 
   __syncwarp();
 }
 
+// a / b in double-float: an FP32 quotient corrected once with the exact
+// remainder (~2^-46 relative).
+__device__ __forceinline__ dfl df_div(dfl a, dfl b) {
+  const float q1 = __fdividef(a.h, b.h);
+  const dfl r = df_add(a, df_neg(df_mul(dfl{q1, 0.f}, b)));
+  const float q2 = __fdividef(r.h, b.h);
+  return df_fast2(q1, q2);
+}
+// sturm_count_sq in double-float: d and e^2 as (hi, lo) pairs, x converted once;
+// pivmin in FP32 range.
+__device__ inline int sturm_count_df(const dfl* d, const dfl* e2, int n, double x, float pivmin) {
+  const dfl nx = df_neg(df_from(x));
+  int cnt = 0;
+  dfl q = df_add(d[0], nx);
+  if (fabsf(q.h) < pivmin) q = dfl{-pivmin, 0.f};
+  cnt += q.h < 0.f;
+  for (int i = 1; i < n; i++) {
+    q = df_add(df_add(d[i], nx), df_neg(df_div(e2[i - 1], q)));
+    if (fabsf(q.h) < pivmin) q = dfl{-pivmin, 0.f};
+    cnt += q.h < 0.f;
+  }
+  return cnt;
+}
+// multisect_eigs with the Sturm counts in double-float (FP32 pipes): the
+// intervals stop at ~2^-44 of ||T|| (atol) or 2^-45 relative.  Meant for all the
+// warps of a CTA at once (t0 = warp, tstride = warps), so each eigenvalue gets
+// several lanes and rounds are few.
+__device__ inline void multisect_eigs_df(const dfl* d, const dfl* e2, int n, int k, int t0, int tstride,
+                                         double lo0, double hi0, float pivmin, double atol, double* w) {
+  const int lane = threadIdx.x & 31;
+  const int ng = (k - t0 + tstride - 1) / tstride;          // eigenvalues of this warp
+  if (ng <= 0) return;
+  const int L = max(1, 32 / ng);
+  const int gmax = 32 / L;
+  const double eps = 2.842170943040401e-14;                 // 2^-45
+  for (int gb = 0; gb < ng; gb += gmax) {
+    const int g = gb + lane / L, q = lane % L;
+    const int t = t0 + g * tstride;
+    const bool mine = (lane / L < gmax) && (g < ng) && (t < k);
+    const int j = n - 1 - t;
+    double lo = lo0, hi = hi0;
+    bool done = !mine;
+    for (int it = 0; it < 200; it++) {
+      if (!__any_sync(0xffffffffu, !done)) break;
+      const double x = lo + (hi - lo) * (double)(q + 1) / (double)(L + 1);
+      bool above = false;
+      if (!done) above = sturm_count_df(d, e2, n, x, pivmin) > j;
+      const unsigned bal = __ballot_sync(0xffffffffu, above);
+      if (!done) {
+        const unsigned bits = (bal >> ((lane / L) * L)) & ((L == 32) ? 0xffffffffu : ((1u << L) - 1u));
+        const int qs = bits ? (__ffs(bits) - 1) : L;
+        const double nlo = (qs == 0) ? lo : lo + (hi - lo) * (double)qs / (double)(L + 1);
+        const double nhi = (qs == L) ? hi : lo + (hi - lo) * (double)(qs + 1) / (double)(L + 1);
+        if (!(nlo > lo || nhi < hi)) done = true;
+        lo = nlo;
+        hi = nhi;
+        if (hi - lo <= fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), atol)) done = true;
+      }
+    }
+    if (mine && q == 0) w[t] = 0.5 * (lo + hi);
+  }
+  __syncwarp();
+}
+
 // One solve (T - lam I) x = y by Gaussian elimination with partial pivoting on
 // the tridiagonal; y is overwritten by x.  u0,u1,u2,mul: n doubles; piv: n ints.
 __device__ inline void tri_factor(const double* d, const double* e, int n, double lam, double small,

@@ -189,9 +189,20 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   __syncthreads();
   // Many kept eigenvalues (k >= 64): whole warps of one eigenvalue per lane (pure
   // bisection, the fewest Sturm counts), so fewer warp instructions feed the FP64
-  // pipe; otherwise four warps, several lanes per eigenvalue.
+  // pipe; otherwise four warps, several lanes per eigenvalue.  The mixed-form
+  // build counts in double-float on every warp (its tridiagonal is double-float).
   const double atol = 4.0 * 2.220446049250313e-16 * s_norm;
-  if (k >= 64) {
+  if (dfl_tridiag) {
+    dfl* dd = reinterpret_cast<dfl*>(ds);
+    dfl* de = reinterpret_cast<dfl*>(e2s);
+    for (int t = threadIdx.x; t < n; t += NT_EIG) {
+      dd[t] = df_from(ds[t]);
+      de[t] = df_from(e2s[t]);
+    }
+    __syncthreads();
+    const float pivf = 1e-30f * (float)fmax(1.0, emax);
+    multisect_eigs_df(dd, de, n, k, threadIdx.x >> 5, NT_EIG / 32, s_lo, s_hi, pivf, 5.7e-14 * s_norm, w);
+  } else if (k >= 64) {
     const int wv = threadIdx.x >> 5;
     if (32 * wv < k) multisect_eigs(ds, e2s, n, k, 32 * wv, 1, 32, s_lo, s_hi, s_piv, atol, w);
   } else if ((threadIdx.x >> 5) < 4) {
