@@ -55,6 +55,41 @@ __host__ __device__ inline View transpose(const View& v) {
   return t;
 }
 
+// ---------------------------------------------------------------- double-float
+// Unevaluated sums hi + lo of two FP32 numbers (~48 significant bits), with the
+// error-free transformations of Knuth (two-sum) and Dekker (fast two-sum) and
+// the FMA-based exact product.  On this part FP32 runs at 64x the FP64 rate, so
+// an FMA in this arithmetic (~16 FP32 operations) costs a quarter of an FP64 FMA.
+struct dfl {
+  float h, l;
+};
+__device__ __forceinline__ dfl df_from(double x) {
+  const float h = (float)x;
+  return dfl{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ dfl df_fast2(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return dfl{s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float e = (a.h - (s - bb)) + (b.h - bb);
+  return df_fast2(s, e + (a.l + b.l));
+}
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_fast2(p, e);
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.h, -a.l}; }
+__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return df_add(df_mul(a, b), c); }   // a b + c
+__device__ __forceinline__ dfl df_shfl_xor(dfl a, int o) {
+  return dfl{__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+}
 // ---------------------------------------------------------------- GEMM
 // Accumulate one TM x TN output tile at (m0, n0) of A[MxK] * B[KxN] into acc,
 // in the arithmetic of V (double, or float for the low-precision products);
@@ -368,6 +403,80 @@ __device__ void cta_gemm_a(int M, int N, int K, double alpha, const VA& A, const
     cta_gemm_r<6>(M, N, K, alpha, A, B, beta, C, ldc, sm);
   else
     cta_gemm_r<4>(M, N, K, alpha, A, B, beta, C, ldc, sm);
+}
+
+
+// C = beta C + alpha A B in double-float arithmetic (FP32 pipes, ~48 bits): the
+// FP64 views are converted as their tiles are staged, the products accumulate
+// as (hi, lo) pairs in the K order of cta_gemm, C is written in FP64.  For the
+// mixed form's FP64-shaped products whose inputs carry fewer bits than that.
+// Tiles (16 R) x (16 R), R x R per thread; sm: 2 TK 16R doubles.
+template <int R, class VA, class VB>
+__device__ void cta_gemm_df_r(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, double* C,
+                              int ldc, double* sm) {
+  constexpr int TMR = 16 * R;
+  dfl* As = reinterpret_cast<dfl*>(sm);
+  dfl* Bs = As + TK * TMR;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += TMR)
+    for (int n0 = 0; n0 < N; n0 += TMR) {
+      dfl acc[R][R];
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int j = 0; j < R; j++) acc[i][j] = dfl{0.f, 0.f};
+      for (int k0 = 0; k0 < K; k0 += TK) {
+#pragma unroll
+        for (int t = 0; t < TMR * TK / NT; t++) {
+          const int e = tid + t * NT, m = e % TMR, k = e / TMR;
+          const int gm = m0 + m, gk = k0 + k;
+          As[k * TMR + m] = (gm < M && gk < K) ? df_from(static_cast<double>(A.get(gm, gk))) : dfl{0.f, 0.f};
+        }
+#pragma unroll
+        for (int t = 0; t < TMR * TK / NT; t++) {
+          const int e = tid + t * NT, n = e % TMR, k = e / TMR;
+          const int gn = n0 + n, gk = k0 + k;
+          Bs[k * TMR + n] = (gn < N && gk < K) ? df_from(static_cast<double>(B.get(gk, gn))) : dfl{0.f, 0.f};
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < TK; k++) {
+          dfl a[R], b[R];
+#pragma unroll
+          for (int i = 0; i < R; i++) a[i] = As[k * TMR + ty + 16 * i];
+#pragma unroll
+          for (int j = 0; j < R; j++) b[j] = Bs[k * TMR + tx + 16 * j];
+#pragma unroll
+          for (int i = 0; i < R; i++)
+#pragma unroll
+            for (int j = 0; j < R; j++) acc[i][j] = df_fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < R; i++)
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+          const int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
+          if (r < M && c < N) {
+            double* cp = C + (size_t)r * ldc + c;
+            *cp = (beta == 0.0 ? 0.0 : beta * *cp) + alpha * df_to(acc[i][j]);
+          }
+        }
+    }
+  __syncthreads();
+}
+// cta_gemm_df_r with 96- or 64-wide tiles, whichever pads less (as cta_gemm_a);
+// sm holds GEMM_SMEM_WIDE doubles.
+template <class VA, class VB>
+__device__ void cta_gemm_df(int M, int N, int K, double alpha, const VA& A, const VB& B, double beta, double* C,
+                            int ldc, double* sm) {
+  const long long p64 = (long long)((M + 63) / 64) * ((N + 63) / 64) * 4096;
+  const long long p96 = (long long)((M + 95) / 96) * ((N + 95) / 96) * 9216;
+  if (p96 < p64)
+    cta_gemm_df_r<6>(M, N, K, alpha, A, B, beta, C, ldc, sm);
+  else
+    cta_gemm_df_r<4>(M, N, K, alpha, A, B, beta, C, ldc, sm);
 }
 
 // Dense float matrix view (element (r,c) at p[r*ld+c], or p[c*ld+r] when tr).

@@ -358,40 +358,7 @@ __device__ inline void cta_tridiag_sym(double* A, int n, int lda, double* d, dou
 }
 
 // ---------------------------------------------------------------- double-float
-// Unevaluated sums hi + lo of two FP32 numbers (~48 significant bits), with the
-// error-free transformations of Knuth (two-sum) and Dekker (fast two-sum) and
-// the FMA-based exact product.  On this part FP32 runs at 64x the FP64 rate, so
-// an FMA in this arithmetic (~16 FP32 operations) costs a quarter of an FP64 FMA.
-struct dfl {
-  float h, l;
-};
-__device__ __forceinline__ dfl df_from(double x) {
-  const float h = (float)x;
-  return dfl{h, (float)(x - (double)h)};
-}
-__device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
-__device__ __forceinline__ dfl df_fast2(float a, float b) {   // |a| >= |b|
-  const float s = a + b;
-  return dfl{s, b - (s - a)};
-}
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-  const float s = a.h + b.h;
-  const float bb = s - a.h;
-  const float e = (a.h - (s - bb)) + (b.h - bb);
-  return df_fast2(s, e + (a.l + b.l));
-}
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-  const float p = a.h * b.h;
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, e);
-  e = fmaf(a.l, b.h, e);
-  return df_fast2(p, e);
-}
-__device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.h, -a.l}; }
-__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return df_add(df_mul(a, b), c); }   // a b + c
-__device__ __forceinline__ dfl df_shfl_xor(dfl a, int o) {
-  return dfl{__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
-}
+// (arithmetic in common.cuh)
 // CTA sum in double-float (fixed order); red: >= 66 floats of shared memory.
 __device__ inline dfl cta_sum_df(dfl v, float* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;

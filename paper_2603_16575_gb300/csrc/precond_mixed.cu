@@ -315,7 +315,10 @@ __global__ void __launch_bounds__(NT, 3) k_pm_eig32_c(const PJob* __restrict__ j
   }
 }
 
-// (4) X = Y W; S~ = W^T (Y^T S Y) W; F~ = W^T F' W; leftovers
+// (4) X = Y W; S~ = W^T (Y^T S Y) W; F~ = W^T F' W; leftovers.  The products run in
+// double-float (~48 bits): W holds FP32 values and Y^T S Y, F' are FP64 with entries
+// ~1, so the leftovers (~1e-6) keep ~9 significant digits.  X = Y W stays FP64:
+// its entries reach lambda_min(S)^(-1/2) and U = P X inherits their rounding.
 __global__ void __launch_bounds__(NT, 2) k_pm_final(Tables t, const PJob* __restrict__ jobs,
                                                  const int* __restrict__ order, int n_jobs, double* slots,
                                                  const long long* off, int max_m, double* scratch, int* err) {
@@ -334,17 +337,17 @@ __global__ void __launch_bounds__(NT, 2) k_pm_final(Tables t, const PJob* __rest
     const PmPair pp = pm_pair(slots, off, jid, m);
     const View Wv = dense_view(pp.W, r, r, r);
     if (i != j) {
-      cta_gemm_a(m, r, r, 1.0, dense_view(pp.Y, m, r, r), Wv, 0.0, jb.X, m, sm);       // X = Y W
+      cta_gemm_a(m, r, r, 1.0, dense_view(pp.Y, m, r, r), Wv, 0.0, jb.X, m, sm);        // X = Y W (FP64)
       for (int idx = threadIdx.x; idx < ni * r; idx += NT) T1[idx] = pp.W[idx];        // (Y^T S Y) W, top rows
-      cta_gemm_a(nk, r, nk, 1.0, dense_view(pp.ZCZ, nk, nk, nk), dense_view(pp.W + (size_t)ni * r, nk, r, r), 0.0,
+      cta_gemm_df(nk, r, nk, 1.0, dense_view(pp.ZCZ, nk, nk, nk), dense_view(pp.W + (size_t)ni * r, nk, r, r), 0.0,
                T1 + (size_t)ni * r, r, sm);
     } else {
       for (int idx = threadIdx.x; idx < m * r; idx += NT) jb.X[(size_t)(idx / r) * m + idx % r] = pp.W[idx];
-      cta_gemm_a(r, r, r, 1.0, dense_view(t.S[t.sf_id[i * n + i]], ni, ni, ni), Wv, 0.0, T1, r, sm);
+      cta_gemm_df(r, r, r, 1.0, dense_view(t.S[t.sf_id[i * n + i]], ni, ni, ni), Wv, 0.0, T1, r, sm);
     }
-    cta_gemm_a(r, r, r, 1.0, transpose(Wv), dense_view(T1, r, r, r), 0.0, St, r, sm);      // S~
-    cta_gemm_a(r, r, r, 1.0, dense_view(pp.Fp, r, r, r), Wv, 0.0, T1, r, sm);
-    cta_gemm_a(r, r, r, 1.0, transpose(Wv), dense_view(T1, r, r, r), 0.0, Ft, r, sm);      // F~
+    cta_gemm_df(r, r, r, 1.0, transpose(Wv), dense_view(T1, r, r, r), 0.0, St, r, sm);      // S~
+    cta_gemm_df(r, r, r, 1.0, dense_view(pp.Fp, r, r, r), Wv, 0.0, T1, r, sm);
+    cta_gemm_df(r, r, r, 1.0, transpose(Wv), dense_view(T1, r, r, r), 0.0, Ft, r, sm);      // F~
     const double fh = 0.5 * (t.f_occ[i * n + i] + t.f_occ[j * n + j]);
     for (int idx = threadIdx.x; idx < r * r; idx += NT) {
       const int a = idx / r, b = idx % r;
