@@ -384,9 +384,10 @@ __device__ inline dfl cta_sum_df(dfl v, float* red) {
 // Outputs in FP64: d, e, tau, and reflector k in row k to the right of the
 // diagonal (A[k][k+1+t] = v_t, v_0 = 1), as cta_tridiag_sym.
 // sm: 4 n + 64 doubles (vp, wp, vk, p as pairs; reductions) + ntw * 32 * 33 doubles of tiles.
+// refl_df: reflector k stored as (hi, lo) pairs instead of FP64 (read by k_eig_back_df).
 template <int NTH>
 __device__ inline void cta_tridiag_sym_df(double* A, int n, int lda, double* d, double* e, double* tau, double* sm,
-                                          int ntw, double* gpart_d) {
+                                          int ntw, double* gpart_d, bool refl_df) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   dfl* vp = reinterpret_cast<dfl*>(sm);   // previous reflector v_{k-1}
   dfl* wp = vp + n;                        // previous w_{k-1}
@@ -438,7 +439,8 @@ __device__ inline void cta_tridiag_sym_df(double* A, int n, int lda, double* d, 
     for (int r = k1 + tid; r < n; r += NTH) {
       const dfl v = (r == k1) ? dfl{1.f, 0.f} : df_mul(vk[r], scd);
       vk[r] = (tk != 0.0) ? v : dfl{0.f, 0.f};
-      A[(size_t)k * lda + r] = df_to(v);          // reflector, row storage (FP64; not read again as a pair)
+      if (refl_df) Ad[(size_t)k * lda + r] = v;    // reflector, row storage (not read again by this sweep)
+      else A[(size_t)k * lda + r] = df_to(v);
     }
     for (int t = tid; t < k1; t += NTH) vk[t] = dfl{0.f, 0.f};
     __syncthreads();

@@ -66,6 +66,7 @@ void launch_tii(const BSrc& src, const double* e_vir, const double* f_occ, int n
 constexpr int ZSMEM_MAX = 160;   // Z kept in shared memory up to this order
 constexpr int NT_EIG = 1024;     // threads of the OSV eigen kernel (more loads in flight)
 constexpr int INV_GROUPS = 4;    // warps running the lane-batched inverse iteration (176 n doubles each)
+constexpr int EB_DF_MAXN = 1536; // double-float back-transformation: the vector in registers up to this order
 
 // Sign eigenvector t (V[t][0..n), eigenvector-major) so that its largest-magnitude
 // entry (lowest index on ties) is positive.  One warp per vector.
@@ -145,7 +146,7 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   __shared__ int s_k, s_nclu;
   __shared__ double s_lo, s_hi, s_piv, s_norm;
   if (ntw >= 2 && dfl_tridiag)
-    cta_tridiag_sym_df<NT_EIG>(A, n, n, d, e, tau, sm, ntw, scr + 3 * n);   // partial sums in the Z room
+    cta_tridiag_sym_df<NT_EIG>(A, n, n, d, e, tau, sm, ntw, scr + 3 * n, n <= EB_DF_MAXN);   // partial sums in the Z room
   else if (ntw >= 2)
     cta_tridiag_sym<NT_EIG>(A, n, n, d, e, tau, sm, ntw, scr + 3 * n);
   else cta_tridiag_col<NT_EIG>(A, n, n, d, e, tau, v, p, red);
@@ -298,6 +299,67 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
 // reflectors stored contiguously in the rows of A and tau in the scratch, then
 // the sign convention of sign_vectors.
 constexpr int EB_WARPS = 8;
+
+// The same back-transformation in double-float for the mixed-form build (its
+// reflectors are stored as (hi, lo) pairs by cta_tridiag_sym_df): the vector
+// lives in registers, NJ elements per lane (n <= 32 NJ), and every reflector
+// costs FP32 instructions only.
+template <int NJ>
+__global__ void __launch_bounds__(EB_WARPS * 32) k_eig_back_df(const double* T, int n, int kmax, double* V,
+                                                              const int* kout, const double* scratch,
+                                                              size_t scr_stride) {
+  const int b = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.y * EB_WARPS + warp;
+  if (t >= kout[b]) return;   // warp-uniform
+  const dfl* Ad = reinterpret_cast<const dfl*>(T + (size_t)b * n * n);
+  const double* tau = scratch + (size_t)b * scr_stride + 2 * n;
+  double* x = V + (size_t)b * n * kmax + (size_t)t * n;
+  dfl xr[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; j++) {
+    const int r = 32 * j + lane;
+    xr[j] = r < n ? df_from(x[r]) : dfl{0.f, 0.f};
+  }
+  for (int kk = n - 3; kk >= 0; kk--) {
+    const double tk = tau[kk];
+    if (tk == 0.0) continue;
+    const dfl* vr = Ad + (size_t)kk * n;   // v at columns kk+1 .. n-1 of row kk
+    dfl s{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+      const int r = 32 * j + lane;
+      if (r > kk && r < n) s = df_fma(vr[r], xr[j], s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = df_add(s, df_shfl_xor(s, o));
+    const dfl ns = df_neg(df_mul(s, df_from(tk)));
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+      const int r = 32 * j + lane;
+      if (r > kk && r < n) xr[j] = df_fma(ns, vr[r], xr[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NJ; j++) {
+    const int r = 32 * j + lane;
+    if (r < n) x[r] = df_to(xr[j]);
+  }
+  __syncwarp();
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int r = lane; r < n; r += 32) {
+    const double a = fabs(x[r]);
+    if (a > best) { best = a; bi = r; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (x[bi] < 0.0)
+    for (int r = lane; r < n; r += 32) x[r] = -x[r];
+}
 __global__ void __launch_bounds__(EB_WARPS * 32) k_eig_back(const double* T, int n, int kmax, double* V,
                                                            const int* kout, const double* scratch,
                                                            size_t scr_stride) {
@@ -373,7 +435,14 @@ void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, 
   note_launch(1);
   if (!zsmem && thr > 0.0) {
     dim3 grid(nb, (std::min(kmax, nv) + EB_WARPS - 1) / EB_WARPS);
-    k_eig_back<<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, eig_osv_scratch_doubles(nv, kmax));
+    const size_t ss = eig_osv_scratch_doubles(nv, kmax);
+    if (dfl_tridiag && ntw >= 2 && nv <= EB_DF_MAXN) {   // reflectors stored as pairs
+      if (nv <= 640) k_eig_back_df<20><<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
+      else if (nv <= 1280) k_eig_back_df<40><<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
+      else k_eig_back_df<48><<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
+    } else {
+      k_eig_back<<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
+    }
     note_launch(1);
   }
 }
