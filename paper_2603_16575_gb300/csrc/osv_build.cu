@@ -246,7 +246,8 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
       for (int g = warp; 32 * g < k; g += INV_GROUPS) {
         const int t = 32 * g + lane;
         if (t < k) {
-          tri_factor_lanes(d, e, n, w[t], small, ui, u1, u2, mul, piv);
+          // the second pass reuses the first pass's factorisation when every group kept its slot
+          if (pass == 0 || k > 32 * INV_GROUPS) tri_factor_lanes(d, e, n, w[t], small, ui, u1, u2, mul, piv);
           if (pass == 0) {
 #pragma unroll 4
             for (int r = 0; r < n; r++) {
