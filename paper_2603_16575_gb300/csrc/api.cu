@@ -485,7 +485,7 @@ double fragment_mixed_flops(const osvmp2_ctx* c, const Frag& f, int iters) {
 // within a batch the tiles are ordered by (x, aux tile, pair) so that the
 // pairs sharing an aux tile of B_x read it while it is resident in L2.
 int gproj_tensor(osvmp2_ctx* c, const std::vector<GJob>& gj, const std::vector<long long>& usrow, const float* Us,
-                 long long us_rows, int ldv, const std::vector<int>& gsrow, float* Gs, int ldg) {
+                 long long us_rows, int ldv, long long lo_shift) {
   const int nv = c->sys.n_vir, nx = c->sys.n_aux, n = c->sys.n_occ;
   if (us_rows + tc::BN >= (long long)INT32_MAX)
     return fail(c, OSVMP2_E_ARG, "U slice store exceeds the tensor-map row range");
@@ -527,8 +527,6 @@ int gproj_tensor(osvmp2_ctx* c, const std::vector<GJob>& gj, const std::vector<l
             jb.m0 = mt * tc::BM;
             jb.n0 = n0;
             jb.s = 0.0;
-            jb.x_row = gsrow[q];
-            jb.x_sstride = g.r;
             jobs.push_back(jb);
           }
         }
@@ -536,7 +534,7 @@ int gproj_tensor(osvmp2_ctx* c, const std::vector<GJob>& gj, const std::vector<l
     TRY(tmp_alloc(c, jd, jobs.size() * sizeof(tc::Job)));
     CK(cudaMemcpyAsync(jd.p, jobs.data(), jobs.size() * sizeof(tc::Job), cudaMemcpyHostToDevice, c->st));
     if (launch_gproj_tc((const float*)bs.p, (long long)nb * tc::NSL * nx, Us, us_rows, nv, ldv, (const tc::Job*)jd.p,
-                        (int)jobs.size(), Gs, ldg, c->err_d, c->st))
+                        (int)jobs.size(), lo_shift, c->err_d, c->st))
       return fail(c, OSVMP2_E_CUDA, "tensor-map encoding for the G projection failed");
     CK(cudaGetLastError());
   }
@@ -874,8 +872,14 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
     CK(cudaMemcpyAsync(c->U_d, uall.data(), uall.size() * sizeof(float*), cudaMemcpyHostToDevice, c->st));
     if (gs_rows + tc::BM >= (long long)INT32_MAX)
       return fail(c, OSVMP2_E_ARG, "G slice store exceeds the tensor-map row range");
-    Tmp ju, jkt, gsl;
+    Tmp ju, jkt, gsl, glo, jgs;
     TRY(tmp_alloc(c, ju, uj.size() * sizeof(UJob)));
+    TRY(tmp_alloc(c, glo, (gfl + 1) * sizeof(float)));   // remainders of the G pairs
+    std::vector<GSJob> gsj;
+    for (size_t q = 0; q < gj.size(); q++) gsj.push_back(GSJob{gj[q].G, gj[q].r, g_gsrow[q]});
+    TRY(tmp_alloc(c, jgs, gsj.size() * sizeof(GSJob)));
+    CK(cudaMemcpyAsync(jgs.p, gsj.data(), gsj.size() * sizeof(GSJob), cudaMemcpyHostToDevice, c->st));
+    const long long lo_shift = (long long)((float*)glo.p - gmem);
     TRY(tmp_alloc(c, jkt, ktj.size() * sizeof(tc::Job)));
     TRY(tmp_alloc(c, gsl, (size_t)gs_rows * ldg * sizeof(float)));
     CK(cudaMemcpyAsync(ju.p, uj.data(), uj.size() * sizeof(UJob), cudaMemcpyHostToDevice, c->st));
@@ -885,7 +889,8 @@ int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osv
     ph_begin(c, OSVMP2_PH_PROJECT);
     launch_ubasis(t, (const UJob*)ju.p, (int)uj.size(), n_cta, (double*)uscr.p, max_r, c->st);
     CK(cudaGetLastError());
-    TRY(gproj_tensor(c, gj, g_usrow, usmem, (long long)us_rows, ldv, g_gsrow, (float*)gsl.p, ldg));
+    TRY(gproj_tensor(c, gj, g_usrow, usmem, (long long)us_rows, ldv, lo_shift));
+    launch_gslices((const GSJob*)jgs.p, (int)gsj.size(), max_r, nx, lo_shift, (float*)gsl.p, ldg, c->st);
     ph_end(c, OSVMP2_PH_PROJECT, f_u + f_g, c->sys.B ? 8.0 * (double)gj.size() * nx * nv : 0.0);
     CK(cudaGetLastError());
     ph_begin(c, OSVMP2_PH_EXCHANGE);

@@ -12,11 +12,10 @@
 // index mu (<= 64 per tile), so the output G[mu][P] is stored with the TMEM
 // lane (aux) as the contiguous index.
 //
-// The epilogue also cuts G (hi + lo, before its rounding to FP32) into the
-// fixed-point slices of G^T along the aux index: the 32 lanes of a drain warp
-// hold 32 consecutive aux rows of one column, i.e. one k-chunk of the next
-// contraction K~_p = G_p,i G_p,j^T (Eq. osv_close_k in the orthonormal pair
-// basis), which then runs on the tensor cores with the same split-precision
+// The epilogue keeps G as a normalised FP32 pair (G, lo), and k_gslices cuts it
+// into the fixed-point slices of G^T along the aux index, the k-chunks of the
+// next contraction K~_p = G_p,i G_p,j^T (Eq. osv_close_k in the orthonormal
+// pair basis), which then runs on the tensor cores with the same split-precision
 // kernel: exact slice products and ~35 bits in K~, where FP32 products of the
 // rounded G would leave a relative error of ~1e-8 in every pair energy.
 //   Gs  [G job][slice][r][ldg]      G_p,x slices, K = n_aux innermost
@@ -63,32 +62,46 @@ void launch_bslices(const BSrc& src, const int* xs, int n_x, float* Bs, int ldv,
   note_launch(1);
 }
 
-// G[mu][P] = hi + lo (TMEM lane = aux row P, column = mu), and the slices of
-// G^T: slice s of row mu at Gs[(x_row + s x_sstride + mu) ldg + P]
-struct EpiGS {
-  static constexpr bool kWarp = true;
-  float* gs;
-  int ldg;
-  __device__ __forceinline__ void warp(const tc::Job& jb, int row, int n0, const uint32_t* h,
-                                       const uint32_t* l) const {
-    const bool ok = row < jb.m_valid;
-    const int P = jb.m0 + row;
-#pragma unroll
-    for (int u = 0; u < 16; u++) {
-      const int c = n0 + u;
-      if (c >= jb.n_valid) break;   // warp-uniform
-      const float hf = __uint_as_float(h[u]), lf = __uint_as_float(l[u]);
-      float v[tc::NSL];
-      tc::warp_fixed_slices(ok ? (double)hf + (double)lf : 0.0, v);
-      if (ok) {
-        static_cast<float*>(jb.out)[(size_t)c * jb.ld_out + row] = hf + lf;
-        const int mu = jb.n0 + c;
-#pragma unroll
-        for (int s = 0; s < tc::NSL; s++) gs[(size_t)(jb.x_row + s * jb.x_sstride + mu) * ldg + P] = v[s];
-      }
-    }
+// G[mu][P] = hi + lo (TMEM lane = aux row P, column = mu), normalised by a
+// two-sum: the leading FP32 part to G (the FP32 G of the gradient) and the
+// remainder to the same position of a second array lo_shift floats further on;
+// k_gslices cuts the pair into the slices of G^T.
+struct EpiG2 {
+  static constexpr bool kWarp = false;
+  long long lo_shift;
+  __device__ __forceinline__ void operator()(const tc::Job& jb, int r, int c, float h, float l) const {
+    float s, e;
+    tc::two_sum(h, l, s, e);
+    float* g = static_cast<float*>(jb.out) + (size_t)c * jb.ld_out + r;
+    g[0] = s;
+    g[lo_shift] = e;
   }
 };
+
+// The slices of G_p,x^T from (G, lo): one warp per (mu, 32-aux chunk), lanes along
+// the aux index; slice s of row mu at Gs[(x_row + s r + mu) ldg + P].
+__global__ void __launch_bounds__(256) k_gslices(const GSJob* __restrict__ jobs, int n_aux, long long lo_shift,
+                                                 float* __restrict__ Gs, int ldg) {
+  const GSJob jb = jobs[blockIdx.y];
+  const int nch = (n_aux + tc::CHUNK - 1) / tc::CHUNK;
+  const long long w = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (w >= (long long)jb.r * nch) return;   // warp-uniform
+  const int mu = (int)(w / nch), P = (int)(w % nch) * tc::CHUNK + (threadIdx.x & 31);
+  const float* g = jb.G + (size_t)mu * n_aux + P;
+  float v[tc::NSL];
+  tc::warp_fixed_slices(P < n_aux ? (double)g[0] + (double)g[lo_shift] : 0.0, v);
+  if (P < n_aux)
+#pragma unroll
+    for (int s2 = 0; s2 < tc::NSL; s2++) Gs[(size_t)(jb.x_row + s2 * jb.r + mu) * ldg + P] = v[s2];
+}
+
+void launch_gslices(const GSJob* jobs, int n_jobs, int max_r, int n_aux, long long lo_shift, float* Gs, int ldg,
+                    cudaStream_t st) {
+  if (!n_jobs) return;
+  const long long warps = (long long)max_r * ((n_aux + tc::CHUNK - 1) / tc::CHUNK);
+  k_gslices<<<dim3((unsigned)((warps + 7) / 8), n_jobs), 256, 0, st>>>(jobs, n_aux, lo_shift, Gs, ldg);
+  note_launch(1);
+}
 
 // out[row][col] = hi + lo (row-major)
 struct EpiRow {
@@ -135,15 +148,15 @@ bool make_slice_map(CUtensorMap* m, const float* base, int n_k, int ldk, long lo
 }
 
 int launch_gproj_tc(const float* Bs, long long a_rows, const float* Us, long long b_rows, int n_vir, int ldv,
-                    const tc::Job* jobs, int n_jobs, float* Gs, int ldg, int* err, cudaStream_t st) {
+                    const tc::Job* jobs, int n_jobs, long long lo_shift, int* err, cudaStream_t st) {
   if (!n_jobs) return 0;
-  if (cudaFuncSetAttribute(tc::k_tf32x3<EpiGS>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) !=
+  if (cudaFuncSetAttribute(tc::k_tf32x3<EpiG2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) !=
       cudaSuccess)
     return -1;
   CUtensorMap ma, mb;
   if (!make_slice_map(&ma, Bs, n_vir, ldv, a_rows, tc::BM) || !make_slice_map(&mb, Us, n_vir, ldv, b_rows, tc::BROWS))
     return -1;
-  tc::k_tf32x3<EpiGS><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_vir, err, EpiGS{Gs, ldg});
+  tc::k_tf32x3<EpiG2><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_vir, err, EpiG2{lo_shift});
   note_launch(1);
   return 0;
 }

@@ -154,10 +154,17 @@ void launch_ubasis(const Tables& t, const UJob* jobs, int n_jobs, int n_cta, dou
 // slot u, slice s, row P at Bs + ((u * tc::NSL + s) * n_aux + P) * ldv
 void launch_bslices(const BSrc& src, const int* xs, int n_x, float* Bs, int ldv, cudaStream_t st);
 // G tiles with the split-TF32 tensor-core kernel: A = Bs (rows a_rows), B = Us (rows b_rows), K = n_vir;
-// each job also writes the slices of its G^T to Gs [rows][ldg] (slice s of row mu at row
-// job.x_row + s * job.x_sstride + mu).  Returns 0, or -1 if a tensor map could not be encoded.
+// G is written as a normalised FP32 pair: the leading part at job.out, the remainder
+// lo_shift floats further on.  Returns 0, or -1 if a tensor map could not be encoded.
 int launch_gproj_tc(const float* Bs, long long a_rows, const float* Us, long long b_rows, int n_vir, int ldv,
-                    const tc::Job* jobs, int n_jobs, float* Gs, int ldg, int* err, cudaStream_t st);
+                    const tc::Job* jobs, int n_jobs, long long lo_shift, int* err, cudaStream_t st);
+// The slices of G^T from the pair (G, lo): slice s of row mu at Gs[(x_row + s r + mu) ldg + P].
+struct GSJob {
+  const float* G;      // [r][n_aux], remainder at G + lo_shift
+  int r, x_row;
+};
+void launch_gslices(const GSJob* jobs, int n_jobs, int max_r, int n_aux, long long lo_shift, float* Gs, int ldg,
+                    cudaStream_t st);
 // K~ = G_i G_j^T tiles from the slices in Gs (rows in total, K = n_aux), FP64 row-major output.
 int launch_kt_tc(const float* Gs, long long rows, int n_aux, int ldg, const tc::Job* jobs, int n_jobs, int* err,
                  cudaStream_t st);
