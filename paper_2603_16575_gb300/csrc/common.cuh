@@ -138,6 +138,50 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   e = (a - (s - bb)) + (b - bb);
 }
 
+// a + x1 y1 + x2 y2 in double-float arithmetic, the products' error terms gathered
+// before one renormalisation (the rank-2 update of the tridiagonalisation sweep).
+__device__ __forceinline__ dfl df_fma2(dfl x1, dfl y1, dfl x2, dfl y2, dfl a) {
+  const float p1 = x1.h * y1.h;
+  float e1 = fmaf(x1.h, y1.h, -p1);
+  e1 = fmaf(x1.h, y1.l, e1);
+  e1 = fmaf(x1.l, y1.h, e1);
+  const float p2 = x2.h * y2.h;
+  float e2 = fmaf(x2.h, y2.h, -p2);
+  e2 = fmaf(x2.h, y2.l, e2);
+  e2 = fmaf(x2.l, y2.h, e2);
+  float s1, t1, s2, t2;
+  two_sum_f(a.h, p1, s1, t1);
+  two_sum_f(s1, p2, s2, t2);
+  return df_fast2(s2, ((a.l + e1) + e2) + (t1 + t2));
+}
+// (h, l) += x y with (h, l) kept unnormalised: the leading sum by an exact two-sum,
+// the error terms gathered in l (renormalised once by df_norm).
+__device__ __forceinline__ void df_acc(float& h, float& l, dfl x, dfl y) {
+  const float p = x.h * y.h;
+  float e = fmaf(x.h, y.h, -p);
+  e = fmaf(x.h, y.l, e);
+  e = fmaf(x.l, y.h, e);
+  float s, t;
+  two_sum_f(h, p, s, t);
+  h = s;
+  l += e + t;
+}
+__device__ __forceinline__ dfl df_norm(float h, float l) {
+  float s, e;
+  two_sum_f(h, l, s, e);
+  return dfl{s, e};
+}
+// a + x y in double-float arithmetic with one renormalisation (df_fma renormalises twice).
+__device__ __forceinline__ dfl df_fma1(dfl x, dfl y, dfl a) {
+  const float p = x.h * y.h;
+  float e = fmaf(x.h, y.h, -p);
+  e = fmaf(x.h, y.l, e);
+  e = fmaf(x.l, y.h, e);
+  float s, t;
+  two_sum_f(a.h, p, s, t);
+  return df_fast2(s, (a.l + e) + t);
+}
+
 // FP32 tile of (16 R) x (16 R) outputs, R x R per thread (thread (ty, tx) owns
 // rows m0 + ty + 16 i and columns n0 + tx + 16 j), accumulated in FP32 over
 // the whole K: for the short contractions (K ~ a pair order) of the coupling
@@ -449,7 +493,7 @@ __device__ void cta_gemm_df_r(int M, int N, int K, double alpha, const VA& A, co
 #pragma unroll
           for (int i = 0; i < R; i++)
 #pragma unroll
-            for (int j = 0; j < R; j++) acc[i][j] = df_fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < R; j++) df_acc(acc[i][j].h, acc[i][j].l, a[i], b[j]);   // unnormalised
         }
         __syncthreads();
       }

@@ -377,40 +377,6 @@ __device__ inline dfl cta_sum_df(dfl v, float* red) {
   return dfl{red[64], red[65]};
 }
 
-// a + x1 y1 + x2 y2 in double-float arithmetic, the products' error terms gathered
-// before one renormalisation (the rank-2 update of the tridiagonalisation sweep).
-__device__ __forceinline__ dfl df_fma2(dfl x1, dfl y1, dfl x2, dfl y2, dfl a) {
-  const float p1 = x1.h * y1.h;
-  float e1 = fmaf(x1.h, y1.h, -p1);
-  e1 = fmaf(x1.h, y1.l, e1);
-  e1 = fmaf(x1.l, y1.h, e1);
-  const float p2 = x2.h * y2.h;
-  float e2 = fmaf(x2.h, y2.h, -p2);
-  e2 = fmaf(x2.h, y2.l, e2);
-  e2 = fmaf(x2.l, y2.h, e2);
-  float s1, t1, s2, t2;
-  two_sum_f(a.h, p1, s1, t1);
-  two_sum_f(s1, p2, s2, t2);
-  return df_fast2(s2, ((a.l + e1) + e2) + (t1 + t2));
-}
-// (h, l) += x y with (h, l) kept unnormalised: the leading sum by an exact two-sum,
-// the error terms gathered in l (renormalised once by df_norm).
-__device__ __forceinline__ void df_acc(float& h, float& l, dfl x, dfl y) {
-  const float p = x.h * y.h;
-  float e = fmaf(x.h, y.h, -p);
-  e = fmaf(x.h, y.l, e);
-  e = fmaf(x.l, y.h, e);
-  float s, t;
-  two_sum_f(h, p, s, t);
-  h = s;
-  l += e + t;
-}
-__device__ __forceinline__ dfl df_norm(float h, float l) {
-  float s, e;
-  two_sum_f(h, l, s, e);
-  return dfl{s, e};
-}
-
 // cta_tridiag_sym in double-float arithmetic, for the mixed-form OSV build
 // (whose T_ii carries ~35 significant bits, so the ~48 bits here do not limit
 // it): the same fused sweep over the lower triangle, with A held as (hi, lo)

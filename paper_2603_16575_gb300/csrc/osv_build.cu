@@ -325,19 +325,23 @@ __global__ void __launch_bounds__(EB_WARPS * 32) k_eig_back_df(const double* T, 
     const double tk = tau[kk];
     if (tk == 0.0) continue;
     const dfl* vr = Ad + (size_t)kk * n;   // v at columns kk+1 .. n-1 of row kk
-    dfl s{0.f, 0.f};
+    const int j0 = (kk + 1) >> 5;          // register blocks below j0 hold no row > kk
+    float sh = 0.f, sl = 0.f;
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
+      if (j < j0) continue;   // warp-uniform
       const int r = 32 * j + lane;
-      if (r > kk && r < n) s = df_fma(vr[r], xr[j], s);
+      if (r > kk && r < n) df_acc(sh, sl, vr[r], xr[j]);
     }
+    dfl s = df_norm(sh, sl);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s = df_add(s, df_shfl_xor(s, o));
     const dfl ns = df_neg(df_mul(s, df_from(tk)));
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
+      if (j < j0) continue;
       const int r = 32 * j + lane;
-      if (r > kk && r < n) xr[j] = df_fma(ns, vr[r], xr[j]);
+      if (r > kk && r < n) xr[j] = df_fma1(ns, vr[r], xr[j]);
     }
   }
 #pragma unroll
