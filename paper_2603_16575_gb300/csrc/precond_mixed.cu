@@ -249,8 +249,8 @@ __global__ void __launch_bounds__(NT, 2) k_pm_fprime(Tables t, const PJob* __res
     // F Y: the first ni columns of Y are unit vectors
     for (int idx = threadIdx.x; idx < m * ni; idx += NT)
       FY[(size_t)(idx / ni) * r + idx % ni] = Fv.get(idx / ni, idx % ni);
-    cta_gemm_a(m, nk, m, 1.0, Fv, dense_view(pp.Y + ni, m, nk, r), 0.0, FY + ni, r, sm);
-    cta_gemm_a(r, r, m, 1.0, transpose(dense_view(pp.Y, m, r, r)), dense_view(FY, m, r, r), 0.0, pp.Fp, r, sm);
+    cta_gemm_df(m, nk, m, 1.0, Fv, dense_view(pp.Y + ni, m, nk, r), 0.0, FY + ni, r, sm);
+    cta_gemm_df(r, r, m, 1.0, transpose(dense_view(pp.Y, m, r, r)), dense_view(FY, m, r, r), 0.0, pp.Fp, r, sm);
   }
 }
 

@@ -5,7 +5,7 @@
 // rounding error by |X|^2.  The columns of U_p are orthonormal in the full
 // virtual space (X^T S X = 1), so every low-precision product is formed with
 // U_p directly:
-//   U_p    = P_p X_p                           FP64 products, stored FP32 [n_vir][r]
+//   U_p    = P_p X_p                           double-float products, stored FP32 [n_vir][r]
 //                                              and as four TF32 slices of U_p^T
 //   G_p,x  = U_p^T B_x   (x = i, j)            split-precision tensor-core products
 //                                              (gproj_tc.cu), stored FP32 [r][n_aux]
@@ -23,7 +23,8 @@
 
 namespace osv {
 
-// U_p = [Q_i Q_j] X_p in FP64, formed transposed (U_p^T [r][n_vir] in the
+// U_p = [Q_i Q_j] X_p in double-float arithmetic (~48 bits, above the ~36 bits
+// its slices carry), formed transposed (U_p^T [r][n_vir] in the
 // per-CTA scratch, so that the slices of U_p^T are cut from contiguous rows),
 // written as FP32 [n_vir][r] through a shared-memory transpose and as the TF32
 // slices of U_p^T.  One CTA per pair (grid-stride).
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(NT) k_ubasis(Tables t, const UJob* __restrict_
     P.rows = nv; P.cols = m; P.rs = nv; P.cs = ni;
     P.b[0][0] = P.b[1][0] = Blk{t.Q[jb.i], ni, 0};
     P.b[0][1] = P.b[1][1] = Blk{nj ? t.Q[jb.j] : t.Q[jb.i], nj ? nj : ni, 0};
-    cta_gemm_a(r, nv, m, 1.0, transpose(dense_view(t.X[pid], m, r, m)), transpose(P), 0.0, Wt, nv, sm);
+    cta_gemm_df(r, nv, m, 1.0, transpose(dense_view(t.X[pid], m, r, m)), transpose(P), 0.0, Wt, nv, sm);
     const size_t sl = (size_t)r * jb.ldv;
     const int nch = (nv + tc::CHUNK - 1) / tc::CHUNK;
     // slices of U^T: one (mu, 32-virtual chunk) per warp step, lanes along the virtuals
