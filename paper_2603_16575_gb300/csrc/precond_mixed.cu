@@ -220,9 +220,10 @@ __global__ void __launch_bounds__(NT, 3) k_pm_overlap_c(Tables t, double tau_s, 
     }
     __syncthreads();
     const View Zv = dense_view(Y + (size_t)ni * r + ni, nj, nk, r);
-    cta_gemm(ni, nk, nj, -1.0, Mv, Zv, 0.0, Y + ni, r, gsm);                                     // -M Z
-    cta_gemm(nj, nk, nj, 1.0, dense_view(C0, nj, nj, nj), Zv, 0.0, CZ, nk, gsm);                // C Z
-    cta_gemm(nk, nk, nj, 1.0, transpose(Zv), dense_view(CZ, nj, nk, nk), 0.0, pp.ZCZ, nk, gsm);  // Z^T C Z
+    // (double-float products; C itself, with its cancellation, is formed in FP64 above)
+    cta_gemm_df_r<4>(ni, nk, nj, -1.0, Mv, Zv, 0.0, Y + ni, r, gsm);                                     // -M Z
+    cta_gemm_df_r<4>(nj, nk, nj, 1.0, dense_view(C0, nj, nj, nj), Zv, 0.0, CZ, nk, gsm);                // C Z
+    cta_gemm_df_r<4>(nk, nk, nj, 1.0, transpose(Zv), dense_view(CZ, nj, nk, nk), 0.0, pp.ZCZ, nk, gsm);  // Z^T C Z
     if (threadIdx.x == 0) *jb.r = r;
   }
 }
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(NT, 2) k_pm_final(Tables t, const PJob* __rest
     const PmPair pp = pm_pair(slots, off, jid, m);
     const View Wv = dense_view(pp.W, r, r, r);
     if (i != j) {
-      cta_gemm_a(m, r, r, 1.0, dense_view(pp.Y, m, r, r), Wv, 0.0, jb.X, m, sm);        // X = Y W (FP64)
+      cta_gemm_df(m, r, r, 1.0, dense_view(pp.Y, m, r, r), Wv, 0.0, jb.X, m, sm);       // X = Y W
       for (int idx = threadIdx.x; idx < ni * r; idx += NT) T1[idx] = pp.W[idx];        // (Y^T S Y) W, top rows
       cta_gemm_df(nk, r, nk, 1.0, dense_view(pp.ZCZ, nk, nk, nk), dense_view(pp.W + (size_t)ni * r, nk, r, r), 0.0,
                T1 + (size_t)ni * r, r, sm);
