@@ -183,7 +183,7 @@ void launch_ktilde(const Tables& t, const KtJob* jobs, int n_jobs, double* scrat
 // per CTA: Y, 1/D (6 + 6 FP64), C as (hi, lo) (12 FP32) + Y32 (6 FP32) + 3 work (FP32) + G0 (6 max_m FP32)
 __host__ __device__ inline size_t frag_mixed_scratch_doubles(int max_m) {
   const size_t M2 = (size_t)max_m * max_m;
-  return 18 * M2 + (15 * M2 + 6 * (size_t)max_m + 1) / 2 + 64;
+  return 24 * M2 + (15 * M2 + 6 * (size_t)max_m + 1) / 2 + 64;
 }
 // Pair-couple overlaps Sigma_(lo,hi) = U_lo^T U_hi (pair ids lo < hi) of one MBE
 // call, stored [r_lo][r_hi] at base + pos[id]; the ids of couples (lo, *) are

@@ -106,18 +106,22 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
   __shared__ int sig_ld[MAX_TERMS], sig_tr[MAX_TERMS];
   const size_t M2 = (size_t)max_m * max_m;
   double* base = scratch + (size_t)blockIdx.x * frag_mixed_scratch_doubles(max_m);
-  double* Y64[6];
+  // the amplitudes, 1/D and K~ as double-float pairs: the update and the energy
+  // run on the FP32 pipes at ~48 bits
+  dfl* Yd[6];
   float* Chi[6];            // C_p as a compensated FP32 pair (Chi + Clo)
   float* Clo[6];
-  double* invD[6];
+  dfl* invD[6];
+  dfl* Ktd[6];
   float* Y32[6];
   for (int u = 0; u < 6; u++) {
-    Y64[u] = base + u * M2;
+    Yd[u] = reinterpret_cast<dfl*>(base + u * M2);
     Chi[u] = reinterpret_cast<float*>(base + 6 * M2) + (size_t)u * M2;
     Clo[u] = reinterpret_cast<float*>(base + 6 * M2) + (size_t)(6 + u) * M2;
-    invD[u] = base + (12 + u) * M2;
+    invD[u] = reinterpret_cast<dfl*>(base + (12 + u) * M2);
+    Ktd[u] = reinterpret_cast<dfl*>(base + (18 + u) * M2);
   }
-  float* fb = reinterpret_cast<float*>(base + 18 * M2);
+  float* fb = reinterpret_cast<float*>(base + 24 * M2);
   for (int u = 0; u < 6; u++) Y32[u] = fb + u * M2;
   float* W32 = fb + 6 * M2;
   float* A1 = fb + 7 * M2;
@@ -207,11 +211,13 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
       const int rp = pr[p];
       const double fij = f[orbs[pa[p]] * n + orbs[pa[p]]] + f[orbs[pb[p]] * n + orbs[pb[p]]];
       const double* et = t.et[pid[p]];
+      const double* Kt = t.Kt[pid[p]];
       for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
-        Y64[p][idx] = 0.0;
+        Yd[p][idx] = dfl{0.f, 0.f};
         Y32[p][idx] = 0.f;
         Pp[p][idx] = 0.f;
-        invD[p][idx] = 1.0 / (fij - et[idx / rp] - et[idx % rp]);   // update denominators, once per fragment
+        invD[p][idx] = df_from(1.0 / (fij - et[idx / rp] - et[idx % rp]));   // update denominators, once per fragment
+        Ktd[p][idx] = df_from(Kt[idx]);
       }
       for (int a = threadIdx.x; a < rp; a += NT) G0[p][a] = (float)(et[a] - 0.5 * fij);
     }
@@ -262,26 +268,31 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
           cta_gemm_f32s<float>(rp, rp, rp, 1.0, ViewF{A2, rp, 0}, ViewF{Gh, rp, 0}, 1.0, Pp[p], rp, fsm, o.tiles);
         }
       }
-      // Y_p <- (K~_p + C_p) / D_p in FP64; energy <K~_p, 2Y_p - Y_p^T>
+      // Y_p <- (K~_p + C_p) / D_p and the energy <K~_p, 2Y_p - Y_p^T>, double-float
       um = 0.0;
       e = 0.0;
       for (int p = 0; p < np; p++) {
         const int rp = pr[p];
-        const double* Kt = t.Kt[pid[p]];
-        double du = 0.0;
+        const dfl* Kd = Ktd[p];
+        dfl* Y = Yd[p];
+        float du = 0.f;
         for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
-          const double y = (Kt[idx] + ((double)Chi[p][idx] + (double)(Clo[p][idx] + Pp[p][idx]))) * invD[p][idx];
-          du = fmax(du, (double)fabsf((float)(y - Y64[p][idx])));
-          Y64[p][idx] = y;
+          float ch, cl;
+          two_sum_f(Chi[p][idx], Clo[p][idx] + Pp[p][idx], ch, cl);
+          const dfl y = df_mul(df_add(Kd[idx], dfl{ch, cl}), invD[p][idx]);
+          const dfl yo = Y[idx];
+          du = fmaxf(du, fabsf((y.h - yo.h) + (y.l - yo.l)));
+          Y[idx] = y;
         }
-        um = fmax(um, cta_max(du, red));
-        double s = 0.0;
+        um = fmax(um, cta_max((double)du, red));
+        float sh = 0.f, sl = 0.f;
         for (int idx = threadIdx.x; idx < rp * rp; idx += NT) {
           const int r = idx / rp, c = idx % rp;
-          s += Kt[idx] * (2.0 * Y64[p][idx] - Y64[p][(size_t)c * rp + r]);
-          Y32[p][idx] = (float)Y64[p][idx];
+          const dfl y = Y[idx];
+          df_acc(sh, sl, Kd[idx], df_add(df_add(y, y), df_neg(Y[(size_t)c * rp + r])));
+          Y32[p][idx] = y.h;
         }
-        s = cta_sum(s, red);
+        const double s = cta_sum((double)sh + (double)sl, red);
         e += (pa[p] == pb[p]) ? s : 2.0 * s;
       }
       if (!isfinite(e) || !isfinite(um)) { status = ERR_NONFINITE; iters = it; break; }
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
       double* dst = Tstore + Toff[fid];
       for (int p = 0; p < np; p++) {
         const int rp = pr[p];
-        for (int idx = threadIdx.x; idx < rp * rp; idx += NT) dst[idx] = Y64[p][idx];
+        for (int idx = threadIdx.x; idx < rp * rp; idx += NT) dst[idx] = df_to(Yd[p][idx]);
         dst += (size_t)pm[p] * pm[p];
       }
     }
