@@ -1128,4 +1128,105 @@ __device__ inline double tri_solve_lanes(int n, double sc, const double* ui, con
   return nn;
 }
 
+// 1/a in double-float: the rounded FP32 reciprocal refined by one Newton step
+// (the residual 1 - a_h r is exact in an FMA), ~47 bits.
+__device__ __forceinline__ dfl df_rcp(dfl a) {
+  const float r = 1.0f / a.h;
+  float e = fmaf(-a.h, r, 1.0f);
+  e = fmaf(-a.l, r, e);
+  return df_fast2(r, r * e);
+}
+// tri_factor_lanes in double-float arithmetic (the mixed-form OSV build): d and e
+// as (hi, lo) pairs, the factors stored as pairs in the same lane-interleaved
+// slots, so the recurrence runs on the FP32 pipes.
+__device__ inline void tri_factor_lanes_df(const dfl* d, const dfl* e, int n, dfl lam, float small, dfl* ui,
+                                           dfl* u1, dfl* u2, dfl* mul, int* piv) {
+  const dfl z{0.f, 0.f}, nl = df_neg(lam);
+  dfl wa = df_add(d[0], nl), wb = (n > 1) ? e[0] : z;
+  for (int i = 0; i + 1 < n; i++) {
+    const dfl c = e[i], a1 = df_add(d[i + 1], nl), b1 = (i + 2 < n) ? e[i + 1] : z;
+    const bool keep = fabsf(wa.h) >= fabsf(c.h);
+    const dfl a = keep ? (wa.h == 0.f ? dfl{small, 0.f} : wa) : c;
+    const dfl inv = df_rcp(a);
+    const dfl m = df_mul(keep ? c : wa, inv);
+    ui[32 * i] = inv;
+    u1[32 * i] = keep ? wb : a1;
+    u2[32 * i] = keep ? z : b1;
+    mul[32 * i] = m;
+    piv[32 * i] = keep ? 0 : 1;
+    const dfl nm = df_neg(m);
+    const dfl na = keep ? df_fma1(nm, wb, a1) : df_fma1(nm, a1, wb);
+    wb = keep ? b1 : df_mul(nm, b1);
+    wa = na;
+  }
+  ui[32 * (n - 1)] = df_rcp(wa.h == 0.f ? dfl{small, 0.f} : wa);
+  u1[32 * (n - 1)] = z;
+  u2[32 * (n - 1)] = z;
+}
+// tri_solve_lanes in double-float: y <- (T - lam I)^{-1} (sc y), returning max |x|
+// (the next solve's scale; the vectors are normalised in FP64 afterwards).
+__device__ inline float tri_solve_lanes_df(int n, float sc, const dfl* ui, const dfl* u1, const dfl* u2,
+                                           const dfl* mul, const int* piv, dfl* y) {
+  constexpr int U = 4;
+  const dfl s{sc, 0.f};
+  dfl cur = df_mul(y[0], s);
+  int i = 0;
+  for (; i + U < n; i += U) {
+    dfl nx[U], mu[U];
+    int pv[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      nx[u] = y[32 * (i + 1 + u)];
+      mu[u] = mul[32 * (i + u)];
+      pv[u] = piv[32 * (i + u)];
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const dfl v = df_mul(nx[u], s);
+      const bool sw = pv[u] != 0;
+      const dfl lo = sw ? v : cur, hi = sw ? cur : v;
+      y[32 * (i + u)] = lo;
+      cur = df_fma1(df_neg(mu[u]), lo, hi);
+    }
+  }
+  for (; i + 1 < n; i++) {
+    const dfl v = df_mul(y[32 * (i + 1)], s);
+    const bool sw = piv[32 * i] != 0;
+    const dfl lo = sw ? v : cur, hi = sw ? cur : v;
+    y[32 * i] = lo;
+    cur = df_fma1(df_neg(mul[32 * i]), lo, hi);
+  }
+  y[32 * (n - 1)] = cur;
+  const dfl z{0.f, 0.f};
+  dfl y1 = z, y2 = z;   // x[i + 1], x[i + 2]
+  float amax = 0.f;
+  i = n - 1;
+  for (; i - U + 1 >= 0; i -= U) {
+    dfl yv[U], a1[U], a2[U], iv[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      yv[u] = y[32 * (i - u)];
+      a1[u] = u1[32 * (i - u)];
+      a2[u] = u2[32 * (i - u)];
+      iv[u] = ui[32 * (i - u)];
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const dfl x = df_mul(df_fma2(df_neg(a1[u]), y1, df_neg(a2[u]), y2, yv[u]), iv[u]);
+      y[32 * (i - u)] = x;
+      amax = fmaxf(amax, fabsf(x.h));
+      y2 = y1;
+      y1 = x;
+    }
+  }
+  for (; i >= 0; i--) {
+    const dfl x = df_mul(df_fma2(df_neg(u1[32 * i]), y1, df_neg(u2[32 * i]), y2, y[32 * i]), ui[32 * i]);
+    y[32 * i] = x;
+    amax = fmaxf(amax, fabsf(x.h));
+    y2 = y1;
+    y1 = x;
+  }
+  return amax;
+}
+
 }  // namespace osv

@@ -61,10 +61,13 @@ int launch_tii_tc(const float* Bt, long long rows, int n_aux, int ldx, const tc:
 // at most kmax per orbital: V [nb][kmax][nv] (eigenvector-major), w [nb][kmax], k [nb], err |= ERR_*.
 // d, e, tau (3 nv) + Z (nv*nv, full path) or the tridiagonalisation's partial sums,
 // then 4 groups x 176 nv of lane-batched inverse iteration (top-k path)
+// Per-orbital scratch of k_eig_osv: d, e, tau; the work room (Z, partial sums,
+// inverse-iteration factors); the kept vectors as double-float pairs (mixed form).
+__host__ __device__ inline size_t eig_osv_work_doubles(int nv) {
+  return (size_t)nv * nv > (size_t)4 * 176 * nv ? (size_t)nv * nv : (size_t)4 * 176 * nv;
+}
 __host__ __device__ inline size_t eig_osv_scratch_doubles(int nv, int kmax) {
-  (void)kmax;
-  const size_t work = (size_t)nv * nv > (size_t)4 * 176 * nv ? (size_t)nv * nv : (size_t)4 * 176 * nv;
-  return (size_t)3 * nv + work + 64;
+  return (size_t)3 * nv + eig_osv_work_doubles(nv) + (size_t)kmax * nv + 64;
 }
 // dfl_tridiag: the top-k path tridiagonalises in double-float arithmetic (the
 // mixed-form OSV build, whose T_ii is a split-precision product).

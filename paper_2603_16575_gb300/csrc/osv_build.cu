@@ -234,8 +234,57 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   // scr + 3n (the tridiagonalisation's partial sums are no longer needed).
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double small = 2.220446049250313e-16 * fmax(s_norm, 1e-300);
+  // The mixed-form build solves in double-float arithmetic (FP32 pipes; its
+  // tridiagonal carries ~48 bits): d and e (and the Gram-Schmidt dots) as pairs in
+  // the tridiagonalisation's tile room, when it holds them and the scales stay
+  // well inside FP32 range.
+  const bool inv_df = dfl_tridiag && ntw >= 2 && 2 * n + k <= ntw * 32 * 33 && s_norm > 1e-12 && s_norm < 1e12;
+  dfl* ddf = reinterpret_cast<dfl*>(sm + 4 * n + 64);
+  dfl* edf = ddf + n;
+  dfl* Vd = reinterpret_cast<dfl*>(scr + 3 * n + eig_osv_work_doubles(n));   // kept vectors, pairs [k][n]
+  dfl* gsd = edf + n;                                                          // -dots of one Gram-Schmidt step [k]
+  if (inv_df) {
+    for (int t = threadIdx.x; t < n; t += NT_EIG) {
+      ddf[t] = df_from(d[t]);
+      edf[t] = (t + 1 < n) ? df_from(e[t]) : dfl{0.f, 0.f};
+    }
+    __syncthreads();
+  }
   for (int pass = 0; pass < 2; pass++) {
-    if (warp < INV_GROUPS) {
+    if (inv_df && warp < INV_GROUPS) {
+      double* base = scr + 3 * n + (size_t)warp * 176 * n;
+      dfl* ui = reinterpret_cast<dfl*>(base) + lane;
+      dfl* u1 = reinterpret_cast<dfl*>(base + 32 * (size_t)n) + lane;
+      dfl* u2 = reinterpret_cast<dfl*>(base + 64 * (size_t)n) + lane;
+      dfl* mul = reinterpret_cast<dfl*>(base + 96 * (size_t)n) + lane;
+      dfl* y = reinterpret_cast<dfl*>(base + 128 * (size_t)n) + lane;
+      int* piv = reinterpret_cast<int*>(base + 160 * (size_t)n) + lane;
+      for (int g = warp; 32 * g < k; g += INV_GROUPS) {
+        const int t = 32 * g + lane;
+        if (t < k) {
+          if (pass == 0 || k > 32 * INV_GROUPS)
+            tri_factor_lanes_df(ddf, edf, n, df_from(w[t]), (float)small, ui, u1, u2, mul, piv);
+          if (pass == 0) {
+#pragma unroll 4
+            for (int r = 0; r < n; r++) {
+              const uint64_t h = draw(0x5eedull + (uint64_t)t, (uint64_t)r);
+              y[32 * r] = dfl{(float)(uint32_t)(h >> 40) * 0x1p-24f - 0.5f, 0.f};
+            }
+          } else {
+#pragma unroll 4
+            for (int r = 0; r < n; r++) y[32 * r] = Vd[(size_t)t * n + r];
+          }
+          float sc = 1.f;   // scale of the previous solve, applied on the next read
+          for (int it = 0; it < 2 - pass; it++) {
+            const float am = tri_solve_lanes_df(n, sc, ui, u1, u2, mul, piv, y);
+            sc = am > 0.f ? 1.f / am : 0.f;
+          }
+          const dfl s{sc, 0.f};
+#pragma unroll 4
+          for (int r = 0; r < n; r++) Vd[(size_t)t * n + r] = df_mul(y[32 * r], s);
+        }
+      }
+    } else if (warp < INV_GROUPS) {
       double* base = scr + 3 * n + (size_t)warp * 176 * n;
       double* ui = base + lane;
       double* u1 = base + 32 * (size_t)n + lane;
@@ -269,7 +318,63 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
       }
     }
     __syncthreads();
-    for (int c = warp; c < s_nclu; c += NT_EIG / 32) {   // Gram-Schmidt within clusters
+    if (inv_df) {
+      // Mixed form: the clusters one after another with the whole CTA, each vector
+      // orthogonalised against the earlier ones of its cluster by classical
+      // Gram-Schmidt applied twice (the dots one warp each, the update one thread
+      // per row), so the loads of a cluster's vectors overlap instead of one warp
+      // waiting on each in turn.  Double-float arithmetic on the pairs in Vd.
+      float* redf = reinterpret_cast<float*>(red);
+      for (int c = 0; c < s_nclu; c++) {
+        const int t0 = clu[c], t1 = clu[c + 1];
+        for (int t = t0; t < t1; t++) {
+          dfl* Vt = Vd + (size_t)t * n;
+          for (int rep = 0; rep < 2 && t > t0; rep++) {
+            for (int q = t0 + warp; q < t; q += NT_EIG / 32) {
+              const dfl* Vq = Vd + (size_t)q * n;
+              float dh = 0.f, dl = 0.f;
+              for (int r0 = lane; r0 < n; r0 += 32 * 4) {
+                dfl x[4], y2[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                  const int r = r0 + 32 * u;
+                  x[u] = r < n ? Vt[r] : dfl{0.f, 0.f};
+                  y2[u] = r < n ? Vq[r] : dfl{0.f, 0.f};
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) df_acc(dh, dl, x[u], y2[u]);
+              }
+              dfl dot = df_norm(dh, dl);
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) dot = df_add(dot, df_shfl_xor(dot, o));
+              if (lane == 0) gsd[q - t0] = df_neg(dot);
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < n; r += NT_EIG) {
+              dfl acc = Vt[r];
+              int q = t0;
+              for (; q + 4 <= t; q += 4) {
+                dfl vq[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) vq[u] = Vd[(size_t)(q + u) * n + r];
+#pragma unroll
+                for (int u = 0; u < 4; u++) acc = df_fma1(gsd[q + u - t0], vq[u], acc);
+              }
+              for (; q < t; q++) acc = df_fma1(gsd[q - t0], Vd[(size_t)q * n + r], acc);
+              Vt[r] = acc;
+            }
+            __syncthreads();
+          }
+          float nh = 0.f, nl = 0.f;
+          for (int r = threadIdx.x; r < n; r += NT_EIG) df_acc(nh, nl, Vt[r], Vt[r]);
+          const double nnd = df_to(cta_sum_df(df_norm(nh, nl), redf));
+          const dfl sc = df_from(nnd > 0.0 ? 1.0 / sqrt(nnd) : 0.0);
+          for (int r = threadIdx.x; r < n; r += NT_EIG) Vt[r] = df_mul(Vt[r], sc);
+          __syncthreads();
+        }
+      }
+    }
+    for (int c = warp; !inv_df && c < s_nclu; c += NT_EIG / 32) {   // Gram-Schmidt within clusters
       const int t0 = clu[c], t1 = clu[c + 1];
       for (int t = t0; t < t1; t++) {
         double* Vt = V + (size_t)t * n;
@@ -289,6 +394,10 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
         __syncwarp();
       }
     }
+    __syncthreads();
+  }
+  if (inv_df) {   // the kept vectors to FP64
+    for (size_t idx = threadIdx.x; idx < (size_t)k * n; idx += NT_EIG) V[idx] = df_to(Vd[idx]);
     __syncthreads();
   }
   // the back-transformation to the virtual basis is k_eig_back
