@@ -156,7 +156,7 @@ int launch_gproj_tc(const float* Bs, long long a_rows, const float* Us, long lon
   CUtensorMap ma, mb;
   if (!make_slice_map(&ma, Bs, n_vir, ldv, a_rows, tc::BM) || !make_slice_map(&mb, Us, n_vir, ldv, b_rows, tc::BROWS))
     return -1;
-  tc::k_tf32x3<EpiG2><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_vir, err, EpiG2{lo_shift});
+  tc::k_tf32x3<EpiG2><<<tc::persistent_grid(n_jobs), tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_jobs, n_vir, err, EpiG2{lo_shift});
   note_launch(1);
   return 0;
 }
@@ -170,7 +170,7 @@ int launch_kt_tc(const float* Gs, long long rows, int n_aux, int ldg, const tc::
   CUtensorMap ma, mb;
   if (!make_slice_map(&ma, Gs, n_aux, ldg, rows, tc::BM) || !make_slice_map(&mb, Gs, n_aux, ldg, rows, tc::BROWS))
     return -1;
-  tc::k_tf32x3<EpiRow64><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_aux, err, EpiRow64{});
+  tc::k_tf32x3<EpiRow64><<<tc::persistent_grid(n_jobs), tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_jobs, n_aux, err, EpiRow64{});
   note_launch(1);
   return 0;
 }
@@ -184,7 +184,7 @@ int launch_rows_tc(const float* A, long long a_rows, const float* B, long long b
   CUtensorMap ma, mb;
   if (!make_slice_map(&ma, A, n_vir, ldv, a_rows, tc::BM) || !make_slice_map(&mb, B, n_vir, ldv, b_rows, tc::BROWS))
     return -1;
-  tc::k_tf32x3<EpiRow><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_vir, err, EpiRow{});
+  tc::k_tf32x3<EpiRow><<<tc::persistent_grid(n_jobs), tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_jobs, n_vir, err, EpiRow{});
   note_launch(1);
   return 0;
 }

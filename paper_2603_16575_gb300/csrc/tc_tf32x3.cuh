@@ -18,7 +18,8 @@
 // fold the three level sums into a TMEM-resident (hi, lo) FP32 pair with
 // error-free two-sums.
 //
-// One CTA per output tile of 128 rows (TMEM lanes) x up to 64 columns:
+// Persistent CTAs (one per SM) over output tiles of 128 rows (TMEM lanes) x up
+// to 64 columns:
 //   warp 0     TMA producer: the eight 128B-swizzled K-major slice tiles of a
 //              k-chunk per stage, two stages
 //   warp 1     TMEM allocation and the single MMA-issuing thread (10 MMAs per
@@ -113,16 +114,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 template <class Epi>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-             const Job* __restrict__ jobs, int K, int* err, Epi epi) {
+             const Job* __restrict__ jobs, int n_jobs, int K, int* err, Epi epi) {
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accf[2], bar_acce[2];
   __shared__ uint32_t s_tmem;
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
   const uint32_t sbase = su32(sm);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Job jb = jobs[blockIdx.x];
-  const int npad = (jb.n_valid + 15) & ~15;
-  const int nbox = (jb.n_valid + BROWS - 1) / BROWS;
   const int nch = (K + BK - 1) / BK;
 
   if (warp == 1) {
@@ -148,107 +146,133 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = s_tmem;
   bool ok = true;
+  // Persistent: the CTA takes tiles blockIdx.x, + gridDim.x, ...; g counts the
+  // k-chunks this CTA has passed through the pipeline, so the stage and
+  // accumulator-buffer phases carry over from one tile to the next and the MMAs
+  // of a tile overlap the epilogue of the one before.  A role leaves its loops at
+  // its first timed-out wait.
 
   if (warp == 0) {
     if (lane == 0) {                                             // ---- TMA producer
-      const uint32_t bytes = NSL * (A_TILE + nbox * BROWS * BK * 4);
-      for (int c = 0; c < nch; c++) {
-        const int s = c & 1;
-        if (c >= NSTAGE) ok &= mbar_wait(su32(&bar_empty[s]), ((c - NSTAGE) >> 1) & 1);
-        const uint32_t fb = su32(&bar_full[s]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes) : "memory");
-        const uint32_t st = sbase + s * STAGE;
-        for (int sl = 0; sl < NSL; sl++)
-          tma_load_2d(st + sl * A_TILE, &tmA, fb, c * BK, jb.a_row + sl * jb.a_sstride);
-        for (int sl = 0; sl < NSL; sl++)
-          for (int bx = 0; bx < nbox; bx++)
-            tma_load_2d(st + NSL * A_TILE + sl * B_TILE + bx * BROWS * BK * 4, &tmB, fb, c * BK,
-                        jb.b_row + sl * jb.b_sstride + bx * BROWS);
+      long long g = 0;
+      for (int tile = blockIdx.x; ok && tile < n_jobs; tile += gridDim.x) {
+        const Job jb = jobs[tile];
+        const int nbox = (jb.n_valid + BROWS - 1) / BROWS;
+        const uint32_t bytes = NSL * (A_TILE + nbox * BROWS * BK * 4);
+        for (int c = 0; c < nch; c++, g++) {
+          const int s = (int)(g & 1);
+          if (g >= NSTAGE) ok &= mbar_wait(su32(&bar_empty[s]), (uint32_t)(((g - NSTAGE) >> 1) & 1));
+          if (!ok) break;
+          const uint32_t fb = su32(&bar_full[s]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes) : "memory");
+          const uint32_t st = sbase + s * STAGE;
+          for (int sl = 0; sl < NSL; sl++)
+            tma_load_2d(st + sl * A_TILE, &tmA, fb, c * BK, jb.a_row + sl * jb.a_sstride);
+          for (int sl = 0; sl < NSL; sl++)
+            for (int bx = 0; bx < nbox; bx++)
+              tma_load_2d(st + NSL * A_TILE + sl * B_TILE + bx * BROWS * BK * 4, &tmB, fb, c * BK,
+                          jb.b_row + sl * jb.b_sstride + bx * BROWS);
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {                                             // ---- MMA issuer
-      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(npad >> 3) << 17) |
-                             ((uint32_t)(BM >> 4) << 24);
       // slice products (A slice, B slice, level accumulator 0/1/2 for levels 2 / 3 / 4-5)
       const int pa[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
       const int pb[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
       const int pl[10] = {0, 1, 1, 2, 2, 2, 2, 2, 2, 2};
-      for (int c = 0; c < nch; c++) {
-        const int s = c & 1, b = c & 1;
-        ok &= mbar_wait(su32(&bar_full[s]), (c >> 1) & 1);
-        if (c >= 2) ok &= mbar_wait(su32(&bar_acce[b]), ((c - 2) >> 1) & 1);
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t st = sbase + s * STAGE;
-        bool first[3] = {true, true, true};
-        for (int q = 0; q < 10; q++) {
-          const uint32_t dacc = tmem + (uint32_t)((3 * b + pl[q]) * BN);
-          for (int ks = 0; ks < BK / 8; ks++) {
-            const uint64_t da = desc_sw128(st + pa[q] * A_TILE + ks * 32);
-            const uint64_t db = desc_sw128(st + NSL * A_TILE + pb[q] * B_TILE + ks * 32);
-            mma_tf32(dacc, da, db, idesc, first[pl[q]] ? 0u : 1u);
-            first[pl[q]] = false;
+      // chunks this CTA runs; a stage is released only to a later chunk (no arrive may
+      // be left in flight when the CTA exits)
+      const long long g_total = (long long)nch * ((n_jobs - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
+      long long g = 0;
+      for (int tile = blockIdx.x; ok && tile < n_jobs; tile += gridDim.x) {
+        const int npad = (jobs[tile].n_valid + 15) & ~15;
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(npad >> 3) << 17) |
+                               ((uint32_t)(BM >> 4) << 24);
+        for (int c = 0; c < nch; c++, g++) {
+          const int s = (int)(g & 1), b = (int)(g & 1);
+          ok &= mbar_wait(su32(&bar_full[s]), (uint32_t)((g >> 1) & 1));
+          if (g >= 2) ok &= mbar_wait(su32(&bar_acce[b]), (uint32_t)(((g - 2) >> 1) & 1));
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t st = sbase + s * STAGE;
+          bool first[3] = {true, true, true};
+          for (int q = 0; q < 10; q++) {
+            const uint32_t dacc = tmem + (uint32_t)((3 * b + pl[q]) * BN);
+            for (int ks = 0; ks < BK / 8; ks++) {
+              const uint64_t da = desc_sw128(st + pa[q] * A_TILE + ks * 32);
+              const uint64_t db = desc_sw128(st + NSL * A_TILE + pb[q] * B_TILE + ks * 32);
+              mma_tf32(dacc, da, db, idesc, first[pl[q]] ? 0u : 1u);
+              first[pl[q]] = false;
+            }
           }
-        }
-        if (c + NSTAGE < nch)
+          if (g + NSTAGE < g_total)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                su32(&bar_empty[s])));
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              su32(&bar_empty[s])));
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            su32(&bar_accf[b])));
+              su32(&bar_accf[b])));
+        }
       }
     }
   } else {                                                       // ---- drain + epilogue (warps 2..5)
     const int q = warp & 3;                                      // TMEM lane quarter of this warp
     const uint32_t lrow = tmem + ((uint32_t)(32 * q) << 16);
-    for (int c = 0; c < nch; c++) {
-      const int b = c & 1;
-      ok &= mbar_wait(su32(&bar_accf[b]), (c >> 1) & 1);
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      for (int n0 = 0; n0 < npad; n0 += 16) {
-        uint32_t x2[16], x3[16], x4[16], h[16], l[16];
-        OSV_TMEM_LD16(lrow + (3 * b + 0) * BN + n0, x2);
-        OSV_TMEM_LD16(lrow + (3 * b + 1) * BN + n0, x3);
-        OSV_TMEM_LD16(lrow + (3 * b + 2) * BN + n0, x4);
-        if (c > 0) {
-          OSV_TMEM_LD16(lrow + COL_HI + n0, h);
-          OSV_TMEM_LD16(lrow + COL_LO + n0, l);
-        } else {
-#pragma unroll
-          for (int u = 0; u < 16; u++) h[u] = l[u] = 0u;
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-        for (int u = 0; u < 16; u++) {
-          float sh = __uint_as_float(h[u]), sl = __uint_as_float(l[u]), e;
-          two_sum(sh, __uint_as_float(x2[u]), sh, e);
-          sl += e;
-          two_sum(sh, __uint_as_float(x3[u]), sh, e);
-          sl += e;
-          two_sum(sh, __uint_as_float(x4[u]), sh, e);
-          sl += e;
-          h[u] = __float_as_uint(sh);
-          l[u] = __float_as_uint(sl);
-        }
-        OSV_TMEM_ST16(lrow + COL_HI + n0, h);
-        OSV_TMEM_ST16(lrow + COL_LO + n0, l);
-      }
-      asm volatile("tcgen05.wait::st.sync.aligned;");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&bar_acce[b])) : "memory");
-    }
     const int row = 32 * q + lane;
-    for (int n0 = 0; n0 < npad; n0 += 16) {
-      uint32_t h[16], l[16];
-      OSV_TMEM_LD16(lrow + COL_HI + n0, h);
-      OSV_TMEM_LD16(lrow + COL_LO + n0, l);
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if constexpr (Epi::kWarp) {
-        epi.warp(jb, row, n0, h, l);
-      } else if (row < jb.m_valid) {
+    long long g = 0;
+    for (int tile = blockIdx.x; ok && tile < n_jobs; tile += gridDim.x) {
+      const Job jb = jobs[tile];
+      const int npad = (jb.n_valid + 15) & ~15;
+      for (int c = 0; c < nch; c++, g++) {
+        const int b = (int)(g & 1);
+        ok &= mbar_wait(su32(&bar_accf[b]), (uint32_t)((g >> 1) & 1));
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int n0 = 0; n0 < npad; n0 += 16) {
+          uint32_t x2[16], x3[16], x4[16], h[16], l[16];
+          OSV_TMEM_LD16(lrow + (3 * b + 0) * BN + n0, x2);
+          OSV_TMEM_LD16(lrow + (3 * b + 1) * BN + n0, x3);
+          OSV_TMEM_LD16(lrow + (3 * b + 2) * BN + n0, x4);
+          if (c > 0) {
+            OSV_TMEM_LD16(lrow + COL_HI + n0, h);
+            OSV_TMEM_LD16(lrow + COL_LO + n0, l);
+          } else {
 #pragma unroll
-        for (int u = 0; u < 16; u++)
-          if (n0 + u < jb.n_valid) epi(jb, row, n0 + u, __uint_as_float(h[u]), __uint_as_float(l[u]));
+            for (int u = 0; u < 16; u++) h[u] = l[u] = 0u;
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int u = 0; u < 16; u++) {
+            float sh = __uint_as_float(h[u]), sl = __uint_as_float(l[u]), e;
+            two_sum(sh, __uint_as_float(x2[u]), sh, e);
+            sl += e;
+            two_sum(sh, __uint_as_float(x3[u]), sh, e);
+            sl += e;
+            two_sum(sh, __uint_as_float(x4[u]), sh, e);
+            sl += e;
+            h[u] = __float_as_uint(sh);
+            l[u] = __float_as_uint(sl);
+          }
+          OSV_TMEM_ST16(lrow + COL_HI + n0, h);
+          OSV_TMEM_ST16(lrow + COL_LO + n0, l);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&bar_acce[b])) : "memory");
+      }
+      if (!ok) break;
+      for (int n0 = 0; n0 < npad; n0 += 16) {
+        uint32_t h[16], l[16];
+        OSV_TMEM_LD16(lrow + COL_HI + n0, h);
+        OSV_TMEM_LD16(lrow + COL_LO + n0, l);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if constexpr (Epi::kWarp) {
+          epi.warp(jb, row, n0, h, l);
+        } else if (row < jb.m_valid) {
+#pragma unroll
+          for (int u = 0; u < 16; u++)
+            if (n0 + u < jb.n_valid) epi(jb, row, n0 + u, __uint_as_float(h[u]), __uint_as_float(l[u]));
+        }
       }
     }
   }
@@ -257,6 +281,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// Grid of the persistent kernel: one CTA per SM, at most one per tile.
+inline int persistent_grid(int n_jobs) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  }
+  return n_jobs < sms ? n_jobs : sms;
 }
 
 }  // namespace tc

@@ -60,7 +60,7 @@ int launch_tii_tc(const float* Bt, long long rows, int n_aux, int ldx, const tc:
   CUtensorMap ma, mb;
   if (!make_slice_map(&ma, Bt, n_aux, ldx, rows, tc::BM) || !make_slice_map(&mb, Bt, n_aux, ldx, rows, tc::BROWS))
     return -1;
-  tc::k_tf32x3<EpiT><<<n_jobs, tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_aux, err, EpiT{e_vir});
+  tc::k_tf32x3<EpiT><<<tc::persistent_grid(n_jobs), tc::NTHREADS, tc::SMEM, st>>>(ma, mb, jobs, n_jobs, n_aux, err, EpiT{e_vir});
   note_launch(1);
   return 0;
 }
