@@ -237,7 +237,7 @@ def run_gpu(args):
             return "alu", peak_fp32, "FP32 SIMT: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz (SGEMM measured 70)"
         if args.prec == "mixed" and name == "eig":
             return "alu", peak_fp32 / 16.0, ("double-float on the FP32 pipes: FP32 peak / 16 instructions per "
-                                              "double-float FMA (the tridiagonalisation; inverse iteration is FP64)")
+                                              "double-float FMA (tridiagonalisation, multisection, inverse iteration)")
         return "alu", peak_fp64, "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal 1.25; DGEMM measured 1.10)"
 
     dom = max(prof.items(), key=lambda kv: kv[1][0])
