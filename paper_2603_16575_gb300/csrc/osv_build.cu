@@ -1,5 +1,6 @@
 // A0: OSV generation.  T_ii from the RI integrals (Eq. mp2_tkk, positive
-// denominator e_a + e_b - 2 f_ii), its FP64 eigen-decomposition (Eq. osv_gen)
+// denominator e_a + e_b - 2 f_ii), its eigen-decomposition (Eq. osv_gen; FP64, or
+// double-float for the mixed form)
 // and the selection omega >= l_osv of Algorithm 3, all on the GPU.
 #include <algorithm>
 
@@ -222,9 +223,10 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   }
   __syncthreads();
   // inverse iteration, parallel over the kept vectors, one vector per LANE
-  // (lane-interleaved factorisations, so every FP64 instruction of a warp works
-  // for 32 vectors): two solves from a seeded start, Gram-Schmidt inside each
-  // cluster of close eigenvalues (warp per cluster, in order), then one more
+  // (lane-interleaved factorisations, so every instruction of a warp works for 32
+  // vectors): two solves from a seeded start, Gram-Schmidt inside each cluster of
+  // close eigenvalues (FP64: a warp per cluster; mixed form: the whole CTA per
+  // cluster, below), then one more
   // solve per vector and the Gram-Schmidt again.  With shifts accurate to
   // ~eps ||T||, one solve leaves a vector contaminated by an eigenvector at
   // distance g at ~eps ||T|| / g, so the vectors separate without

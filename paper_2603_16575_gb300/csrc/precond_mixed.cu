@@ -1,7 +1,7 @@
 // A3 for the mixed form: a basis X of the pair space with X^T F X ~ diag(e~) and
 // X^T S X ~ 1 (Eq. prec_eig), plus the exact leftovers
 //   S^ = X^T S X - 1,   G^ = (X^T F X - diag(e~)) - (f_ii + f_jj)/2 S^
-// (FP64 products, stored FP32: they are ~1e-7) that the mixed fragment solver
+// (double-float products, stored FP32: they are ~1e-7) that the mixed fragment solver
 // adds to its update, so the iteration's fixed point is the exact one whatever
 // the accuracy of X.
 //
@@ -12,7 +12,7 @@
 // gives Y^T S Y = blockdiag(1, Z^T C Z) = 1.  The eigenvalues of S are 1 and
 // 1 +- sigma_k (sigma_k^2 = 1 - mu_k), and a direction is dropped exactly when
 // the canonical orthogonalisation drops the eigenvalue 1 - sigma_k =
-// mu_k / (1 + sigma_k) below tau_s (1 + sigma_max).  Then F' = Y^T F Y (FP64,
+// mu_k / (1 + sigma_k) below tau_s (1 + sigma_max).  Then F' = Y^T F Y (double-float,
 // entries bounded by the virtual energies whatever the conditioning of Y) is
 // diagonalised in FP32 (F' = W diag(e~) W^T) and X = Y W.  A diagonal pair has
 // S_(ii,ii) = Q_i^T Q_i = 1: Y = 1, F' = F_(i,i).
@@ -21,10 +21,15 @@
 // descending order, so the largest start first):
 //   (1a) C = 1 - M^T M, Householder tridiagonalisation and Z (FP64, CTA);
 //   (1b) the QR bulge chase of every C, one pair per thread (FP64);
-//   (1c) recorded rotations applied to Z, kept directions, Y, Z^T C Z (CTA);
-//   (2)  F' = Y^T F Y (tiled FP64 GEMMs, CTA);
+//   (1c) recorded rotations applied to Z, kept directions, Y, Z^T C Z (CTA; the
+//        products with Z in double-float);
+//   (2)  F' = Y^T F Y (tiled double-float GEMMs, CTA);
 //   (3a-c) the same three steps for the FP32 eigen-decomposition of F';
-//   (4)  X = Y W and the leftovers (tiled FP64 GEMMs, CTA).
+//   (4)  X = Y W and the leftovers (tiled double-float GEMMs, CTA).
+// C and its eigen-decomposition stay FP64: C = 1 - M^T M cancels, and its small
+// eigenvalues set both the kept directions and Z.  The products with Z, Y and W
+// carry ~2^-48 relative error; it enters X, U = P X and the leftovers alike, so
+// the fixed point does not move.
 // The eigen-solver is Householder + implicit QR (eig.cuh) with the chase run
 // per thread over many pairs at once and its rotations recorded, then applied
 // to the eigenvectors (kept column-major, so the rotations are coalesced) by a
@@ -318,8 +323,10 @@ __global__ void __launch_bounds__(NT, 3) k_pm_eig32_c(const PJob* __restrict__ j
 
 // (4) X = Y W; S~ = W^T (Y^T S Y) W; F~ = W^T F' W; leftovers.  The products run in
 // double-float (~48 bits): W holds FP32 values and Y^T S Y, F' are FP64 with entries
-// ~1, so the leftovers (~1e-6) keep ~9 significant digits.  X = Y W stays FP64:
-// its entries reach lambda_min(S)^(-1/2) and U = P X inherits their rounding.
+// ~1, so the leftovers (~1e-6) keep ~9 significant digits.  X = Y W (entries up to
+// lambda_min(S)^(-1/2)) is double-float as well: U = P X and the leftovers are
+// formed from the same X, so its ~2^-48 relative rounding does not move the
+// fixed point.
 __global__ void __launch_bounds__(NT, 2) k_pm_final(Tables t, const PJob* __restrict__ jobs,
                                                  const int* __restrict__ order, int n_jobs, double* slots,
                                                  const long long* off, int max_m, double* scratch, int* err) {

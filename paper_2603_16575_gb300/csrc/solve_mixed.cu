@@ -23,8 +23,9 @@
 // Y by ~ eps_32 |c| / |D| ~ 1e-9 relative.  The coupling products are FP32 (K =
 // a pair order), Sigma_pq comes from the split-precision table, and C_p is
 // accumulated over its terms in a compensated FP32 pair (two-sum: no FP64
-// arithmetic, whose throughput is 1/64 of FP32 here).  K~_p, 1/D_p, Y_p (master
-// copy), the update and the energy <K~_p, 2Y_p - Y_p^T> are FP64.
+// arithmetic, whose throughput is 1/64 of FP32 here).  K~_p, 1/D_p and Y_p (master
+// copy) are double-float pairs (~48 bits), and so are the update and the energy
+// <K~_p, 2Y_p - Y_p^T>.  The energy sum over the pairs and fragments is FP64.
 #include "pairview.cuh"
 
 namespace osv {
