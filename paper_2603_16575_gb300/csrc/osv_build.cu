@@ -420,11 +420,16 @@ template <int NJ>
 __global__ void __launch_bounds__(EB_WARPS * 32) k_eig_back_df(const double* T, int n, int kmax, double* V,
                                                               const int* kout, const double* scratch,
                                                               size_t scr_stride) {
+  __shared__ dfl s_tau[EB_DF_MAXN];   // tau as pairs: no global load or FP64 work per reflector
   const int b = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.y * EB_WARPS + warp;
-  if (t >= kout[b]) return;   // warp-uniform
-  const dfl* Ad = reinterpret_cast<const dfl*>(T + (size_t)b * n * n);
+  const int kb = kout[b];
+  if ((int)blockIdx.y * EB_WARPS >= kb) return;   // CTA-uniform
   const double* tau = scratch + (size_t)b * scr_stride + 2 * n;
+  for (int i = threadIdx.x; i < n; i += EB_WARPS * 32) s_tau[i] = df_from(tau[i]);
+  __syncthreads();
+  if (t >= kb) return;   // warp-uniform
+  const dfl* Ad = reinterpret_cast<const dfl*>(T + (size_t)b * n * n);
   double* x = V + (size_t)b * n * kmax + (size_t)t * n;
   dfl xr[NJ];
 #pragma unroll
@@ -433,8 +438,8 @@ __global__ void __launch_bounds__(EB_WARPS * 32) k_eig_back_df(const double* T, 
     xr[j] = r < n ? df_from(x[r]) : dfl{0.f, 0.f};
   }
   for (int kk = n - 3; kk >= 0; kk--) {
-    const double tk = tau[kk];
-    if (tk == 0.0) continue;
+    const dfl tk = s_tau[kk];
+    if (tk.h == 0.f) continue;
     const dfl* vr = Ad + (size_t)kk * n;   // v at columns kk+1 .. n-1 of row kk
     const int j0 = (kk + 1) >> 5;          // register blocks below j0 hold no row > kk
     float sh = 0.f, sl = 0.f;
@@ -447,7 +452,7 @@ __global__ void __launch_bounds__(EB_WARPS * 32) k_eig_back_df(const double* T, 
     dfl s = df_norm(sh, sl);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s = df_add(s, df_shfl_xor(s, o));
-    const dfl ns = df_neg(df_mul(s, df_from(tk)));
+    const dfl ns = df_neg(df_mul(s, tk));
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
       if (j < j0) continue;
