@@ -228,6 +228,10 @@ def test_mixed_osv_build_matches_oracle(n_vir, l_osv, lam):
         wr = o.omega[i]
         assert np.abs(w - wr).max() < 1e-9 * wr.max()
         assert np.allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-11)
+        # eigenvectors of the FP64 T_ii (Eq. osv_gen): the residual is set by the ~35-bit
+        # T_ii, whatever the clustering of the kept eigenvalues
+        T = oracle.semicanonical_tii(s.B_block(i), s.e_vir, s.f_occ[i, i])
+        assert np.abs(T @ Q - Q * w).max() < 1e-8 * wr.max()
     ctx.close()
 
 
