@@ -31,8 +31,17 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 R2_CUT, R3_CUT, L_OSV = 8.0, 6.0, 1e-4
-# Measured on this GB300 pool (peaks file + FP64 unit count x clock):
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 DFMA/clk/SM at the 2070 MHz maximum -> 1.258
+# Denominators the peaks file does not carry, measured on this GB300 pool with
+# `python bench.py --measure-peaks` (torch GEMMs at 8192^3, best of 10, CUDA
+# events); the figures and the run are in profiles/peaks_fp64_tf32_fp32.md.
+MEASURED_GEMM_PEAKS = {"fp64_tflops": 1.10, "tf32_tflops": 1021.0, "fp32_tflops": None,
+                       "source": "round-trip torch.matmul 8192^3 on a GB300 of this pool"}
+FP32_SIMT_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12    # 128 FFMA/clk/SM at the 2070 MHz maximum -> 80.5
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernels,
+# from one ncu capture on the 48-orbital case scaled to the bench workload by the
+# units each launch processes (profiles/traffic_mbe3_n48.md); None until captured
+# for the kernel as it stands.
+KERNEL_TRAFFIC = {}
 
 
 def load_peaks():
@@ -97,6 +106,55 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def fragment_energies(ctx):
+    """{orbital tuple: E_C} of the ctx's last MBE(3) call."""
+    orbs, _, e = ctx.fragment_results()
+    return {tuple(int(x) for x in o if x >= 0): float(v) for o, v in zip(orbs, e)}
+
+
+def projection_flops(ctx, s, n_osv):
+    """Algorithmic A1 work of one step: B~_i^(x) = B_i^T Q_x for every x in
+    dom(i) = {i} + the kept pair partners of i, i.e. 2 n_aux n_vir N_i per
+    orbital with N_i = sum of n_x over dom(i) (Eq. osv_imua)."""
+    orbs, _, _ = ctx.fragment_results()
+    dom = [{i} for i in range(s.n_occ)]
+    for o in orbs:
+        if o[1] >= 0 and o[2] < 0:
+            dom[o[0]].add(int(o[1]))
+            dom[o[1]].add(int(o[0]))
+    return sum(2.0 * s.n_aux * s.n_vir * sum(int(n_osv[x]) for x in d) for d in dom)
+
+
+def measure_peaks():
+    """FP64, TF32 and FP32 (no TF32) GEMM throughput with torch at 8192^3: the
+    denominators of the FP64, split-TF32 and FP32 rooflines."""
+    import torch
+    dev = torch.device("cuda:0")
+    n = 8192
+    out = {}
+    for name, dt, tf32 in (("fp64_tflops", torch.float64, False), ("tf32_tflops", torch.float32, True),
+                           ("fp32_tflops", torch.float32, False), ("bf16_tflops", torch.bfloat16, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device=dev, dtype=dt)
+        b = torch.randn(n, n, device=dev, dtype=dt)
+        c = a @ b
+        best = 1e30
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[name] = 2.0 * n ** 3 / best / 1e12
+        del a, b, c
+        torch.cuda.empty_cache()
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["how"] = "torch.matmul 8192^3, best of 10, CUDA events; tf32 = float32 with allow_tf32"
+    out["gpu"] = torch.cuda.get_device_name(0)
+    return out
 
 
 def dist_env():
@@ -167,6 +225,7 @@ def run_gpu(args):
             torch.distributed.barrier()
     launches = pkg.osvmp2.kernel_launches() - launches0
     prof = ctx.profile(reset=True)
+    gpu_frag_e = {("fp64_form" if args.prec == "fp64" else "mixed_form"): fragment_energies(ctx)}
     plan = ctx.solve_plan() if args.prec == "mixed" else None
     a0_ms = sum(prof.get(k, (0.0,))[0] for k in ("tii", "eig")) / args.steps
     err = None
@@ -184,6 +243,7 @@ def run_gpu(args):
         E64 = ctx.mbe3_energy(R2_CUT, R3_CUT, "fp64")[0]
         ev1.record(stream)
         ev1.synchronize()
+        gpu_frag_e["fp64_form"] = fragment_energies(ctx)
         t64 = ev0.elapsed_time(ev1) / 1e3
         err = {"energy_fp64_form": E64, "abs_err_eh": abs(E - E64), "rel_err": abs(E - E64) / abs(E64),
                "fp64_form_ms_per_step": 1e3 * t64, "fp64_form_fragments_per_s": n_frag / t64}
@@ -220,38 +280,58 @@ def run_gpu(args):
     e2e_value = world * n_frag / statistics.median(e2e_t)
 
     # ---- roofline of the dominant kernel (largest device time in the timed region)
-    peak_fp64 = FP64_PEAK_TFLOPS
-    peak_fp32 = 152 * 128 * 2 * 2.070e9 / 1e12                 # 128 FFMA/clk/SM -> 80.5 TF/s
-
-    # split-precision tensor-core contractions: 10 TF32 slice products per algorithmic
-    # product; TF32 peak = measured BF16 peak x nominal TF32/BF16 ratio (1.1/2.25 PF)
-    peak_tf32 = peaks["bf16_tflops"] * 1.1 / 2.25
-    peak_split = peak_tf32 / 10.0
-
-    def phase_peak(name):
-        """(bound, peak TFLOP/s, source) of a phase in the arithmetic it runs in."""
-        if args.prec == "mixed" and name in ("tii", "project"):
-            return ("tensor", peak_split, f"split-TF32 on tcgen05: TF32 peak {peak_tf32:.0f} TF/s (measured BF16 "
-                    f"{peaks['bf16_tflops']:.0f} x 1.1/2.25) / 10 slice products")
-        if args.prec == "mixed" and name in ("exchange", "solve"):
-            return "alu", peak_fp32, "FP32 SIMT: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz (SGEMM measured 70)"
-        if args.prec == "mixed" and name == "eig":
-            return "alu", peak_fp32 / 16.0, ("double-float on the FP32 pipes: FP32 peak / 16 instructions per "
-                                              "double-float FMA (tridiagonalisation, multisection, inverse iteration)")
-        return "alu", peak_fp64, "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal 1.25; DGEMM measured 1.10)"
-
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    name, (ms, fl, by, calls) = dom
-    per_launch_s = ms / 1e3 / max(calls, 1)
-    bound, peak, src = phase_peak(name)
-    achieved = fl / max(calls, 1) / per_launch_s / 1e12 if fl > 0 else None
-    roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_source": src}
+    gemm = MEASURED_GEMM_PEAKS
+    peak_fp64 = gemm["fp64_tflops"]
+    peak_fp32 = gemm["fp32_tflops"] or FP32_SIMT_PEAK
+    peak_split = gemm["tf32_tflops"] / 10.0       # split-TF32: 10 TF32 slice products per product
+    a1_flops = projection_flops(ctx, s, n_osv) * args.steps   # SURVEY-style A1: 2 n_aux n_vir N_i per orbital
+    kern = {
+        # phase key: (kernel, bound, peak TFLOP/s, peak source, algorithmic flops in the timed region)
+        "k_eig": ("k_eig_osv", "alu",
+                  peak_fp32 / 16.0 if args.prec == "mixed" else peak_fp64,
+                  ("double-float on the FP32 pipes: FP32 peak / 16 instructions per double-float FMA"
+                   if args.prec == "mixed" else "FP64 DGEMM measured"),
+                  prof.get("k_eig", (0, 0))[1]),
+        "k_gproj": ("k_tf32x3<EpiG2>", "tensor", peak_split,
+                    f"split-TF32 on tcgen05: measured TF32 {gemm['tf32_tflops']:.0f} TF/s / 10 slice products",
+                    a1_flops),
+        "k_fragsolve": ("k_frag_solve_mixed" if args.prec == "mixed" else "k_frag_solve", "alu",
+                        peak_fp32 if args.prec == "mixed" else peak_fp64,
+                        "FP32 SIMT" if args.prec == "mixed" else "FP64 DGEMM measured",
+                        prof.get("k_fragsolve", (0, 0))[1]),
+    }
+    kernels = {}
+    for key, (kname, bound, peak, src, alg) in kern.items():
+        if key not in prof or prof[key][0] <= 0:
+            continue
+        ms, fl, _, calls = prof[key]
+        per_launch_s = ms / 1e3 / max(calls, 1)
+        achieved = alg / max(calls, 1) / per_launch_s / 1e12 if alg else None
+        kernels[kname] = {"phase": key, "ms_per_step": ms / args.steps, "launches_per_step": calls / args.steps,
+                          "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                          "frac": (achieved / peak) if achieved else None, "peak_source": src + " (of measured)",
+                          "algorithmic_flops_per_step": alg / args.steps,
+                          "performed_flops_per_step": fl / args.steps}
+    dom = max(kernels.items(), key=lambda kv: kv[1]["ms_per_step"])
+    dname, d = dom
+    tr = KERNEL_TRAFFIC.get(dname)
+    roof = {"kernel": dname, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
+            "frac": d["frac"], "traffic": tr, "peak_source": d["peak_source"],
+            "per_launch": "algorithmic flops per launch / CUDA-event time per launch (library stream)"}
+    top = ("tii", "eig", "sf", "project", "exchange", "precond", "solve")
     phases = {}
+    alg_total = 0.0
     for k, v in prof.items():
-        b_, p_, _ = phase_peak(k)
-        tf = (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 and v[1] else None
-        phases[k] = {"ms_per_step": v[0] / args.steps, "tflops": tf, "frac": (tf / p_) if tf else None}
+        fl = a1_flops if (k == "project" and args.prec == "mixed") else v[1]
+        if k in top:
+            alg_total += fl
+        tf = (fl / (v[0] / 1e3) / 1e12) if v[0] > 0 and fl else None
+        phases[k] = {"ms_per_step": v[0] / args.steps, "tflops": tf}
+    effective = {"value": alg_total / t_tot / 1e12 if t_tot > 0 else None, "unit": "TFLOP/s",
+                 "counted": "A0 T_ii + eig, A1 projection (2 n_aux n_vir N_i per orbital), A2 K/S/F, "
+                            "A3, A4 solver operations, per step"}
+    if args.prec == "mixed":
+        effective["projection_overhead"] = prof.get("project", (0, 0))[1] / max(a1_flops, 1.0)
 
     out = {
         "metric": "MBE(3) fragments/s",
@@ -280,11 +360,20 @@ def run_gpu(args):
                 "d2h_bytes_per_step": 8},
         "gpu_launches": int(launches),
         "roofline": roof,
+        "kernels": kernels,
+        "effective_tflops": effective,
         "phases": phases,
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_budget)
+        out["cpu_baseline"], ref_e = cpu_baseline(args, budget_s=args.cpu_budget)
+        out["energy_vs_oracle"] = {}
+        for form, got in gpu_frag_e.items():
+            errs = [(abs(got[o] - e), abs(got[o] - e) / abs(e)) for o, e in ref_e.items() if o in got]
+            if errs:
+                out["energy_vs_oracle"][form] = {"fragments": len(errs), "max_abs_eh": max(a for a, _ in errs),
+                                                 "max_rel": max(r for _, r in errs),
+                                                 "sample": "fragments of the oracle CPU sample"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -307,20 +396,21 @@ def cpu_sample(args, budget_s: float):
     t0 = time.perf_counter()
     osys = oracle.OSVSystem(s.B_block, s.n_occ, s.e_vir, s.f_occ, l_osv=L_OSV, orbitals=near)
     done = 0
+    energies = {}
     for orbs, c in frags:
-        osys.solve(orbs)
+        energies[tuple(orbs)] = osys.solve(orbs).energy
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return done, dt, k
+    return done, dt, k, energies
 
 
 def cpu_baseline(args, budget_s: float):
-    done, dt, k = cpu_sample(args, budget_s)
-    return {"value": done / dt, "unit": "fragments/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"OSV build of the {k} orbitals nearest orbital 0 + the {done} MBE(3) fragments inside "
-                      f"that set ({dt:.1f} s, NumPy FP64, BLAS threads = all cores)"}
+    done, dt, k, energies = cpu_sample(args, budget_s)
+    return ({"value": done / dt, "unit": "fragments/s", "cores": os.cpu_count(), "kind": "oracle",
+             "sample": f"OSV build of the {k} orbitals nearest orbital 0 + the {done} MBE(3) fragments inside "
+                       f"that set ({dt:.1f} s, NumPy FP64, BLAS threads = all cores)"}, energies)
 
 
 def run_reference(args):
@@ -331,7 +421,7 @@ def run_reference(args):
         cpu_sample(args, args.cpu_budget)
     vals, times, frags = [], [], 0
     for _ in range(args.steps):
-        done, dt, k = cpu_sample(args, args.cpu_budget)
+        done, dt, k, _ = cpu_sample(args, args.cpu_budget)
         vals.append(done / dt)
         times.append(dt)
         frags = done
@@ -361,7 +451,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--cpu-orbitals", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--measure-peaks", action="store_true",
+                    help="print the FP64 / TF32 / FP32 / BF16 GEMM throughput of GPU 0 and exit")
     args = ap.parse_args()
+    if args.measure_peaks:
+        print(json.dumps(measure_peaks()), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

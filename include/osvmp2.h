@@ -51,7 +51,10 @@ typedef enum {
   OSVMP2_E_NOMEM = 3,    /* device allocation failed */
   OSVMP2_E_NOCONV = 4,   /* amplitude iterations hit max_iter (see osvmp2_mbe_stats) */
   OSVMP2_E_NUMERIC = 5,  /* eigen-solver did not converge or produced non-finite values */
-  OSVMP2_E_STATE = 6     /* call order violated (e.g. pair_integrals before build_osv) */
+  OSVMP2_E_STATE = 6,    /* call order violated (e.g. pair_integrals before build_osv) */
+  OSVMP2_E_TIMEOUT = 7   /* a bounded device-side wait (a tensor-core pipeline barrier) gave up:
+                            the kernel left its loops early, released its tensor memory and
+                            flagged the call; the call's results are invalid */
 } osvmp2_status;
 
 /* Arithmetic of the projection/exchange contractions (A1-A2) and of the residual
@@ -78,7 +81,11 @@ typedef struct {
                           largest pair order times the candidate launch shapes of the mixed
                           fragment solve and keeps the fastest (osvmp2_get_solve_plan); 1: fixed
                           default shape.  The energies are identical either way. */
-  int32_t reserved[5];
+  int32_t mem_cap_mib; /* 0 (default): no limit.  Otherwise the device memory this ctx may hold at
+                          once (its cache, pair store and temporaries), in MiB; a request beyond it
+                          fails with OSVMP2_E_NOMEM as a failed cudaMalloc would.  Library extension
+                          for callers that run under a memory budget. */
+  int32_t reserved[4];
 } osvmp2_opts;
 
 /* Synthetic or caller-supplied system.  All arrays are read by the kernels. */
@@ -218,7 +225,13 @@ enum {
   OSVMP2_PH_MBE_SUM = 7,   /* A5: weighted fragment-energy sum */
   OSVMP2_PH_SUBSOLVE = 8,  /* A4: pair-parallel subsystem solve (osvmp2_solve) */
   OSVMP2_PH_GRAD = 9,      /* A6: adjoint kernels */
-  OSVMP2_NPHASE = 12
+  /* single kernels, timed inside the phases above */
+  OSVMP2_PH_K_GPROJ = 10,  /* mixed A1: the tensor-core G = U^T B launches (inside PROJECT) */
+  OSVMP2_PH_K_EIG = 11,    /* A0: the OSV eigen-decomposition launches, without the
+                              back-transformation (inside EIG) */
+  OSVMP2_PH_K_FRAGSOLVE = 12, /* A4: the persistent fragment solve and its energy sum (inside SOLVE) */
+  OSVMP2_PH_SIGMA = 13,    /* mixed A4 set-up: pair-couple overlaps on the tensor cores (inside SOLVE) */
+  OSVMP2_NPHASE = 16
 };
 /* Accumulated since the last reset, per phase (host arrays of OSVMP2_NPHASE, any
  * may be NULL): device milliseconds, algorithmic FP operations (GEMM-shaped
@@ -250,15 +263,21 @@ int osvmp2_generate_B(int32_t n_occ, int32_t n_vir, int32_t n_aux, uint64_t seed
  *   S_dev, F_dev : device [m][m] row-major S_(ij,ij), F_(ij,ij)     (read)
  *   X_dev        : device [m][m] row-major, columns 0..r-1 written  (out)
  *   et_dev       : device [m], entries 0..r-1 written               (out)
- *   r_dev        : device int32, r, or -1 if an eigen-solve failed  (out)
+ *   r_dev        : device int32, r (out): the number of kept directions; 0 if S has no
+ *                  eigenvalue above tau_s * max (e.g. S = 0: X and e~ are then not
+ *                  written); -1 if an eigen-solve failed or an eigenvalue of S or of
+ *                  Y^T F Y is not finite (NaN or Inf in S or F)
  *   cuda_stream  : cudaStream_t to queue the single kernel on (NULL = legacy default)
  *   err, err_len : optional host buffer for a one-line error message
  * Returns OSVMP2_E_ARG (with a message) for null pointers, tau_s < 0, or m outside
  * 1..OSVMP2_NOALLOC_MAX_M, OSVMP2_E_CUDA if the launch fails.  The call is
  * asynchronous; outputs are ready when the stream reaches the kernel's end.
- * The first call on each device (with that device current) looks up the
- * device address of the static scratch with cudaGetSymbolAddress; make that
- * first call before any stream capture.  Every call shares the one scratch
+ * Every call looks up the device address of the static scratch in the
+ * caller's current context with cudaGetSymbolAddress (host code cannot use the
+ * array's name as a device address), so a reset or replaced context never sees
+ * a stale address.  The first call in a context may load the library's device
+ * code into it (lazy module loading); make that first call before any stream
+ * capture.  Every call shares the one scratch
  * array and the kernel writes each scratch element before reading it, so
  * nothing from an earlier call needs clearing -- but calls whose kernels
  * overlap on the GPU (different streams without ordering) race on that array:

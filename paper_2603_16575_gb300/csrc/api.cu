@@ -66,6 +66,8 @@ struct SolvePlan {
 
 struct osvmp2_ctx {
   DevPool pool;
+  size_t held = 0;                                  // device bytes this ctx holds from the driver
+  std::unordered_map<void*, size_t> raw_size;       // every driver block it holds, with its size
   std::map<std::pair<int, int>, SolvePlan> plans;   // mixed solve plans by (n_frag, max_m)
   SolvePlan last_plan;
   cudaStream_t cap_st = nullptr;      // private stream used only to record the solve graph
@@ -120,8 +122,10 @@ struct osvmp2_ctx {
   std::vector<Frag> frags;
   std::vector<FragOut> frag_out;
   // per-phase device time (CUDA events on st) and algorithmic flops, accumulated
-  cudaEvent_t ev0[OSVMP2_NPHASE] = {}, ev1[OSVMP2_NPHASE] = {};
-  bool pending[OSVMP2_NPHASE] = {};
+  // a phase may be entered several times between collections (batched
+  // launches): each entry takes the next (begin, end) pair of its event pool
+  std::vector<cudaEvent_t> ph_ev[OSVMP2_NPHASE];
+  size_t ph_used[OSVMP2_NPHASE] = {};
   double ms[OSVMP2_NPHASE] = {};
   double flops[OSVMP2_NPHASE] = {};
   double bytes[OSVMP2_NPHASE] = {};
@@ -156,10 +160,33 @@ int fail(osvmp2_ctx* c, int code, const char* fmt, ...) {
     if (s_) return s_;     \
   } while (0)
 
+// Every driver allocation of a ctx goes through raw_malloc / raw_free, which
+// keep the byte count that the optional cap (opts.mem_cap_mib) is checked
+// against; a request beyond the cap fails as a failed cudaMalloc would.
+cudaError_t raw_malloc(osvmp2_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (c->opts.mem_cap_mib > 0 && c->held + bytes > ((size_t)c->opts.mem_cap_mib << 20))
+    return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) {
+    c->held += bytes;
+    c->raw_size[*p] = bytes;
+  }
+  return e;
+}
+void raw_free(osvmp2_ctx* c, void* p) {
+  auto it = c->raw_size.find(p);
+  if (it != c->raw_size.end()) {
+    c->held -= it->second;
+    c->raw_size.erase(it);
+  }
+  cudaFree(p);
+}
+
 int dalloc(osvmp2_ctx* c, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = raw_malloc(c, p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, OSVMP2_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
@@ -183,7 +210,7 @@ void pool_trim(osvmp2_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   for (auto& kv : c->pool.free_blocks) {
     c->pool.size_of.erase(kv.second);
-    cudaFree(kv.second);
+    raw_free(c, kv.second);
   }
   c->pool.free_blocks.clear();
 }
@@ -196,11 +223,11 @@ cudaError_t pool_get(osvmp2_ctx* c, void** p, size_t bytes) {
     c->pool.free_blocks.erase(it);
     return cudaSuccess;
   }
-  cudaError_t e = cudaMalloc(p, r);
+  cudaError_t e = raw_malloc(c, p, r);
   if (e != cudaSuccess) {
     cudaGetLastError();
     pool_trim(c);
-    e = cudaMalloc(p, r);
+    e = raw_malloc(c, p, r);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -214,7 +241,7 @@ void pool_put(osvmp2_ctx* c, void* p) {
   if (!p) return;
   auto s = c->pool.size_of.find(p);
   if (s == c->pool.size_of.end()) {
-    cudaFree(p);
+    raw_free(c, p);
     return;
   }
   c->pool.free_blocks.emplace(s->second, p);
@@ -241,7 +268,7 @@ int tmp_alloc(osvmp2_ctx* c, Tmp& t, size_t bytes) {
 
 void free_system(osvmp2_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
-  for (void* p : c->sys_allocs) cudaFree(p);
+  for (void* p : c->sys_allocs) raw_free(c, p);
   c->sys_allocs.clear();
   for (void* p : c->pair_allocs) pool_put(c, p);
   c->pair_allocs.clear();
@@ -296,27 +323,42 @@ int check_err_flag(osvmp2_ctx* c, const char* where) {
   if (h & ERR_EIG) return fail(c, OSVMP2_E_NUMERIC, "%s: eigen-solver did not converge", where);
   if (h & ERR_NONFINITE) return fail(c, OSVMP2_E_NUMERIC, "%s: non-finite values", where);
   if (h & ERR_SIZE) return fail(c, OSVMP2_E_NUMERIC, "%s: size limit exceeded", where);
-  if (h & ERR_TIMEOUT) return fail(c, OSVMP2_E_CUDA, "%s: a tensor-core pipeline wait timed out", where);
+  if (h & ERR_TIMEOUT) return fail(c, OSVMP2_E_TIMEOUT, "%s: a tensor-core pipeline wait timed out", where);
   return 0;
 }
 
-void ph_begin(osvmp2_ctx* c, int ph) { cudaEventRecord(c->ev0[ph], c->st); }
+void ph_begin(osvmp2_ctx* c, int ph) {
+  auto& ev = c->ph_ev[ph];
+  while (ev.size() < c->ph_used[ph] + 2) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return;   // timing is best effort: this entry goes untimed
+    }
+    ev.push_back(e);
+  }
+  cudaEventRecord(ev[c->ph_used[ph]], c->st);
+}
 void ph_end(osvmp2_ctx* c, int ph, double flops, double bytes = 0.0) {
-  cudaEventRecord(c->ev1[ph], c->st);
-  c->pending[ph] = true;
+  auto& ev = c->ph_ev[ph];
+  if (ev.size() >= c->ph_used[ph] + 2) {
+    cudaEventRecord(ev[c->ph_used[ph] + 1], c->st);
+    c->ph_used[ph] += 2;
+  }
   c->flops[ph] += flops;
   c->bytes[ph] += bytes;
   c->calls[ph]++;
 }
 // Call after a stream synchronisation: fold finished phase timings in.
 void ph_collect(osvmp2_ctx* c) {
-  for (int ph = 0; ph < OSVMP2_NPHASE; ph++)
-    if (c->pending[ph]) {
+  for (int ph = 0; ph < OSVMP2_NPHASE; ph++) {
+    for (size_t k = 0; k + 1 < c->ph_used[ph]; k += 2) {
       float t = 0.f;
-      if (cudaEventElapsedTime(&t, c->ev0[ph], c->ev1[ph]) == cudaSuccess) c->ms[ph] += t;
+      if (cudaEventElapsedTime(&t, c->ph_ev[ph][k], c->ph_ev[ph][k + 1]) == cudaSuccess) c->ms[ph] += t;
       else cudaGetLastError();
-      c->pending[ph] = false;
     }
+    c->ph_used[ph] = 0;
+  }
 }
 
 template <class T>
@@ -533,15 +575,40 @@ int gproj_tensor(osvmp2_ctx* c, const std::vector<GJob>& gj, const std::vector<l
     Tmp jd;
     TRY(tmp_alloc(c, jd, jobs.size() * sizeof(tc::Job)));
     CK(cudaMemcpyAsync(jd.p, jobs.data(), jobs.size() * sizeof(tc::Job), cudaMemcpyHostToDevice, c->st));
+    double fl = 0.0;
+    for (const tc::Job& jb : jobs) fl += 2.0 * (double)jb.m_valid * jb.n_valid * nv;
+    ph_begin(c, OSVMP2_PH_K_GPROJ);
     if (launch_gproj_tc((const float*)bs.p, (long long)nb * tc::NSL * nx, Us, us_rows, nv, ldv, (const tc::Job*)jd.p,
                         (int)jobs.size(), lo_shift, c->err_d, c->st))
       return fail(c, OSVMP2_E_CUDA, "tensor-map encoding for the G projection failed");
+    ph_end(c, OSVMP2_PH_K_GPROJ, fl);
     CK(cudaGetLastError());
   }
   return 0;
 }
 
+int ensure_pairs_impl(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osvmp2_prec prec);
+
+// A failure part-way through leaves pairs marked as pending and blocks only
+// partly written; the whole pair store is dropped then (the OSVs are kept), so
+// the next call on the ctx rebuilds what it needs instead of using them.
 int ensure_pairs(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osvmp2_prec prec) {
+  if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "osvmp2_build_osv has not been called");
+  if (prec != OSVMP2_FP64 && prec != OSVMP2_MIXED) return fail(c, OSVMP2_E_ARG, "unknown precision %d", (int)prec);
+  for (auto& p : req)
+    if (p.first < 0 || p.second < 0 || p.first >= c->sys.n_occ || p.second >= c->sys.n_occ || p.first > p.second)
+      return fail(c, OSVMP2_E_ARG, "pair (%d,%d) invalid: need 0 <= i <= j < n_occ", p.first, p.second);
+  const int rc = ensure_pairs_impl(c, req, prec);
+  if (rc != 0 && rc != OSVMP2_E_STATE && c->have_osv) {
+    const std::string msg = c->err;
+    cudaGetLastError();
+    reset_pairs(c);
+    c->err = msg;
+  }
+  return rc;
+}
+
+int ensure_pairs_impl(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req, osvmp2_prec prec) {
   if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "osvmp2_build_osv has not been called");
   if (prec != OSVMP2_FP64 && prec != OSVMP2_MIXED) return fail(c, OSVMP2_E_ARG, "unknown precision %d", (int)prec);
   if (c->pair_prec >= 0 && c->pair_prec != (int)prec) TRY(reset_pairs(c));
@@ -932,7 +999,7 @@ void osvmp2_default_opts(osvmp2_opts* o) {
 }
 
 static bool opts_valid(const osvmp2_opts& o) {
-  return o.max_iter > 0 && o.tau_s >= 0 && o.tol_update > 0 && o.tol_energy > 0 &&
+  return o.max_iter > 0 && o.tau_s >= 0 && o.tol_update > 0 && o.tol_energy > 0 && o.mem_cap_mib >= 0 &&
          (o.osv_prec == OSVMP2_FP64 || o.osv_prec == OSVMP2_MIXED) && (o.no_autotune == 0 || o.no_autotune == 1);
 }
 
@@ -969,10 +1036,6 @@ int osvmp2_create(osvmp2_ctx** out, int device, void* cuda_stream, const osvmp2_
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc(&c->err_d, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->scal_d, 16 * sizeof(double));
-  for (int ph = 0; ph < OSVMP2_NPHASE && e == cudaSuccess; ph++) {
-    e = cudaEventCreate(&c->ev0[ph]);
-    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1[ph]);
-  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -991,10 +1054,8 @@ void osvmp2_destroy(osvmp2_ctx* c) {
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
   if (c->err_d) cudaFree(c->err_d);
   if (c->scal_d) cudaFree(c->scal_d);
-  for (int ph = 0; ph < OSVMP2_NPHASE; ph++) {
-    if (c->ev0[ph]) cudaEventDestroy(c->ev0[ph]);
-    if (c->ev1[ph]) cudaEventDestroy(c->ev1[ph]);
-  }
+  for (int ph = 0; ph < OSVMP2_NPHASE; ph++)
+    for (cudaEvent_t e : c->ph_ev[ph]) cudaEventDestroy(e);
   delete c;
 }
 
@@ -1116,12 +1177,17 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
     ph_end(c, OSVMP2_PH_TII, (double)b * nv * (double)nv * s->n_aux, s->B ? 8.0 * b * (double)nv * s->n_aux : 0.0);
     CK(cudaGetLastError());
     ph_begin(c, OSVMP2_PH_EIG);
-    launch_eig_osv((double*)Tm.p, b, nv, l_osv, kmax, (double*)Vm.p, (double*)wm.p, (int*)km.p, (double*)sm.p,
-                   c->err_d, tii_tc, c->st);
     {
       const double nd = nv;
       const bool full = (nv <= 160) || (l_osv <= 0.0);
-      ph_end(c, OSVMP2_PH_EIG, (double)b * (full ? 9.0 * nd * nd * nd : (4.0 / 3.0) * nd * nd * nd));
+      const double fl = (double)b * (full ? 9.0 * nd * nd * nd : (4.0 / 3.0) * nd * nd * nd);
+      ph_begin(c, OSVMP2_PH_K_EIG);
+      launch_eig_osv((double*)Tm.p, b, nv, l_osv, kmax, (double*)Vm.p, (double*)wm.p, (int*)km.p, (double*)sm.p,
+                     c->err_d, tii_tc, c->st);
+      ph_end(c, OSVMP2_PH_K_EIG, fl);
+      launch_eig_back((double*)Tm.p, b, nv, l_osv, kmax, (double*)Vm.p, (const int*)km.p, (double*)sm.p, tii_tc,
+                      c->st);
+      ph_end(c, OSVMP2_PH_EIG, fl);
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(kh.data(), km.p, b * sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -1507,7 +1573,9 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
   ph_begin(c, OSVMP2_PH_SOLVE);
   if (prec == OSVMP2_MIXED) {
     CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
+    ph_begin(c, OSVMP2_PH_SIGMA);
     TRY(build_sigma_table(c, sig));
+    ph_end(c, OSVMP2_PH_SIGMA, 0.0);
     const Tables tb = tables(c);
     auto solve = [&](const SolvePlan& pl, cudaStream_t st) {
       SolveOpts o = so;
@@ -1557,6 +1625,7 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
     // private stream, launched on the ctx stream; an instantiated graph is
     // updated in place when only its arguments changed)
     bool graphed = false;
+    ph_begin(c, OSVMP2_PH_K_FRAGSOLVE);
     if (!c->cap_st) cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking);
     if (c->cap_st && cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       solve(it->second, c->cap_st);
@@ -1584,10 +1653,13 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
       solve(it->second, c->st);
       launch_weighted_sum((const FragOut*)d_out.p, (const int*)d_w.p, nf, c->scal_d, c->st);
     }
+    ph_end(c, OSVMP2_PH_K_FRAGSOLVE, 0.0);
   } else {
+    ph_begin(c, OSVMP2_PH_K_FRAGSOLVE);
     launch_frag_solve(tables(c), (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, so, (double*)d_scr.p, n_cta,
                       (int*)d_cnt.p, (FragOut*)d_out.p, tdst, (const long long*)d_toff.p, c->st);
     launch_weighted_sum((const FragOut*)d_out.p, (const int*)d_w.p, nf, c->scal_d, c->st);
+    ph_end(c, OSVMP2_PH_K_FRAGSOLVE, 0.0);
   }
   CK(cudaGetLastError());
   ph_end(c, OSVMP2_PH_SOLVE, 0.0);
@@ -1604,6 +1676,7 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
     f_solve += (prec == OSVMP2_MIXED) ? fragment_mixed_flops(c, c->frags[f], c->frag_out[f].iters)
                                       : c->frag_out[f].iters * fragment_iter_flops(c, c->frags[f]);
   c->flops[OSVMP2_PH_SOLVE] += f_solve;
+  c->flops[OSVMP2_PH_K_FRAGSOLVE] += f_solve;
   int unconv = 0, maxit = 0;
   int64_t worst = -1;
   double maxu = 0.0;

@@ -73,6 +73,10 @@ __host__ __device__ inline size_t eig_osv_scratch_doubles(int nv, int kmax) {
 // mixed-form OSV build, whose T_ii is a split-precision product).
 void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, double* w, int* k,
                     double* scratch, int* err, bool dfl_tridiag, cudaStream_t st);
+// Back-transformation of the kept eigenvectors of the top-k path (n_vir above
+// the shared-memory limit, thr > 0) after launch_eig_osv; a no-op otherwise.
+void launch_eig_back(double* T, int nb, int nv, double thr, int kmax, double* V, const int* k, double* scratch,
+                     bool dfl_tridiag, cudaStream_t st);
 // Copy V[b][:, :k_b] into the packed Q store (Q[i0+b] as [nv][k]).
 void launch_pack_q(const double* V, const double* w, int nb, int nv, int kmax, const int* k,
                    double* const* Qdst, double* const* wdst, cudaStream_t st);

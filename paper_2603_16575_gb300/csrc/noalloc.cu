@@ -11,7 +11,6 @@
 // latency-critical loop in which a cudaMalloc (which may synchronise the
 // device) is unacceptable.
 #include <cstdio>
-#include <mutex>
 
 #include "osvmp2.h"
 #include "eig.cuh"
@@ -61,16 +60,22 @@ __global__ void __launch_bounds__(NT) k_precond_dense(const double* __restrict__
   int rc = cta_syev(Sw, m, m, ws, Z, ldz, e, tau, esm);
   if (threadIdx.x == 0) {
     double smax = 0.0;
-    for (int c = 0; c < m; c++) smax = fmax(smax, ws[c]);
+    bool finite = true;
+    for (int c = 0; c < m; c++) {
+      finite = finite && isfinite(ws[c]);
+      smax = fmax(smax, ws[c]);
+    }
     int r = 0;
     for (int c = 0; c < m; c++)
       if (ws[c] > tau_s * smax) keep[r++] = c;
-    s_r = (rc == 0) ? r : -1;
+    s_r = (rc != 0 || !finite) ? -1 : r;
   }
   __syncthreads();
   const int r = s_r;
-  if (r < 0) {
-    if (threadIdx.x == 0) *r_out = -1;
+  if (r <= 0) {
+    // r == 0: S has no eigenvalue above tau_s * max (e.g. S = 0); nothing to
+    // diagonalise, X and e~ are left untouched
+    if (threadIdx.x == 0) *r_out = r;
     return;
   }
   for (int idx = threadIdx.x; idx < m * r; idx += NT) {
@@ -87,12 +92,12 @@ __global__ void __launch_bounds__(NT) k_precond_dense(const double* __restrict__
   rc = cta_syev(Fp, r, r, w2, Z2, ldz2, e, tau, esm);
   cta_gemm(m, r, r, 1.0, Yv, dense_view(Z2, r, r, ldz2), 0.0, X, m, gsm);
   for (int c = threadIdx.x; c < r; c += NT) et[c] = w2[c];
-  if (threadIdx.x == 0) *r_out = (rc == 0) ? r : -1;
+  if (threadIdx.x == 0) {
+    bool finite = true;
+    for (int c = 0; c < r; c++) finite = finite && isfinite(w2[c]);
+    *r_out = (rc == 0 && finite) ? r : -1;
+  }
 }
-
-// Device address of g_noalloc_scratch, looked up once per device.
-static double* g_scratch_addr[64] = {};
-static std::mutex g_scratch_mu;
 
 }  // namespace osv
 
@@ -112,39 +117,30 @@ extern "C" int osvmp2_precond_noalloc(const double* S, const double* F, int32_t 
     msg(b);
     return OSVMP2_E_ARG;
   }
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+  // Set-up, done on every call with the caller's device and context current:
+  // the device address of the static scratch in this context (host code only
+  // sees a host-side stand-in for the array; a kernel given that stand-in
+  // would read the wrong memory) and the kernel's shared-memory limit.  Both
+  // are look-ups that allocate nothing once the library's module is loaded in
+  // the context; the first call in a context may load it (lazy module
+  // loading), which is why that call should come before any stream capture.
+  // Nothing is cached across calls, so a context that was reset or replaced
+  // (cudaDeviceReset, a plug-in's own context) never sees a stale address.
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, osv::g_noalloc_scratch) != cudaSuccess || !p) {
     cudaGetLastError();
-    msg("osvmp2_precond_noalloc: no current CUDA device");
+    msg("osvmp2_precond_noalloc: cudaGetSymbolAddress of the static scratch failed (no usable CUDA device?)");
     return OSVMP2_E_CUDA;
   }
-  double* scratch;
-  {
-    std::lock_guard<std::mutex> lk(osv::g_scratch_mu);
-    if (!osv::g_scratch_addr[dev]) {
-      // set-up on the first call for this device (with this device current)
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, osv::g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        cudaGetLastError();
-        msg("osvmp2_precond_noalloc: cudaGetSymbolAddress of the static scratch failed");
-        return OSVMP2_E_CUDA;
-      }
-      osv::g_scratch_addr[dev] = static_cast<double*>(p);
-      const size_t smem = (size_t)(osv::GEMM_SMEM_DOUBLES + 4 * OSVMP2_NOALLOC_MAX_M + 64 +
-                                   osv::NOALLOC_ZMAX * (osv::NOALLOC_ZMAX + 1)) * sizeof(double);
-      if (cudaFuncSetAttribute(osv::k_precond_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess) {
-        cudaGetLastError();
-        osv::g_scratch_addr[dev] = nullptr;
-        msg("osvmp2_precond_noalloc: cudaFuncSetAttribute failed");
-        return OSVMP2_E_CUDA;
-      }
-    }
-    scratch = osv::g_scratch_addr[dev];
-  }
+  double* scratch = static_cast<double*>(p);
   const size_t smem = (size_t)(osv::GEMM_SMEM_DOUBLES + 4 * OSVMP2_NOALLOC_MAX_M + 64 +
                                osv::NOALLOC_ZMAX * (osv::NOALLOC_ZMAX + 1)) * sizeof(double);
+  if (cudaFuncSetAttribute(osv::k_precond_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    msg("osvmp2_precond_noalloc: cudaFuncSetAttribute failed");
+    return OSVMP2_E_CUDA;
+  }
   osv::k_precond_dense<<<1, osv::NT, smem, (cudaStream_t)cuda_stream>>>(S, F, m, tau_s, X, et, r_dev, scratch);
   osv::note_launch(1);
   const cudaError_t e = cudaGetLastError();

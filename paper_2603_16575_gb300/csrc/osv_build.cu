@@ -540,32 +540,41 @@ __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double th
   }
 }
 
+// Warps of 32 x 33-double tiles in the shared memory of the top-k path's
+// symmetric tridiagonalisation (0 when fewer than two fit).
+static int eig_tile_warps(int nv, double thr) {
+  if (nv <= ZSMEM_MAX || !(thr > 0.0)) return 0;
+  const size_t cap = (size_t)224 * 1024 / sizeof(double), base = (size_t)4 * nv + 64, tile = 32 * 33;
+  const int ntw = cap > base ? (int)std::min<size_t>(NT_EIG / 32, (cap - base) / tile) : 0;
+  return ntw >= 2 ? ntw : 0;
+}
+
 void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, double* w, int* k,
                     double* scratch, int* err, bool dfl_tridiag, cudaStream_t st) {
   const int zsmem = nv <= ZSMEM_MAX;
   size_t smem = (size_t)(4 * nv + 64) * sizeof(double);
-  int ntw = 0;
+  const int ntw = eig_tile_warps(nv, thr);
   if (zsmem) smem += (size_t)nv * (nv + 1) * sizeof(double);
-  else if (thr > 0.0) {   // tiles of the symmetric tridiagonalisation: one warp per 32 x 33 doubles that fit
-    const size_t cap = (size_t)224 * 1024 / sizeof(double), base = (size_t)4 * nv + 64, tile = 32 * 33;
-    ntw = cap > base ? (int)std::min<size_t>(NT_EIG / 32, (cap - base) / tile) : 0;
-    if (ntw >= 2) smem += (size_t)ntw * tile * sizeof(double);
-  }
+  else if (ntw >= 2) smem += (size_t)ntw * 32 * 33 * sizeof(double);
   cudaFuncSetAttribute(k_eig_osv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_eig_osv<<<nb, NT_EIG, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem, ntw, dfl_tridiag ? 1 : 0);
   note_launch(1);
-  if (!zsmem && thr > 0.0) {
-    dim3 grid(nb, (std::min(kmax, nv) + EB_WARPS - 1) / EB_WARPS);
-    const size_t ss = eig_osv_scratch_doubles(nv, kmax);
-    if (dfl_tridiag && ntw >= 2 && nv <= EB_DF_MAXN) {   // reflectors stored as pairs
-      if (nv <= 640) k_eig_back_df<20><<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
-      else if (nv <= 1280) k_eig_back_df<40><<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
-      else k_eig_back_df<48><<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
-    } else {
-      k_eig_back<<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
-    }
-    note_launch(1);
+}
+
+void launch_eig_back(double* T, int nb, int nv, double thr, int kmax, double* V, const int* k, double* scratch,
+                     bool dfl_tridiag, cudaStream_t st) {
+  if (nv <= ZSMEM_MAX || !(thr > 0.0)) return;   // the other paths form the eigenvectors in k_eig_osv
+  const int ntw = eig_tile_warps(nv, thr);
+  dim3 grid(nb, (std::min(kmax, nv) + EB_WARPS - 1) / EB_WARPS);
+  const size_t ss = eig_osv_scratch_doubles(nv, kmax);
+  if (dfl_tridiag && ntw >= 2 && nv <= EB_DF_MAXN) {   // reflectors stored as pairs
+    if (nv <= 640) k_eig_back_df<20><<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
+    else if (nv <= 1280) k_eig_back_df<40><<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
+    else k_eig_back_df<48><<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
+  } else {
+    k_eig_back<<<grid, EB_WARPS * 32, 0, st>>>(T, nv, kmax, V, k, scratch, ss);
   }
+  note_launch(1);
 }
 
 __global__ void k_pack_q(const double* V, const double* w, int nv, int kmax, const int* k,

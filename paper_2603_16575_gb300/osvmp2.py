@@ -20,14 +20,15 @@ OSVMP2_FP64 = 0
 OSVMP2_MIXED = 1
 PREC = {"fp64": OSVMP2_FP64, "mixed": OSVMP2_MIXED}
 
-STATUS = {0: "OK", 1: "E_ARG", 2: "E_CUDA", 3: "E_NOMEM", 4: "E_NOCONV", 5: "E_NUMERIC", 6: "E_STATE"}
+STATUS = {0: "OK", 1: "E_ARG", 2: "E_CUDA", 3: "E_NOMEM", 4: "E_NOCONV", 5: "E_NUMERIC", 6: "E_STATE",
+          7: "E_TIMEOUT"}
 STATUS_CODES = {v: k for k, v in STATUS.items()}
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("tau_s", ctypes.c_double), ("tol_update", ctypes.c_double), ("tol_energy", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("osv_prec", ctypes.c_int32), ("no_autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("mem_cap_mib", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class System(ctypes.Structure):
@@ -158,12 +159,30 @@ NOALLOC_MAX_M = 256
 
 def precond_noalloc(S, F, tau_s, X, et, r, stream=None) -> None:
     """Allocation-free preconditioner of one pair (osvmp2_precond_noalloc): S, F
-    [m, m] float64 CUDA tensors in, X [m, m], et [m] float64 and r [1] int32 CUDA
-    tensors out (preallocated by the caller).  Raises on a non-OK status."""
+    [m, m] float64 CUDA tensors in, X [m, m], et [>= m] float64 and r [>= 1] int32
+    CUDA tensors out, preallocated by the caller on the same device.  r receives
+    the number of kept directions (0 if S has none above tau_s * max, -1 if an
+    eigen-solve failed or met a non-finite value).  Raises TypeError or
+    ValueError for tensors of the wrong kind or size (the kernel would otherwise
+    write past their end), OSVMP2Error on a non-OK status."""
     import torch
-    _need_f64_cuda(S, "S")
-    _need_f64_cuda(F, "F")
+    for t, name in ((S, "S"), (F, "F"), (X, "X"), (et, "et")):
+        _need_f64_cuda(t, name)
+    if not (isinstance(r, torch.Tensor) and r.is_cuda and r.dtype == torch.int32):
+        raise TypeError("r must be an int32 CUDA tensor")
+    if S.dim() != 2 or S.shape[0] != S.shape[1]:
+        raise ValueError(f"S must be square, got {tuple(S.shape)}")
     m = S.shape[0]
+    if tuple(F.shape) != (m, m):
+        raise ValueError(f"F must have S's shape {(m, m)}, got {tuple(F.shape)}")
+    if tuple(X.shape) != (m, m):
+        raise ValueError(f"X must be [{m}, {m}], got {tuple(X.shape)}")
+    if et.numel() < m:
+        raise ValueError(f"et needs at least {m} entries, got {et.numel()}")
+    if r.numel() < 1:
+        raise ValueError("r needs one element")
+    if len({t.device for t in (S, F, X, et, r)}) != 1:
+        raise ValueError("S, F, X, et and r must be on one device")
     st = stream if stream is not None else torch.cuda.current_stream(S.device).cuda_stream
     buf = ctypes.create_string_buffer(256)
     code = lib().osvmp2_precond_noalloc(_ptr(S), _ptr(F), m, tau_s, _ptr(X), _ptr(et), _ptr(r), st, buf, 256)
@@ -303,7 +322,7 @@ class Context:
         return e.value, st.as_dict()
 
     PHASES = ["tii", "eig", "sf", "project", "exchange", "precond", "solve", "mbe_sum", "subsolve", "grad",
-              "spare10", "spare11"]
+              "k_gproj", "k_eig", "k_fragsolve", "sigma", "spare14", "spare15"]
 
     def profile(self, reset: bool = False):
         """Per-phase {name: (ms, flops, bytes, calls)} accumulated since the last reset."""

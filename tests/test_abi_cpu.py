@@ -69,3 +69,16 @@ def test_bad_arguments_are_rejected(lib):
     n = ctypes.c_int64(0)
     assert lib.osvmp2_mbe3_fragments(None, 3, 1.0, 1.0, 0, None, None, ctypes.byref(n)) == 1
     assert lib.osvmp2_create(None, 0, None, None) == 1
+
+
+def test_status_codes_match_the_header(lib):
+    """The binding's status table is the header's enum (E_TIMEOUT included), and the
+    options struct has the header's size (56 bytes)."""
+    from paper_2603_16575_gb300 import osvmp2
+    h = open(os.path.join(ROOT, "include", "osvmp2.h")).read()
+    enum = dict((name, int(v)) for name, v in re.findall(r"OSVMP2_(OK|E_[A-Z]+)\s*=\s*(\d+)", h))
+    assert enum["E_TIMEOUT"] == 7
+    assert {v: k for k, v in enum.items()} == osvmp2.STATUS
+    assert ctypes.sizeof(osvmp2.Opts) == 56
+    o = osvmp2.default_opts()
+    assert o.mem_cap_mib == 0

@@ -74,6 +74,39 @@ def test_osv_diagonalises_tii(l_osv):
         assert np.all(Q[big, np.arange(Q.shape[1])] > 0)
 
 
+def test_semicanonical_tii_is_the_single_orbital_amplitude():
+    """Eq. mp2_tmat at i = j: the amplitude of a one-orbital cluster (Eq. res_close with
+    k = i only, which keeps f_ii alone even for a non-diagonal Fock block) is
+    T_ii^ab = K_ii^ab / (2 f_ii - e_a - e_b).  Obtained here from the untruncated
+    iterative solve (pinned to the closed form, and independent of the OSVs' T_ii once
+    they span the whole space), its negative must be the semi-canonical T_ii of
+    Eq. mp2_tkk under reading R4."""
+    s = synth.make_system(3, 14, 40, seed=37, lam=2.0, f_off=3e-2)
+    o = oracle.OSVSystem(s.B_block, 3, s.e_vir, s.f_occ, l_osv=0.0)
+    for i in range(3):
+        r = o.solve((i,), tol=1e-14, e_tol=1e-16, max_iter=200)
+        T_full = o.Q[i] @ r.T[(i, i)] @ o.Q[i].T
+        Ts = oracle.semicanonical_tii(s.B_block(i), s.e_vir, s.f_occ[i, i])
+        assert np.abs(-T_full - Ts).max() < 1e-11 * np.abs(Ts).max()
+
+
+@pytest.mark.parametrize("slip", ["f_ii for 2 f_ii", "sign of the denominator"])
+def test_planted_tii_mistakes_fail_the_amplitude_pin(monkeypatch, slip):
+    """A dropped factor 2 on f_ii, or the opposite sign of Eq. mp2_tkk's literal form,
+    fails the one-orbital amplitude pin above."""
+    s = synth.make_system(2, 14, 40, seed=37, lam=2.0, f_off=3e-2)
+    o = oracle.OSVSystem(s.B_block, 2, s.e_vir, s.f_occ, l_osv=0.0)
+    r = o.solve((0,), tol=1e-14, e_tol=1e-16, max_iter=200)
+    T_full = o.Q[0] @ r.T[(0, 0)] @ o.Q[0].T
+    if slip == "f_ii for 2 f_ii":
+        bad = lambda B, e, f: (B @ B.T) / (e[:, None] + e[None, :] - f)
+    else:
+        bad = lambda B, e, f: (B @ B.T) / (2.0 * f - e[:, None] - e[None, :])
+    monkeypatch.setattr(oracle, "semicanonical_tii", bad)
+    Ts = oracle.semicanonical_tii(s.B_block(0), s.e_vir, s.f_occ[0, 0])
+    assert np.abs(-T_full - Ts).max() > 1e-3 * np.abs(Ts).max()
+
+
 def test_preconditioner_invariants():
     s = synth.make_system(3, 14, 30, seed=4, lam=3.0)
     o = oracle.OSVSystem(s.B_block, 3, s.e_vir, s.f_occ, l_osv=1e-4)
@@ -238,7 +271,7 @@ def test_gradient_matches_central_differences():
     h = 1e-5
     rng = np.random.default_rng(3)
     scale = np.abs(dB).max()
-    for _ in range(12):
+    for _ in range(200):
         i, a, p = rng.integers(4), rng.integers(10), rng.integers(16)
         Bp, Bm = Bs.copy(), Bs.copy()
         Bp[i, a, p] += h
