@@ -34,8 +34,8 @@ R2_CUT, R3_CUT, L_OSV = 8.0, 6.0, 1e-4
 # Denominators the peaks file does not carry, measured on this GB300 pool with
 # `python bench.py --measure-peaks` (torch GEMMs at 8192^3, best of 10, CUDA
 # events); the figures and the run are in profiles/peaks_fp64_tf32_fp32.md.
-MEASURED_GEMM_PEAKS = {"fp64_tflops": 1.10, "tf32_tflops": 1021.0, "fp32_tflops": None,
-                       "source": "round-trip torch.matmul 8192^3 on a GB300 of this pool"}
+MEASURED_GEMM_PEAKS = {"fp64_tflops": 1.099, "tf32_tflops": 1037.8, "fp32_tflops": 69.86,
+                       "source": "torch.matmul 8192^3 on a GB300 of this pool, best of 10"}
 FP32_SIMT_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12    # 128 FFMA/clk/SM at the 2070 MHz maximum -> 80.5
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernels,
 # from one ncu capture on the 48-orbital case scaled to the bench workload by the

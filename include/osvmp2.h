@@ -265,8 +265,8 @@ int osvmp2_generate_B(int32_t n_occ, int32_t n_vir, int32_t n_aux, uint64_t seed
  *   et_dev       : device [m], entries 0..r-1 written               (out)
  *   r_dev        : device int32, r (out): the number of kept directions; 0 if S has no
  *                  eigenvalue above tau_s * max (e.g. S = 0: X and e~ are then not
- *                  written); -1 if an eigen-solve failed or an eigenvalue of S or of
- *                  Y^T F Y is not finite (NaN or Inf in S or F)
+ *                  written); -1 if S or F holds a NaN or Inf, or an eigen-solve
+ *                  failed or gave a non-finite eigenvalue
  *   cuda_stream  : cudaStream_t to queue the single kernel on (NULL = legacy default)
  *   err, err_len : optional host buffer for a one-line error message
  * Returns OSVMP2_E_ARG (with a message) for null pointers, tau_s < 0, or m outside

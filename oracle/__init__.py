@@ -10,4 +10,6 @@ from .osv_mp2 import (  # noqa: F401
     exchange_block, preconditioner, Fragment, FragmentResult, solve_fragment,
     solve_fragment_dense, canonical_mp2_energy, dist2, mbe3_fragments,
     OSVSystem, fragment_gradient, mbe3_energy_gradient,
+    s2b_metric, s2b_matrix, s3b_metric, Screen, screened_fragments, mbe3_diagonal_amplitudes,
+    WeakResult, weak_pair, weak_residual, mbe3_screened_energy,
 )

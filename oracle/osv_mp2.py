@@ -37,6 +37,14 @@ reason, in the design notes):
       eigenvector signed so its largest-magnitude entry is positive
   R10 fragments: pairs with d^2 <= r2^2, triples whose three pairs all satisfy
       d^2 <= r3^2 (and are kept pairs); squared distances summed x, y, z in order
+  R16 screened clusters: close pairs s2b >= 1e-2, weak 1e-7 <= s2b < 1e-2; a
+      triple is a candidate only when its three pairs are close, kept when
+      s3b >= 0.2 (keeps the cluster list closed under subsets)
+  R17 the garbled weak-pair residual, Eq. (res_weak), is read as
+      K + F_(i,i) T + T F_(j,j) - (f_ii + f_jj) T - f_ij [T_(i,i) S_(i,j) + S_(i,j) T_(j,j)]
+      (the full residual projected onto Q_i x Q_j with k restricted to {i, j})
+  R18 weak-pair energy: 2 <K_(i,j), T_(i,j)> per ordered pair, both orders
+      counted, with T_(i,i) the MBE(3) diagonal amplitude of Eq. (tmbediag)
 """
 from __future__ import annotations
 
@@ -435,3 +443,144 @@ def mbe3_energy_gradient(osys: OSVSystem, r_occ: np.ndarray, r2: float, r3: floa
         de += c * ge
         df += c * gf
     return E, dB, de, df
+
+
+# --------------------------------------------------------------------------
+# Pair screening and weak pairs: Eqs. (s2b), (s3b), (osv_weak_k), (res_weak);
+# the weak-pair branch of Algorithm 7
+# --------------------------------------------------------------------------
+def s2b_metric(Q: Sequence[np.ndarray], i: int, j: int) -> float:
+    """s2b_ij = sum_{mu nu} <mu_i|nu_j>^2 / sqrt(n_i n_j)   (Eq. s2b)."""
+    S = Q[i].T @ Q[j]
+    return float(np.sum(S * S)) / np.sqrt(Q[i].shape[1] * Q[j].shape[1])
+
+
+def s2b_matrix(Q: Sequence[np.ndarray]) -> np.ndarray:
+    n = len(Q)
+    M = np.ones((n, n))
+    for i in range(n):
+        for j in range(i + 1, n):
+            M[i, j] = M[j, i] = s2b_metric(Q, i, j)
+    return M
+
+
+def s3b_metric(s2b: np.ndarray, i: int, j: int, k: int) -> float:
+    """s3b_ijk = (s2b_ij + s2b_ik + s2b_jk) / 3   (Eq. s3b)."""
+    return (s2b[i, j] + s2b[i, k] + s2b[j, k]) / 3.0
+
+
+@dataclasses.dataclass
+class Screen:
+    """Pair-class cuts of Section 3.4: distant below s2b_distant, weak up to
+    s2b_close, close above; triples of close pairs kept when s3b >= s3b_min."""
+    s2b_distant: float = 1e-7
+    s2b_close: float = 1e-2
+    s3b_min: float = 0.2
+
+
+def screened_fragments(s2b: np.ndarray, scr: Screen):
+    """Clusters and weak pairs selected by s2b / s3b (reading R16).
+
+    close pairs: s2b >= s2b_close; weak pairs: s2b_distant <= s2b < s2b_close;
+    triples: all three pairs close and s3b >= s3b_min (so every kept cluster's
+    sub-clusters are kept).  Weights are the inclusion-exclusion weights of
+    Eqs. (tmbediag)-(deltaoff), as in mbe3_fragments.  Returns
+    (list of (orbs, weight) -- singles, pairs, triples, each lexicographic --,
+     list of weak pairs (i, j), i < j, lexicographic)."""
+    n = s2b.shape[0]
+    close = [(i, j) for i in range(n) for j in range(i + 1, n) if s2b[i, j] >= scr.s2b_close]
+    weak = [(i, j) for i in range(n) for j in range(i + 1, n) if scr.s2b_distant <= s2b[i, j] < scr.s2b_close]
+    is_close = np.zeros((n, n), dtype=bool)
+    for (i, j) in close:
+        is_close[i, j] = is_close[j, i] = True
+    triples = [(i, j, k) for i in range(n) for j in range(i + 1, n) if is_close[i, j]
+               for k in range(j + 1, n) if is_close[i, k] and is_close[j, k] and s3b_metric(s2b, i, j, k) >= scr.s3b_min]
+    return _weighted(n, close, triples), weak
+
+
+def _weighted(n, pairs, triples):
+    tri_per_pair: Dict[Pair, int] = {}
+    tri_per_orb = np.zeros(n, dtype=np.int64)
+    pair_per_orb = np.zeros(n, dtype=np.int64)
+    for (i, j) in pairs:
+        pair_per_orb[i] += 1
+        pair_per_orb[j] += 1
+    for (i, j, k) in triples:
+        for p in ((i, j), (i, k), (j, k)):
+            tri_per_pair[p] = tri_per_pair.get(p, 0) + 1
+        for x in (i, j, k):
+            tri_per_orb[x] += 1
+    frags = [((i,), int(1 - pair_per_orb[i] + tri_per_orb[i])) for i in range(n)]
+    frags += [((i, j), int(1 - tri_per_pair.get((i, j), 0))) for (i, j) in pairs]
+    frags += [(t, 1) for t in triples]
+    return frags
+
+
+def mbe3_diagonal_amplitudes(results, frags) -> Dict[int, np.ndarray]:
+    """T_(ii,ii) in the basis Q_i from the cluster amplitudes, Eq. (tmbediag):
+    T^i + sum_k dT^{i,k} + sum_{k>l} dT^{i,k,l} = sum over kept clusters C that
+    contain i of c_C T^C_(ii,ii)."""
+    out: Dict[int, np.ndarray] = {}
+    for res, (orbs, c) in zip(results, frags):
+        for i in orbs:
+            t = c * res.T[(i, i)]
+            out[i] = out[i] + t if i in out else t
+    return out
+
+
+@dataclasses.dataclass
+class WeakResult:
+    pair: Pair
+    energy: float          # both orders of the pair
+    T: np.ndarray          # T_(i,j) in the single-block basis Q_i (rows) x Q_j (columns)
+
+
+def weak_pair(Q: Sequence[np.ndarray], Bfun: Callable[[int], np.ndarray], f_occ: np.ndarray,
+              e_vir: np.ndarray, i: int, j: int, T_ii: np.ndarray, T_jj: np.ndarray) -> WeakResult:
+    """Non-iterative weak-pair amplitude and energy (Algorithm 7, weak pairs).
+
+    K_(i,j) = Gamma~_i^{mu_i} Gamma~_j^{nu_j}            (Eq. osv_weak_k)
+    R_(i,j) = K_(i,j) + F_(i,i) T + T F_(j,j) - (f_ii + f_jj) T
+              - f_ij [T_(i,i) S_(i,j) + S_(i,j) T_(j,j)]   (Eq. res_weak, reading R17)
+    With S_(i,i) = 1 the preconditioner of the diagonal pair diagonalises
+    F_(i,i) (Eq. prec_eig), so one update from T = 0 solves R = 0 exactly:
+    T = X_i [X_i^T R(0) X_j / (f_ii + f_jj - e~_i - e~_j)] X_j^T.
+    Energy: 2 <K_(i,j), T> per ordered pair with the exchange term dropped
+    (reading R18), both orders counted."""
+    Li = Q[i].T @ Bfun(i)          # OSV-projected integrals of Eq. (osv_imua), diagonal blocks only
+    Lj = Q[j].T @ Bfun(j)
+    K = Li @ Lj.T
+    S = Q[i].T @ Q[j]
+    Fii = Q[i].T @ (e_vir[:, None] * Q[i])
+    Fjj = Q[j].T @ (e_vir[:, None] * Q[j])
+    Xi, Ei = preconditioner(Q[i].T @ Q[i], Fii, 0.0)
+    Xj, Ej = preconditioner(Q[j].T @ Q[j], Fjj, 0.0)
+    R0 = K - f_occ[i, j] * (T_ii @ S + S @ T_jj)
+    D = f_occ[i, i] + f_occ[j, j] - Ei[:, None] - Ej[None, :]
+    T = Xi @ ((Xi.T @ R0 @ Xj) / D) @ Xj.T
+    return WeakResult((i, j), 4.0 * float(np.sum(K * T)), T)
+
+
+def weak_residual(Q, Bfun, f_occ, e_vir, i, j, T, T_ii, T_jj) -> np.ndarray:
+    """R_(i,j) of Eq. (res_weak) (reading R17) for a given T_(i,j)."""
+    K = (Q[i].T @ Bfun(i)) @ (Q[j].T @ Bfun(j)).T
+    S = Q[i].T @ Q[j]
+    Fii = Q[i].T @ (e_vir[:, None] * Q[i])
+    Fjj = Q[j].T @ (e_vir[:, None] * Q[j])
+    return (K + Fii @ T + T @ Fjj - (f_occ[i, i] + f_occ[j, j]) * T
+            - f_occ[i, j] * (T_ii @ S + S @ T_jj))
+
+
+def mbe3_screened_energy(osys: "OSVSystem", scr: Screen, **kw):
+    """MBE(3) energy with the paper's cluster selection (Section 3.4) and the
+    weak pairs of Algorithm 7: E = sum_C c_C E_C + sum_weak E_ij.
+    Returns (E, E_weak, per-fragment [(orbs, c, E_C)], [WeakResult], s2b)."""
+    s2b = s2b_matrix(osys.Q)
+    frags, weak = screened_fragments(s2b, scr)
+    results = [osys.solve(orbs, **kw) for orbs, _ in frags]
+    E = sum(c * r.energy for (orbs, c), r in zip(frags, results))
+    Tdiag = mbe3_diagonal_amplitudes(results, frags)
+    wres = [weak_pair(osys.Q, osys.B, osys.f_occ, osys.e_vir, i, j, Tdiag[i], Tdiag[j]) for (i, j) in weak]
+    E_weak = sum(w.energy for w in wres)
+    per = [(orbs, c, r.energy) for (orbs, c), r in zip(frags, results)]
+    return E + E_weak, E_weak, per, wres, s2b

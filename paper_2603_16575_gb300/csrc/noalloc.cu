@@ -50,11 +50,19 @@ __global__ void __launch_bounds__(NT) k_precond_dense(const double* __restrict__
   double* tau = e + m;
   double* ws = tau + m;
   double* w2 = ws + m;
+  int bad = 0;
   for (int idx = threadIdx.x; idx < m * m; idx += NT) {
-    Sw[idx] = S[idx];
-    Fw[idx] = F[idx];
+    const double sv = S[idx], fv = F[idx];
+    bad |= !isfinite(sv) || !isfinite(fv);
+    Sw[idx] = sv;
+    Fw[idx] = fv;
   }
-  __syncthreads();
+  // a NaN or Inf in S or F is refused up front: the eigen-solver's scalings
+  // (fmax over magnitudes) would otherwise drop it silently
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0) *r_out = -1;
+    return;
+  }
   double* Z = (m <= NOALLOC_ZMAX) ? zsm : Zg;
   const int ldz = (m <= NOALLOC_ZMAX) ? m + 1 : m;
   int rc = cta_syev(Sw, m, m, ws, Z, ldz, e, tau, esm);
