@@ -109,7 +109,18 @@ typedef struct {
   int64_t worst_fragment;              /* index of the first unconverged fragment, or -1 */
   double max_update;                   /* largest final max|R~/D| over fragments */
   double flops;                        /* algorithmic FP operations of A1-A5 in this call */
+  int64_t n_weak;                      /* weak pairs (osvmp2_mbe3_energy_screened; 0 otherwise) */
 } osvmp2_mbe_stats;
+
+/* Pair-class cuts of the paper's cluster selection (Section 3.4), applied to
+ * s2b_ij = sum_{mu nu} <mu_i|nu_j>^2 / sqrt(n_i n_j) (Eq. s2b). */
+typedef struct {
+  double s2b_distant;  /* pairs with s2b below this are distant and dropped      (paper: 1e-7) */
+  double s2b_close;    /* pairs with s2b >= this are close (MBE clusters); the
+                          rest are weak (single-block, non-iterative)            (paper: 1e-2) */
+  double s3b_min;      /* a triple of three close pairs is kept when
+                          s3b = (s2b_ij + s2b_ik + s2b_jk) / 3 >= this (Eq. s3b) (paper: 0.2)  */
+} osvmp2_screen;
 
 /* ---- context ------------------------------------------------------------ */
 
@@ -201,6 +212,33 @@ int osvmp2_fragment_results(osvmp2_ctx *ctx, int64_t *n_frag_out, int32_t *orbs,
 int osvmp2_mbe3_fragments(const double *r_occ, int32_t n_occ, double r2_cut, double r3_cut,
                           int64_t cap, int32_t *orbs_out, int32_t *weights_out, int64_t *n_out);
 
+/* ---- A5 with the paper's cluster selection (Section 3.4; Eqs. s2b, s3b) ----
+ * s2b of every pair i < j, computed on the GPU in FP64 from the OSVs of the
+ * last osvmp2_build_osv.  Host outputs, each may be NULL: s2b_out [n_occ][n_occ]
+ * (symmetric, diagonal 1), class_out [n_occ][n_occ] (2 close, 1 weak, 0 distant;
+ * diagonal 2), counts [3] (close, weak, distant pairs i < j). */
+int osvmp2_pair_screening(osvmp2_ctx *ctx, const osvmp2_screen *scr, double *s2b_out, int32_t *class_out,
+                          int64_t *counts);
+
+/* MBE(3) energy over the clusters the screening selects -- every single, every
+ * close pair, every triple of close pairs with s3b >= s3b_min, weights as in
+ * osvmp2_mbe3_energy -- plus the weak pairs (Algorithm 7, weak branch): for
+ * each weak pair the single-block residual (Eq. res_weak, read as
+ * K_(i,j) + F_(i,i) T + T F_(j,j) - (f_ii + f_jj) T - f_ij [T_(i,i) S_(i,j) + S_(i,j) T_(j,j)]
+ * with K_(i,j) from Eq. osv_weak_k and T_(i,i) the MBE(3) diagonal amplitude of
+ * Eq. tmbediag) solved in one update in the eigenbases of F_(i,i), F_(j,j); its
+ * energy 2 <K_(i,j), T_(i,j)> per ordered pair, both orders counted.  The
+ * weak-pair arithmetic is FP64 in both forms; prec selects the clusters' form.
+ * e_out (host) = cluster sum + weak sum; e_weak_out (host, nullable) = weak sum.
+ * Distances (r_occ) are not used. */
+int osvmp2_mbe3_energy_screened(osvmp2_ctx *ctx, const osvmp2_screen *scr, osvmp2_prec prec, double *e_out,
+                                double *e_weak_out, osvmp2_mbe_stats *stats);
+
+/* Weak pairs of the last osvmp2_mbe3_energy_screened (empty after other calls):
+ * *n_out = count; pairs (host [n][2], i < j, lexicographic) and energies
+ * (host [n], both orders) may be NULL. */
+int osvmp2_weak_results(osvmp2_ctx *ctx, int64_t *n_out, int32_t *pairs, double *energies);
+
 /* ---- A6: frozen-OSV gradient --------------------------------------------
  * MBE(3) energy as osvmp2_mbe3_energy, plus (device outputs, each may be NULL):
  *   dE_dB [n_occ][n_vir][n_aux]: dE/dB[i,a,P] = 4 sum_C c_C sum_j (T~_ij^C B_j)[a,P]
@@ -231,6 +269,8 @@ enum {
                               back-transformation (inside EIG) */
   OSVMP2_PH_K_FRAGSOLVE = 12, /* A4: the persistent fragment solve and its energy sum (inside SOLVE) */
   OSVMP2_PH_SIGMA = 13,    /* mixed A4 set-up: pair-couple overlaps on the tensor cores (inside SOLVE) */
+  OSVMP2_PH_WEAK = 14,     /* weak pairs: diagonal amplitudes, S blocks, K_(i,j), solve */
+  OSVMP2_PH_SCREEN = 15,   /* s2b of every pair */
   OSVMP2_NPHASE = 16
 };
 /* Accumulated since the last reset, per phase (host arrays of OSVMP2_NPHASE, any

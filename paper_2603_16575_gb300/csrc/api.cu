@@ -121,6 +121,8 @@ struct osvmp2_ctx {
   // last MBE call
   std::vector<Frag> frags;
   std::vector<FragOut> frag_out;
+  std::vector<std::pair<int, int>> weak;   // weak pairs of the last screened call
+  std::vector<double> weak_e;              // and their energies (both orders)
   // per-phase device time (CUDA events on st) and algorithmic flops, accumulated
   // a phase may be entered several times between collections (batched
   // launches): each entry takes the next (begin, end) pair of its event pool
@@ -280,7 +282,7 @@ void free_system(osvmp2_ctx* c) {
   c->U_h.clear(); c->Gi_h.clear(); c->Gj_h.clear(); c->Sh_h.clear(); c->Gh_h.clear();
   c->us_base_h.clear(); c->us_alloc_rows_h.clear(); c->us_row_h.clear();
   c->m_h.clear(); c->pi_h.clear(); c->pj_h.clear();
-  c->frags.clear(); c->frag_out.clear();
+  c->frags.clear(); c->frag_out.clear(); c->weak.clear(); c->weak_e.clear();
   c->n_osv_d = nullptr; c->Q_d = nullptr; c->sf_id_d = nullptr; c->S_d = c->F_d = nullptr;
   c->pair_id_d = nullptr; c->K_d = c->X_d = c->et_d = c->Kt_d = nullptr; c->r_d = nullptr; c->U_d = nullptr;
   c->Sh_d = c->Gh_d = nullptr;
@@ -402,6 +404,51 @@ void enumerate_fragments(const double* r, int n, double r2, double r3, std::vect
       if (!ok3[(size_t)i * n + j]) continue;
       for (int k = j + 1; k < n; k++) {
         if (!ok3[(size_t)i * n + k] || !ok3[(size_t)j * n + k]) continue;
+        triples.push_back(Frag{{i, j, k}, 1});
+        tri_cnt[i]++; tri_cnt[j]++; tri_cnt[k]++;
+        tri_pair[(size_t)i * n + j]++;
+        tri_pair[(size_t)i * n + k]++;
+        tri_pair[(size_t)j * n + k]++;
+      }
+    }
+  for (int i = 0; i < n; i++) out.push_back(Frag{{i, -1, -1}, 1 - pair_cnt[i] + tri_cnt[i]});
+  for (auto& p : pairs) {
+    p.weight = 1 - tri_pair[(size_t)p.orbs[0] * n + p.orbs[1]];
+    out.push_back(p);
+  }
+  for (auto& t : triples) out.push_back(t);
+}
+
+// Clusters selected by s2b / s3b (Section 3.4): close pairs s2b >= close, weak
+// pairs distant <= s2b < close, triples of three close pairs with
+// (s2b_ij + s2b_ik + s2b_jk) / 3 >= s3b_min; weights as in enumerate_fragments.
+// s2b: host [n][n], symmetric.
+void screened_fragments(const double* s2b, int n, const osvmp2_screen& sc, std::vector<Frag>& out,
+                        std::vector<std::pair<int, int>>& weak) {
+  out.clear();
+  weak.clear();
+  std::vector<unsigned char> close((size_t)n * n, 0);
+  std::vector<int> pair_cnt(n, 0), tri_cnt(n, 0), tri_pair((size_t)n * n, 0);
+  std::vector<Frag> pairs, triples;
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) {
+      const double v = s2b[(size_t)i * n + j];
+      if (v >= sc.s2b_close) {
+        close[(size_t)i * n + j] = close[(size_t)j * n + i] = 1;
+        pairs.push_back(Frag{{i, j, -1}, 0});
+        pair_cnt[i]++;
+        pair_cnt[j]++;
+      } else if (v >= sc.s2b_distant) {
+        weak.push_back({i, j});
+      }
+    }
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) {
+      if (!close[(size_t)i * n + j]) continue;
+      for (int k = j + 1; k < n; k++) {
+        if (!close[(size_t)i * n + k] || !close[(size_t)j * n + k]) continue;
+        const double s3 = (s2b[(size_t)i * n + j] + s2b[(size_t)i * n + k] + s2b[(size_t)j * n + k]) / 3.0;
+        if (!(s3 >= sc.s3b_min)) continue;
         triples.push_back(Frag{{i, j, k}, 1});
         tri_cnt[i]++; tri_cnt[j]++; tri_cnt[k]++;
         tri_pair[(size_t)i * n + j]++;
@@ -982,6 +1029,96 @@ int ensure_pairs_impl(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& req
   return 0;
 }
 
+// S/F blocks (x < y) that are not built yet, without the pair data around them
+// (the weak pairs need S_(i,j) only).
+int ensure_sf_blocks_impl(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& blocks) {
+  const int n = c->sys.n_occ;
+  std::vector<SFJob> sfj;
+  size_t dbl = 0;
+  for (auto& b : blocks) {
+    const size_t id = (size_t)b.first * n + b.second;
+    if (c->sf_id[id] == -1) {
+      c->sf_id[id] = -2;
+      sfj.push_back(SFJob{b.first, b.second, nullptr, nullptr});
+      dbl += 2 * (size_t)c->n_osv[b.first] * c->n_osv[b.second];
+    }
+  }
+  if (sfj.empty()) return 0;
+  double* mem = nullptr;
+  TRY(palloc(c, &mem, dbl));
+  size_t off = 0;
+  double fl = 0.0;
+  for (auto& j : sfj) {
+    const size_t sz = (size_t)c->n_osv[j.x] * c->n_osv[j.y];
+    j.S = mem + off;
+    j.F = mem + off + sz;
+    off += 2 * sz;
+    c->sf_id[(size_t)j.x * n + j.y] = (int)c->S_h.size();
+    c->S_h.push_back(j.S);
+    c->F_h.push_back(j.F);
+    fl += 4.0 * c->sys.n_vir * (double)c->n_osv[j.x] * c->n_osv[j.y];
+  }
+  TRY(upload(c, c->sf_id_d, c->sf_id));
+  TRY(upload(c, c->S_d, c->S_h));
+  TRY(upload(c, c->F_d, c->F_h));
+  Tmp jd;
+  TRY(tmp_alloc(c, jd, sfj.size() * sizeof(SFJob)));
+  CK(cudaMemcpyAsync(jd.p, sfj.data(), sfj.size() * sizeof(SFJob), cudaMemcpyHostToDevice, c->st));
+  ph_begin(c, OSVMP2_PH_SF);
+  launch_sf(tables(c), c->sys.e_vir, (const SFJob*)jd.p, (int)sfj.size(), 0, c->st);
+  ph_end(c, OSVMP2_PH_SF, fl);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  return 0;
+}
+int ensure_sf_blocks(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& blocks) {
+  const int rc = ensure_sf_blocks_impl(c, blocks);
+  if (rc != 0) {
+    const std::string msg = c->err;
+    cudaGetLastError();
+    reset_pairs(c);
+    c->err = msg;
+  }
+  return rc;
+}
+
+// s2b of every pair (Eq. s2b) on the device, into a host [n][n] matrix (diagonal 1).
+int compute_s2b(osvmp2_ctx* c, std::vector<double>& s2b) {
+  const int n = c->sys.n_occ;
+  s2b.assign((size_t)n * n, 1.0);
+  std::vector<int2> pl;
+  pl.reserve((size_t)n * (n - 1) / 2);
+  double fl = 0.0;
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) {
+      pl.push_back(make_int2(i, j));
+      fl += 2.0 * c->sys.n_vir * (double)c->n_osv[i] * c->n_osv[j];
+    }
+  if (pl.empty()) return 0;
+  Tmp pd, vd;
+  TRY(tmp_alloc(c, pd, pl.size() * sizeof(int2)));
+  TRY(tmp_alloc(c, vd, pl.size() * sizeof(double)));
+  CK(cudaMemcpyAsync(pd.p, pl.data(), pl.size() * sizeof(int2), cudaMemcpyHostToDevice, c->st));
+  ph_begin(c, OSVMP2_PH_SCREEN);
+  launch_s2b(tables(c), (const int2*)pd.p, (int)pl.size(), (double*)vd.p,
+             (int)std::min<size_t>(pl.size(), 4 * (size_t)c->num_sms), c->st);
+  ph_end(c, OSVMP2_PH_SCREEN, fl);
+  CK(cudaGetLastError());
+  std::vector<double> v(pl.size());
+  CK(cudaMemcpyAsync(v.data(), vd.p, v.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (size_t q = 0; q < pl.size(); q++) {
+    s2b[(size_t)pl[q].x * n + pl[q].y] = v[q];
+    s2b[(size_t)pl[q].y * n + pl[q].x] = v[q];
+  }
+  return 0;
+}
+
+bool screen_valid(const osvmp2_screen* sc) {
+  return sc && sc->s2b_distant >= 0.0 && sc->s2b_close >= sc->s2b_distant && sc->s3b_min >= 0.0 &&
+         std::isfinite(sc->s2b_close) && std::isfinite(sc->s3b_min);
+}
+
 }  // namespace
 
 // ============================================================== C ABI
@@ -1492,10 +1629,8 @@ int build_sigma_table(osvmp2_ctx* c, SigmaStore& ss) {
   return 0;
 }
 
-// MBE(3) energy; with tstore != NULL the converged amplitudes of every fragment
-// are kept (fragment f at tstore + toff[f], local pairs a<=b in order).
-static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out,
-                     osvmp2_mbe_stats* stats, Tmp* tstore, std::vector<long long>* toff) {
+// Distance-rule fragment list of osvmp2_mbe3_energy / osvmp2_energy_grad into c->frags.
+static int distance_fragments(osvmp2_ctx* c, double r2, double r3, double* e_out) {
   if (!c) return OSVMP2_E_ARG;
   c->err.clear();
   if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "osvmp2_build_osv has not been called");
@@ -1503,8 +1638,18 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
   if (c->r_occ.empty()) return fail(c, OSVMP2_E_ARG, "system has no r_occ (needed for fragment lists)");
   if (!(r2 >= 0) || !(r3 >= 0)) return fail(c, OSVMP2_E_ARG, "cutoffs must be >= 0");
   CK(cudaSetDevice(c->device));
+  enumerate_fragments(c->r_occ.data(), c->sys.n_occ, r2, r3, c->frags);
+  c->weak.clear();
+  c->weak_e.clear();
+  return 0;
+}
+
+// MBE(3) energy of the fragments in c->frags; with tstore != NULL the converged
+// amplitudes of every fragment are kept (fragment f at tstore + toff[f], local
+// pairs a<=b in order).
+static int mbe3_core(osvmp2_ctx* c, osvmp2_prec prec, double* e_out, osvmp2_mbe_stats* stats, Tmp* tstore,
+                     std::vector<long long>* toff) {
   const int n = c->sys.n_occ;
-  enumerate_fragments(c->r_occ.data(), n, r2, r3, c->frags);
   const int nf = (int)c->frags.size();
   std::vector<std::pair<int, int>> req;
   int64_t ns = 0, npair = 0, ntri = 0;
@@ -1699,6 +1844,7 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
     stats->worst_fragment = worst;
     stats->max_update = maxu;
     stats->flops = f_solve;
+    stats->n_weak = 0;
   }
   if (unconv)
     return fail(c, OSVMP2_E_NOCONV, "%d fragment(s) did not converge; first is fragment %lld", unconv,
@@ -1708,7 +1854,220 @@ static int mbe3_core(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, doub
 
 int osvmp2_mbe3_energy(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out,
                        osvmp2_mbe_stats* stats) {
-  return mbe3_core(c, r2, r3, prec, e_out, stats, nullptr, nullptr);
+  TRY(distance_fragments(c, r2, r3, e_out));
+  return mbe3_core(c, prec, e_out, stats, nullptr, nullptr);
+}
+
+int osvmp2_pair_screening(osvmp2_ctx* c, const osvmp2_screen* sc, double* s2b_out, int32_t* class_out,
+                          int64_t* counts) {
+  if (!c) return OSVMP2_E_ARG;
+  c->err.clear();
+  if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "osvmp2_build_osv has not been called");
+  if (!screen_valid(sc)) return fail(c, OSVMP2_E_ARG, "invalid screening thresholds");
+  CK(cudaSetDevice(c->device));
+  const int n = c->sys.n_occ;
+  std::vector<double> s2b;
+  TRY(compute_s2b(c, s2b));
+  int64_t cnt[3] = {0, 0, 0};
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      const double v = s2b[(size_t)i * n + j];
+      const int cl = (i == j || v >= sc->s2b_close) ? 2 : (v >= sc->s2b_distant ? 1 : 0);
+      if (class_out) class_out[(size_t)i * n + j] = cl;
+      if (i < j) cnt[2 - cl]++;
+    }
+  if (s2b_out) std::copy(s2b.begin(), s2b.end(), s2b_out);
+  if (counts) std::copy(cnt, cnt + 3, counts);
+  return OSVMP2_OK;
+}
+
+int osvmp2_mbe3_energy_screened(osvmp2_ctx* c, const osvmp2_screen* sc, osvmp2_prec prec, double* e_out,
+                                double* e_weak_out, osvmp2_mbe_stats* stats) {
+  if (!c) return OSVMP2_E_ARG;
+  c->err.clear();
+  if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "osvmp2_build_osv has not been called");
+  if (!e_out) return fail(c, OSVMP2_E_ARG, "e_out is required");
+  if (!screen_valid(sc)) return fail(c, OSVMP2_E_ARG, "invalid screening thresholds");
+  if (prec != OSVMP2_FP64 && prec != OSVMP2_MIXED) return fail(c, OSVMP2_E_ARG, "unknown precision %d", (int)prec);
+  CK(cudaSetDevice(c->device));
+  const int n = c->sys.n_occ, nx = c->sys.n_aux;
+  const bool mixed = prec == OSVMP2_MIXED;
+  std::vector<double> s2b;
+  TRY(compute_s2b(c, s2b));
+  std::vector<std::pair<int, int>> weak;
+  screened_fragments(s2b.data(), n, *sc, c->frags, weak);
+  c->weak.clear();
+  c->weak_e.clear();
+  Tmp tstore;
+  std::vector<long long> toff;
+  double e_cl = 0.0;
+  TRY(mbe3_core(c, prec, &e_cl, stats, weak.empty() ? nullptr : &tstore, &toff));
+  double e_weak = 0.0;
+  if (!weak.empty()) {
+    ph_begin(c, OSVMP2_PH_WEAK);
+    std::vector<int> need(n, 0);
+    for (auto& w : weak) need[w.first] = need[w.second] = 1;
+    // T_(ii,ii) of Eq. (tmbediag): the weighted (ii) amplitudes of the clusters containing i
+    std::vector<std::vector<GradContrib>> con(n);
+    for (size_t f = 0; f < c->frags.size(); f++) {
+      const Frag& fr = c->frags[f];
+      int orbs[3], nc = 0;
+      for (int u = 0; u < 3; u++)
+        if (fr.orbs[u] >= 0) orbs[nc++] = fr.orbs[u];
+      long long off = toff[f];
+      for (int a = 0; a < nc; a++)
+        for (int b = a; b < nc; b++) {
+          const long long m = pair_dim_h(c, orbs[a], orbs[b]);
+          if (a == b && need[orbs[a]] && fr.weight != 0)
+            con[orbs[a]].push_back(GradContrib{(const double*)tstore.p + off, fr.weight});
+          off += m * m;
+        }
+    }
+    std::vector<DiagJob> dj;
+    std::vector<GradContrib> cflat;
+    std::vector<size_t> doff(n, 0);
+    size_t tsz = 0;
+    int max_n = 1;
+    for (int i = 0; i < n; i++) {
+      if (!need[i]) continue;
+      const int pid = c->pair_id[(size_t)i * n + i];
+      if (pid < 0) return fail(c, OSVMP2_E_STATE, "diagonal pair (%d,%d) not built", i, i);
+      DiagJob d{i, pid, (int)cflat.size(), 0, nullptr};
+      for (auto& x : con[i]) cflat.push_back(x);
+      d.c1 = (int)cflat.size();
+      doff[i] = tsz;
+      tsz += (size_t)c->n_osv[i] * c->n_osv[i];
+      max_n = std::max(max_n, c->n_osv[i]);
+      dj.push_back(d);
+    }
+    Tmp tdiag, d_dj, d_cf, dscr;
+    TRY(tmp_alloc(c, tdiag, tsz * sizeof(double)));
+    for (auto& d : dj) d.T = (double*)tdiag.p + doff[d.i];
+    TRY(tmp_alloc(c, d_dj, dj.size() * sizeof(DiagJob)));
+    TRY(tmp_alloc(c, d_cf, std::max<size_t>(1, cflat.size()) * sizeof(GradContrib)));
+    const int n_cta_d = std::max(1, std::min((int)dj.size(), 2 * c->num_sms));
+    TRY(tmp_alloc(c, dscr, (size_t)n_cta_d * 2 * max_n * max_n * sizeof(double)));
+    CK(cudaMemcpyAsync(d_dj.p, dj.data(), dj.size() * sizeof(DiagJob), cudaMemcpyHostToDevice, c->st));
+    if (!cflat.empty())
+      CK(cudaMemcpyAsync(d_cf.p, cflat.data(), cflat.size() * sizeof(GradContrib), cudaMemcpyHostToDevice, c->st));
+    launch_diag_amp(tables(c), (const DiagJob*)d_dj.p, (int)dj.size(), (const GradContrib*)d_cf.p, mixed ? 1 : 0,
+                    (double*)dscr.p, max_n, n_cta_d, c->st);
+    CK(cudaGetLastError());
+    // S_(i,j) of the weak pairs
+    TRY(ensure_sf_blocks(c, weak));
+    // FP64 diagonal projections B~_i^(i) (Eq. osv_imua) and exact eigenbases of F_(i,i)
+    std::vector<const double*> bii(n, nullptr), xi(n, nullptr), ei(n, nullptr);
+    Tmp projm, d_pj, xm, em, rm, d_pc, pscr;
+    if (!mixed) {
+      for (int i = 0; i < n; i++) {
+        if (!need[i]) continue;
+        const int id = c->bt_id[(size_t)i * n + i], pid = c->pair_id[(size_t)i * n + i];
+        if (id < 0) return fail(c, OSVMP2_E_STATE, "projection of orbital %d not built", i);
+        bii[i] = c->bt_h[id];
+        xi[i] = c->X_h[pid];
+        ei[i] = c->et_h[pid];
+      }
+    } else {
+      std::vector<ProjJob> pj;
+      std::vector<PJob> pc;
+      size_t psz = 0, xsz = 0, esz = 0;
+      for (int i = 0; i < n; i++)
+        if (need[i]) {
+          psz += (size_t)nx * c->n_osv[i];
+          xsz += (size_t)c->n_osv[i] * c->n_osv[i];
+          esz += c->n_osv[i];
+        }
+      TRY(tmp_alloc(c, projm, psz * sizeof(double)));
+      TRY(tmp_alloc(c, xm, xsz * sizeof(double)));
+      TRY(tmp_alloc(c, em, esz * sizeof(double)));
+      TRY(tmp_alloc(c, rm, (size_t)n * sizeof(int)));
+      size_t po = 0, xo = 0, eo = 0;
+      double fl = 0.0;
+      for (int i = 0; i < n; i++) {
+        if (!need[i]) continue;
+        double* out = (double*)projm.p + po;
+        pj.push_back(ProjJob{i, i, out});
+        bii[i] = out;
+        po += (size_t)nx * c->n_osv[i];
+        double* X = (double*)xm.p + xo;
+        double* e = (double*)em.p + eo;
+        pc.push_back(PJob{i, i, X, e, (int*)rm.p + pc.size(), nullptr, nullptr});
+        xi[i] = X;
+        ei[i] = e;
+        xo += (size_t)c->n_osv[i] * c->n_osv[i];
+        eo += c->n_osv[i];
+        fl += 2.0 * nx * (double)c->sys.n_vir * c->n_osv[i];
+      }
+      TRY(tmp_alloc(c, d_pj, pj.size() * sizeof(ProjJob)));
+      TRY(tmp_alloc(c, d_pc, pc.size() * sizeof(PJob)));
+      CK(cudaMemcpyAsync(d_pj.p, pj.data(), pj.size() * sizeof(ProjJob), cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(d_pc.p, pc.data(), pc.size() * sizeof(PJob), cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
+      const Tables t = tables(c);
+      launch_project(bsrc(c), t, (const ProjJob*)d_pj.p, (int)pj.size(), max_n, 0, c->st);
+      CK(cudaGetLastError());
+      const int np = (int)pc.size();
+      if (max_n <= PW_MAX_ORDER) {
+        const int nw = std::min(np, 16 * c->num_sms);
+        TRY(tmp_alloc(c, pscr, precond_w_scratch_doubles(max_n, nw) * sizeof(double)));
+        launch_precond_w(t, c->opts.tau_s, (const PJob*)d_pc.p, np, max_n, (double*)pscr.p, nw, c->err_d, c->st);
+      } else {
+        const int nc = std::min(np, 2 * c->num_sms);
+        TRY(tmp_alloc(c, pscr, (size_t)nc * precond_scratch_doubles(max_n) * sizeof(double)));
+        launch_precond(t, c->opts.tau_s, (const PJob*)d_pc.p, np, max_n, (double*)pscr.p, nc, c->err_d, c->st);
+      }
+      CK(cudaGetLastError());
+      TRY(check_err_flag(c, "weak-pair eigenbases"));
+      c->flops[OSVMP2_PH_WEAK] += fl;
+    }
+    std::vector<WeakJob> wj;
+    double fl = 0.0;
+    for (auto& w : weak) {
+      const int i = w.first, j = w.second;
+      const int id = c->sf_id[(size_t)i * n + j];
+      WeakJob jb{i, j, bii[i], bii[j], c->S_h[id], (const double*)tdiag.p + doff[i],
+                 (const double*)tdiag.p + doff[j], xi[i], xi[j], ei[i], ei[j], c->n_osv[i], c->n_osv[j]};
+      wj.push_back(jb);
+      const double ni = c->n_osv[i], nj = c->n_osv[j];
+      fl += 2.0 * nx * ni * nj + 2.0 * (ni * ni * nj + ni * nj * nj) * 3.0;
+    }
+    Tmp d_wj, wscr, we;
+    const int n_cta_w = std::max(1, std::min((int)wj.size(), 2 * c->num_sms));
+    TRY(tmp_alloc(c, d_wj, wj.size() * sizeof(WeakJob)));
+    TRY(tmp_alloc(c, wscr, (size_t)n_cta_w * 4 * max_n * max_n * sizeof(double)));
+    TRY(tmp_alloc(c, we, wj.size() * sizeof(double)));
+    CK(cudaMemcpyAsync(d_wj.p, wj.data(), wj.size() * sizeof(WeakJob), cudaMemcpyHostToDevice, c->st));
+    launch_weak(tables(c), nx, (const WeakJob*)d_wj.p, (int)wj.size(), (double*)wscr.p, max_n, n_cta_w,
+                (double*)we.p, c->st);
+    CK(cudaGetLastError());
+    ph_end(c, OSVMP2_PH_WEAK, fl);
+    c->weak_e.resize(wj.size());
+    CK(cudaMemcpyAsync(c->weak_e.data(), we.p, wj.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    ph_collect(c);
+    c->weak = weak;
+    for (double v : c->weak_e) {
+      if (!std::isfinite(v)) return fail(c, OSVMP2_E_NUMERIC, "non-finite weak-pair energy");
+      e_weak += v;
+    }
+  }
+  if (stats) stats->n_weak = (int64_t)weak.size();
+  *e_out = e_cl + e_weak;
+  if (e_weak_out) *e_weak_out = e_weak;
+  return OSVMP2_OK;
+}
+
+int osvmp2_weak_results(osvmp2_ctx* c, int64_t* n_out, int32_t* pairs, double* energies) {
+  if (!c || !n_out) return OSVMP2_E_ARG;
+  *n_out = (int64_t)c->weak.size();
+  for (size_t q = 0; q < c->weak.size(); q++) {
+    if (pairs) {
+      pairs[2 * q] = c->weak[q].first;
+      pairs[2 * q + 1] = c->weak[q].second;
+    }
+    if (energies) energies[q] = q < c->weak_e.size() ? c->weak_e[q] : 0.0;
+  }
+  return OSVMP2_OK;
 }
 
 int osvmp2_profile(osvmp2_ctx* c, double* ms, double* flops, double* bytes, int64_t* calls, int reset) {
@@ -1743,7 +2102,8 @@ int osvmp2_energy_grad(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, do
   if (!c) return OSVMP2_E_ARG;
   Tmp tstore;
   std::vector<long long> toff;
-  TRY(mbe3_core(c, r2, r3, prec, e_out, stats, &tstore, &toff));
+  TRY(distance_fragments(c, r2, r3, e_out));
+  TRY(mbe3_core(c, prec, e_out, stats, &tstore, &toff));
   const int n = c->sys.n_occ, nv = c->sys.n_vir, nx = c->sys.n_aux;
   const int nf = (int)c->frags.size();
   // unique pairs of the fragment list, each with its (fragment-ordered) contributions

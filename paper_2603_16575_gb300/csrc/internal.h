@@ -233,6 +233,35 @@ struct GradContrib {       // one fragment's amplitude of a pair and the fragmen
   const double* T;
   int weight;
 };
+
+// ---- pair screening and weak pairs (screen.cu), FP64 in both forms
+// s2b[p] of the pairs (i, j) = pairs[p] (Eq. s2b), grid-stride over n_cta CTAs.
+void launch_s2b(const Tables& t, const int2* pairs, int n_pairs, double* s2b, int n_cta, cudaStream_t st);
+struct DiagJob {           // T_ii (raw basis, [n_i][n_i]) = sum of contributions [c0, c1)
+  int i, pid;              // orbital, id of the pair (i, i)
+  int c0, c1;
+  double* T;
+};
+// mixed != 0: contributions are Y (r x r) of the pair (i,i)'s preconditioner basis.
+// scratch: 2 max_n^2 doubles per CTA.
+void launch_diag_amp(const Tables& t, const DiagJob* jobs, int n_jobs, const GradContrib* contrib, int mixed,
+                     double* scratch, int max_n, int n_cta, cudaStream_t st);
+struct WeakJob {           // weak pair (i, j), i < j
+  int i, j;
+  const double* Bii;       // B~_i^(i) [n_aux][n_i]
+  const double* Bjj;       // B~_j^(j) [n_aux][n_j]
+  const double* S;         // S_(i,j) [n_i][n_j]
+  const double* Ti;        // MBE(3) diagonal amplitude T_(i,i) [n_i][n_i]
+  const double* Tj;
+  const double* Xi;        // eigenvectors of F_(i,i) (columns), row stride ldxi
+  const double* Xj;
+  const double* ei;        // their eigenvalues
+  const double* ej;
+  int ldxi, ldxj;
+};
+// Weak-pair energies (both orders) into e_out[job]; scratch: 4 max_n^2 doubles per CTA.
+void launch_weak(const Tables& t, int n_aux, const WeakJob* jobs, int n_jobs, double* scratch, int max_n, int n_cta,
+                 double* e_out, cudaStream_t st);
 struct GradPairJob {       // W_p = sum c T~, H_p = sum c (T~ S T^T + [i!=j] T~^T S T)
   int i, j;
   int c0, c1;              // contributions [c0, c1)

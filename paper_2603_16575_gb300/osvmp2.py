@@ -41,10 +41,18 @@ class MbeStats(ctypes.Structure):
     _fields_ = [("n_single", ctypes.c_int64), ("n_pair", ctypes.c_int64), ("n_triple", ctypes.c_int64),
                 ("n_pair_blocks", ctypes.c_int64), ("max_iter_used", ctypes.c_int32),
                 ("n_unconverged", ctypes.c_int32), ("worst_fragment", ctypes.c_int64),
-                ("max_update", ctypes.c_double), ("flops", ctypes.c_double)]
+                ("max_update", ctypes.c_double), ("flops", ctypes.c_double), ("n_weak", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Screen(ctypes.Structure):
+    """Pair-class cuts (paper defaults 1e-7, 1e-2, 0.2)."""
+    _fields_ = [("s2b_distant", ctypes.c_double), ("s2b_close", ctypes.c_double), ("s3b_min", ctypes.c_double)]
+
+    def __init__(self, s2b_distant=1e-7, s2b_close=1e-2, s3b_min=0.2):
+        super().__init__(s2b_distant, s2b_close, s3b_min)
 
 
 # name -> (restype, argtypes); every function declared in include/osvmp2.h
@@ -69,6 +77,10 @@ SIGNATURES = {
     "osvmp2_profile": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
     "osvmp2_mbe3_fragments": (ctypes.c_int, [_P, _I32, _D, _D, _I64, _P, _P, _P]),
     "osvmp2_energy_grad": (ctypes.c_int, [_P, _D, _D, ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(MbeStats)]),
+    "osvmp2_pair_screening": (ctypes.c_int, [_P, ctypes.POINTER(Screen), _P, _P, _P]),
+    "osvmp2_mbe3_energy_screened": (ctypes.c_int, [_P, ctypes.POINTER(Screen), ctypes.c_int, _P, _P,
+                                                   ctypes.POINTER(MbeStats)]),
+    "osvmp2_weak_results": (ctypes.c_int, [_P, _P, _P, _P]),
     "osvmp2_precond_noalloc": (ctypes.c_int, [_P, _P, _I32, _D, _P, _P, _P, _P, ctypes.c_char_p, _I32]),
     "osvmp2_generate_B": (ctypes.c_int, [_I32, _I32, _I32, ctypes.c_uint64, _P, _I32, _I32, _P, _P]),
 }
@@ -322,7 +334,40 @@ class Context:
         return e.value, st.as_dict()
 
     PHASES = ["tii", "eig", "sf", "project", "exchange", "precond", "solve", "mbe_sum", "subsolve", "grad",
-              "k_gproj", "k_eig", "k_fragsolve", "sigma", "spare14", "spare15"]
+              "k_gproj", "k_eig", "k_fragsolve", "sigma", "weak", "screen"]
+
+    # ---- A5 with the paper's cluster selection
+    def pair_screening(self, screen: Optional[Screen] = None):
+        """(s2b [n,n], class [n,n] (2 close, 1 weak, 0 distant), counts (close, weak, distant))."""
+        sc = screen or Screen()
+        n = self.n_occ
+        s2b = np.zeros((n, n))
+        cls = np.zeros((n, n), dtype=np.int32)
+        cnt = np.zeros(3, dtype=np.int64)
+        self._check("osvmp2_pair_screening",
+                    lib().osvmp2_pair_screening(self._h, ctypes.byref(sc), _ptr(s2b), _ptr(cls), _ptr(cnt)))
+        return s2b, cls, tuple(int(x) for x in cnt)
+
+    def mbe3_energy_screened(self, prec: str = "fp64", screen: Optional[Screen] = None):
+        """(E, E_weak, stats) of the MBE(3) energy over the s2b/s3b-selected clusters plus weak pairs."""
+        sc = screen or Screen()
+        e = ctypes.c_double(0.0)
+        ew = ctypes.c_double(0.0)
+        st = MbeStats()
+        self._check("osvmp2_mbe3_energy_screened",
+                    lib().osvmp2_mbe3_energy_screened(self._h, ctypes.byref(sc), PREC[prec], ctypes.addressof(e),
+                                                      ctypes.addressof(ew), ctypes.byref(st)))
+        return e.value, ew.value, st.as_dict()
+
+    def weak_results(self):
+        """(pairs [n,2] int32, energies [n]) of the last screened call."""
+        n = ctypes.c_int64(0)
+        self._check("osvmp2_weak_results", lib().osvmp2_weak_results(self._h, ctypes.byref(n), None, None))
+        pairs = np.empty((n.value, 2), dtype=np.int32)
+        e = np.empty(n.value)
+        self._check("osvmp2_weak_results",
+                    lib().osvmp2_weak_results(self._h, ctypes.byref(n), _ptr(pairs), _ptr(e)))
+        return pairs, e
 
     def profile(self, reset: bool = False):
         """Per-phase {name: (ms, flops, bytes, calls)} accumulated since the last reset."""
