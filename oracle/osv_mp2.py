@@ -584,3 +584,60 @@ def mbe3_screened_energy(osys: "OSVSystem", scr: Screen, **kw):
     E_weak = sum(w.energy for w in wres)
     per = [(orbs, c, r.energy) for (orbs, c), r in zip(frags, results)]
     return E + E_weak, E_weak, per, wres, s2b
+
+
+# --------------------------------------------------------------------------
+# Randomized OSV generation: Algorithm 3 with Eqs. (rsvd_z), (tsub),
+# (tii_rsvd), (back_q) and (rsvd_za)
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class RandomizedOSV:
+    Q: np.ndarray          # kept OSVs [n_vir, n_i], descending omega, sign convention R9
+    omega: np.ndarray      # kept singular values of T~ (>= l_osv)
+    Z: np.ndarray          # orthonormal rows of the range finder [n_rosv, n_vir]
+    n_rosv: int            # rows taken (s at exit)
+    window_max: float      # max norm of the r look-ahead rows at exit
+
+
+def randomized_osv(T: np.ndarray, l_osv: float, gauss_row: Callable[[int], np.ndarray], r: int = 10,
+                   n_max: int = 0) -> RandomizedOSV:
+    """Adaptive randomized range finder on the rows of T_ii, then a low-rank SVD.
+
+    gauss_row(k) gives Gaussian row k of the method's random draws (k = 0..r-1
+    form G, k = r + s - 1 gives the fresh row g-bar^(s) of G-bar); the draws are
+    inputs, not generated here.  Steps in the order of Algorithm 3:
+      Y = G T (r rows); while the largest row norm of Y exceeds
+      l_osv / (10 sqrt(2/pi)): s += 1; z^(s) from y^(s) by Eq. (rsvd_za)
+      (projected against Z^(s-1), normalised) and appended to Z; the window
+      shifts; the new last row is g-bar^(s) T (I - Z^(s-1)^T Z^(s-1)); every
+      window row loses its z^(s) component (Y -= Y z^T z).
+      T~ = Z T (Eq. tsub), T~ = Q~ omega V~^T (Eq. tii_rsvd), Q = Z^T Q~
+      (Eq. back_q), kept where omega >= l_osv.
+    n_max (0: n_vir) caps the rows; reaching it is reported through n_rosv."""
+    nv = T.shape[0]
+    n_max = n_max or nv
+    thr = l_osv / (10.0 * np.sqrt(2.0 / np.pi))
+    Y = np.stack([gauss_row(k) @ T for k in range(r)])
+    Z = np.zeros((0, nv))
+    s = 0
+    while s < n_max and np.max(np.linalg.norm(Y, axis=1)) > thr:
+        s += 1
+        zt = Y[0] - (Y[0] @ Z.T) @ Z                    # Eq. (rsvd_za)
+        z = zt / np.linalg.norm(zt)
+        Z_prev = Z
+        Z = np.vstack([Z, z])
+        ybar = gauss_row(r + s - 1) @ T
+        ynew = ybar - (ybar @ Z_prev.T) @ Z_prev
+        Y = np.vstack([Y[1:], ynew])
+        Y = Y - np.outer(Y @ z, z)
+    Tt = Z @ T                                          # Eq. (tsub)
+    Qt, w, _ = np.linalg.svd(Tt, full_matrices=False)   # Eq. (tii_rsvd)
+    Q = Z.T @ Qt                                        # Eq. (back_q)
+    keep = w >= l_osv
+    Q, w = Q[:, keep], w[keep]
+    if Q.shape[1]:
+        big = np.argmax(np.abs(Q), axis=0)
+        sgn = np.sign(Q[big, np.arange(Q.shape[1])])
+        sgn[sgn == 0] = 1.0
+        Q = Q * sgn
+    return RandomizedOSV(np.ascontiguousarray(Q), w, Z, s, float(np.max(np.linalg.norm(Y, axis=1))))

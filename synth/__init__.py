@@ -53,7 +53,9 @@ MIX1 = 0xBF58476D1CE4E5B9
 MIX2 = 0x94D049BB133111EB
 
 # stream ids
-S_OCC_POS, S_VIR_POS, S_OCC_E, S_VIR_E, S_B, S_JITTER = 1, 2, 3, 4, 5, 6
+S_OCC_POS, S_VIR_POS, S_OCC_E, S_VIR_E, S_B, S_JITTER, S_ROSV = 1, 2, 3, 4, 5, 6, 7
+# rows of the randomized OSV draws per orbital (counter layout of gauss_rows)
+ROSV_ROWS_PER_ORBITAL = 1 << 16
 
 _U64 = np.uint64
 _MASK = (1 << 64) - 1
@@ -197,6 +199,15 @@ WORKLOADS = {
     "grad_n64": dict(n_occ=64, n_vir=320, n_aux=1200, lam=1.0, geometry="box"),
     "chain_n800": dict(n_occ=800, n_vir=6000, n_aux=16000, lam=1.0, geometry="chain"),
 }
+
+
+def gauss_row(seed: int, i: int, k: int, n_vir: int) -> np.ndarray:
+    """Row k of the Gaussian draws of orbital i for the randomized OSV range
+    finder: z(key(seed, S_ROSV), (i * 2^16 + k) * n_vir + a), a = 0..n_vir-1,
+    the Irwin-Hall(12) normal defined above.  The device draws the same numbers
+    from the same definition."""
+    base = (i * ROSV_ROWS_PER_ORBITAL + k) * n_vir
+    return normal_ih12(stream_key(seed, S_ROSV), np.arange(n_vir, dtype=_U64) + _U64(base))
 
 
 def workload(name: str, seed: int = 0, **over) -> System:
