@@ -189,13 +189,15 @@ def run_gpu(args):
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
     stream.synchronize()
     osv_prec = "mixed" if args.prec == "mixed" else "fp64"
-    ctx = pkg.Context(local, stream=stream, osv_prec=osv_prec)
+    ctx = pkg.Context(local, stream=stream, osv_prec=osv_prec, osv_method=args.osv_method)
 
     def step(B_in=B, env_in=env, f_in=f_occ, e_in=e_vir):
         kw = dict(B=B_in) if B_in is not None else dict(env=env_in, seed=s.seed, n_aux=s.n_aux)
         n_osv = ctx.build_osv(f_in, e_in, L_OSV, r_occ=s.r_occ, **kw)
         if args.grad:
             E, dB, df, de, st = ctx.energy_grad(R2_CUT, R3_CUT, args.prec)
+        elif args.screen:
+            E, _, st = ctx.mbe3_energy_screened(args.prec)
         else:
             E, st = ctx.mbe3_energy(R2_CUT, R3_CUT, args.prec)
         return E, st, n_osv
@@ -240,7 +242,7 @@ def run_gpu(args):
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         ctx.build_osv(f_occ, e_vir, L_OSV, r_occ=s.r_occ, **kw)
-        E64 = ctx.mbe3_energy(R2_CUT, R3_CUT, "fp64")[0]
+        E64 = (ctx.mbe3_energy_screened("fp64")[0] if args.screen else ctx.mbe3_energy(R2_CUT, R3_CUT, "fp64")[0])
         ev1.record(stream)
         ev1.synchronize()
         gpu_frag_e["fp64_form"] = fragment_energies(ctx)
@@ -347,8 +349,11 @@ def run_gpu(args):
         "dtype": "f64" if args.prec == "fp64" else "split-tf32+f32+f64",
         "data": "synthetic",
         "config": {"workload": f"{args.workload} (n_occ={s.n_occ}, n_vir={s.n_vir}, n_aux={s.n_aux}, "
-                               f"lambda={s.lam} A, l_osv={L_OSV}, r2={R2_CUT} A, r3={R3_CUT} A)",
+                               f"lambda={s.lam} A, l_osv={L_OSV}, " +
+                               ("s2b/s3b screening 1e-7/1e-2/0.2 with weak pairs)" if args.screen
+                                else f"r2={R2_CUT} A, r3={R3_CUT} A)"),
                    "prec": args.prec, "b_mode": args.b_mode, "grad": bool(args.grad),
+                   "osv_method": args.osv_method, "n_weak": int(st.get("n_weak", 0)),
                    "fragments": n_frag, "n_single": int(st["n_single"]), "n_pair": int(st["n_pair"]),
                    "n_triple": int(st["n_triple"]), "n_osv_mean": float(np.mean(n_osv)),
                    "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{world}",
@@ -394,7 +399,13 @@ def cpu_sample(args, budget_s: float):
     sel = set(near)
     frags = [(o, c) for o, c in oracle.mbe3_fragments(s.r_occ, R2_CUT, R3_CUT) if set(o) <= sel]
     t0 = time.perf_counter()
-    osys = oracle.OSVSystem(s.B_block, s.n_occ, s.e_vir, s.f_occ, l_osv=L_OSV, orbitals=near)
+    if args.osv_method == "randomized":
+        osys = oracle.OSVSystem(s.B_block, s.n_occ, s.e_vir, s.f_occ, l_osv=L_OSV, orbitals=[])
+        gauss = lambda i, k: synth.gauss_row(s.seed, i, k, s.n_vir)
+        osys.Q, osys.omega, _ = oracle.build_osv_randomized(osys.B, s.n_occ, s.e_vir, s.f_occ, L_OSV, gauss,
+                                                            orbitals=near)
+    else:
+        osys = oracle.OSVSystem(s.B_block, s.n_occ, s.e_vir, s.f_occ, l_osv=L_OSV, orbitals=near)
     done = 0
     energies = {}
     for orbs, c in frags:
@@ -447,6 +458,10 @@ def main():
     ap.add_argument("--workload", default="mbe3_n128", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--b-mode", choices=["regen", "stored"], default="regen")
     ap.add_argument("--grad", action="store_true")
+    ap.add_argument("--osv-method", choices=["exact", "randomized"], default="exact",
+                    help="OSV generation: full eigen-decomposition or the randomized range finder (Algorithm 3)")
+    ap.add_argument("--screen", action="store_true",
+                    help="cluster selection by s2b/s3b with weak pairs instead of the 8/6 A distance rule")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--cpu-orbitals", type=int, default=10)

@@ -85,7 +85,15 @@ typedef struct {
                           once (its cache, pair store and temporaries), in MiB; a request beyond it
                           fails with OSVMP2_E_NOMEM as a failed cudaMalloc would.  Library extension
                           for callers that run under a memory budget. */
-  int32_t reserved[4];
+  int32_t osv_method;  /* OSV generation in osvmp2_build_osv: 0 (default) full eigen-decomposition
+                          of T_ii; 1 randomized (Algorithm 3): adaptive range finder on Gaussian rows
+                          (look-ahead r = 10, stop when every look-ahead row has norm
+                          <= l_osv / (10 sqrt(2/pi))), then the SVD of T~ = Z T_ii through the
+                          eigen-decomposition of T~ T~^T.  The Gaussian draws are the Irwin-Hall(12)
+                          normals of the system's seed, stream 7, counter (i 2^16 + k) n_vir + a. */
+  int32_t rosv_max_rows; /* randomized OSVs: rows the range finder may take per orbital (0: min(n_vir,
+                          256)); running out is OSVMP2_E_NUMERIC. */
+  int32_t reserved[2];
 } osvmp2_opts;
 
 /* Synthetic or caller-supplied system.  All arrays are read by the kernels. */

@@ -12,5 +12,5 @@ from .osv_mp2 import (  # noqa: F401
     OSVSystem, fragment_gradient, mbe3_energy_gradient,
     s2b_metric, s2b_matrix, s3b_metric, Screen, screened_fragments, mbe3_diagonal_amplitudes,
     WeakResult, weak_pair, weak_residual, mbe3_screened_energy,
-    RandomizedOSV, randomized_osv,
+    RandomizedOSV, randomized_osv, build_osv_randomized,
 )

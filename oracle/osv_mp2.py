@@ -641,3 +641,16 @@ def randomized_osv(T: np.ndarray, l_osv: float, gauss_row: Callable[[int], np.nd
         sgn[sgn == 0] = 1.0
         Q = Q * sgn
     return RandomizedOSV(np.ascontiguousarray(Q), w, Z, s, float(np.max(np.linalg.norm(Y, axis=1))))
+
+
+def build_osv_randomized(Bfun: Callable[[int], np.ndarray], n_occ: int, e_vir: np.ndarray, f_occ: np.ndarray,
+                         l_osv: float, gauss: Callable[[int, int], np.ndarray], r: int = 10, n_max: int = 0,
+                         orbitals=None):
+    """Randomized OSVs of every orbital (Algorithm 3); gauss(i, k) is Gaussian row k
+    of orbital i.  Returns (Q list, omega list, RandomizedOSV list)."""
+    Q, W, R = [None] * n_occ, [None] * n_occ, [None] * n_occ
+    for i in (range(n_occ) if orbitals is None else orbitals):
+        T = semicanonical_tii(Bfun(i), e_vir, f_occ[i, i])
+        R[i] = randomized_osv(T, l_osv, lambda k, i=i: gauss(i, k), r=r, n_max=n_max)
+        Q[i], W[i] = R[i].Q, R[i].omega
+    return Q, W, R

@@ -1137,6 +1137,7 @@ void osvmp2_default_opts(osvmp2_opts* o) {
 
 static bool opts_valid(const osvmp2_opts& o) {
   return o.max_iter > 0 && o.tau_s >= 0 && o.tol_update > 0 && o.tol_energy > 0 && o.mem_cap_mib >= 0 &&
+         (o.osv_method == 0 || o.osv_method == 1) && o.rosv_max_rows >= 0 &&
          (o.osv_prec == OSVMP2_FP64 || o.osv_prec == OSVMP2_MIXED) && (o.no_autotune == 0 || o.no_autotune == 1);
 }
 
@@ -1238,6 +1239,78 @@ int tii_tensor(osvmp2_ctx* c, int i0, int b, double* T, float* Bt, int nsl, int 
   return 0;
 }
 
+// Randomized OSVs of orbitals [i0, i0+b) from their T_ii in T (Algorithm 3):
+// V [b][kmax][nv], w [b][kmax], k [b] as the exact path writes them.
+static int rosv_batch(osvmp2_ctx* c, double* T, int b, int i0, double l_osv, int n_max, int kmax, bool tensor,
+                      const RosvLayout& rl, double* scr, float* slices, uint64_t key, double* V, double* w, int* k,
+                      std::vector<int>& nrows_h) {
+  const int nv = c->sys.n_vir, rows = rl.rows;
+  double* Y = scr + rl.y;
+  double* Z = scr + rl.z;
+  double* Tt = scr + rl.tt;
+  int* nrows = reinterpret_cast<int*>(scr + rl.nrows);
+  auto tc_jobs = [&](int u, int m_rows, double* out, int out_rows, std::vector<tc::Job>& jobs) {
+    const long long base = (long long)u * tc::NSL * (nv + rows);
+    for (int m0 = 0; m0 < m_rows; m0 += tc::BM)
+      for (int n0 = 0; n0 < nv; n0 += tc::BN) {
+        tc::Job jb{};
+        jb.a_row = (int)(base + (long long)tc::NSL * nv + m0);
+        jb.a_sstride = rows;
+        jb.b_row = (int)(base + n0);
+        jb.b_sstride = nv;
+        jb.m_valid = std::min(tc::BM, m_rows - m0);
+        jb.n_valid = std::min(tc::BN, nv - n0);
+        jb.out = out + ((size_t)u * out_rows + m0) * nv + n0;
+        jb.ld_out = nv;
+        jb.m0 = m0;
+        jb.n0 = n0;
+        jobs.push_back(jb);
+      }
+  };
+  auto run_tc = [&](std::vector<tc::Job>& jobs) -> int {
+    if (jobs.empty()) return 0;
+    Tmp jd;
+    TRY(tmp_alloc(c, jd, jobs.size() * sizeof(tc::Job)));
+    CK(cudaMemcpyAsync(jd.p, jobs.data(), jobs.size() * sizeof(tc::Job), cudaMemcpyHostToDevice, c->st));
+    if (launch_kt_tc(slices, rl.store_rows, nv, rl.ldk, (const tc::Job*)jd.p, (int)jobs.size(), c->err_d, c->st))
+      return fail(c, OSVMP2_E_CUDA, "tensor-map encoding for the randomized OSVs failed");
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));   // the job list is a temporary
+    return 0;
+  };
+  double fl = 2.0 * rows * (double)nv * nv * b;
+  if (tensor) {
+    launch_rosv_slices(0, T, b, nv, i0, key, nullptr, nullptr, rows, slices, rl.ldk, c->st);
+    launch_rosv_slices(1, T, b, nv, i0, key, nullptr, nullptr, rows, slices, rl.ldk, c->st);
+    CK(cudaGetLastError());
+    std::vector<tc::Job> jobs;
+    for (int u = 0; u < b; u++) tc_jobs(u, rows, Y, rows, jobs);
+    TRY(run_tc(jobs));
+  } else {
+    launch_rosv_gemm64(0, T, b, nv, i0, key, nullptr, nullptr, rows, Y, c->st);
+    CK(cudaGetLastError());
+  }
+  launch_rosv_finder(Y, b, nv, ROSV_WINDOW, n_max, l_osv, Z, nrows, scr + rl.wmax, c->err_d, c->st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(nrows_h.data(), nrows, b * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int u = 0; u < b; u++) fl += 2.0 * nrows_h[u] * (double)nv * nv + 2.0 * nrows_h[u] * (double)nrows_h[u] * nv;
+  if (tensor) {
+    launch_rosv_slices(2, T, b, nv, i0, key, Z, nrows, rows, slices, rl.ldk, c->st);
+    CK(cudaGetLastError());
+    std::vector<tc::Job> jobs;
+    for (int u = 0; u < b; u++) tc_jobs(u, nrows_h[u], Tt, n_max, jobs);
+    TRY(run_tc(jobs));
+  } else {
+    launch_rosv_gemm64(1, T, b, nv, i0, key, Z, nrows, n_max, Tt, c->st);
+    CK(cudaGetLastError());
+  }
+  launch_rosv_svd(Tt, Z, nrows, b, nv, n_max, l_osv, kmax, V, w, k, scr + rl.svd, c->err_d, c->st);
+  CK(cudaGetLastError());
+  c->flops[OSVMP2_PH_EIG] += fl;
+  return 0;
+}
+
 int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_t* n_osv_host) {
   if (!c || !s) return OSVMP2_E_ARG;
   c->err.clear();
@@ -1246,6 +1319,8 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   if (!s->B && !s->env) return fail(c, OSVMP2_E_ARG, "either B or env must be given");
   if (!s->f_occ || !s->e_vir) return fail(c, OSVMP2_E_ARG, "f_occ and e_vir are required");
   if ((int64_t)s->n_occ * s->n_occ > (int64_t)1 << 30) return fail(c, OSVMP2_E_ARG, "n_occ too large");
+  if (c->opts.osv_method == 1 && !(l_osv > 0.0))
+    return fail(c, OSVMP2_E_ARG, "randomized OSVs need l_osv > 0 (the range finder stops on it)");
   CK(cudaSetDevice(c->device));
   free_system(c);
   c->sys = *s;
@@ -1278,8 +1353,13 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   TRY(upload(c, c->pair_id_d, c->pair_id));
   // batch the orbitals so that T, V and the eigen scratch stay within ~4 GB, in
   // batches of equal size (one CTA per orbital in the eigen kernel)
-  const int kmax = nv;
-  const size_t per = ((size_t)nv * nv * 2 + kmax + eig_osv_scratch_doubles(nv, kmax)) * sizeof(double);
+  const bool rosv = c->opts.osv_method == 1;
+  const int n_max = rosv ? std::min(nv, c->opts.rosv_max_rows > 0 ? c->opts.rosv_max_rows : 256) : 0;
+  const int kmax = rosv ? n_max : nv;
+  const RosvLayout rl1 = rosv_layout(1, nv, ROSV_WINDOW, std::max(n_max, 1), kmax);
+  const size_t per = ((size_t)nv * nv + (size_t)nv * kmax + kmax +
+                      (rosv ? rl1.total + (size_t)tc::NSL * (nv + rl1.rows) * rl1.ldk / 2 + 1
+                            : (size_t)nv * nv + eig_osv_scratch_doubles(nv, kmax))) * sizeof(double);
   int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, ((size_t)4 << 30) / per));
   nb = std::min(nb, 4 * c->num_sms);
   {
@@ -1296,7 +1376,18 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   TRY(tmp_alloc(c, Vm, (size_t)nb * nv * kmax * sizeof(double)));
   TRY(tmp_alloc(c, wm, (size_t)nb * kmax * sizeof(double)));
   TRY(tmp_alloc(c, km, (size_t)nb * sizeof(int)));
-  TRY(tmp_alloc(c, sm, (size_t)nb * eig_osv_scratch_doubles(nv, kmax) * sizeof(double)));
+  const RosvLayout rl = rosv_layout(nb, nv, ROSV_WINDOW, std::max(n_max, 1), kmax);
+  Tmp rsl;
+  if (rosv) {
+    TRY(tmp_alloc(c, sm, rl.total * sizeof(double)));
+    if (tii_tc) TRY(tmp_alloc(c, rsl, (size_t)rl.store_rows * rl.ldk * sizeof(float)));
+    if (tii_tc && rl.store_rows + tc::BM >= (long long)INT32_MAX)
+      return fail(c, OSVMP2_E_ARG, "randomized OSV slice store exceeds the tensor-map row range");
+  } else {
+    TRY(tmp_alloc(c, sm, (size_t)nb * eig_osv_scratch_doubles(nv, kmax) * sizeof(double)));
+  }
+  std::vector<int> nrows_h(nb);
+  const uint64_t rosv_key = mix64((uint64_t)s->seed ^ (7ull * STREAM_MUL));
   Tmp qtab;
   TRY(tmp_alloc(c, qtab, 2 * (size_t)nb * sizeof(double*)));
   c->n_osv.assign(n, 0);
@@ -1314,7 +1405,18 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
     ph_end(c, OSVMP2_PH_TII, (double)b * nv * (double)nv * s->n_aux, s->B ? 8.0 * b * (double)nv * s->n_aux : 0.0);
     CK(cudaGetLastError());
     ph_begin(c, OSVMP2_PH_EIG);
-    {
+    if (rosv) {
+      TRY(rosv_batch(c, (double*)Tm.p, b, i0, l_osv, n_max, kmax, tii_tc, rl, (double*)sm.p, (float*)rsl.p, rosv_key,
+                     (double*)Vm.p, (double*)wm.p, (int*)km.p, nrows_h));
+      ph_end(c, OSVMP2_PH_EIG, 0.0);
+      int h = 0;
+      CK(cudaMemcpyAsync(&h, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      if (h & ERR_SIZE)
+        return fail(c, OSVMP2_E_NUMERIC,
+                    "randomized OSVs: the range finder needs more than %d rows for an orbital of [%d, %d) "
+                    "(raise opts.rosv_max_rows)", n_max, i0, i0 + b);
+    } else {
       const double nd = nv;
       const bool full = (nv <= 160) || (l_osv <= 0.0);
       const double fl = (double)b * (full ? 9.0 * nd * nd * nd : (4.0 / 3.0) * nd * nd * nd);

@@ -77,6 +77,30 @@ void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, 
 // the shared-memory limit, thr > 0) after launch_eig_osv; a no-op otherwise.
 void launch_eig_back(double* T, int nb, int nv, double thr, int kmax, double* V, const int* k, double* scratch,
                      bool dfl_tridiag, cudaStream_t st);
+// Randomized OSVs (rosv.cu; Algorithm 3) for a batch of nb orbitals with T_ii in
+// T [nb][nv][nv].  Scratch layout (offsets in doubles) from rosv_layout; the
+// Gaussian draw k of orbital i, entry a, is the Irwin-Hall normal of counter
+// (i * ROSV_ROWS_PER_ORBITAL + k) * nv + a on the key of stream 7 of the seed.
+constexpr uint64_t ROSV_ROWS_PER_ORBITAL = 1ull << 16;
+constexpr int ROSV_WINDOW = 10;   // look-ahead rows r of the range finder
+struct RosvLayout {
+  int rows;                 // r + n_max Gaussian rows per orbital
+  size_t y, z, tt, svd, svd_per, wmax, nrows, total;
+  int ldk;                  // row stride of the TF32 slice store (mixed form)
+  long long store_rows;     // rows of the slice store: nb * NSL * (nv + rows)
+};
+RosvLayout rosv_layout(int nb, int nv, int r, int n_max, int kmax);
+// FP64 form: out[u] = A_u T_u with A_u the Gaussian rows (mode 0, rows rows) or
+// Z_u (mode 1, nrows[u] of n_max = rows rows).
+void launch_rosv_gemm64(int mode, const double* T, int nb, int nv, int i0, uint64_t key, const double* Z,
+                        const int* nrows, int rows, double* out, cudaStream_t st);
+// Mixed form: TF32 slices (K = nv) of T rows (part 0), Gaussian rows (1) or Z rows (2).
+void launch_rosv_slices(int part, const double* T, int nb, int nv, int i0, uint64_t key, const double* Z,
+                        const int* nrows, int rows, float* slices, int ldk, cudaStream_t st);
+void launch_rosv_finder(double* Y, int nb, int nv, int r, int n_max, double l_osv, double* Z, int* nrows,
+                        double* wmax, int* err, cudaStream_t st);
+void launch_rosv_svd(const double* Tt, const double* Z, const int* nrows, int nb, int nv, int n_max, double l_osv,
+                     int kmax, double* V, double* w, int* k, double* svd, int* err, cudaStream_t st);
 // Copy V[b][:, :k_b] into the packed Q store (Q[i0+b] as [nv][k]).
 void launch_pack_q(const double* V, const double* w, int nb, int nv, int kmax, const int* k,
                    double* const* Qdst, double* const* wdst, cudaStream_t st);

@@ -1,0 +1,305 @@
+// Randomized OSV generation (Algorithm 3; Eqs. rsvd_z, tsub, tii_rsvd, back_q,
+// rsvd_za), per orbital batch, replacing the full eigen-decomposition of T_ii:
+//   Ybar = [G; Gbar] T_ii      r + n_max Gaussian rows (counter-based draws)
+//   range finder              rows of Ybar taken in order, each orthogonalised
+//                             against Z (Eq. rsvd_za), until the r look-ahead
+//                             rows all have norm <= l_osv / (10 sqrt(2/pi))
+//   T~ = Z T_ii               (Eq. tsub)
+//   T~ = Q~ omega V~^T        (Eq. tii_rsvd) through the eigen-decomposition of
+//                             T~ T~^T (omega^2, Q~)
+//   Q = Z^T Q~                (Eq. back_q), kept where omega >= l_osv
+// The two GEMMs run in FP64 (FP64 form) or as split-TF32 tensor-core
+// contractions with FP64 results (mixed form); the range finder and the small
+// eigen-decomposition are FP64 in both.
+#include "internal.h"
+#include "eig.cuh"
+#include "tc_tf32x3.cuh"
+
+namespace osv {
+
+__device__ __forceinline__ double gauss_draw(uint64_t key, int i, int k, int nv, int a) {
+  return ih12(key, ((uint64_t)i * ROSV_ROWS_PER_ORBITAL + (uint64_t)k) * (uint64_t)nv + (uint64_t)a);
+}
+
+struct GaussRows {        // A(k, a) = Gaussian draw k of orbital i
+  uint64_t key;
+  int i, nv;
+  __device__ __forceinline__ double get(int k, int a) const { return gauss_draw(key, i, k, nv, a); }
+};
+struct Rows64 {           // A(r, c) = p[r * ld + c]
+  const double* p;
+  int ld;
+  __device__ __forceinline__ double get(int r, int c) const { return p[(size_t)r * ld + c]; }
+};
+
+// FP64 form: out[u] (rows x nv) = A_u T_u, A_u the Gaussian rows (mode 0) or Z_u (mode 1,
+// rows limited to nrows[u]).  grid: (orbital, row tile, column tile).
+__global__ void __launch_bounds__(NT) k_rosv_gemm64(int mode, const double* __restrict__ T, int nv, int i0,
+                                                    uint64_t key, const double* __restrict__ Z, const int* nrows,
+                                                    int rows, double* out) {
+  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  const int u = blockIdx.x;
+  const int M = mode == 0 ? rows : min(rows, nrows[u]);
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.z * TN;
+  if (m0 >= M) return;
+  const double* Tu = T + (size_t)u * nv * nv;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+  if (mode == 0) tile_mma(M, nv, nv, m0, n0, GaussRows{key, i0 + u, nv}, Rows64{Tu, nv}, acc, sm);
+  else tile_mma(M, nv, nv, m0, n0, Rows64{Z + (size_t)u * rows * nv, nv}, Rows64{Tu, nv}, acc, sm);
+  double* o = out + (size_t)u * rows * nv;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const int rr = m0 + ty + 16 * a, cc = n0 + tx + 16 * b;
+      if (rr < M && cc < nv) o[(size_t)rr * nv + cc] = acc[a][b];
+    }
+}
+
+// Mixed form: TF32 slices along K = n_vir of T_u rows (part 0), of the Gaussian
+// rows (part 1) or of Z_u rows (part 2) into the store of orbital u:
+//   T   slice s row a : base_u + s * nv + a
+//   G/Z slice s row k : base_u + NSL * nv + s * rows + k,  base_u = u * NSL * (nv + rows)
+// One warp per (row, 32-wide chunk); rows past nrows[u] (part 2) are written as zeros.
+__global__ void __launch_bounds__(256) k_rosv_slices(int part, const double* __restrict__ T, int nv, int i0,
+                                                     uint64_t key, const double* __restrict__ Z, const int* nrows,
+                                                     int rows, float* __restrict__ S, int ldk) {
+  const int u = blockIdx.y;
+  const int nch = (nv + tc::CHUNK - 1) / tc::CHUNK;
+  const int nr = part == 0 ? nv : rows;
+  const long long w = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (w >= (long long)nr * nch) return;   // warp-uniform
+  const int row = (int)(w / nch), k = (int)(w % nch) * tc::CHUNK + (threadIdx.x & 31);
+  double x = 0.0;
+  if (k < nv) {
+    if (part == 0) x = T[((size_t)u * nv + row) * nv + k];
+    else if (part == 1) x = gauss_draw(key, i0 + u, row, nv, k);
+    else if (row < nrows[u]) x = Z[((size_t)u * rows + row) * nv + k];
+  }
+  float v[tc::NSL];
+  tc::warp_fixed_slices(x, v);
+  if (k < nv) {
+    const size_t base = (size_t)u * tc::NSL * (nv + rows);
+    const size_t r0 = part == 0 ? base + row : base + (size_t)tc::NSL * nv + row;
+    const size_t ss = part == 0 ? (size_t)nv : (size_t)rows;
+#pragma unroll
+    for (int s = 0; s < tc::NSL; s++) S[(r0 + s * ss) * ldk + k] = v[s];
+  }
+}
+
+// Sum of x_a y_a over a < n by one warp (fixed order: lane stride, then the shuffle tree).
+__device__ __forceinline__ double warp_dot(const double* x, const double* y, int n) {
+  double s = 0.0;
+  for (int a = threadIdx.x & 31; a < n; a += 32) s = fma(x[a], y[a], s);
+  return warp_sum(s);
+}
+
+// The adaptive range finder of one orbital per CTA.  Y (r + n_max rows of the
+// orbital's Ybar) is updated in place: before step s (0-based) the look-ahead
+// window is rows s .. s+r-1.  Z receives the orthonormal rows, nrows the count.
+__global__ void __launch_bounds__(NT) k_rosv_finder(double* Yall, int nv, int r, int n_max, double thr, double* Zall,
+                                                    int* nrows, double* wmax, int* err) {
+  extern __shared__ double dyn[];
+  double* c = dyn;                 // n_max dot products
+  double* nrm = dyn + n_max;       // r window norms / dots
+  __shared__ double s_scale;
+  const int u = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NW = NT / 32;
+  double* Y = Yall + (size_t)u * (r + n_max) * nv;
+  double* Z = Zall + (size_t)u * n_max * nv;
+  int s = 0;
+  double mx = 0.0;
+  for (;;) {
+    for (int w = warp; w < r; w += NW) {
+      const double* y = Y + (size_t)(s + w) * nv;
+      const double d = warp_dot(y, y, nv);
+      if (lane == 0) nrm[w] = sqrt(d);
+    }
+    __syncthreads();
+    mx = 0.0;
+    for (int w = 0; w < r; w++) mx = fmax(mx, nrm[w]);
+    if (!(mx > thr) || s >= n_max) break;
+    // z^(s) = y^(s) (1 - Z^T Z) / norm   (Eq. rsvd_za)
+    const double* y = Y + (size_t)s * nv;
+    for (int q = warp; q < s; q += NW) {
+      const double d = warp_dot(y, Z + (size_t)q * nv, nv);
+      if (lane == 0) c[q] = d;
+    }
+    __syncthreads();
+    double* z = Z + (size_t)s * nv;
+    for (int a = threadIdx.x; a < nv; a += NT) {
+      double v = y[a];
+      for (int q = 0; q < s; q++) v = fma(-c[q], Z[(size_t)q * nv + a], v);
+      z[a] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const double d = warp_dot(z, z, nv);
+      if (lane == 0) s_scale = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+    }
+    __syncthreads();
+    const double sc = s_scale;
+    for (int a = threadIdx.x; a < nv; a += NT) z[a] *= sc;
+    // the fresh row g-bar^(s) T, projected against Z^(s-1) (rows 0 .. s-1 of Z)
+    double* yn = Y + (size_t)(s + r) * nv;
+    for (int q = warp; q < s; q += NW) {
+      const double d = warp_dot(yn, Z + (size_t)q * nv, nv);
+      if (lane == 0) c[q] = d;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < nv; a += NT) {
+      double v = yn[a];
+      for (int q = 0; q < s; q++) v = fma(-c[q], Z[(size_t)q * nv + a], v);
+      yn[a] = v;
+    }
+    __syncthreads();
+    // window rows s+1 .. s+r lose their z^(s) component
+    for (int w = warp; w < r; w += NW) {
+      const double d = warp_dot(Y + (size_t)(s + 1 + w) * nv, z, nv);
+      if (lane == 0) nrm[w] = d;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < r * nv; idx += NT) {
+      const int w = idx / nv, a = idx % nv;
+      Y[(size_t)(s + 1 + w) * nv + a] = fma(-nrm[w], z[a], Y[(size_t)(s + 1 + w) * nv + a]);
+    }
+    __syncthreads();
+    s++;
+  }
+  if (threadIdx.x == 0) {
+    nrows[u] = s;
+    wmax[u] = mx;
+    if (mx > thr) atomicOr(err, ERR_SIZE);   // the row budget ran out before the window vanished
+  }
+}
+
+// Low-rank SVD of T~ (nrows x nv) through T~ T~^T = Q~ omega^2 Q~^T, then
+// Q = Z^T Q~ for omega >= thr (descending), signed so that the largest-magnitude
+// entry of each vector is positive.  V [kmax][nv], w [kmax], k per orbital.
+// scratch per orbital: n_max^2 (M) + n_max^2 (eigenvectors) + n_max * kmax (selected) + 3 n_max.
+__global__ void __launch_bounds__(NT) k_rosv_svd(const double* Ttall, const double* Zall, const int* nrows, int nv,
+                                                 int n_max, double thr, int kmax, double* Vall, double* wall,
+                                                 int* kout, double* scratch, int* err) {
+  extern __shared__ double dyn[];
+  double* gsm = dyn;                              // GEMM_SMEM_DOUBLES
+  double* esm = dyn + GEMM_SMEM_DOUBLES;          // 4 n_max + 33 (cta_syev)
+  __shared__ int s_k;
+  const int u = blockIdx.x;
+  const int n = nrows[u];
+  const size_t N2 = (size_t)n_max * n_max;
+  double* M = scratch + (size_t)u * (2 * N2 + (size_t)n_max * kmax + 3 * (size_t)n_max);
+  double* E = M + N2;
+  double* Es = E + N2;
+  double* lam = Es + (size_t)n_max * kmax;
+  double* ee = lam + n_max;
+  double* tau = ee + n_max;
+  int* idx = reinterpret_cast<int*>(tau);         // reused after the eigen-solve
+  const double* Tt = Ttall + (size_t)u * n_max * nv;
+  const double* Z = Zall + (size_t)u * n_max * nv;
+  double* V = Vall + (size_t)u * kmax * nv;
+  if (n == 0) {
+    if (threadIdx.x == 0) kout[u] = 0;
+    return;
+  }
+  const View Tv = dense_view(Tt, n, nv, nv);
+  cta_gemm(n, n, nv, 1.0, Tv, transpose(Tv), 0.0, M, n, gsm);
+  const int rc = cta_syev(M, n, n, lam, E, n, ee, tau, esm);
+  if (threadIdx.x == 0) {
+    if (rc) atomicOr(err, ERR_EIG);
+    int k = 0;
+    for (int t = 0; t < n; t++) {
+      const double om = sqrt(fmax(lam[t], 0.0));
+      if (om >= thr && isfinite(om)) idx[k++] = t;
+    }
+    for (int a = 1; a < k; a++) {                 // descending omega, stable
+      const int v = idx[a];
+      int b = a - 1;
+      while (b >= 0 && lam[idx[b]] < lam[v]) { idx[b + 1] = idx[b]; b--; }
+      idx[b + 1] = v;
+    }
+    if (k > kmax) { k = kmax; atomicOr(err, ERR_SIZE); }
+    s_k = k;
+  }
+  __syncthreads();
+  const int k = s_k;
+  for (int e = threadIdx.x; e < n * k; e += NT) Es[e] = E[(size_t)(e / k) * n + idx[e % k]];
+  for (int t = threadIdx.x; t < k; t += NT) wall[(size_t)u * kmax + t] = sqrt(fmax(lam[idx[t]], 0.0));
+  __syncthreads();
+  // V (k x nv) = Es^T Z
+  cta_gemm(k, nv, n, 1.0, transpose(dense_view(Es, n, k, k)), dense_view(Z, n, nv, nv), 0.0, V, nv, gsm);
+  // sign: the largest-magnitude entry (first on ties) positive
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = warp; t < k; t += NT / 32) {
+    double* v = V + (size_t)t * nv;
+    double best = -1.0;
+    int bi = nv;
+    for (int a = lane; a < nv; a += 32) {
+      const double m = fabs(v[a]);
+      if (m > best) { best = m; bi = a; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    const bool neg = v[bi] < 0.0;
+    __syncwarp();
+    if (neg)
+      for (int a = lane; a < nv; a += 32) v[a] = -v[a];
+  }
+  if (threadIdx.x == 0) kout[u] = k;
+}
+
+RosvLayout rosv_layout(int nb, int nv, int r, int n_max, int kmax) {
+  RosvLayout L;
+  L.rows = r + n_max;
+  L.y = 0;
+  L.z = L.y + (size_t)nb * L.rows * nv;
+  L.tt = L.z + (size_t)nb * n_max * nv;
+  L.svd = L.tt + (size_t)nb * n_max * nv;
+  L.svd_per = 2 * (size_t)n_max * n_max + (size_t)n_max * kmax + 3 * (size_t)n_max;
+  L.wmax = L.svd + (size_t)nb * L.svd_per;
+  L.nrows = L.wmax + nb;
+  L.total = L.nrows + (size_t)nb + 64;
+  L.ldk = (nv + 3) & ~3;
+  L.store_rows = (long long)nb * tc::NSL * (nv + L.rows);
+  return L;
+}
+
+void launch_rosv_gemm64(int mode, const double* T, int nb, int nv, int i0, uint64_t key, const double* Z,
+                        const int* nrows, int rows, double* out, cudaStream_t st) {
+  dim3 g(nb, (rows + TM - 1) / TM, (nv + TN - 1) / TN);
+  k_rosv_gemm64<<<g, NT, 0, st>>>(mode, T, nv, i0, key, Z, nrows, rows, out);
+  note_launch(1);
+}
+
+void launch_rosv_slices(int part, const double* T, int nb, int nv, int i0, uint64_t key, const double* Z,
+                        const int* nrows, int rows, float* slices, int ldk, cudaStream_t st) {
+  const int nch = (nv + tc::CHUNK - 1) / tc::CHUNK;
+  const long long nr = part == 0 ? nv : rows;
+  dim3 g((unsigned)((nr * nch + 7) / 8), nb);
+  k_rosv_slices<<<g, 256, 0, st>>>(part, T, nv, i0, key, Z, nrows, rows, slices, ldk);
+  note_launch(1);
+}
+
+void launch_rosv_finder(double* Y, int nb, int nv, int r, int n_max, double l_osv, double* Z, int* nrows,
+                        double* wmax, int* err, cudaStream_t st) {
+  const double thr = l_osv / (10.0 * 0.7978845608028654);   // l_osv / (10 sqrt(2/pi))
+  k_rosv_finder<<<nb, NT, (size_t)(n_max + r) * sizeof(double), st>>>(Y, nv, r, n_max, thr, Z, nrows, wmax, err);
+  note_launch(1);
+}
+
+void launch_rosv_svd(const double* Tt, const double* Z, const int* nrows, int nb, int nv, int n_max, double l_osv,
+                     int kmax, double* V, double* w, int* k, double* svd, int* err, cudaStream_t st) {
+  const size_t ssm = (size_t)(GEMM_SMEM_DOUBLES + 4 * n_max + 33) * sizeof(double);
+  cudaFuncSetAttribute(k_rosv_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+  k_rosv_svd<<<nb, NT, ssm, st>>>(Tt, Z, nrows, nv, n_max, l_osv, kmax, V, w, k, svd, err);
+  note_launch(1);
+}
+
+}  // namespace osv

@@ -28,7 +28,8 @@ STATUS_CODES = {v: k for k, v in STATUS.items()}
 class Opts(ctypes.Structure):
     _fields_ = [("tau_s", ctypes.c_double), ("tol_update", ctypes.c_double), ("tol_energy", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("osv_prec", ctypes.c_int32), ("no_autotune", ctypes.c_int32),
-                ("mem_cap_mib", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("mem_cap_mib", ctypes.c_int32), ("osv_method", ctypes.c_int32), ("rosv_max_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class System(ctypes.Structure):
@@ -206,6 +207,8 @@ def _apply_opts(o: Opts, kw) -> None:
     for k, v in kw.items():
         if k == "osv_prec" and isinstance(v, str):
             v = PREC[v]
+        if k == "osv_method" and isinstance(v, str):
+            v = {"exact": 0, "randomized": 1}[v]
         setattr(o, k, v)
 
 
