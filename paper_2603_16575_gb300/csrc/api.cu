@@ -1280,8 +1280,8 @@ static int rosv_batch(osvmp2_ctx* c, double* T, int b, int i0, double l_osv, int
   };
   double fl = 2.0 * rows * (double)nv * nv * b;
   if (tensor) {
-    launch_rosv_slices(0, T, b, nv, i0, key, nullptr, nullptr, rows, slices, rl.ldk, c->st);
-    launch_rosv_slices(1, T, b, nv, i0, key, nullptr, nullptr, rows, slices, rl.ldk, c->st);
+    launch_rosv_slices(0, T, b, nv, i0, key, nullptr, 0, nullptr, rows, slices, rl.ldk, c->st);
+    launch_rosv_slices(1, T, b, nv, i0, key, nullptr, 0, nullptr, rows, slices, rl.ldk, c->st);
     CK(cudaGetLastError());
     std::vector<tc::Job> jobs;
     for (int u = 0; u < b; u++) tc_jobs(u, rows, Y, rows, jobs);
@@ -1296,7 +1296,7 @@ static int rosv_batch(osvmp2_ctx* c, double* T, int b, int i0, double l_osv, int
   CK(cudaStreamSynchronize(c->st));
   for (int u = 0; u < b; u++) fl += 2.0 * nrows_h[u] * (double)nv * nv + 2.0 * nrows_h[u] * (double)nrows_h[u] * nv;
   if (tensor) {
-    launch_rosv_slices(2, T, b, nv, i0, key, Z, nrows, rows, slices, rl.ldk, c->st);
+    launch_rosv_slices(2, T, b, nv, i0, key, Z, n_max, nrows, rows, slices, rl.ldk, c->st);
     CK(cudaGetLastError());
     std::vector<tc::Job> jobs;
     for (int u = 0; u < b; u++) tc_jobs(u, nrows_h[u], Tt, n_max, jobs);

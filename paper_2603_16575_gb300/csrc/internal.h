@@ -96,7 +96,7 @@ void launch_rosv_gemm64(int mode, const double* T, int nb, int nv, int i0, uint6
                         const int* nrows, int rows, double* out, cudaStream_t st);
 // Mixed form: TF32 slices (K = nv) of T rows (part 0), Gaussian rows (1) or Z rows (2).
 void launch_rosv_slices(int part, const double* T, int nb, int nv, int i0, uint64_t key, const double* Z,
-                        const int* nrows, int rows, float* slices, int ldk, cudaStream_t st);
+                        int z_rows, const int* nrows, int rows, float* slices, int ldk, cudaStream_t st);
 void launch_rosv_finder(double* Y, int nb, int nv, int r, int n_max, double l_osv, double* Z, int* nrows,
                         double* wmax, int* err, cudaStream_t st);
 void launch_rosv_svd(const double* Tt, const double* Z, const int* nrows, int nb, int nv, int n_max, double l_osv,

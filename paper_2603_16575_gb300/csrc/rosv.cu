@@ -67,11 +67,11 @@ __global__ void __launch_bounds__(NT) k_rosv_gemm64(int mode, const double* __re
 //   G/Z slice s row k : base_u + NSL * nv + s * rows + k,  base_u = u * NSL * (nv + rows)
 // One warp per (row, 32-wide chunk); rows past nrows[u] (part 2) are written as zeros.
 __global__ void __launch_bounds__(256) k_rosv_slices(int part, const double* __restrict__ T, int nv, int i0,
-                                                     uint64_t key, const double* __restrict__ Z, const int* nrows,
-                                                     int rows, float* __restrict__ S, int ldk) {
+                                                     uint64_t key, const double* __restrict__ Z, int z_rows,
+                                                     const int* nrows, int rows, float* __restrict__ S, int ldk) {
   const int u = blockIdx.y;
   const int nch = (nv + tc::CHUNK - 1) / tc::CHUNK;
-  const int nr = part == 0 ? nv : rows;
+  const int nr = part == 0 ? nv : rows;   // part 2 writes zeros for rows >= nrows[u] (<= z_rows)
   const long long w = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (w >= (long long)nr * nch) return;   // warp-uniform
   const int row = (int)(w / nch), k = (int)(w % nch) * tc::CHUNK + (threadIdx.x & 31);
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_rosv_slices(int part, const double* __r
   if (k < nv) {
     if (part == 0) x = T[((size_t)u * nv + row) * nv + k];
     else if (part == 1) x = gauss_draw(key, i0 + u, row, nv, k);
-    else if (row < nrows[u]) x = Z[((size_t)u * rows + row) * nv + k];
+    else if (row < nrows[u]) x = Z[((size_t)u * z_rows + row) * nv + k];   // Z: [orbital][z_rows][nv]
   }
   float v[tc::NSL];
   tc::warp_fixed_slices(x, v);
@@ -279,11 +279,11 @@ void launch_rosv_gemm64(int mode, const double* T, int nb, int nv, int i0, uint6
 }
 
 void launch_rosv_slices(int part, const double* T, int nb, int nv, int i0, uint64_t key, const double* Z,
-                        const int* nrows, int rows, float* slices, int ldk, cudaStream_t st) {
+                        int z_rows, const int* nrows, int rows, float* slices, int ldk, cudaStream_t st) {
   const int nch = (nv + tc::CHUNK - 1) / tc::CHUNK;
   const long long nr = part == 0 ? nv : rows;
   dim3 g((unsigned)((nr * nch + 7) / 8), nb);
-  k_rosv_slices<<<g, 256, 0, st>>>(part, T, nv, i0, key, Z, nrows, rows, slices, ldk);
+  k_rosv_slices<<<g, 256, 0, st>>>(part, T, nv, i0, key, Z, z_rows, nrows, rows, slices, ldk);
   note_launch(1);
 }
 
