@@ -1305,7 +1305,48 @@ static int rosv_batch(osvmp2_ctx* c, double* T, int b, int i0, double l_osv, int
     launch_rosv_gemm64(1, T, b, nv, i0, key, Z, nrows, n_max, Tt, c->st);
     CK(cudaGetLastError());
   }
-  launch_rosv_svd(Tt, Z, nrows, b, nv, n_max, l_osv, kmax, V, w, k, scr + rl.svd, c->err_d, c->st);
+  // SVD of T~ through T~ T~^T = Q~ omega^2 Q~^T: the Gram matrices (padded to the
+  // batch's largest row count; the padding adds only zero eigenvalues, never kept)
+  // go through the OSV eigen-kernel with the cut l_osv^2, then Q = Z^T Q~.
+  int ldm = 1;
+  for (int u = 0; u < b; u++) ldm = std::max(ldm, nrows_h[u]);
+  double* M = scr + rl.svd;
+  double* Vs = M + (size_t)b * ldm * ldm;
+  double* ws = Vs + (size_t)b * ldm * ldm;
+  int* ks = reinterpret_cast<int*>(ws + (size_t)b * ldm);
+  double* es = ws + (size_t)b * ldm + b;
+  if (tensor) {
+    CK(cudaMemsetAsync(M, 0, (size_t)b * ldm * ldm * sizeof(double), c->st));
+    launch_rosv_slices(3, T, b, nv, i0, key, Tt, n_max, nrows, rows, slices, rl.ldk, c->st);
+    CK(cudaGetLastError());
+    std::vector<tc::Job> jobs;
+    for (int u = 0; u < b; u++) {
+      const long long base = (long long)u * tc::NSL * (nv + rows);
+      for (int m0 = 0; m0 < nrows_h[u]; m0 += tc::BM)
+        for (int n0 = 0; n0 < nrows_h[u]; n0 += tc::BN) {
+          tc::Job jb{};
+          jb.a_row = (int)(base + m0);
+          jb.a_sstride = nv;
+          jb.b_row = (int)(base + n0);
+          jb.b_sstride = nv;
+          jb.m_valid = std::min(tc::BM, nrows_h[u] - m0);
+          jb.n_valid = std::min(tc::BN, nrows_h[u] - n0);
+          jb.out = M + (size_t)u * ldm * ldm + (size_t)m0 * ldm + n0;
+          jb.ld_out = ldm;
+          jb.m0 = m0;
+          jb.n0 = n0;
+          jobs.push_back(jb);
+        }
+    }
+    TRY(run_tc(jobs));
+  } else {
+    launch_rosv_gram64(Tt, nrows, b, nv, n_max, ldm, M, c->st);
+    CK(cudaGetLastError());
+  }
+  const double thr2 = l_osv * l_osv;
+  launch_eig_osv(M, b, ldm, thr2, ldm, Vs, ws, ks, es, c->err_d, false, c->st);
+  launch_eig_back(M, b, ldm, thr2, ldm, Vs, ks, es, false, c->st);
+  launch_rosv_backq(Vs, ws, ks, Z, nrows, b, nv, n_max, ldm, kmax, V, w, k, c->st);
   CK(cudaGetLastError());
   c->flops[OSVMP2_PH_EIG] += fl;
   return 0;

@@ -99,8 +99,12 @@ void launch_rosv_slices(int part, const double* T, int nb, int nv, int i0, uint6
                         int z_rows, const int* nrows, int rows, float* slices, int ldk, cudaStream_t st);
 void launch_rosv_finder(double* Y, int nb, int nv, int r, int n_max, double l_osv, double* Z, int* nrows,
                         double* wmax, int* err, cudaStream_t st);
-void launch_rosv_svd(const double* Tt, const double* Z, const int* nrows, int nb, int nv, int n_max, double l_osv,
-                     int kmax, double* V, double* w, int* k, double* svd, int* err, cudaStream_t st);
+// FP64 form: M[u] = T~ T~^T ([nb][ldm][ldm], zero outside nrows[u]).
+void launch_rosv_gram64(const double* Tt, const int* nrows, int nb, int nv, int n_max, int ldm, double* M,
+                        cudaStream_t st);
+// Q = Q~^T Z and omega = sqrt(eigenvalues of M) for the ks[u] kept eigenvectors Vs ([nb][ldm][ldm]).
+void launch_rosv_backq(const double* Vs, const double* ws, const int* ks, const double* Z, const int* nrows, int nb,
+                       int nv, int n_max, int ldm, int kmax, double* V, double* w, int* k, cudaStream_t st);
 // Copy V[b][:, :k_b] into the packed Q store (Q[i0+b] as [nv][k]).
 void launch_pack_q(const double* V, const double* w, int nb, int nv, int kmax, const int* k,
                    double* const* Qdst, double* const* wdst, cudaStream_t st);

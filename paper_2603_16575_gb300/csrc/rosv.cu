@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_rosv_slices(int part, const double* __r
                                                      const int* nrows, int rows, float* __restrict__ S, int ldk) {
   const int u = blockIdx.y;
   const int nch = (nv + tc::CHUNK - 1) / tc::CHUNK;
-  const int nr = part == 0 ? nv : rows;   // part 2 writes zeros for rows >= nrows[u] (<= z_rows)
+  const int nr = (part == 0 || part == 3) ? nv : rows;   // parts 2, 3 write zeros for rows >= nrows[u]
   const long long w = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (w >= (long long)nr * nch) return;   // warp-uniform
   const int row = (int)(w / nch), k = (int)(w % nch) * tc::CHUNK + (threadIdx.x & 31);
@@ -79,24 +79,33 @@ __global__ void __launch_bounds__(256) k_rosv_slices(int part, const double* __r
   if (k < nv) {
     if (part == 0) x = T[((size_t)u * nv + row) * nv + k];
     else if (part == 1) x = gauss_draw(key, i0 + u, row, nv, k);
-    else if (row < nrows[u]) x = Z[((size_t)u * z_rows + row) * nv + k];   // Z: [orbital][z_rows][nv]
+    else if (row < nrows[u]) x = Z[((size_t)u * z_rows + row) * nv + k];   // Z or T~: [orbital][z_rows][nv]
   }
   float v[tc::NSL];
   tc::warp_fixed_slices(x, v);
   if (k < nv) {
     const size_t base = (size_t)u * tc::NSL * (nv + rows);
-    const size_t r0 = part == 0 ? base + row : base + (size_t)tc::NSL * nv + row;
-    const size_t ss = part == 0 ? (size_t)nv : (size_t)rows;
+    const bool treg = part == 0 || part == 3;   // T region (T, then T~) or G region (G, then Z)
+    const size_t r0 = treg ? base + row : base + (size_t)tc::NSL * nv + row;
+    const size_t ss = treg ? (size_t)nv : (size_t)rows;
 #pragma unroll
     for (int s = 0; s < tc::NSL; s++) S[(r0 + s * ss) * ldk + k] = v[s];
   }
 }
 
-// Sum of x_a y_a over a < n by one warp (fixed order: lane stride, then the shuffle tree).
+// Sum of x_a y_a over a < n by one warp: four interleaved partial sums per lane
+// (independent loads in flight), combined in a fixed order, then the shuffle tree.
 __device__ __forceinline__ double warp_dot(const double* x, const double* y, int n) {
-  double s = 0.0;
-  for (int a = threadIdx.x & 31; a < n; a += 32) s = fma(x[a], y[a], s);
-  return warp_sum(s);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int a = threadIdx.x & 31;
+  for (; a + 96 < n; a += 128) {
+    s0 = fma(x[a], y[a], s0);
+    s1 = fma(x[a + 32], y[a + 32], s1);
+    s2 = fma(x[a + 64], y[a + 64], s2);
+    s3 = fma(x[a + 96], y[a + 96], s3);
+  }
+  for (; a < n; a += 32) s0 = fma(x[a], y[a], s0);
+  return warp_sum((s0 + s1) + (s2 + s3));
 }
 
 // The adaptive range finder of one orbital per CTA.  Y (r + n_max rows of the
@@ -178,61 +187,33 @@ __global__ void __launch_bounds__(NT) k_rosv_finder(double* Yall, int nv, int r,
   }
 }
 
-// Low-rank SVD of T~ (nrows x nv) through T~ T~^T = Q~ omega^2 Q~^T, then
-// Q = Z^T Q~ for omega >= thr (descending), signed so that the largest-magnitude
-// entry of each vector is positive.  V [kmax][nv], w [kmax], k per orbital.
-// scratch per orbital: n_max^2 (M) + n_max^2 (eigenvectors) + n_max * kmax (selected) + 3 n_max.
-__global__ void __launch_bounds__(NT) k_rosv_svd(const double* Ttall, const double* Zall, const int* nrows, int nv,
-                                                 int n_max, double thr, int kmax, double* Vall, double* wall,
-                                                 int* kout, double* scratch, int* err) {
-  extern __shared__ double dyn[];
-  double* gsm = dyn;                              // GEMM_SMEM_DOUBLES
-  double* esm = dyn + GEMM_SMEM_DOUBLES;          // 4 n_max + 33 (cta_syev)
-  __shared__ int s_k;
+// FP64 form: M[u] (nb x nb padded, zeros outside n = nrows[u]) = T~ T~^T.
+__global__ void __launch_bounds__(NT) k_rosv_gram64(const double* Ttall, const int* nrows, int nv, int n_max, int ldm,
+                                                    double* Mall) {
+  __shared__ double sm[GEMM_SMEM_DOUBLES];
   const int u = blockIdx.x;
   const int n = nrows[u];
-  const size_t N2 = (size_t)n_max * n_max;
-  double* M = scratch + (size_t)u * (2 * N2 + (size_t)n_max * kmax + 3 * (size_t)n_max);
-  double* E = M + N2;
-  double* Es = E + N2;
-  double* lam = Es + (size_t)n_max * kmax;
-  double* ee = lam + n_max;
-  double* tau = ee + n_max;
-  int* idx = reinterpret_cast<int*>(tau);         // reused after the eigen-solve
-  const double* Tt = Ttall + (size_t)u * n_max * nv;
-  const double* Z = Zall + (size_t)u * n_max * nv;
+  double* M = Mall + (size_t)u * ldm * ldm;
+  for (int e = threadIdx.x; e < ldm * ldm; e += NT) M[e] = 0.0;
+  __syncthreads();
+  const View Tv = dense_view(Ttall + (size_t)u * n_max * nv, n, nv, nv);
+  cta_gemm(n, n, nv, 1.0, Tv, transpose(Tv), 0.0, M, ldm, sm);
+}
+
+// Q (k x nv) = Q~^T Z from the eigenvectors Q~ of M (eigenvector-major [kmax][ldm],
+// descending eigenvalues omega^2), omega = sqrt; each vector signed so that its
+// largest-magnitude entry (the first on ties) is positive.
+__global__ void __launch_bounds__(NT) k_rosv_backq(const double* Vsall, const double* wsall, const int* ks,
+                                                   const double* Zall, const int* nrows, int nv, int n_max, int ldm,
+                                                   int kmax, double* Vall, double* wall, int* kout) {
+  __shared__ double sm[GEMM_SMEM_DOUBLES];
+  const int u = blockIdx.x;
+  const int n = nrows[u], k = ks[u];
+  const double* Vs = Vsall + (size_t)u * ldm * ldm;
   double* V = Vall + (size_t)u * kmax * nv;
-  if (n == 0) {
-    if (threadIdx.x == 0) kout[u] = 0;
-    return;
-  }
-  const View Tv = dense_view(Tt, n, nv, nv);
-  cta_gemm(n, n, nv, 1.0, Tv, transpose(Tv), 0.0, M, n, gsm);
-  const int rc = cta_syev(M, n, n, lam, E, n, ee, tau, esm);
-  if (threadIdx.x == 0) {
-    if (rc) atomicOr(err, ERR_EIG);
-    int k = 0;
-    for (int t = 0; t < n; t++) {
-      const double om = sqrt(fmax(lam[t], 0.0));
-      if (om >= thr && isfinite(om)) idx[k++] = t;
-    }
-    for (int a = 1; a < k; a++) {                 // descending omega, stable
-      const int v = idx[a];
-      int b = a - 1;
-      while (b >= 0 && lam[idx[b]] < lam[v]) { idx[b + 1] = idx[b]; b--; }
-      idx[b + 1] = v;
-    }
-    if (k > kmax) { k = kmax; atomicOr(err, ERR_SIZE); }
-    s_k = k;
-  }
-  __syncthreads();
-  const int k = s_k;
-  for (int e = threadIdx.x; e < n * k; e += NT) Es[e] = E[(size_t)(e / k) * n + idx[e % k]];
-  for (int t = threadIdx.x; t < k; t += NT) wall[(size_t)u * kmax + t] = sqrt(fmax(lam[idx[t]], 0.0));
-  __syncthreads();
-  // V (k x nv) = Es^T Z
-  cta_gemm(k, nv, n, 1.0, transpose(dense_view(Es, n, k, k)), dense_view(Z, n, nv, nv), 0.0, V, nv, gsm);
-  // sign: the largest-magnitude entry (first on ties) positive
+  cta_gemm(k, nv, n, 1.0, dense_view(Vs, k, n, ldm), dense_view(Zall + (size_t)u * n_max * nv, n, nv, nv), 0.0, V,
+           nv, sm);
+  for (int t = threadIdx.x; t < k; t += NT) wall[(size_t)u * kmax + t] = sqrt(fmax(wsall[(size_t)u * ldm + t], 0.0));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int t = warp; t < k; t += NT / 32) {
     double* v = V + (size_t)t * nv;
@@ -262,7 +243,8 @@ RosvLayout rosv_layout(int nb, int nv, int r, int n_max, int kmax) {
   L.z = L.y + (size_t)nb * L.rows * nv;
   L.tt = L.z + (size_t)nb * n_max * nv;
   L.svd = L.tt + (size_t)nb * n_max * nv;
-  L.svd_per = 2 * (size_t)n_max * n_max + (size_t)n_max * kmax + 3 * (size_t)n_max;
+  (void)kmax;
+  L.svd_per = 2 * (size_t)n_max * n_max + 2 * (size_t)n_max + eig_osv_scratch_doubles(n_max, n_max);
   L.wmax = L.svd + (size_t)nb * L.svd_per;
   L.nrows = L.wmax + nb;
   L.total = L.nrows + (size_t)nb + 64;
@@ -294,11 +276,15 @@ void launch_rosv_finder(double* Y, int nb, int nv, int r, int n_max, double l_os
   note_launch(1);
 }
 
-void launch_rosv_svd(const double* Tt, const double* Z, const int* nrows, int nb, int nv, int n_max, double l_osv,
-                     int kmax, double* V, double* w, int* k, double* svd, int* err, cudaStream_t st) {
-  const size_t ssm = (size_t)(GEMM_SMEM_DOUBLES + 4 * n_max + 33) * sizeof(double);
-  cudaFuncSetAttribute(k_rosv_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
-  k_rosv_svd<<<nb, NT, ssm, st>>>(Tt, Z, nrows, nv, n_max, l_osv, kmax, V, w, k, svd, err);
+void launch_rosv_gram64(const double* Tt, const int* nrows, int nb, int nv, int n_max, int ldm, double* M,
+                        cudaStream_t st) {
+  k_rosv_gram64<<<nb, NT, 0, st>>>(Tt, nrows, nv, n_max, ldm, M);
+  note_launch(1);
+}
+
+void launch_rosv_backq(const double* Vs, const double* ws, const int* ks, const double* Z, const int* nrows, int nb,
+                       int nv, int n_max, int ldm, int kmax, double* V, double* w, int* k, cudaStream_t st) {
+  k_rosv_backq<<<nb, NT, 0, st>>>(Vs, ws, ks, Z, nrows, nv, n_max, ldm, kmax, V, w, k);
   note_launch(1);
 }
 
