@@ -93,29 +93,40 @@ __global__ void __launch_bounds__(256) k_rosv_slices(int part, const double* __r
   }
 }
 
-// Sum of x_a y_a over a < n by one warp: four interleaved partial sums per lane
-// (independent loads in flight), combined in a fixed order, then the shuffle tree.
-__device__ __forceinline__ double warp_dot(const double* x, const double* y, int n) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int a = threadIdx.x & 31;
-  for (; a + 96 < n; a += 128) {
-    s0 = fma(x[a], y[a], s0);
-    s1 = fma(x[a + 32], y[a + 32], s1);
-    s2 = fma(x[a + 64], y[a + 64], s2);
-    s3 = fma(x[a + 96], y[a + 96], s3);
+// out[q] = rows[q] . v for q < count (rows nv apart), v in shared memory; each warp
+// takes groups of eight rows with eight partial sums per lane in flight, then the
+// shuffle tree (fixed order).
+__device__ void block_dots(const double* rows, int count, const double* v, int nv, double* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NW = NT / 32;
+  for (int q0 = warp * 8; q0 < count; q0 += NW * 8) {
+    double acc[8];
+#pragma unroll
+    for (int t = 0; t < 8; t++) acc[t] = 0.0;
+    for (int a = lane; a < nv; a += 32) {
+      const double va = v[a];
+#pragma unroll
+      for (int t = 0; t < 8; t++)
+        if (q0 + t < count) acc[t] = fma(rows[(size_t)(q0 + t) * nv + a], va, acc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+      const double sum = warp_sum(acc[t]);
+      if (lane == 0 && q0 + t < count) out[q0 + t] = sum;
+    }
   }
-  for (; a < n; a += 32) s0 = fma(x[a], y[a], s0);
-  return warp_sum((s0 + s1) + (s2 + s3));
 }
 
 // The adaptive range finder of one orbital per CTA.  Y (r + n_max rows of the
 // orbital's Ybar) is updated in place: before step s (0-based) the look-ahead
 // window is rows s .. s+r-1.  Z receives the orthonormal rows, nrows the count.
+// Shared memory: the vector being orthogonalised (nv), the dots (n_max + r).
 __global__ void __launch_bounds__(NT) k_rosv_finder(double* Yall, int nv, int r, int n_max, double thr, double* Zall,
                                                     int* nrows, double* wmax, int* err) {
   extern __shared__ double dyn[];
-  double* c = dyn;                 // n_max dot products
-  double* nrm = dyn + n_max;       // r window norms / dots
+  double* vec = dyn;               // nv
+  double* c = dyn + nv;            // n_max dot products
+  double* nrm = c + n_max;         // r window norms / dots
   __shared__ double s_scale;
   const int u = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NW = NT / 32;
@@ -126,7 +137,9 @@ __global__ void __launch_bounds__(NT) k_rosv_finder(double* Yall, int nv, int r,
   for (;;) {
     for (int w = warp; w < r; w += NW) {
       const double* y = Y + (size_t)(s + w) * nv;
-      const double d = warp_dot(y, y, nv);
+      double d = 0.0;
+      for (int a = lane; a < nv; a += 32) d = fma(y[a], y[a], d);
+      d = warp_sum(d);
       if (lane == 0) nrm[w] = sqrt(d);
     }
     __syncthreads();
@@ -135,20 +148,21 @@ __global__ void __launch_bounds__(NT) k_rosv_finder(double* Yall, int nv, int r,
     if (!(mx > thr) || s >= n_max) break;
     // z^(s) = y^(s) (1 - Z^T Z) / norm   (Eq. rsvd_za)
     const double* y = Y + (size_t)s * nv;
-    for (int q = warp; q < s; q += NW) {
-      const double d = warp_dot(y, Z + (size_t)q * nv, nv);
-      if (lane == 0) c[q] = d;
-    }
+    for (int a = threadIdx.x; a < nv; a += NT) vec[a] = y[a];
+    __syncthreads();
+    block_dots(Z, s, vec, nv, c);
     __syncthreads();
     double* z = Z + (size_t)s * nv;
     for (int a = threadIdx.x; a < nv; a += NT) {
-      double v = y[a];
+      double v = vec[a];
       for (int q = 0; q < s; q++) v = fma(-c[q], Z[(size_t)q * nv + a], v);
       z[a] = v;
     }
     __syncthreads();
     if (warp == 0) {
-      const double d = warp_dot(z, z, nv);
+      double d = 0.0;
+      for (int a = lane; a < nv; a += 32) d = fma(z[a], z[a], d);
+      d = warp_sum(d);
       if (lane == 0) s_scale = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
     }
     __syncthreads();
@@ -156,26 +170,23 @@ __global__ void __launch_bounds__(NT) k_rosv_finder(double* Yall, int nv, int r,
     for (int a = threadIdx.x; a < nv; a += NT) z[a] *= sc;
     // the fresh row g-bar^(s) T, projected against Z^(s-1) (rows 0 .. s-1 of Z)
     double* yn = Y + (size_t)(s + r) * nv;
-    for (int q = warp; q < s; q += NW) {
-      const double d = warp_dot(yn, Z + (size_t)q * nv, nv);
-      if (lane == 0) c[q] = d;
-    }
+    for (int a = threadIdx.x; a < nv; a += NT) vec[a] = yn[a];
+    __syncthreads();
+    block_dots(Z, s, vec, nv, c);
     __syncthreads();
     for (int a = threadIdx.x; a < nv; a += NT) {
-      double v = yn[a];
+      double v = vec[a];
       for (int q = 0; q < s; q++) v = fma(-c[q], Z[(size_t)q * nv + a], v);
       yn[a] = v;
     }
-    __syncthreads();
     // window rows s+1 .. s+r lose their z^(s) component
-    for (int w = warp; w < r; w += NW) {
-      const double d = warp_dot(Y + (size_t)(s + 1 + w) * nv, z, nv);
-      if (lane == 0) nrm[w] = d;
-    }
+    for (int a = threadIdx.x; a < nv; a += NT) vec[a] = z[a];
+    __syncthreads();
+    block_dots(Y + (size_t)(s + 1) * nv, r, vec, nv, nrm);
     __syncthreads();
     for (int idx = threadIdx.x; idx < r * nv; idx += NT) {
       const int w = idx / nv, a = idx % nv;
-      Y[(size_t)(s + 1 + w) * nv + a] = fma(-nrm[w], z[a], Y[(size_t)(s + 1 + w) * nv + a]);
+      Y[(size_t)(s + 1 + w) * nv + a] = fma(-nrm[w], vec[a], Y[(size_t)(s + 1 + w) * nv + a]);
     }
     __syncthreads();
     s++;
@@ -272,7 +283,9 @@ void launch_rosv_slices(int part, const double* T, int nb, int nv, int i0, uint6
 void launch_rosv_finder(double* Y, int nb, int nv, int r, int n_max, double l_osv, double* Z, int* nrows,
                         double* wmax, int* err, cudaStream_t st) {
   const double thr = l_osv / (10.0 * 0.7978845608028654);   // l_osv / (10 sqrt(2/pi))
-  k_rosv_finder<<<nb, NT, (size_t)(n_max + r) * sizeof(double), st>>>(Y, nv, r, n_max, thr, Z, nrows, wmax, err);
+  const size_t smem = (size_t)(nv + n_max + r) * sizeof(double);
+  cudaFuncSetAttribute(k_rosv_finder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_rosv_finder<<<nb, NT, smem, st>>>(Y, nv, r, n_max, thr, Z, nrows, wmax, err);
   note_launch(1);
 }
 
