@@ -96,9 +96,11 @@ __global__ void __launch_bounds__(256) k_rosv_slices(int part, const double* __r
 // out[q] = rows[q] . v for q < count (rows nv apart), v in shared memory; each warp
 // takes groups of eight rows with eight partial sums per lane in flight, then the
 // shuffle tree (fixed order).
+constexpr int NT_F = 1024;   // threads of the range-finder CTA
+
 __device__ void block_dots(const double* rows, int count, const double* v, int nv, double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NW = NT / 32;
+  constexpr int NW = NT_F / 32;
   for (int q0 = warp * 8; q0 < count; q0 += NW * 8) {
     double acc[8];
 #pragma unroll
@@ -121,7 +123,21 @@ __device__ void block_dots(const double* rows, int count, const double* v, int n
 // orbital's Ybar) is updated in place: before step s (0-based) the look-ahead
 // window is rows s .. s+r-1.  Z receives the orthonormal rows, nrows the count.
 // Shared memory: the vector being orthogonalised (nv), the dots (n_max + r).
-__global__ void __launch_bounds__(NT) k_rosv_finder(double* Yall, int nv, int r, int n_max, double thr, double* Zall,
+// v - sum_{q < s} c_q Z_q at entry a: four independent chains (q mod 4), combined in a fixed order.
+__device__ __forceinline__ double project_out(double v, const double* c, const double* Z, int s, int nv, int a) {
+  double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+  int q = 0;
+  for (; q + 3 < s; q += 4) {
+    p0 = fma(c[q], Z[(size_t)q * nv + a], p0);
+    p1 = fma(c[q + 1], Z[(size_t)(q + 1) * nv + a], p1);
+    p2 = fma(c[q + 2], Z[(size_t)(q + 2) * nv + a], p2);
+    p3 = fma(c[q + 3], Z[(size_t)(q + 3) * nv + a], p3);
+  }
+  for (; q < s; q++) p0 = fma(c[q], Z[(size_t)q * nv + a], p0);
+  return v - ((p0 + p1) + (p2 + p3));
+}
+
+__global__ void __launch_bounds__(NT_F) k_rosv_finder(double* Yall, int nv, int r, int n_max, double thr, double* Zall,
                                                     int* nrows, double* wmax, int* err) {
   extern __shared__ double dyn[];
   double* vec = dyn;               // nv
@@ -129,7 +145,7 @@ __global__ void __launch_bounds__(NT) k_rosv_finder(double* Yall, int nv, int r,
   double* nrm = c + n_max;         // r window norms / dots
   __shared__ double s_scale;
   const int u = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int NW = NT / 32;
+  constexpr int NW = NT_F / 32;
   double* Y = Yall + (size_t)u * (r + n_max) * nv;
   double* Z = Zall + (size_t)u * n_max * nv;
   int s = 0;
@@ -148,16 +164,12 @@ __global__ void __launch_bounds__(NT) k_rosv_finder(double* Yall, int nv, int r,
     if (!(mx > thr) || s >= n_max) break;
     // z^(s) = y^(s) (1 - Z^T Z) / norm   (Eq. rsvd_za)
     const double* y = Y + (size_t)s * nv;
-    for (int a = threadIdx.x; a < nv; a += NT) vec[a] = y[a];
+    for (int a = threadIdx.x; a < nv; a += NT_F) vec[a] = y[a];
     __syncthreads();
     block_dots(Z, s, vec, nv, c);
     __syncthreads();
     double* z = Z + (size_t)s * nv;
-    for (int a = threadIdx.x; a < nv; a += NT) {
-      double v = vec[a];
-      for (int q = 0; q < s; q++) v = fma(-c[q], Z[(size_t)q * nv + a], v);
-      z[a] = v;
-    }
+    for (int a = threadIdx.x; a < nv; a += NT_F) z[a] = project_out(vec[a], c, Z, s, nv, a);
     __syncthreads();
     if (warp == 0) {
       double d = 0.0;
@@ -167,24 +179,20 @@ __global__ void __launch_bounds__(NT) k_rosv_finder(double* Yall, int nv, int r,
     }
     __syncthreads();
     const double sc = s_scale;
-    for (int a = threadIdx.x; a < nv; a += NT) z[a] *= sc;
+    for (int a = threadIdx.x; a < nv; a += NT_F) z[a] *= sc;
     // the fresh row g-bar^(s) T, projected against Z^(s-1) (rows 0 .. s-1 of Z)
     double* yn = Y + (size_t)(s + r) * nv;
-    for (int a = threadIdx.x; a < nv; a += NT) vec[a] = yn[a];
+    for (int a = threadIdx.x; a < nv; a += NT_F) vec[a] = yn[a];
     __syncthreads();
     block_dots(Z, s, vec, nv, c);
     __syncthreads();
-    for (int a = threadIdx.x; a < nv; a += NT) {
-      double v = vec[a];
-      for (int q = 0; q < s; q++) v = fma(-c[q], Z[(size_t)q * nv + a], v);
-      yn[a] = v;
-    }
+    for (int a = threadIdx.x; a < nv; a += NT_F) yn[a] = project_out(vec[a], c, Z, s, nv, a);
     // window rows s+1 .. s+r lose their z^(s) component
-    for (int a = threadIdx.x; a < nv; a += NT) vec[a] = z[a];
+    for (int a = threadIdx.x; a < nv; a += NT_F) vec[a] = z[a];
     __syncthreads();
     block_dots(Y + (size_t)(s + 1) * nv, r, vec, nv, nrm);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < r * nv; idx += NT) {
+    for (int idx = threadIdx.x; idx < r * nv; idx += NT_F) {
       const int w = idx / nv, a = idx % nv;
       Y[(size_t)(s + 1 + w) * nv + a] = fma(-nrm[w], vec[a], Y[(size_t)(s + 1 + w) * nv + a]);
     }
@@ -285,7 +293,7 @@ void launch_rosv_finder(double* Y, int nb, int nv, int r, int n_max, double l_os
   const double thr = l_osv / (10.0 * 0.7978845608028654);   // l_osv / (10 sqrt(2/pi))
   const size_t smem = (size_t)(nv + n_max + r) * sizeof(double);
   cudaFuncSetAttribute(k_rosv_finder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_rosv_finder<<<nb, NT, smem, st>>>(Y, nv, r, n_max, thr, Z, nrows, wmax, err);
+  k_rosv_finder<<<nb, NT_F, smem, st>>>(Y, nv, r, n_max, thr, Z, nrows, wmax, err);
   note_launch(1);
 }
 
