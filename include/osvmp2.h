@@ -68,7 +68,9 @@ typedef enum {
 typedef struct {
   double tau_s;       /* drop S_(ij,ij) eigenvalues below tau_s * max eigenvalue (default 1e-10) */
   double tol_update;  /* stop when max |R~ / D| below this ...                (default 1e-7)  */
-  double tol_energy;  /* ... and |E_C(it) - E_C(it-1)| below this, Eh         (default 1e-13) */
+  double tol_energy;  /* ... and |E_C(it) - E_C(it-1)| below this, Eh         (default 1e-13;
+                          fragment solves use at least 16 ulps of |E_C|, the FP64 rounding floor
+                          of the fragment energy, and the mixed form 1e-11 |E_C|) */
                       /* (the energy test does the fine convergence: the update
                           has a rounding floor of ~eps*cond(S_(ij,ij)))       */
   int32_t max_iter;   /* amplitude iterations per fragment                    (default 100) */

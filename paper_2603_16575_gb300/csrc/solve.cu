@@ -166,7 +166,13 @@ __global__ void __launch_bounds__(NT) k_frag_solve(Tables t, const int* __restri
           e += pair_energy(t.K[t.pair_id[i * t.n_occ + j]], T[lpair(a, b, nc)], pair_dim(t, i, j), a == b, red);
         }
       if (!isfinite(e) || !isfinite(um)) { status = ERR_NONFINITE; iters = it; break; }
-      if (um < o.tol_update && fabs(e - e_prev) < o.tol_energy) { status = 0; iters = it; break; }
+      // energy test: tol_energy, or 16 ulps of |E_C| where that is larger (the
+      // fragment energy cannot be resolved below its rounding floor)
+      if (um < o.tol_update && fabs(e - e_prev) < fmax(o.tol_energy, 3.5527136788005009e-15 * fabs(e))) {
+        status = 0;
+        iters = it;
+        break;
+      }
       e_prev = e;
     }
     if (threadIdx.x == 0) out[fid] = FragOut{e, um, iters, status};
