@@ -14,3 +14,4 @@ from .osv_mp2 import (  # noqa: F401
     WeakResult, weak_pair, weak_residual, mbe3_screened_energy,
     RandomizedOSV, randomized_osv, build_osv_randomized,
 )
+from .pm_localization import charge_tensor, pm_functional, PMResult, pm_localize  # noqa: F401,E402

@@ -210,6 +210,47 @@ def gauss_row(seed: int, i: int, k: int, n_vir: int) -> np.ndarray:
     return normal_ih12(stream_key(seed, S_ROSV), np.arange(n_vir, dtype=_U64) + _U64(base))
 
 
+S_LOC, S_ROT = 8, 9
+
+
+@dataclasses.dataclass
+class LocSystem:
+    """Delocalized orthonormal orbitals for the localization step: C = L R with L
+    orthonormal orbitals each mostly on its own atom (the target of the
+    localization) and R a Haar-random orthogonal mixing.  C is [n_ao, n_occ]
+    with n_ao = ao_per_atom * n_atom; atom_ao are the AO offsets of the atoms."""
+    C: np.ndarray
+    L: np.ndarray
+    atom_ao: np.ndarray
+    r_atom: np.ndarray
+
+
+def make_loc_system(n_occ: int, ao_per_atom: int = 4, seed: int = 0, tail: float = 0.3,
+                    decay: float = 1.5) -> LocSystem:
+    """n_occ atoms in the water-cluster box (constant density), one localized
+    orbital per atom: its own AOs carry Irwin-Hall(12) normal weights, the AOs of
+    other atoms tail * exp(-d / decay) times normal weights; orthonormalised by QR
+    (input preparation), then mixed by a Haar rotation (QR of a normal matrix with
+    the signs of R's diagonal fixed)."""
+    n_atom = n_occ
+    n_ao = ao_per_atom * n_atom
+    L_box = 10.0 * (n_occ / 20.0) ** (1.0 / 3.0)
+    r = L_box * uniform(stream_key(seed, S_OCC_POS), np.arange(3 * n_atom)).reshape(n_atom, 3)
+    d = _pairwise_dist(r, r)
+    z = normal_ih12(stream_key(seed, S_LOC), np.arange(n_ao * n_occ, dtype=_U64)).reshape(n_ao, n_occ)
+    atom_of_ao = np.repeat(np.arange(n_atom), ao_per_atom)
+    env = tail * np.exp(-d[atom_of_ao, :] / decay)
+    env[atom_of_ao[:, None] == np.arange(n_occ)[None, :]] = 1.0
+    Lmat, R0 = np.linalg.qr(z * env)
+    Lmat = Lmat * np.sign(np.diag(R0))[None, :]
+    g = normal_ih12(stream_key(seed, S_ROT), np.arange(n_occ * n_occ, dtype=_U64)).reshape(n_occ, n_occ)
+    Qr, Rr = np.linalg.qr(g)
+    Qr = Qr * np.sign(np.diag(Rr))[None, :]
+    C = Lmat @ Qr
+    return LocSystem(np.ascontiguousarray(C), np.ascontiguousarray(Lmat),
+                     np.arange(0, n_ao + 1, ao_per_atom, dtype=np.int32), r)
+
+
 def workload(name: str, seed: int = 0, **over) -> System:
     kw = dict(WORKLOADS[name])
     kw.update(over)
