@@ -249,6 +249,24 @@ int osvmp2_mbe3_energy_screened(osvmp2_ctx *ctx, const osvmp2_screen *scr, osvmp
  * (host [n], both orders) may be NULL. */
 int osvmp2_weak_results(osvmp2_ctx *ctx, int64_t *n_out, int32_t *pairs, double *energies);
 
+/* ---- occupied-orbital localization (Section 3.2, Algorithm 2, Eq. loc_theta) ----
+ * Jacobi-sweep Pipek-Mezey localization with Loewdin charges.  C: device
+ * [n_ao][n_occ], orthonormal columns in an orthonormal (Loewdin) AO basis;
+ * atom_ao: host [n_atom + 1] AO offsets of the atoms (0 ... n_ao, ascending).
+ * P^A_ij = sum_{alpha in A} C_alpha,i C_alpha,j; sweeps over the pairs i < j in
+ * order with a_ij = sum_A (P^A_ij)^2 - (P^A_ii - P^A_jj)^2 / 4,
+ * b_ij = sum_A P^A_ij (P^A_ii - P^A_jj), theta = atan2(b_ij, -a_ij) / 4 (the
+ * branch that maximises the functional), rotation skipped when
+ * |sin theta| < 1e-10; a sweep adds sqrt(a^2 + b^2)(1 - cos 4 theta) to dL, and
+ * the sweeps stop when dL <= l_loc (paper: 1e-3).
+ * U: device [n_occ][n_occ] out, the localized orbitals are C U; L_out (host,
+ * nullable): sum_{i,A} (P^A_ii)^2 at the end; sweeps_out (host, nullable).
+ * OSVMP2_E_NOCONV after max_sweeps sweeps (U and L then hold the last state).
+ * Uses the ctx's stream and memory cache only; needs no system. */
+int osvmp2_localize_pm(osvmp2_ctx *ctx, const double *C_dev, int32_t n_ao, int32_t n_occ, const int32_t *atom_ao,
+                       int32_t n_atom, double l_loc, int32_t max_sweeps, double *U_dev, double *L_out,
+                       int32_t *sweeps_out);
+
 /* ---- A6: frozen-OSV gradient --------------------------------------------
  * MBE(3) energy as osvmp2_mbe3_energy, plus (device outputs, each may be NULL):
  *   dE_dB [n_occ][n_vir][n_aux]: dE/dB[i,a,P] = 4 sum_C c_C sum_j (T~_ij^C B_j)[a,P]
@@ -281,7 +299,8 @@ enum {
   OSVMP2_PH_SIGMA = 13,    /* mixed A4 set-up: pair-couple overlaps on the tensor cores (inside SOLVE) */
   OSVMP2_PH_WEAK = 14,     /* weak pairs: diagonal amplitudes, S blocks, K_(i,j), solve */
   OSVMP2_PH_SCREEN = 15,   /* s2b of every pair */
-  OSVMP2_NPHASE = 16
+  OSVMP2_PH_LOCALIZE = 16, /* Pipek-Mezey localization (osvmp2_localize_pm) */
+  OSVMP2_NPHASE = 20
 };
 /* Accumulated since the last reset, per phase (host arrays of OSVMP2_NPHASE, any
  * may be NULL): device milliseconds, algorithmic FP operations (GEMM-shaped

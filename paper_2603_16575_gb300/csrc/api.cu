@@ -2213,6 +2213,42 @@ int osvmp2_weak_results(osvmp2_ctx* c, int64_t* n_out, int32_t* pairs, double* e
   return OSVMP2_OK;
 }
 
+int osvmp2_localize_pm(osvmp2_ctx* c, const double* C, int32_t n_ao, int32_t n_occ, const int32_t* atom_ao,
+                       int32_t n_atom, double l_loc, int32_t max_sweeps, double* U, double* L_out, int32_t* sweeps_out) {
+  if (!c) return OSVMP2_E_ARG;
+  c->err.clear();
+  if (!C || !U || !atom_ao || n_occ < 1 || n_atom < 1 || n_ao < n_occ || max_sweeps < 1 || !(l_loc >= 0.0))
+    return fail(c, OSVMP2_E_ARG, "localize: bad arguments");
+  if (atom_ao[0] != 0 || atom_ao[n_atom] != n_ao)
+    return fail(c, OSVMP2_E_ARG, "localize: atom_ao must run from 0 to n_ao");
+  for (int a = 0; a < n_atom; a++)
+    if (atom_ao[a + 1] < atom_ao[a]) return fail(c, OSVMP2_E_ARG, "localize: atom_ao must be ascending");
+  if ((double)n_occ * n_occ * n_atom > 4e9) return fail(c, OSVMP2_E_ARG, "localize: charge tensor too large");
+  CK(cudaSetDevice(c->device));
+  Tmp P, ao, out, stat;
+  TRY(tmp_alloc(c, P, (size_t)n_occ * n_occ * n_atom * sizeof(double)));
+  TRY(tmp_alloc(c, ao, (size_t)(n_atom + 1) * sizeof(int)));
+  TRY(tmp_alloc(c, out, 2 * sizeof(double)));
+  TRY(tmp_alloc(c, stat, 2 * sizeof(int)));
+  CK(cudaMemcpyAsync(ao.p, atom_ao, (size_t)(n_atom + 1) * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  ph_begin(c, OSVMP2_PH_LOCALIZE);
+  launch_pm_localize(C, n_ao, n_occ, (const int*)ao.p, n_atom, l_loc, max_sweeps, (double*)P.p, U, (double*)out.p,
+                     (int*)stat.p, c->num_sms, c->st);
+  ph_end(c, OSVMP2_PH_LOCALIZE, 0.0);
+  CK(cudaGetLastError());
+  double ho[2];
+  int hs[2];
+  CK(cudaMemcpyAsync(ho, out.p, sizeof ho, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(hs, stat.p, sizeof hs, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  ph_collect(c);
+  if (L_out) *L_out = ho[0];
+  if (sweeps_out) *sweeps_out = hs[0];
+  if (!std::isfinite(ho[0])) return fail(c, OSVMP2_E_NUMERIC, "localize: non-finite functional");
+  if (!hs[1]) return fail(c, OSVMP2_E_NOCONV, "localize: dL = %.3e after %d sweeps", ho[1], hs[0]);
+  return OSVMP2_OK;
+}
+
 int osvmp2_profile(osvmp2_ctx* c, double* ms, double* flops, double* bytes, int64_t* calls, int reset) {
   if (!c) return OSVMP2_E_ARG;
   CK(cudaStreamSynchronize(c->st));

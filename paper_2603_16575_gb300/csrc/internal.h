@@ -262,6 +262,12 @@ struct GradContrib {       // one fragment's amplitude of a pair and the fragmen
   int weight;
 };
 
+// ---- occupied-orbital localization (localize.cu; Algorithm 2)
+// P: scratch [n][n][n_atom]; U out [n][n]; out[0] = L, out[1] = last dL; status[0] = sweeps,
+// status[1] = 1 if converged (device).
+void launch_pm_localize(const double* C, int n_ao, int n, const int* atom_ao, int n_atom, double l_loc, int max_sweeps,
+                        double* P, double* U, double* out, int* status, int num_sms, cudaStream_t st);
+
 // ---- pair screening and weak pairs (screen.cu), FP64 in both forms
 // s2b[p] of the pairs (i, j) = pairs[p] (Eq. s2b), grid-stride over n_cta CTAs.
 void launch_s2b(const Tables& t, const int2* pairs, int n_pairs, double* s2b, int n_cta, cudaStream_t st);

@@ -82,6 +82,7 @@ SIGNATURES = {
     "osvmp2_mbe3_energy_screened": (ctypes.c_int, [_P, ctypes.POINTER(Screen), ctypes.c_int, _P, _P,
                                                    ctypes.POINTER(MbeStats)]),
     "osvmp2_weak_results": (ctypes.c_int, [_P, _P, _P, _P]),
+    "osvmp2_localize_pm": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _I32, _D, _I32, _P, _P, _P]),
     "osvmp2_precond_noalloc": (ctypes.c_int, [_P, _P, _I32, _D, _P, _P, _P, _P, ctypes.c_char_p, _I32]),
     "osvmp2_generate_B": (ctypes.c_int, [_I32, _I32, _I32, ctypes.c_uint64, _P, _I32, _I32, _P, _P]),
 }
@@ -337,7 +338,24 @@ class Context:
         return e.value, st.as_dict()
 
     PHASES = ["tii", "eig", "sf", "project", "exchange", "precond", "solve", "mbe_sum", "subsolve", "grad",
-              "k_gproj", "k_eig", "k_fragsolve", "sigma", "weak", "screen"]
+              "k_gproj", "k_eig", "k_fragsolve", "sigma", "weak", "screen", "localize", "spare17", "spare18",
+              "spare19"]
+
+    # ---- occupied-orbital localization (Algorithm 2)
+    def localize_pm(self, C, atom_ao, l_loc: float = 1e-3, max_sweeps: int = 100):
+        """Pipek-Mezey localization of the columns of C (float64 CUDA [n_ao, n_occ]);
+        atom_ao: AO offsets of the atoms.  Returns (U [n_occ, n_occ] CUDA tensor, L, sweeps)."""
+        import torch
+        _need_f64_cuda(C, "C")
+        n_ao, n = C.shape
+        ao = np.ascontiguousarray(np.asarray(atom_ao, dtype=np.int32))
+        U = torch.empty((n, n), dtype=torch.float64, device=C.device)
+        L = ctypes.c_double(0.0)
+        sw = ctypes.c_int32(0)
+        self._check("osvmp2_localize_pm",
+                    lib().osvmp2_localize_pm(self._h, _ptr(C), n_ao, n, _ptr(ao), ao.shape[0] - 1, l_loc, max_sweeps,
+                                             _ptr(U), ctypes.addressof(L), ctypes.addressof(sw)))
+        return U, L.value, sw.value
 
     # ---- A5 with the paper's cluster selection
     def pair_screening(self, screen: Optional[Screen] = None):
