@@ -37,11 +37,11 @@ R2_CUT, R3_CUT, L_OSV = 8.0, 6.0, 1e-4
 MEASURED_GEMM_PEAKS = {"fp64_tflops": 1.099, "tf32_tflops": 1037.8, "fp32_tflops": 69.86,
                        "source": "torch.matmul 8192^3 on a GB300 of this pool, best of 10"}
 FP32_SIMT_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12    # 128 FFMA/clk/SM at the 2070 MHz maximum -> 80.5
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernels,
-# from one ncu capture on the 48-orbital case scaled to the bench workload by the
-# units each launch processes (profiles/traffic_mbe3_n48.md); None until captured
-# for the kernel as it stands.
-KERNEL_TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
+# from one single-pass ncu capture of the bench workload
+# (profiles/traffic_k_eig_osv_mbe3_n128.md); kernels without a capture of their
+# current code report null.
+KERNEL_TRAFFIC = {"k_eig_osv": 34.05e9 + 42.26e9}   # 128-orbital workload itself (1 pass), bytes per launch
 
 
 def load_peaks():
@@ -316,7 +316,8 @@ def run_gpu(args):
                           "performed_flops_per_step": fl / args.steps}
     dom = max(kernels.items(), key=lambda kv: kv[1]["ms_per_step"])
     dname, d = dom
-    tr = KERNEL_TRAFFIC.get(dname)
+    tr = KERNEL_TRAFFIC.get(dname) if (args.workload == "mbe3_n128" and args.osv_method == "exact" and
+                                       args.prec == "mixed") else None
     roof = {"kernel": dname, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
             "frac": d["frac"], "traffic": tr, "peak_source": d["peak_source"],
             "per_launch": "algorithmic flops per launch / CUDA-event time per launch (library stream)"}

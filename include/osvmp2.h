@@ -53,7 +53,8 @@ typedef enum {
   OSVMP2_E_NUMERIC = 5,  /* eigen-solver did not converge or produced non-finite values */
   OSVMP2_E_STATE = 6,    /* call order violated (e.g. pair_integrals before build_osv) */
   OSVMP2_E_TIMEOUT = 7   /* a bounded device-side wait (a tensor-core pipeline barrier) gave up:
-                            the kernel left its loops early, released its tensor memory and
+                            the kernel left its loops early, waited (bounded) for its copies and
+                            tensor-core operations in flight, released its tensor memory and
                             flagged the call; the call's results are invalid */
 } osvmp2_status;
 

@@ -26,8 +26,10 @@
 //              8-wide k-step)
 //   warps 2-5  drain and the transposed epilogue store
 // TMEM columns: two buffers of three level accumulators (6 x 64), hi and lo.
-// Every mbarrier wait is bounded; a timeout sets ERR_TC_TIMEOUT in *err and
-// the CTA runs to completion without hanging.
+// Every mbarrier wait is bounded; a timeout sets ERR_TC_TIMEOUT in *err, the
+// roles leave their loops, the producer waits (bounded) for its copies in flight
+// and the MMA thread for its last commit, and the CTA frees its tensor memory
+// and returns without hanging.
 #pragma once
 #include <cuda.h>
 #include <stdint.h>
@@ -174,6 +176,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                           jb.b_row + sl * jb.b_sstride + bx * BROWS);
         }
       }
+      if (!ok) {
+        // leaving early: let the copies already issued land first (bounded waits).  Only
+        // the last armed chunk of each stage can be outstanding: a stage is re-armed only
+        // after its previous chunk was consumed.
+        for (long long gg = g - 1; gg >= 0 && gg >= g - NSTAGE; gg--)
+          mbar_wait(su32(&bar_full[gg & 1]), (uint32_t)((gg >> 1) & 1));
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {                                             // ---- MMA issuer
@@ -213,6 +222,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               su32(&bar_accf[b])));
         }
       }
+      // leaving early: the last commit completes when every MMA issued so far has, so
+      // wait for it (bounded) before the tensor memory is released
+      if (!ok && g > 0) mbar_wait(su32(&bar_accf[(g - 1) & 1]), (uint32_t)(((g - 1) >> 1) & 1));
     }
   } else {                                                       // ---- drain + epilogue (warps 2..5)
     const int q = warp & 3;                                      // TMEM lane quarter of this warp
