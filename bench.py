@@ -204,6 +204,13 @@ def run_gpu(args):
 
     for _ in range(args.warmup):
         E, st, n_osv = step()
+    grad_check = None
+    if args.grad and rank == 0 and not args.no_cpu_baseline:
+        # dE/dB of orbital 0 gets contributions only from the fragments containing it, so
+        # the oracle checks those rows exactly from a small sample of fragments
+        _, dB, df, de, _ = ctx.energy_grad(R2_CUT, R3_CUT, args.prec)
+        grad_check = gradient_vs_oracle(s, dB[0].cpu().numpy(), osv_method=args.osv_method)
+        del dB, df, de
     n_frag = int(st["n_single"] + st["n_pair"] + st["n_triple"])
     ctx.profile(reset=True)
     launches0 = pkg.osvmp2.kernel_launches()
@@ -365,6 +372,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": "fragments/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": 8},
         "gpu_launches": int(launches),
+        "gradient_vs_oracle": grad_check,
         "roofline": roof,
         "kernels": kernels,
         "effective_tflops": effective,
@@ -432,6 +440,25 @@ def cpu_sample(args, budget_s: float):
             break
     dt = time.perf_counter() - t0
     return done, dt, k, energies
+
+
+def gradient_vs_oracle(s, dB0, osv_method="exact"):
+    """Frozen-OSV dE/dB[0] from the oracle, summed over the fragments that contain
+    orbital 0, against the GPU's row block (same OSV rule)."""
+    import oracle
+    frags = [(o, c) for o, c in oracle.mbe3_fragments(s.r_occ, R2_CUT, R3_CUT) if 0 in o and c != 0]
+    orbs = sorted({x for o, _ in frags for x in o})
+    t0 = time.perf_counter()
+    osys = oracle.OSVSystem(s.B_block, s.n_occ, s.e_vir, s.f_occ, l_osv=L_OSV, orbitals=orbs)
+    ref = np.zeros((s.n_vir, s.n_aux))
+    for o, c in frags:
+        fr = osys.fragment(o)
+        res = oracle.solve_fragment(fr)
+        gB, _, _ = oracle.fragment_gradient(fr, res, osys.B, s.n_occ, s.n_vir, s.n_aux)
+        ref += c * gB[0]
+    err = float(np.abs(dB0 - ref).max())
+    return {"rows": "dE/dB[0] (every fragment containing orbital 0)", "fragments": len(frags),
+            "max_abs": err, "max_rel": err / float(np.abs(ref).max()), "oracle_s": time.perf_counter() - t0}
 
 
 def cpu_baseline(args, budget_s: float):

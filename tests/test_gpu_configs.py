@@ -152,3 +152,27 @@ def test_calls_out_of_order_give_state_errors():
     assert L.osvmp2_get_pair_blocks(ctx._h, 0, 3, None, None, None) == E_STATE
     assert L.osvmp2_get_precond(ctx._h, 0, 3, None, None, None) == E_STATE
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-6)])
+def test_gradient_rows_at_the_gradient_workload_shape(prec, tol):
+    """64 orbitals / 320 virtuals / 1200 aux: the frozen-OSV dE/dB rows of orbital 0,
+    which only the fragments containing it feed, against the oracle (relative to their
+    largest entry)."""
+    from paper_2603_16575_gb300 import Context
+    s = synth.workload("grad_n64", seed=0)
+    ctx = Context(0, osv_prec="fp64")
+    _build(ctx, s, 1e-4)
+    E, dB, df, de, st = ctx.energy_grad(8.0, 6.0, prec)
+    assert st["n_unconverged"] == 0
+    frags = [(o, c) for o, c in oracle.mbe3_fragments(s.r_occ, 8.0, 6.0) if 0 in o and c != 0]
+    orbs = sorted({x for o, _ in frags for x in o})
+    osys = oracle.OSVSystem(s.B_block, s.n_occ, s.e_vir, s.f_occ, l_osv=1e-4, orbitals=orbs)
+    ref = np.zeros((s.n_vir, s.n_aux))
+    for o, c in frags:
+        fr = osys.fragment(o)
+        gB, _, _ = oracle.fragment_gradient(fr, oracle.solve_fragment(fr), osys.B, s.n_occ, s.n_vir, s.n_aux)
+        ref += c * gB[0]
+    got = dB[0].cpu().numpy()
+    assert np.abs(got - ref).max() < tol * np.abs(ref).max()
+    ctx.close()
