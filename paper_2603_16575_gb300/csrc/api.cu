@@ -598,12 +598,21 @@ int gproj_tensor(osvmp2_ctx* c, const std::vector<GJob>& gj, const std::vector<l
     const int nb = (int)std::min(per_batch, xs.size() - b0);
     launch_bslices(bsrc(c), (const int*)xd.p + b0, nb, (float*)bs.p, ldv, c->st);
     CK(cudaGetLastError());
+    // Tile order: per orbital x, blocks of PB (pair, column tile) jobs, each with all
+    // its aux tiles; a wave of the persistent grid then holds every aux tile of B_x
+    // and only PB tiles of the U slices, so the B_x tiles stay in L2 across the
+    // waves of x and every U tile is read once.
+    const int PB = std::max(1, c->num_sms / std::max(1, n_mt));
     std::vector<tc::Job> jobs;
-    for (int u = 0; u < nb; u++)
-      for (int mt = 0; mt < n_mt; mt++)
-        for (int q : by_x[xs[b0 + u]]) {
-          const GJob& g = gj[q];
-          for (int n0 = 0; n0 < g.r; n0 += tc::BN) {
+    for (int u = 0; u < nb; u++) {
+      std::vector<std::pair<int, int>> pn;   // (G job, first column)
+      for (int q : by_x[xs[b0 + u]])
+        for (int n0 = 0; n0 < gj[q].r; n0 += tc::BN) pn.push_back({q, n0});
+      for (size_t p0 = 0; p0 < pn.size(); p0 += PB)
+        for (int mt = 0; mt < n_mt; mt++)
+          for (size_t pp = p0; pp < std::min(pn.size(), p0 + (size_t)PB); pp++) {
+            const int q = pn[pp].first, n0 = pn[pp].second;
+            const GJob& g = gj[q];
             tc::Job jb;
             jb.a_row = u * tc::NSL * nx + mt * tc::BM;
             jb.a_sstride = nx;
@@ -618,7 +627,7 @@ int gproj_tensor(osvmp2_ctx* c, const std::vector<GJob>& gj, const std::vector<l
             jb.s = 0.0;
             jobs.push_back(jb);
           }
-        }
+    }
     Tmp jd;
     TRY(tmp_alloc(c, jd, jobs.size() * sizeof(tc::Job)));
     CK(cudaMemcpyAsync(jd.p, jobs.data(), jobs.size() * sizeof(tc::Job), cudaMemcpyHostToDevice, c->st));
