@@ -2234,17 +2234,26 @@ int osvmp2_localize_pm(osvmp2_ctx* c, const double* C, int32_t n_ao, int32_t n_o
     if (atom_ao[a + 1] < atom_ao[a]) return fail(c, OSVMP2_E_ARG, "localize: atom_ao must be ascending");
   if ((double)n_occ * n_occ * n_atom > 4e9) return fail(c, OSVMP2_E_ARG, "localize: charge tensor too large");
   CK(cudaSetDevice(c->device));
-  Tmp P, ao, out, stat;
+  Tmp P, ao, out, stat, part, bar;
   TRY(tmp_alloc(c, P, (size_t)n_occ * n_occ * n_atom * sizeof(double)));
   TRY(tmp_alloc(c, ao, (size_t)(n_atom + 1) * sizeof(int)));
   TRY(tmp_alloc(c, out, 2 * sizeof(double)));
   TRY(tmp_alloc(c, stat, 2 * sizeof(int)));
+  TRY(tmp_alloc(c, part, 4 * (size_t)std::max(1, std::min(n_atom, c->num_sms)) * sizeof(double)));
+  TRY(tmp_alloc(c, bar, 2 * sizeof(unsigned)));
   CK(cudaMemcpyAsync(ao.p, atom_ao, (size_t)(n_atom + 1) * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
   ph_begin(c, OSVMP2_PH_LOCALIZE);
-  launch_pm_localize(C, n_ao, n_occ, (const int*)ao.p, n_atom, l_loc, max_sweeps, (double*)P.p, U, (double*)out.p,
-                     (int*)stat.p, c->num_sms, c->st);
+  // whole-GPU form (atoms over a cooperative grid) when its CTAs can all be resident,
+  // else the one-CTA form; both follow the same sequence of rotations
+  if (!launch_pm_localize_grid(C, n_occ, (const int*)ao.p, n_atom, l_loc, max_sweeps, (double*)P.p, U,
+                               (double*)out.p, (int*)stat.p, (double*)part.p, (unsigned*)bar.p, c->err_d, c->num_sms,
+                               c->st))
+    launch_pm_localize(C, n_ao, n_occ, (const int*)ao.p, n_atom, l_loc, max_sweeps, (double*)P.p, U, (double*)out.p,
+                       (int*)stat.p, c->num_sms, c->st);
   ph_end(c, OSVMP2_PH_LOCALIZE, 0.0);
   CK(cudaGetLastError());
+  TRY(check_err_flag(c, "localize"));
   double ho[2];
   int hs[2];
   CK(cudaMemcpyAsync(ho, out.p, sizeof ho, cudaMemcpyDeviceToHost, c->st));

@@ -267,6 +267,13 @@ struct GradContrib {       // one fragment's amplitude of a pair and the fragmen
 // status[1] = 1 if converged (device).
 void launch_pm_localize(const double* C, int n_ao, int n, const int* atom_ao, int n_atom, double l_loc, int max_sweeps,
                         double* P, double* U, double* out, int* status, int num_sms, cudaStream_t st);
+// The same sweeps over a cooperative grid (atoms spread over the CTAs, one bounded grid
+// barrier per rotation); false when the grid cannot be co-resident (nothing launched
+// then).  part: 4 * min(n_atom, num_sms) doubles; bar: 2 unsigned; err |= ERR_TIMEOUT
+// if a barrier wait gave up.
+bool launch_pm_localize_grid(const double* C, int n, const int* atom_ao, int n_atom, double l_loc, int max_sweeps,
+                             double* P, double* U, double* out, int* status, double* part, unsigned* bar, int* err,
+                             int num_sms, cudaStream_t st);
 
 // ---- pair screening and weak pairs (screen.cu), FP64 in both forms
 // s2b[p] of the pairs (i, j) = pairs[p] (Eq. s2b), grid-stride over n_cta CTAs.
