@@ -507,8 +507,9 @@ def main():
     ap.add_argument("--screen", action="store_true",
                     help="cluster selection by s2b/s3b with weak pairs instead of the 8/6 A distance rule")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--cpu-orbitals", type=int, default=10)
+    ap.add_argument("--cpu-budget", type=float, default=25.0)
+    # 16 orbitals: 293 fragments, 18.3 per OSV build (the full workload has 23.8)
+    ap.add_argument("--cpu-orbitals", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--measure-peaks", action="store_true",
                     help="print the FP64 / TF32 / FP32 / BF16 GEMM throughput of GPU 0 and exit")
