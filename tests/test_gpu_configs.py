@@ -177,3 +177,36 @@ def test_gradient_rows_at_the_gradient_workload_shape(prec, tol):
     got = dB[0].cpu().numpy()
     assert np.abs(got - ref).max() < tol * np.abs(ref).max()
     ctx.close()
+
+
+@pytest.mark.parametrize("osv_method,prec", [("exact", "fp64"), ("exact", "mixed"), ("randomized", "mixed")])
+def test_second_config_fragments_match_oracle(osv_method, prec):
+    """256 orbitals / 1200 virtuals / 4800 aux (the second workload's full size): the
+    fragments among the 6 orbitals nearest orbital 0, solved inside the whole MBE(3)
+    launch, against the oracle with the same OSV rule."""
+    from paper_2603_16575_gb300 import Context
+    s = synth.workload("osv_n256", seed=0)
+    d = np.linalg.norm(s.r_occ - s.r_occ[0], axis=1)
+    near = sorted(np.argsort(d, kind="stable")[:6].tolist())
+    frags = [o for o, _ in oracle.mbe3_fragments(s.r_occ, 8.0, 6.0) if set(o) <= set(near)]
+    if osv_method == "randomized":
+        osys = oracle.OSVSystem(s.B_block, s.n_occ, s.e_vir, s.f_occ, l_osv=1e-4, orbitals=[])
+        gauss = lambda i, k: synth.gauss_row(s.seed, i, k, s.n_vir)
+        osys.Q, osys.omega, _ = oracle.build_osv_randomized(osys.B, s.n_occ, s.e_vir, s.f_occ, 1e-4, gauss,
+                                                            orbitals=near)
+    else:
+        osys = oracle.OSVSystem(s.B_block, s.n_occ, s.e_vir, s.f_occ, l_osv=1e-4, orbitals=near)
+    ctx = Context(0, osv_prec="fp64" if prec == "fp64" else "mixed", osv_method=osv_method)
+    n_osv = _build(ctx, s, 1e-4)
+    assert all(int(n_osv[i]) == osys.Q[i].shape[1] for i in near)
+    E, st = ctx.mbe3_energy(8.0, 6.0, prec)
+    assert st["n_unconverged"] == 0
+    got = _gpu_fragment_energies(ctx)
+    assert len(frags) >= 10
+    for o in frags:
+        e_ref = osys.solve(o).energy
+        if prec == "fp64":
+            assert abs(got[o] - e_ref) < 1e-9, (o, got[o], e_ref)
+        else:
+            assert abs(got[o] - e_ref) < 1e-7 * abs(e_ref), (o, got[o], e_ref)
+    ctx.close()
