@@ -2107,33 +2107,33 @@ int osvmp2_mbe3_energy_screened(osvmp2_ctx* c, const osvmp2_screen* sc, osvmp2_p
     CK(cudaGetLastError());
     // S_(i,j) of the weak pairs
     TRY(ensure_sf_blocks(c, weak));
-    // FP64 diagonal projections B~_i^(i) (Eq. osv_imua) and exact eigenbases of F_(i,i)
+    // diagonal projections B~_i^(i) (Eq. osv_imua): the FP64 form's own; the mixed form
+    // forms them for the weak-pair orbitals in double-float.  Eigenbases of F_(i,i):
+    // the preconditioners of the diagonal pairs (exact in the FP64 form, the mixed
+    // basis otherwise; k_weak then iterates on the raw-basis residual).
     std::vector<const double*> bii(n, nullptr), xi(n, nullptr), ei(n, nullptr);
-    Tmp projm, d_pj, xm, em, rm, d_pc, pscr;
-    if (!mixed) {
-      for (int i = 0; i < n; i++) {
-        if (!need[i]) continue;
-        const int id = c->bt_id[(size_t)i * n + i], pid = c->pair_id[(size_t)i * n + i];
+    Tmp projm, d_pj;
+    for (int i = 0; i < n; i++) {
+      if (!need[i]) continue;
+      const int pid = c->pair_id[(size_t)i * n + i];
+      if (c->r_h[pid] != c->n_osv[i])
+        return fail(c, OSVMP2_E_NUMERIC, "diagonal pair (%d,%d): preconditioner rank %d below %d", i, i, c->r_h[pid],
+                    c->n_osv[i]);
+      xi[i] = c->X_h[pid];
+      ei[i] = c->et_h[pid];
+      if (!mixed) {
+        const int id = c->bt_id[(size_t)i * n + i];
         if (id < 0) return fail(c, OSVMP2_E_STATE, "projection of orbital %d not built", i);
         bii[i] = c->bt_h[id];
-        xi[i] = c->X_h[pid];
-        ei[i] = c->et_h[pid];
       }
-    } else {
+    }
+    if (mixed) {
       std::vector<ProjJob> pj;
-      std::vector<PJob> pc;
-      size_t psz = 0, xsz = 0, esz = 0;
+      size_t psz = 0;
       for (int i = 0; i < n; i++)
-        if (need[i]) {
-          psz += (size_t)nx * c->n_osv[i];
-          xsz += (size_t)c->n_osv[i] * c->n_osv[i];
-          esz += c->n_osv[i];
-        }
+        if (need[i]) psz += (size_t)nx * c->n_osv[i];
       TRY(tmp_alloc(c, projm, psz * sizeof(double)));
-      TRY(tmp_alloc(c, xm, xsz * sizeof(double)));
-      TRY(tmp_alloc(c, em, esz * sizeof(double)));
-      TRY(tmp_alloc(c, rm, (size_t)n * sizeof(int)));
-      size_t po = 0, xo = 0, eo = 0;
+      size_t po = 0;
       double fl = 0.0;
       for (int i = 0; i < n; i++) {
         if (!need[i]) continue;
@@ -2141,35 +2141,12 @@ int osvmp2_mbe3_energy_screened(osvmp2_ctx* c, const osvmp2_screen* sc, osvmp2_p
         pj.push_back(ProjJob{i, i, out});
         bii[i] = out;
         po += (size_t)nx * c->n_osv[i];
-        double* X = (double*)xm.p + xo;
-        double* e = (double*)em.p + eo;
-        pc.push_back(PJob{i, i, X, e, (int*)rm.p + pc.size(), nullptr, nullptr});
-        xi[i] = X;
-        ei[i] = e;
-        xo += (size_t)c->n_osv[i] * c->n_osv[i];
-        eo += c->n_osv[i];
         fl += 2.0 * nx * (double)c->sys.n_vir * c->n_osv[i];
       }
       TRY(tmp_alloc(c, d_pj, pj.size() * sizeof(ProjJob)));
-      TRY(tmp_alloc(c, d_pc, pc.size() * sizeof(PJob)));
       CK(cudaMemcpyAsync(d_pj.p, pj.data(), pj.size() * sizeof(ProjJob), cudaMemcpyHostToDevice, c->st));
-      CK(cudaMemcpyAsync(d_pc.p, pc.data(), pc.size() * sizeof(PJob), cudaMemcpyHostToDevice, c->st));
-      CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
-      const Tables t = tables(c);
-      launch_project(bsrc(c), t, (const ProjJob*)d_pj.p, (int)pj.size(), max_n, 0, c->st);
+      launch_project_df(bsrc(c), tables(c), (const ProjJob*)d_pj.p, (int)pj.size(), c->st);
       CK(cudaGetLastError());
-      const int np = (int)pc.size();
-      if (max_n <= PW_MAX_ORDER) {
-        const int nw = std::min(np, 16 * c->num_sms);
-        TRY(tmp_alloc(c, pscr, precond_w_scratch_doubles(max_n, nw) * sizeof(double)));
-        launch_precond_w(t, c->opts.tau_s, (const PJob*)d_pc.p, np, max_n, (double*)pscr.p, nw, c->err_d, c->st);
-      } else {
-        const int nc = std::min(np, 2 * c->num_sms);
-        TRY(tmp_alloc(c, pscr, (size_t)nc * precond_scratch_doubles(max_n) * sizeof(double)));
-        launch_precond(t, c->opts.tau_s, (const PJob*)d_pc.p, np, max_n, (double*)pscr.p, nc, c->err_d, c->st);
-      }
-      CK(cudaGetLastError());
-      TRY(check_err_flag(c, "weak-pair eigenbases"));
       c->flops[OSVMP2_PH_WEAK] += fl;
     }
     std::vector<WeakJob> wj;
@@ -2178,7 +2155,8 @@ int osvmp2_mbe3_energy_screened(osvmp2_ctx* c, const osvmp2_screen* sc, osvmp2_p
       const int i = w.first, j = w.second;
       const int id = c->sf_id[(size_t)i * n + j];
       WeakJob jb{i, j, bii[i], bii[j], c->S_h[id], (const double*)tdiag.p + doff[i],
-                 (const double*)tdiag.p + doff[j], xi[i], xi[j], ei[i], ei[j], c->n_osv[i], c->n_osv[j]};
+                 (const double*)tdiag.p + doff[j], xi[i], xi[j], ei[i], ei[j], c->n_osv[i], c->n_osv[j],
+                 c->F_h[c->sf_id[(size_t)i * n + i]], c->F_h[c->sf_id[(size_t)j * n + j]]};
       wj.push_back(jb);
       const double ni = c->n_osv[i], nj = c->n_osv[j];
       fl += 2.0 * nx * ni * nj + 2.0 * (ni * ni * nj + ni * nj * nj) * 3.0;
@@ -2186,11 +2164,11 @@ int osvmp2_mbe3_energy_screened(osvmp2_ctx* c, const osvmp2_screen* sc, osvmp2_p
     Tmp d_wj, wscr, we;
     const int n_cta_w = std::max(1, std::min((int)wj.size(), 2 * c->num_sms));
     TRY(tmp_alloc(c, d_wj, wj.size() * sizeof(WeakJob)));
-    TRY(tmp_alloc(c, wscr, (size_t)n_cta_w * 4 * max_n * max_n * sizeof(double)));
+    TRY(tmp_alloc(c, wscr, (size_t)n_cta_w * 6 * max_n * max_n * sizeof(double)));
     TRY(tmp_alloc(c, we, wj.size() * sizeof(double)));
     CK(cudaMemcpyAsync(d_wj.p, wj.data(), wj.size() * sizeof(WeakJob), cudaMemcpyHostToDevice, c->st));
     launch_weak(tables(c), nx, (const WeakJob*)d_wj.p, (int)wj.size(), (double*)wscr.p, max_n, n_cta_w,
-                (double*)we.p, c->st);
+                (double*)we.p, mixed ? 1 : 0, c->st);
     CK(cudaGetLastError());
     ph_end(c, OSVMP2_PH_WEAK, fl);
     c->weak_e.resize(wj.size());

@@ -294,15 +294,19 @@ struct WeakJob {           // weak pair (i, j), i < j
   const double* S;         // S_(i,j) [n_i][n_j]
   const double* Ti;        // MBE(3) diagonal amplitude T_(i,i) [n_i][n_i]
   const double* Tj;
-  const double* Xi;        // eigenvectors of F_(i,i) (columns), row stride ldxi
-  const double* Xj;
+  const double* Xi;        // eigenbasis of F_(i,i) (columns; exact in the FP64 form, the mixed
+  const double* Xj;        //   preconditioner basis of the pair (i,i) otherwise), row stride ldxi
   const double* ei;        // their eigenvalues
   const double* ej;
   int ldxi, ldxj;
+  const double* Fi;        // F_(i,i) [n_i][n_i], F_(j,j) (mixed form's residual updates)
+  const double* Fj;
 };
-// Weak-pair energies (both orders) into e_out[job]; scratch: 4 max_n^2 doubles per CTA.
+// Weak-pair energies (both orders) into e_out[job]; scratch: 6 max_n^2 doubles per CTA.
 void launch_weak(const Tables& t, int n_aux, const WeakJob* jobs, int n_jobs, double* scratch, int max_n, int n_cta,
-                 double* e_out, cudaStream_t st);
+                 double* e_out, int mixed, cudaStream_t st);
+// Mixed form: B~_i^(i) = B_i^T Q_i in double-float for the jobs (i, x = i, out [n_aux][n_i]).
+void launch_project_df(const BSrc& src, const Tables& t, const ProjJob* jobs, int n_jobs, cudaStream_t st);
 struct GradPairJob {       // W_p = sum c T~, H_p = sum c (T~ S T^T + [i!=j] T~^T S T)
   int i, j;
   int c0, c1;              // contributions [c0, c1)
