@@ -395,7 +395,27 @@ def run_gpu(args):
     out["localization"] = {"n_occ": n_l, "n_atom": len(ls.atom_ao) - 1, "n_ao": ls.C.shape[0], "l_loc": 1e-3,
                            "sweeps": sw, "ms": 1e3 * t_loc, "functional": L_loc,
                            "pair_rotations_per_s": sw * n_l * (n_l - 1) / 2 / t_loc}
+    # ---- the 20-orbital untruncated system (n_vir = 100, n_aux = 400): the full
+    # osvmp2_solve over every pair in FP64, outside the timed step
+    sc = synth.workload("canonical_n20", seed=args.seed)
+    ctx20 = pkg.Context(local, stream=stream)
+    with torch.cuda.stream(stream):
+        a20 = [torch.tensor(x, device=dev) for x in (sc.f_occ, sc.e_vir, sc.env)]
+        ctx20.build_osv(a20[0], a20[1], 0.0, env=a20[2], seed=sc.seed, n_aux=sc.n_aux, r_occ=sc.r_occ)
+        ctx20.solve(range(sc.n_occ))                 # warm-up (pair blocks, preconditioners)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        E20, _, it20 = ctx20.solve(range(sc.n_occ))
+        ev1.record(stream)
+    ev1.synchronize()
+    out["full_solve_n20"] = {"workload": "20 orbitals, 100 virtuals, 400 aux, untruncated (pair order 200)",
+                             "energy": E20, "iterations": it20, "ms": ev0.elapsed_time(ev1),
+                             "pairs": sc.n_occ * (sc.n_occ + 1) // 2}
+    ctx20.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        e_cf = oracle.canonical_mp2_energy(sc.B_block, sc.n_occ, sc.f_occ, sc.e_vir)
+        out["full_solve_n20"]["abs_err_vs_closed_form_eh"] = abs(E20 - e_cf)
         out["cpu_baseline"], ref_e = cpu_baseline(args, budget_s=args.cpu_budget)
         out["energy_vs_oracle"] = {}
         for form, got in gpu_frag_e.items():
