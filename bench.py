@@ -191,6 +191,9 @@ def run_gpu(args):
     osv_prec = "mixed" if args.prec == "mixed" else "fp64"
     ctx = pkg.Context(local, stream=stream, osv_prec=osv_prec, osv_method=args.osv_method)
 
+    if args.osv_only:
+        return run_osv_only(args, ctx, s, env, f_occ, e_vir, stream, flush, dev, pkg, torch)
+
     def step(B_in=B, env_in=env, f_in=f_occ, e_in=e_vir):
         kw = dict(B=B_in) if B_in is not None else dict(env=env_in, seed=s.seed, n_aux=s.n_aux)
         n_osv = ctx.build_osv(f_in, e_in, L_OSV, r_occ=s.r_occ, **kw)
@@ -462,6 +465,66 @@ def cpu_sample(args, budget_s: float):
     return done, dt, k, energies
 
 
+def run_osv_only(args, ctx, s, env, f_occ, e_vir, stream, flush, dev, pkg, torch):
+    """A0 alone (T_ii and the OSVs of every orbital, B regenerated on the device):
+    orbitals/s, for workloads whose pair steps are out of reach (the 800-orbital
+    chain).  With the CPU leg on, the OSVs of two orbitals are checked against the
+    oracle with the same OSV rule."""
+    def step():
+        return ctx.build_osv(f_occ, e_vir, L_OSV, env=env, seed=s.seed, n_aux=s.n_aux, r_occ=s.r_occ)
+    for _ in range(args.warmup):
+        n_osv = step()
+    ctx.profile(reset=True)
+    launches0 = pkg.osvmp2.kernel_launches()
+    t_steps = []
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            n_osv = step()
+            ev1.record(stream)
+            ev1.synchronize()
+            t_steps.append(ev0.elapsed_time(ev1) / 1e3)
+    prof = ctx.profile(reset=True)
+    t_tot = sum(t_steps)
+    out = {"metric": "OSV build orbitals/s", "value": s.n_occ * args.steps / t_tot, "unit": "orbitals/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "split-tf32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
+           "config": {"workload": f"{args.workload} (n_occ={s.n_occ}, n_vir={s.n_vir}, n_aux={s.n_aux}, "
+                                  f"{s.geometry}, lambda={s.lam} A, l_osv={L_OSV}), A0 only",
+                      "osv_method": args.osv_method, "osv_prec": args.prec, "b_mode": "regen",
+                      "n_osv_min": int(n_osv.min()), "n_osv_max": int(n_osv.max()),
+                      "n_osv_mean": float(np.mean(n_osv)),
+                      "l2": "256 MB buffer written between timed steps"},
+           "gpu_launches": int(pkg.osvmp2.kernel_launches() - launches0),
+           "phases": {k: {"ms_per_step": v[0] / args.steps,
+                          "tflops": (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 and v[1] else None}
+                      for k, v in prof.items()},
+           "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        import oracle
+        chk = {}
+        for i in (0, s.n_occ // 2):
+            Qg, wg = (x.cpu().numpy() for x in ctx.get_osv(i))
+            T = oracle.semicanonical_tii(s.B_block(i), s.e_vir, s.f_occ[i, i])
+            if args.osv_method == "randomized":
+                ro = oracle.randomized_osv(T, L_OSV, lambda k, i=i: synth.gauss_row(s.seed, i, k, s.n_vir))
+                Qr, wr = ro.Q, ro.omega
+            else:
+                Qr, wr = oracle.osv_from_tii(T, L_OSV)
+            same = Qg.shape[1] == Qr.shape[1]
+            chk[str(i)] = {"n_osv": int(Qg.shape[1]), "n_osv_oracle": int(Qr.shape[1]),
+                           "omega_max_rel_err": float(np.abs(wg - wr).max() / wr.max()) if same else None,
+                           "projector_max_err": float(np.abs(Qg @ Qg.T - Qr @ Qr.T).max()) if same else None}
+        out["osv_vs_oracle"] = chk
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def gradient_vs_oracle(s, dB0, osv_method="exact"):
     """Frozen-OSV dE/dB[0] from the oracle, summed over the fragments that contain
     orbital 0, against the GPU's row block (same OSV rule)."""
@@ -524,6 +587,8 @@ def main():
     ap.add_argument("--grad", action="store_true")
     ap.add_argument("--osv-method", choices=["exact", "randomized"], default="exact",
                     help="OSV generation: full eigen-decomposition or the randomized range finder (Algorithm 3)")
+    ap.add_argument("--osv-only", action="store_true",
+                    help="time the OSV build (A0) alone, in orbitals/s")
     ap.add_argument("--screen", action="store_true",
                     help="cluster selection by s2b/s3b with weak pairs instead of the 8/6 A distance rule")
     ap.add_argument("--seed", type=int, default=0)
