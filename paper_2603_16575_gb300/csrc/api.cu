@@ -1401,7 +1401,7 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   c->bt_id.assign((size_t)n * n, -1);
   TRY(upload(c, c->sf_id_d, c->sf_id));
   TRY(upload(c, c->pair_id_d, c->pair_id));
-  // batch the orbitals so that T, V and the eigen scratch stay within ~4 GB, in
+  // batch the orbitals so that T, V and the eigen scratch stay within the budget below, in
   // batches of equal size (one CTA per orbital in the eigen kernel)
   const bool rosv = c->opts.osv_method == 1;
   const int n_max = rosv ? std::min(nv, c->opts.rosv_max_rows > 0 ? c->opts.rosv_max_rows : 256) : 0;
@@ -1410,7 +1410,16 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   const size_t per = ((size_t)nv * nv + (size_t)nv * kmax + kmax +
                       (rosv ? rl1.total + (size_t)tc::NSL * (nv + rl1.rows) * rl1.ldk / 2 + 1
                             : (size_t)nv * nv + eig_osv_scratch_doubles(nv, kmax))) * sizeof(double);
-  int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, ((size_t)4 << 30) / per));
+  // batch budget: a quarter of the free device memory, at most 64 GB (at most half of
+  // the ctx's cap when one is set), at least 4 GB
+  size_t budget = (size_t)4 << 30;
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = std::max(budget, std::min(fr / 4, (size_t)64 << 30));
+    else cudaGetLastError();
+    if (c->opts.mem_cap_mib > 0) budget = std::min(budget, ((size_t)c->opts.mem_cap_mib << 20) / 2);
+  }
+  int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, budget / per));
   nb = std::min(nb, 4 * c->num_sms);
   {
     const int nbatch = (n + nb - 1) / nb;
