@@ -10,6 +10,7 @@ from .osv_mp2 import (  # noqa: F401
     exchange_block, preconditioner, Fragment, FragmentResult, solve_fragment,
     solve_fragment_dense, canonical_mp2_energy, dist2, mbe3_fragments,
     OSVSystem, fragment_gradient, mbe3_energy_gradient,
+    fragment_dE_dQ, osv_response, tii_adjoint, mbe3_energy_gradient_relaxed,
     s2b_metric, s2b_matrix, s3b_metric, Screen, screened_fragments, mbe3_diagonal_amplitudes,
     WeakResult, weak_pair, weak_residual, mbe3_screened_energy,
     RandomizedOSV, randomized_osv, build_osv_randomized,

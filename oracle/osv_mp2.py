@@ -20,7 +20,9 @@ MBE(3)-OSV-MP2" (arXiv 2603.16575):
 * MBE(3) -- the amplitude expansion Eqs. (tmbediag)-(deltaoff) collected into
   inclusion-exclusion weights on the fragment energies.
 * gradient -- Hellmann-Feynman derivative of the Hylleraas functional that
-  Eq. (res_close) makes stationary (Section 2), with the OSVs held fixed.
+  Eq. (res_close) makes stationary (Section 2), with the OSVs held fixed; the
+  OSV-relaxed form adds the first-order response of the kept eigenvectors of
+  Eq. (osv_gen) to T_ii of Eq. (mp2_tkk).
 
 Readings where the paper is silent or garbled (each one is listed, with its
 reason, in the design notes):
@@ -45,6 +47,10 @@ reason, in the design notes):
       (the full residual projected onto Q_i x Q_j with k restricted to {i, j})
   R18 weak-pair energy: 2 <K_(i,j), T_(i,j)> per ordered pair, both orders
       counted, with T_(i,i) the MBE(3) diagonal amplitude of Eq. (tmbediag)
+  R23 the OSV-relaxed gradient (named as future work in the conclusions) is the
+      derivative with every orbital's OSV count held fixed: the truncated energy
+      jumps where an eigenvalue of T_ii crosses l_osv, and the response term
+      scales with 1 / (eigenvalue gap at the cut), which is reported
 """
 from __future__ import annotations
 
@@ -443,6 +449,114 @@ def mbe3_energy_gradient(osys: OSVSystem, r_occ: np.ndarray, r2: float, r3: floa
         de += c * ge
         df += c * gf
     return E, dB, de, df
+
+
+# --------------------------------------------------------------------------
+# OSV-relaxed gradient: the frozen-OSV derivative plus the response of the
+# OSVs of Eq. (osv_gen) to T_ii of Eq. (mp2_tkk) (reading R23)
+# --------------------------------------------------------------------------
+def fragment_dE_dQ(frag: Fragment, res: FragmentResult, Bfun: Callable[[int], np.ndarray],
+                   e_vir: np.ndarray) -> Dict[int, np.ndarray]:
+    """dE_C/dQ_x [n_vir, n_x] for every LMO x of the fragment, B, e and f fixed.
+
+    With the amplitudes stationary, E_C is the Hylleraas functional of the
+    frozen-OSV gradient with T_ij(full) = P_ij T_ij P_ij^T, and its variation
+    in the full amplitudes is dE = 2 sum_(ordered ij) <dT_ij, R~_ij>, where
+    R_ij = B_i B_j^T + diag(e) T_ij + T_ij diag(e) - sum_k (f_ik T_kj + f_kj T_ik)
+    is the full-space residual of Eq. (res_close) and R~ = 2R - R^T.  Both
+    orders of a pair i < j give the same term (R_ji = R_ij^T), so per stored
+    pair dE = alpha <R~ P T^T + R~^T P T, dP> with alpha = 4 (i < j) or 2
+    (i = j), and the columns of dP that belong to Q_x are dQ_x.
+    """
+    o = frag.orbs
+    e = np.asarray(e_vir, dtype=np.float64)
+    Tf = {}
+    for (i, j) in frag.pairs:
+        full = frag.P[(i, j)] @ res.T[(i, j)] @ frag.P[(i, j)].T
+        Tf[(i, j)] = full
+        Tf[(j, i)] = full.T
+    B = {x: Bfun(x) for x in o}
+    G = {x: np.zeros((e.size, frag.n[x])) for x in o}
+    for (i, j) in frag.pairs:
+        R = B[i] @ B[j].T + e[:, None] * Tf[(i, j)] + Tf[(i, j)] * e[None, :]
+        for k in o:
+            R -= frag.f[i, k] * Tf[(k, j)] + frag.f[k, j] * Tf[(i, k)]
+        Rt = 2.0 * R - R.T
+        P, T = frag.P[(i, j)], res.T[(i, j)]
+        D = (2.0 if i == j else 4.0) * (Rt @ P @ T.T + Rt.T @ P @ T)
+        ni = frag.n[i]
+        G[i] += D[:, :ni]
+        if i != j:
+            G[j] += D[:, ni:]
+    return G
+
+
+def osv_response(T_ii: np.ndarray, Q_i: np.ndarray, G_i: np.ndarray) -> Tuple[np.ndarray, float]:
+    """Adjoint of T_ii: the symmetric Z with dE = <Z, dT_ii> for the energy's
+    dependence on the kept eigenvectors Q_i of Eq. (osv_gen), count held fixed.
+
+    First-order perturbation of the eigenvectors of a symmetric matrix,
+    dq_k = sum_(l != k) z_l (z_l^T dT q_k) / (omega_k - omega_l), summed over the
+    discarded eigenvectors z_l only: the kept-kept terms cancel because E does
+    not change under a rotation of Q_i within its span.  Returns (Z, gap) with
+    gap = omega_(n_i - 1) - omega_(n_i), the eigenvalue gap at the cut.
+    """
+    w, V = np.linalg.eigh(T_ii)
+    order = np.argsort(-w, kind="stable")
+    w, V = w[order], V[:, order]
+    ni = Q_i.shape[1]
+    if ni == w.size:
+        return np.zeros_like(T_ii), np.inf
+    Zd, wd = V[:, ni:], w[ni:]
+    Y = (Zd.T @ G_i) / (w[None, :ni] - wd[:, None])
+    Xr = Zd @ Y
+    Z = 0.5 * (Xr @ Q_i.T + Q_i @ Xr.T)
+    return Z, float(w[ni - 1] - w[ni])
+
+
+def tii_adjoint(Z: np.ndarray, B_i: np.ndarray, e_vir: np.ndarray, f_ii: float):
+    """Chain rule through T_ii = B_i B_i^T / (e_a + e_b - 2 f_ii) (Eq. mp2_tkk, R4)
+    for dE = <Z, dT_ii>, Z symmetric: (dE/dB_i, dE/de_vir, dE/df_ii)."""
+    D = e_vir[:, None] + e_vir[None, :] - 2.0 * f_ii
+    T = (B_i @ B_i.T) / D
+    W = Z / D
+    ZT = Z * T / D
+    return 2.0 * W @ B_i, -2.0 * ZT.sum(axis=1), 2.0 * float(ZT.sum())
+
+
+def mbe3_energy_gradient_relaxed(osys: OSVSystem, r_occ: np.ndarray, r2: float, r3: float,
+                                 n_vir: int, n_aux: int, **kw):
+    """E, dE/dB, dE/de_vir, dE/df (symmetrised) for MBE(3) with the OSVs rebuilt
+    from B, e and f (reading R23), and the smallest eigenvalue gap at the cut."""
+    n = osys.n_occ
+    dB = np.zeros((n, n_vir, n_aux))
+    de = np.zeros(n_vir)
+    df = np.zeros((n, n))
+    GQ: Dict[int, np.ndarray] = {}
+    E = 0.0
+    for orbs, c in mbe3_fragments(r_occ, r2, r3):
+        if c == 0:
+            continue
+        frag = osys.fragment(orbs)
+        res = solve_fragment(frag, **kw)
+        E += c * res.energy
+        gB, ge, gf = fragment_gradient(frag, res, osys.B, n, n_vir, n_aux)
+        for i, v in gB.items():
+            dB[i] += c * v
+        de += c * ge
+        df += c * gf
+        for x, g in fragment_dE_dQ(frag, res, osys.B, osys.e_vir).items():
+            GQ[x] = GQ.get(x, 0.0) + c * g
+    gap = np.inf
+    for x, g in sorted(GQ.items()):
+        T_xx = semicanonical_tii(osys.B(x), osys.e_vir, osys.f_occ[x, x])
+        Z, gx = osv_response(T_xx, osys.Q[x], g)
+        gap = min(gap, gx)
+        gB, ge, gf = tii_adjoint(Z, osys.B(x), osys.e_vir, osys.f_occ[x, x])
+        dB[x] += gB
+        de += ge
+        df[x, x] += gf
+    return E, dB, de, df, gap
 
 
 # --------------------------------------------------------------------------
