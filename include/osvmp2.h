@@ -15,6 +15,7 @@
  *   A5  MBE(3) energy (Eqs. tmbediag-deltaoff as fragment weights)
  *                                                              -> osvmp2_mbe3_energy
  *   A6  frozen-OSV adjoint dE/dB, dE/de_vir, dE/df             -> osvmp2_energy_grad
+ *       the same with the OSV response (relaxed OSVs)           -> osvmp2_energy_grad_relaxed
  *
  * Conventions (all entry points):
  *   - Every function returns an osvmp2_status; nothing throws across the ABI.
@@ -279,6 +280,28 @@ int osvmp2_energy_grad(osvmp2_ctx *ctx, double r2_cut, double r3_cut, osvmp2_pre
                        double *e_out, double *dE_dB, double *dE_df, double *dE_de,
                        osvmp2_mbe_stats *stats);
 
+/* ---- A6 with relaxed OSVs --------------------------------------------------
+ * The gradient of osvmp2_energy_grad plus the response of the kept OSVs of every
+ * orbital to T_ii (Eq. osv_gen on the T_ii of Eq. mp2_tkk), i.e. the derivative of
+ * the MBE(3) energy with the OSVs rebuilt from B, e_vir and f_occ.  The OSV count of
+ * every orbital is held fixed: the truncated energy jumps where an eigenvalue of T_ii
+ * crosses l_osv, and the response scales with 1 / (eigenvalue gap at the cut), whose
+ * smallest value over the orbitals is written to *min_gap_out (may be NULL).
+ *   dE/dQ_x: the Q_x columns of alpha [R~ P T^T + R~^T P T] over the stored pairs of
+ *            every fragment (weights c_C), R the full-space residual of Eq. res_close,
+ *            R~ = 2R - R^T, alpha = 4 (i < j) or 2 (i = j);
+ *   Z_x    = sym(Z_d Y Q_x^T), Y_lk = z_l^T (dE/dq_k) / (omega_k - omega_l) over the
+ *            discarded eigenpairs (omega_l, z_l) of T_xx;
+ *   dE/dB_x += 2 (Z_x / D) B_x, dE/de_a -= 2 sum_(x,b) (Z_x T_xx / D)_ab,
+ *   dE/df_xx += 2 sum (Z_x T_xx / D),  D_ab = e_a + e_b - 2 f_xx.
+ * FP64 form only (the pair store of an FP64 osvmp2_mbe3_energy), exact OSVs only
+ * (opts.osv_method 0): OSVMP2_E_ARG otherwise.  OSVMP2_E_NUMERIC when the FP64
+ * eigenvalues of T_xx give another count above l_osv than the built OSVs, or no
+ * positive gap at the cut.  Outputs as osvmp2_energy_grad (overwritten). */
+int osvmp2_energy_grad_relaxed(osvmp2_ctx *ctx, double r2_cut, double r3_cut, double *e_out,
+                               double *dE_dB, double *dE_df, double *dE_de,
+                               osvmp2_mbe_stats *stats, double *min_gap_out);
+
 /* ---- profiling -----------------------------------------------------------
  * Phases timed with CUDA events on the ctx stream around their kernels. */
 enum {
@@ -301,6 +324,7 @@ enum {
   OSVMP2_PH_WEAK = 14,     /* weak pairs: diagonal amplitudes, S blocks, K_(i,j), solve */
   OSVMP2_PH_SCREEN = 15,   /* s2b of every pair */
   OSVMP2_PH_LOCALIZE = 16, /* Pipek-Mezey localization (osvmp2_localize_pm) */
+  OSVMP2_PH_RELAX = 17,    /* A6 relaxed: OSV response (osvmp2_energy_grad_relaxed) */
   OSVMP2_NPHASE = 20
 };
 /* Accumulated since the last reset, per phase (host arrays of OSVMP2_NPHASE, any

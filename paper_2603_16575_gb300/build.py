@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libosvmp2.so")
-SOURCES = ["api.cu", "regen.cu", "osv_build.cu", "pair_integrals.cu", "precond.cu", "precond_w.cu", "precond_mixed.cu", "solve.cu", "ubasis.cu", "gproj_tc.cu", "tii_tc.cu", "solve_mixed.cu", "grad.cu", "grad_mixed.cu", "screen.cu", "rosv.cu", "localize.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "regen.cu", "osv_build.cu", "pair_integrals.cu", "precond.cu", "precond_w.cu", "precond_mixed.cu", "solve.cu", "ubasis.cu", "gproj_tc.cu", "tii_tc.cu", "solve_mixed.cu", "grad.cu", "grad_mixed.cu", "grad_relax.cu", "screen.cu", "rosv.cu", "localize.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

@@ -89,6 +89,7 @@ struct osvmp2_ctx {
   bool have_osv = false;
   std::vector<int> n_osv;
   std::vector<double*> Qp, Wp;
+  double l_osv = 0.0;        // cut of the last OSV build
   int cap_pairs = 0;
   // device tables
   int* n_osv_d = nullptr;
@@ -1375,6 +1376,7 @@ int osvmp2_build_osv(osvmp2_ctx* c, const osvmp2_system* s, double l_osv, int32_
   free_system(c);
   c->sys = *s;
   c->have_sys = true;
+  c->l_osv = l_osv;
   c->key = mix64((uint64_t)s->seed ^ (STREAM_B * STREAM_MUL));
   c->r_occ.clear();
   if (s->r_occ) c->r_occ.assign(s->r_occ, s->r_occ + 3 * (size_t)s->n_occ);
@@ -2281,8 +2283,184 @@ int osvmp2_fragment_results(osvmp2_ctx* c, int64_t* n_out, int32_t* orbs, int32_
   return OSVMP2_OK;
 }
 
-int osvmp2_energy_grad(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out, double* dE_dB,
-                       double* dE_df, double* dE_de, osvmp2_mbe_stats* stats) {
+// OSV response of the relaxed gradient (FP64 form), added to the frozen outputs:
+// dE/dQ_x from the exchange part per pair and the rest per fragment, then per batch
+// of orbitals T_xx again, all its eigenpairs, the response Z_x and its chain rule.
+static int relax_osv(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& plist,
+                     const std::vector<GradPairJob>& pjobs, const double* tstore, const std::vector<long long>& toff,
+                     int max_m, double* dE_dB, double* dE_df, double* dE_de, double* gap_out) {
+  const int n = c->sys.n_occ, nv = c->sys.n_vir, nx = c->sys.n_aux;
+  const int np = (int)plist.size(), nf = (int)c->frags.size();
+  const Tables t = tables(c);
+  const BSrc bs = bsrc(c);
+  auto bt = [&](int a, int x) -> const double* {
+    const int id = c->bt_id[(size_t)a * n + x];
+    return id >= 0 ? (const double*)c->bt_h[id] : nullptr;
+  };
+  double fl = 0.0;
+  ph_begin(c, OSVMP2_PH_RELAX);
+  // exchange part per stored pair
+  std::vector<size_t> koff(np + 1, 0);
+  for (int q = 0; q < np; q++) koff[q + 1] = koff[q] + (size_t)nv * pair_dim_h(c, plist[q].first, plist[q].second);
+  Tmp dk, kscr, d_kj;
+  TRY(tmp_alloc(c, dk, std::max<size_t>(1, koff[np]) * sizeof(double)));
+  std::vector<RelaxKJob> kj(np);
+  for (int q = 0; q < np; q++) {
+    const int i = plist[q].first, j = plist[q].second;
+    RelaxKJob& k = kj[q];
+    k.i = i;
+    k.j = j;
+    k.W = pjobs[q].W;
+    k.bt_ii = bt(i, i);
+    k.bt_ij = (i != j) ? bt(i, j) : nullptr;
+    k.bt_ji = (i != j) ? bt(j, i) : nullptr;
+    k.bt_jj = (i != j) ? bt(j, j) : nullptr;
+    if (!k.bt_ii || (i != j && (!k.bt_ij || !k.bt_ji || !k.bt_jj)))
+      return fail(c, OSVMP2_E_STATE, "relaxed gradient: the projections of pair (%d, %d) are missing", i, j);
+    k.out = (double*)dk.p + koff[q];
+    const double m = pair_dim_h(c, i, j);
+    fl += 4.0 * nx * m * m + 4.0 * nv * (double)nx * m;
+  }
+  const int n_cta_k = std::max(1, std::min(np, 2 * c->num_sms));
+  TRY(tmp_alloc(c, kscr, (size_t)n_cta_k * 2 * nx * std::max(max_m, 1) * sizeof(double)));
+  TRY(tmp_alloc(c, d_kj, std::max<size_t>(1, kj.size()) * sizeof(RelaxKJob)));
+  if (np) CK(cudaMemcpyAsync(d_kj.p, kj.data(), kj.size() * sizeof(RelaxKJob), cudaMemcpyHostToDevice, c->st));
+  launch_relax_kpart(t, bs, (const RelaxKJob*)d_kj.p, np, (double*)kscr.p, n_cta_k, max_m, c->st);
+  CK(cudaGetLastError());
+  // the rest per fragment, into one slot per (fragment, orbital)
+  std::vector<std::vector<RelaxGTerm>> gt(n);
+  size_t slot_total = 0;
+  for (int f = 0; f < nf; f++)
+    if (c->frags[f].weight != 0)
+      for (int u = 0; u < 3; u++)
+        if (c->frags[f].orbs[u] >= 0) slot_total += (size_t)nv * c->n_osv[c->frags[f].orbs[u]];
+  Tmp slots, fscr, d_fj;
+  TRY(tmp_alloc(c, slots, std::max<size_t>(1, slot_total) * sizeof(double)));
+  std::vector<RelaxFragJob> fj;
+  size_t so = 0;
+  for (int f = 0; f < nf; f++) {
+    const Frag& fr = c->frags[f];
+    if (fr.weight == 0) continue;
+    RelaxFragJob jb{};
+    jb.no = 0;
+    jb.c = (double)fr.weight;
+    jb.T = tstore + toff[f];
+    for (int u = 0; u < 3; u++)
+      if (fr.orbs[u] >= 0) {
+        const int x = fr.orbs[u];
+        jb.orbs[jb.no] = x;
+        jb.slot[jb.no] = (double*)slots.p + so;
+        gt[x].push_back(RelaxGTerm{jb.slot[jb.no], c->n_osv[x], 0});
+        so += (size_t)nv * c->n_osv[x];
+        jb.no++;
+      }
+    for (int a = 0; a < jb.no; a++)
+      for (int b = a; b < jb.no; b++) {
+        const double m = pair_dim_h(c, jb.orbs[a], jb.orbs[b]);
+        fl += 6.0 * nv * m * m + 6.0 * (double)nv * nv * m;
+      }
+    fj.push_back(jb);
+  }
+  const int n_cta_f = std::max(1, std::min((int)fj.size(), c->num_sms));
+  const size_t scr_per = 7 * (size_t)nv * nv + 3 * (size_t)nv * std::max(max_m, 1);
+  TRY(tmp_alloc(c, fscr, (size_t)n_cta_f * scr_per * sizeof(double)));
+  TRY(tmp_alloc(c, d_fj, std::max<size_t>(1, fj.size()) * sizeof(RelaxFragJob)));
+  if (!fj.empty())
+    CK(cudaMemcpyAsync(d_fj.p, fj.data(), fj.size() * sizeof(RelaxFragJob), cudaMemcpyHostToDevice, c->st));
+  launch_relax_frag(t, c->sys.e_vir, (const RelaxFragJob*)d_fj.p, (int)fj.size(), (double*)fscr.p, scr_per, n_cta_f,
+                    max_m, c->st);
+  CK(cudaGetLastError());
+  // G_x: fragment slots (fragment order), then the exchange parts (pair order)
+  for (int q = 0; q < np; q++) {
+    const int i = plist[q].first, j = plist[q].second, m = pair_dim_h(c, i, j);
+    gt[i].push_back(RelaxGTerm{(const double*)dk.p + koff[q], m, 0});
+    if (i != j) gt[j].push_back(RelaxGTerm{(const double*)dk.p + koff[q], m, c->n_osv[i]});
+  }
+  std::vector<RelaxGJob> gj(n);
+  std::vector<RelaxGTerm> gflat;
+  std::vector<size_t> goff(n + 1, 0);
+  for (int x = 0; x < n; x++) goff[x + 1] = goff[x] + (size_t)nv * c->n_osv[x];
+  Tmp gmem, d_gj, d_gt;
+  TRY(tmp_alloc(c, gmem, goff[n] * sizeof(double)));
+  for (int x = 0; x < n; x++) {
+    gj[x] = RelaxGJob{x, (int)gflat.size(), 0, (double*)gmem.p + goff[x]};
+    for (auto& tm : gt[x]) gflat.push_back(tm);
+    gj[x].t1 = (int)gflat.size();
+  }
+  TRY(tmp_alloc(c, d_gj, gj.size() * sizeof(RelaxGJob)));
+  TRY(tmp_alloc(c, d_gt, std::max<size_t>(1, gflat.size()) * sizeof(RelaxGTerm)));
+  CK(cudaMemcpyAsync(d_gj.p, gj.data(), gj.size() * sizeof(RelaxGJob), cudaMemcpyHostToDevice, c->st));
+  if (!gflat.empty())
+    CK(cudaMemcpyAsync(d_gt.p, gflat.data(), gflat.size() * sizeof(RelaxGTerm), cudaMemcpyHostToDevice, c->st));
+  launch_relax_gather(nv, c->n_osv_d, (const RelaxGJob*)d_gj.p, n, (const RelaxGTerm*)d_gt.p, c->st);
+  CK(cudaGetLastError());
+  // per batch of orbitals: T_xx, all its eigenpairs, the response and its chain rule
+  const size_t V2 = (size_t)nv * nv;
+  const size_t per = (4 * V2 + 2 * (size_t)nv * nv + 3 * (size_t)nv + 1 + eig_osv_scratch_doubles(nv, nv)) * sizeof(double);
+  int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, ((size_t)8 << 30) / per));
+  nb = std::min(nb, 4 * c->num_sms);
+  Tmp Tm, Tc, Vm, wm, km, em, Zm, Ym, Xm, dem, dfm, d_rj;
+  TRY(tmp_alloc(c, Tm, (size_t)nb * V2 * sizeof(double)));
+  TRY(tmp_alloc(c, Tc, (size_t)nb * V2 * sizeof(double)));
+  TRY(tmp_alloc(c, Vm, (size_t)nb * V2 * sizeof(double)));
+  TRY(tmp_alloc(c, wm, (size_t)nb * nv * sizeof(double)));
+  TRY(tmp_alloc(c, km, (size_t)nb * sizeof(int)));
+  TRY(tmp_alloc(c, em, (size_t)nb * eig_osv_scratch_doubles(nv, nv) * sizeof(double)));
+  TRY(tmp_alloc(c, Zm, (size_t)nb * V2 * sizeof(double)));
+  TRY(tmp_alloc(c, Ym, (size_t)nb * V2 * sizeof(double)));
+  TRY(tmp_alloc(c, Xm, (size_t)nb * V2 * sizeof(double)));
+  TRY(tmp_alloc(c, dem, (size_t)nb * nv * sizeof(double)));
+  TRY(tmp_alloc(c, dfm, (size_t)nb * sizeof(double)));
+  TRY(tmp_alloc(c, d_rj, (size_t)nb * sizeof(RelaxRJob)));
+  double gap = INFINITY;
+  std::vector<double> wh((size_t)nb * nv);
+  std::vector<RelaxRJob> rj(nb);
+  for (int i0 = 0; i0 < n; i0 += nb) {
+    const int b = std::min(nb, n - i0);
+    launch_tii(bs, c->sys.e_vir, c->sys.f_occ, n, i0, b, (double*)Tm.p, c->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(Tc.p, Tm.p, (size_t)b * V2 * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    launch_eig_osv((double*)Tm.p, b, nv, 0.0, nv, (double*)Vm.p, (double*)wm.p, (int*)km.p, (double*)em.p, c->err_d,
+                   false, c->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(wh.data(), wm.p, (size_t)b * nv * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    TRY(check_err_flag(c, "relaxed gradient: eigen-decomposition of T_ii"));
+    for (int u = 0; u < b; u++) {
+      const int x = i0 + u, nk = c->n_osv[x];
+      const double* w = wh.data() + (size_t)u * nv;
+      int cnt = 0;
+      while (cnt < nv && (c->l_osv <= 0.0 || w[cnt] >= c->l_osv)) cnt++;
+      if (cnt != nk)
+        return fail(c, OSVMP2_E_NUMERIC,
+                    "relaxed gradient: orbital %d has %d eigenvalues of T_ii above l_osv in FP64, %d OSVs built", x,
+                    cnt, nk);
+      if (nk < nv) {
+        const double g = w[nk - 1] - w[nk];
+        if (!(g > 0.0))
+          return fail(c, OSVMP2_E_NUMERIC, "relaxed gradient: no eigenvalue gap at the OSV cut of orbital %d", x);
+        gap = std::min(gap, g);
+      }
+      rj[u] = RelaxRJob{x, (const double*)Vm.p + u * V2, (const double*)wm.p + (size_t)u * nv,
+                        (const double*)Tc.p + u * V2, (const double*)gmem.p + goff[x], (double*)Zm.p + u * V2,
+                        (double*)Ym.p + u * V2, (double*)Xm.p + u * V2, (double*)dem.p + (size_t)u * nv,
+                        (double*)dfm.p + u};
+      const double nd = nv - nk;
+      fl += (double)nv * nv * nx + 9.0 * (double)nv * nv * nv + 4.0 * nd * nk * nv + 4.0 * (double)nv * nv * nk +
+            2.0 * (double)nv * nv * nx;
+    }
+    CK(cudaMemcpyAsync(d_rj.p, rj.data(), (size_t)b * sizeof(RelaxRJob), cudaMemcpyHostToDevice, c->st));
+    launch_relax_resp(t, bs, c->sys.e_vir, (const RelaxRJob*)d_rj.p, b, dE_dB, dE_de, dE_df, c->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));   // rj is rewritten by the next batch
+  }
+  ph_end(c, OSVMP2_PH_RELAX, fl);
+  if (gap_out) *gap_out = gap;
+  return OSVMP2_OK;
+}
+
+static int energy_grad_impl(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out, double* dE_dB,
+                            double* dE_df, double* dE_de, osvmp2_mbe_stats* stats, bool relaxed, double* gap_out) {
   if (!c) return OSVMP2_E_ARG;
   Tmp tstore;
   std::vector<long long> toff;
@@ -2538,9 +2716,25 @@ int osvmp2_energy_grad(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, do
     CK(cudaGetLastError());
   }
   ph_end(c, OSVMP2_PH_GRAD, fl);
+  if (relaxed) TRY(relax_osv(c, plist, pjobs, (const double*)tstore.p, toff, max_m, dE_dB, dE_df, dE_de, gap_out));
   CK(cudaStreamSynchronize(c->st));
   ph_collect(c);
   return check_err_flag(c, "gradient");
+}
+
+int osvmp2_energy_grad(osvmp2_ctx* c, double r2, double r3, osvmp2_prec prec, double* e_out, double* dE_dB,
+                       double* dE_df, double* dE_de, osvmp2_mbe_stats* stats) {
+  return energy_grad_impl(c, r2, r3, prec, e_out, dE_dB, dE_df, dE_de, stats, false, nullptr);
+}
+
+int osvmp2_energy_grad_relaxed(osvmp2_ctx* c, double r2, double r3, double* e_out, double* dE_dB, double* dE_df,
+                               double* dE_de, osvmp2_mbe_stats* stats, double* min_gap_out) {
+  if (!c) return OSVMP2_E_ARG;
+  c->err.clear();
+  if (!c->have_osv) return fail(c, OSVMP2_E_STATE, "no OSVs built");
+  if (c->opts.osv_method != 0)
+    return fail(c, OSVMP2_E_ARG, "the relaxed gradient needs exact OSVs (opts.osv_method 0)");
+  return energy_grad_impl(c, r2, r3, OSVMP2_FP64, e_out, dE_dB, dE_df, dE_de, stats, true, min_gap_out);
 }
 
 }  // extern "C"

@@ -345,6 +345,53 @@ void launch_grad_Y(const Tables& t, int n_aux, const GradYJob* jobs, int n_jobs,
                    cudaStream_t st);
 void launch_grad_dB(const Tables& t, int n_aux, const GradBJob* jobs, int n_jobs, const GradBTerm* terms, double* dB,
                     cudaStream_t st);
+
+// ---- A6, OSV-relaxed part (grad_relax.cu)
+struct RelaxKJob {          // exchange part of dP_(i,j): alpha [B_i (A_j W~^T) + B_j (A_i W~)]
+  int i, j;
+  const double* W;          // W~ = sum_C c_C T~ [m][m]
+  const double* bt_ii;      // B_i^T Q_i [n_aux][n_i]
+  const double* bt_ij;      // B_i^T Q_j (unused for i = j)
+  const double* bt_ji;      // B_j^T Q_i
+  const double* bt_jj;      // B_j^T Q_j
+  double* out;              // [n_vir][m]
+};
+struct RelaxFragJob {       // the rest of dP for every pair of one fragment
+  int orbs[3];
+  int no;
+  double c;                 // fragment weight
+  const double* T;          // the fragment's amplitudes, pairs (a <= b) in order
+  double* slot[3];          // [n_vir][n_x] per orbital of the fragment
+};
+struct RelaxGTerm {         // a block of columns added into G_x
+  const double* p;
+  int ld, col0;
+};
+struct RelaxGJob {          // G_x = dE/dQ_x [n_vir][n_x] = sum of terms [t0, t1)
+  int x;
+  int t0, t1;
+  double* G;
+};
+struct RelaxRJob {          // eigenvector response of orbital x
+  int x;
+  const double* V;          // all eigenvectors of T_xx, eigenvector-major, descending eigenvalues
+  const double* w;          // [n_vir] eigenvalues, descending
+  const double* T;          // T_xx [n_vir][n_vir]
+  const double* G;          // dE/dQ_x [n_vir][n_x]
+  double* Z;                // [n_vir][n_vir]: the adjoint of T_xx, then Z / D
+  double* Y;                // [n_vir - n_x][n_x]
+  double* Xr;               // [n_vir][n_x]
+  double* de;               // [n_vir]
+  double* df;               // [1]
+};
+void launch_relax_kpart(const Tables& t, const BSrc& bs, const RelaxKJob* jobs, int n_jobs, double* scratch,
+                        int n_cta, int max_m, cudaStream_t st);
+void launch_relax_frag(const Tables& t, const double* e_vir, const RelaxFragJob* jobs, int n_jobs, double* scratch,
+                       size_t scr_per, int n_cta, int max_m, cudaStream_t st);
+void launch_relax_gather(int n_vir, const int* n_osv, const RelaxGJob* jobs, int n_jobs, const RelaxGTerm* terms,
+                         cudaStream_t st);
+void launch_relax_resp(const Tables& t, const BSrc& bs, const double* e_vir, const RelaxRJob* jobs, int nb,
+                       double* dB, double* de, double* df, cudaStream_t st);
 void launch_grad_de_reduce(const double* dpair, int n_pairs, int nv, double* de, cudaStream_t st);
 void launch_grad_df_reduce(const Tables& t, const int* frag_orbs, const double* gfrag, int n_frag, const int* fptr,
                            const int* flist, double* df, cudaStream_t st);

@@ -78,6 +78,7 @@ SIGNATURES = {
     "osvmp2_profile": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
     "osvmp2_mbe3_fragments": (ctypes.c_int, [_P, _I32, _D, _D, _I64, _P, _P, _P]),
     "osvmp2_energy_grad": (ctypes.c_int, [_P, _D, _D, ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(MbeStats)]),
+    "osvmp2_energy_grad_relaxed": (ctypes.c_int, [_P, _D, _D, _P, _P, _P, _P, ctypes.POINTER(MbeStats), _P]),
     "osvmp2_pair_screening": (ctypes.c_int, [_P, ctypes.POINTER(Screen), _P, _P, _P]),
     "osvmp2_mbe3_energy_screened": (ctypes.c_int, [_P, ctypes.POINTER(Screen), ctypes.c_int, _P, _P,
                                                    ctypes.POINTER(MbeStats)]),
@@ -338,7 +339,7 @@ class Context:
         return e.value, st.as_dict()
 
     PHASES = ["tii", "eig", "sf", "project", "exchange", "precond", "solve", "mbe_sum", "subsolve", "grad",
-              "k_gproj", "k_eig", "k_fragsolve", "sigma", "weak", "screen", "localize", "spare17", "spare18",
+              "k_gproj", "k_eig", "k_fragsolve", "sigma", "weak", "screen", "localize", "relax", "spare18",
               "spare19"]
 
     # ---- occupied-orbital localization (Algorithm 2)
@@ -421,6 +422,22 @@ class Context:
                     lib().osvmp2_energy_grad(self._h, r2_cut, r3_cut, PREC[prec], ctypes.addressof(e), _ptr(dB),
                                              _ptr(df), _ptr(de), ctypes.byref(st)))
         return e.value, dB, df, de, st.as_dict()
+
+    def energy_grad_relaxed(self, r2_cut: float, r3_cut: float, want_dB: bool = True):
+        """energy_grad (FP64 form) plus the response of the OSVs to T_ii, counts held
+        fixed.  Returns (E, dB, df, de, stats, smallest eigenvalue gap at the OSV cut)."""
+        import torch
+        dev = f"cuda:{self.device}"
+        dB = torch.empty((self.n_occ, self.n_vir, self.n_aux), dtype=torch.float64, device=dev) if want_dB else None
+        df = torch.empty((self.n_occ, self.n_occ), dtype=torch.float64, device=dev)
+        de = torch.empty(self.n_vir, dtype=torch.float64, device=dev)
+        e = ctypes.c_double(0.0)
+        gap = ctypes.c_double(0.0)
+        st = MbeStats()
+        self._check("osvmp2_energy_grad_relaxed",
+                    lib().osvmp2_energy_grad_relaxed(self._h, r2_cut, r3_cut, ctypes.addressof(e), _ptr(dB), _ptr(df),
+                                                     _ptr(de), ctypes.byref(st), ctypes.addressof(gap)))
+        return e.value, dB, df, de, st.as_dict(), gap.value
 
 
 def mbe3_energy_function():
