@@ -197,7 +197,9 @@ def run_gpu(args):
     def step(B_in=B, env_in=env, f_in=f_occ, e_in=e_vir):
         kw = dict(B=B_in) if B_in is not None else dict(env=env_in, seed=s.seed, n_aux=s.n_aux)
         n_osv = ctx.build_osv(f_in, e_in, L_OSV, r_occ=s.r_occ, **kw)
-        if args.grad:
+        if args.grad and args.relaxed:
+            E, dB, df, de, st, _ = ctx.energy_grad_relaxed(R2_CUT, R3_CUT)
+        elif args.grad:
             E, dB, df, de, st = ctx.energy_grad(R2_CUT, R3_CUT, args.prec)
         elif args.screen:
             E, _, st = ctx.mbe3_energy_screened(args.prec)
@@ -211,8 +213,13 @@ def run_gpu(args):
     if args.grad and rank == 0 and not args.no_cpu_baseline:
         # dE/dB of orbital 0 gets contributions only from the fragments containing it, so
         # the oracle checks those rows exactly from a small sample of fragments
-        _, dB, df, de, _ = ctx.energy_grad(R2_CUT, R3_CUT, args.prec)
-        grad_check = gradient_vs_oracle(s, dB[0].cpu().numpy(), osv_method=args.osv_method)
+        if args.relaxed:
+            _, dB, df, de, _, gap = ctx.energy_grad_relaxed(R2_CUT, R3_CUT)
+        else:
+            _, dB, df, de, _ = ctx.energy_grad(R2_CUT, R3_CUT, args.prec)
+        grad_check = gradient_vs_oracle(s, dB[0].cpu().numpy(), osv_method=args.osv_method, relaxed=args.relaxed)
+        if args.relaxed:
+            grad_check["min_gap_at_osv_cut"] = gap
         del dB, df, de
     n_frag = int(st["n_single"] + st["n_pair"] + st["n_triple"])
     ctx.profile(reset=True)
@@ -364,6 +371,7 @@ def run_gpu(args):
                                ("s2b/s3b screening 1e-7/1e-2/0.2 with weak pairs)" if args.screen
                                 else f"r2={R2_CUT} A, r3={R3_CUT} A)"),
                    "prec": args.prec, "b_mode": args.b_mode, "grad": bool(args.grad),
+                   "osv_relaxed": bool(args.grad and args.relaxed),
                    "osv_method": args.osv_method, "n_weak": int(st.get("n_weak", 0)),
                    "fragments": n_frag, "n_single": int(st["n_single"]), "n_pair": int(st["n_pair"]),
                    "n_triple": int(st["n_triple"]), "n_osv_mean": float(np.mean(n_osv)),
@@ -525,22 +533,31 @@ def run_osv_only(args, ctx, s, env, f_occ, e_vir, stream, flush, dev, pkg, torch
     ctx.close()
 
 
-def gradient_vs_oracle(s, dB0, osv_method="exact"):
-    """Frozen-OSV dE/dB[0] from the oracle, summed over the fragments that contain
-    orbital 0, against the GPU's row block (same OSV rule)."""
+def gradient_vs_oracle(s, dB0, osv_method="exact", relaxed=False):
+    """dE/dB[0] from the oracle, summed over the fragments that contain orbital 0,
+    against the GPU's row block (same OSV rule); with relaxed, plus the response of
+    Q_0 to T_00, which only those fragments feed."""
     import oracle
     frags = [(o, c) for o, c in oracle.mbe3_fragments(s.r_occ, R2_CUT, R3_CUT) if 0 in o and c != 0]
     orbs = sorted({x for o, _ in frags for x in o})
     t0 = time.perf_counter()
     osys = oracle.OSVSystem(s.B_block, s.n_occ, s.e_vir, s.f_occ, l_osv=L_OSV, orbitals=orbs)
     ref = np.zeros((s.n_vir, s.n_aux))
+    G0 = 0.0
     for o, c in frags:
         fr = osys.fragment(o)
         res = oracle.solve_fragment(fr)
         gB, _, _ = oracle.fragment_gradient(fr, res, osys.B, s.n_occ, s.n_vir, s.n_aux)
         ref += c * gB[0]
+        if relaxed:
+            G0 = G0 + c * oracle.fragment_dE_dQ(fr, res, osys.B, s.e_vir)[0]
+    if relaxed:
+        T00 = oracle.semicanonical_tii(osys.B(0), s.e_vir, s.f_occ[0, 0])
+        Z, _ = oracle.osv_response(T00, osys.Q[0], G0)
+        ref += oracle.tii_adjoint(Z, osys.B(0), s.e_vir, s.f_occ[0, 0])[0]
     err = float(np.abs(dB0 - ref).max())
-    return {"rows": "dE/dB[0] (every fragment containing orbital 0)", "fragments": len(frags),
+    return {"rows": "dE/dB[0] (every fragment containing orbital 0)" + (", OSVs relaxed" if relaxed else ""),
+            "fragments": len(frags),
             "max_abs": err, "max_rel": err / float(np.abs(ref).max()), "oracle_s": time.perf_counter() - t0}
 
 
@@ -585,6 +602,8 @@ def main():
     ap.add_argument("--workload", default="mbe3_n128", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--b-mode", choices=["regen", "stored"], default="regen")
     ap.add_argument("--grad", action="store_true")
+    ap.add_argument("--relaxed", action="store_true",
+                    help="with --grad: the OSV-relaxed gradient (FP64 form, exact OSVs)")
     ap.add_argument("--osv-method", choices=["exact", "randomized"], default="exact",
                     help="OSV generation: full eigen-decomposition or the randomized range finder (Algorithm 3)")
     ap.add_argument("--osv-only", action="store_true",
@@ -599,6 +618,8 @@ def main():
     ap.add_argument("--measure-peaks", action="store_true",
                     help="print the FP64 / TF32 / FP32 / BF16 GEMM throughput of GPU 0 and exit")
     args = ap.parse_args()
+    if args.relaxed and not (args.grad and args.prec == "fp64" and args.osv_method == "exact"):
+        ap.error("--relaxed needs --grad --prec fp64 with exact OSVs")
     if args.measure_peaks:
         print(json.dumps(measure_peaks()), flush=True)
         return
