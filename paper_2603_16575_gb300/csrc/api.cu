@@ -2361,8 +2361,16 @@ static int relax_osv(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& plis
       }
     fj.push_back(jb);
   }
-  const int n_cta_f = std::max(1, std::min((int)fj.size(), c->num_sms));
+  // one CTA per fragment in flight, at most one per SM, their scratch within a quarter of the free memory
   const size_t scr_per = 7 * (size_t)nv * nv + 3 * (size_t)nv * std::max(max_m, 1);
+  int n_cta_f = std::max(1, std::min((int)fj.size(), c->num_sms));
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+      n_cta_f = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_cta_f, fr / 4 / (scr_per * sizeof(double))));
+    else
+      cudaGetLastError();
+  }
   TRY(tmp_alloc(c, fscr, (size_t)n_cta_f * scr_per * sizeof(double)));
   TRY(tmp_alloc(c, d_fj, std::max<size_t>(1, fj.size()) * sizeof(RelaxFragJob)));
   if (!fj.empty())
