@@ -2354,16 +2354,25 @@ static int relax_osv(osvmp2_ctx* c, const std::vector<std::pair<int, int>>& plis
         so += (size_t)nv * c->n_osv[x];
         jb.no++;
       }
+    double rows = 0.0;
+    for (int a = 0; a < jb.no; a++) rows += c->n_osv[jb.orbs[a]];
     for (int a = 0; a < jb.no; a++)
       for (int b = a; b < jb.no; b++) {
         const double m = pair_dim_h(c, jb.orbs[a], jb.orbs[b]);
-        fl += 6.0 * nv * m * m + 6.0 * (double)nv * nv * m;
+        fl += 2.0 * (8.0 * m * m * m + (double)nv * m * (m + rows));   // self terms, Q_x products
+        for (int k = 0; k < jb.no; k++)                                  // couplings (x, y) = (k, b), (a, k)
+          for (int s2 = 0; s2 < 2; s2++) {
+            const int x = s2 ? a : k, y = s2 ? k : b;
+            const double mq = pair_dim_h(c, jb.orbs[std::min(x, y)], jb.orbs[std::max(x, y)]);
+            fl += 4.0 * (mq * mq * m + mq * m * m);
+          }
       }
     fj.push_back(jb);
   }
-  // one CTA per fragment in flight, at most one per SM, their scratch within a quarter of the free memory
-  const size_t scr_per = 7 * (size_t)nv * nv + 3 * (size_t)nv * std::max(max_m, 1);
-  int n_cta_f = std::max(1, std::min((int)fj.size(), c->num_sms));
+  // one CTA per fragment in flight, two per SM (112 registers x 256 threads each), their scratch
+  // within a quarter of the free memory
+  const size_t scr_per = 8 * (size_t)std::max(max_m, 1) * std::max(max_m, 1) + (size_t)nv * std::max(max_m, 1);
+  int n_cta_f = std::max(1, std::min((int)fj.size(), 2 * c->num_sms));
   {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)

@@ -10,7 +10,7 @@
 // dP_p that belong to Q_x are dQ_x.  The exchange part is linear in the
 // amplitudes and runs once per pair on W~_p = sum_C c_C T~_p:
 //   alpha [B_i (A_j W~^T) + B_j (A_i W~)],  A_x = B_x^T P_p  (the stored projections);
-// the rest runs per fragment in the full virtual space.  Then, per orbital x,
+// the rest runs per fragment in the OSV bases, from the stored S and F blocks.  Then, per orbital x,
 // with the eigenpairs (omega, z) of T_xx (descending) and the OSV count n_x
 // held fixed (the energy jumps where an eigenvalue crosses l_osv):
 //   Y_lk = z_l^T g_k / (omega_k - omega_l) over the discarded l,
@@ -74,90 +74,119 @@ __global__ void __launch_bounds__(NT) k_relax_kpart(Tables t, BSrc bs, const Rel
   }
 }
 
-// ---- the rest, one CTA per fragment in the full virtual space; the Q_x columns of
-// every pair's dP are summed (in pair order) into the fragment's slot of orbital x.
+// ---- the rest, one CTA per fragment, in the OSV bases: with T~ = 2T - T^T,
+//   dP_u = c alpha [R_L P T~^T + R_L^T P T~]   (R_L: the residual without exchange)
+//        = diag(e) P_u (T S_uu T~^T + T^T S_uu T~) + P_u (T F_uu T~^T + T^T F_uu T~)
+//          + sum over (x, y) in {(k, j), (i, k)} of coef P_q (op(T_q) S_qu T~^T + op(T_q)^T S_qu T~)
+// (coef = -f_ik, -f_kj; q the stored pair of (x, y), op the transpose when x > y,
+// because T_(x,y)(full) = P_q op(T_q) P_q^T).  The small factors are summed per
+// orbital block of the fragment (N: plain, Ne: scaled by e), then multiplied by Q_x.
+// The Q_x columns of every pair's dP are summed (in pair order) into the fragment's
+// slot of orbital x.
 __global__ void __launch_bounds__(NT) k_relax_frag(Tables t, const double* __restrict__ e_vir,
                                                    const RelaxFragJob* __restrict__ jobs, int n_jobs,
                                                    double* scratch, size_t scr_per, int max_m) {
   __shared__ double sm[GEMM_SMEM_DOUBLES];
   const int nv = t.n_vir, n = t.n_occ;
-  const size_t V2 = (size_t)nv * nv;
-  double* TF = scratch + (size_t)blockIdx.x * scr_per;   // up to 6 pairs, nv x nv each
-  double* XL = TF + 6 * V2;
-  double* Y = XL + V2;                                    // P T    [nv][m]
-  double* Yt = Y + (size_t)nv * max_m;                    // P T^T  [nv][m]
-  double* Dt = Yt + (size_t)nv * max_m;                   // dP     [nv][m]
+  const size_t M2 = (size_t)max_m * max_m;
+  double* Tt = scratch + (size_t)blockIdx.x * scr_per;   // T~ of the pair   [m][m]
+  double* W1 = Tt + M2;                                   // op(T_q) S_qu     [m_q][m]
+  double* N = W1 + M2;                                    // per-block factors [sum n_x][m]
+  double* Ne = N + 3 * M2;
+  double* Dt = Ne + 3 * M2;                               // dP               [nv][m]
   for (int jid = blockIdx.x; jid < n_jobs; jid += gridDim.x) {
     const RelaxFragJob jb = jobs[jid];
     const int no = jb.no;
-    int pi[6], pj[6], pm[6], uid[9];
+    int pi[6], pj[6], pm[6], uid[9], off[3], nb[3];
     const double* Tp[6];
-    int np = 0;
-    size_t off = 0;
+    int np = 0, rows = 0;
+    size_t o = 0;
+    for (int a = 0; a < no; a++) {
+      nb[a] = t.n_osv[jb.orbs[a]];
+      off[a] = rows;
+      rows += nb[a];
+    }
     for (int a = 0; a < no; a++)
       for (int b = a; b < no; b++) {
         pi[np] = jb.orbs[a];
         pj[np] = jb.orbs[b];
         pm[np] = pair_dim(t, pi[np], pj[np]);
-        Tp[np] = jb.T + off;
-        off += (size_t)pm[np] * pm[np];
+        Tp[np] = jb.T + o;
+        o += (size_t)pm[np] * pm[np];
         uid[a * 3 + b] = uid[b * 3 + a] = np;
         np++;
       }
-    for (int a = 0; a < no; a++) {
-      const size_t len = (size_t)nv * t.n_osv[jb.orbs[a]];
-      for (size_t idx = threadIdx.x; idx < len; idx += NT) jb.slot[a][idx] = 0.0;
-    }
-    // full-space amplitudes T_u = P_u T_u P_u^T
-    for (int u = 0; u < np; u++) {
-      const int m = pm[u];
-      const View P = pbasis(t, pi[u], pj[u]);
-      cta_gemm(nv, m, m, 1.0, P, dense_view(Tp[u], m, m, m), 0.0, Y, m, sm);
-      cta_gemm(nv, nv, m, 1.0, dense_view(Y, nv, m, m), transpose(P), 0.0, TF + (size_t)u * V2, nv, sm);
-    }
-    for (int u = 0; u < np; u++) {
-      const int i = pi[u], j = pj[u], m = pm[u];
-      int ai = 0, aj = 0;
-      for (int a = 0; a < no; a++) {
-        if (jb.orbs[a] == i) ai = a;
-        if (jb.orbs[a] == j) aj = a;
-      }
-      const double scale = ((i == j) ? 2.0 : 4.0) * jb.c;
-      // residual (without exchange) at (a, b): element (a, b) of the ordered pair (x, y)
-      // is TF_(x<=y)[a][b], or TF_(y,x)[b][a] for x > y
-      auto rl = [&](int a, int b) {
-        double r = (e_vir[a] + e_vir[b]) * TF[(size_t)u * V2 + (size_t)a * nv + b];
-        for (int k = 0; k < no; k++) {
-          const int ok = jb.orbs[k];
-          const double fik = t.f_occ[(size_t)i * n + ok], fkj = t.f_occ[(size_t)ok * n + j];
-          const double* Tkj = TF + (size_t)uid[k * 3 + aj] * V2;
-          const double* Tik = TF + (size_t)uid[ai * 3 + k] * V2;
-          const double vkj = (k <= aj) ? Tkj[(size_t)a * nv + b] : Tkj[(size_t)b * nv + a];
-          const double vik = (ai <= k) ? Tik[(size_t)a * nv + b] : Tik[(size_t)b * nv + a];
-          r -= fik * vkj + fkj * vik;
+    for (int a = 0; a < no; a++)
+      for (size_t idx = threadIdx.x; idx < (size_t)nv * nb[a]; idx += NT) jb.slot[a][idx] = 0.0;
+    int u = 0;
+    for (int ua = 0; ua < no; ua++)
+      for (int ub = ua; ub < no; ub++, u++) {
+        const int i = pi[u], j = pj[u], m = pm[u];
+        const double ac = ((i == j) ? 2.0 : 4.0) * jb.c;
+        const double* T = Tp[u];
+        for (int idx = threadIdx.x; idx < m * m; idx += NT) {
+          const int r = idx / m, c = idx % m;
+          Tt[idx] = 2.0 * T[idx] - T[(size_t)c * m + r];
         }
-        return r;
-      };
-      for (size_t idx = threadIdx.x; idx < V2; idx += NT) {
-        const int a = (int)(idx / nv), b = (int)(idx % nv);
-        XL[idx] = scale * (2.0 * rl(a, b) - rl(b, a));
+        for (size_t idx = threadIdx.x; idx < (size_t)rows * m; idx += NT) { N[idx] = 0.0; Ne[idx] = 0.0; }
+        __syncthreads();
+        const View Ttv = dense_view(Tt, m, m, m);
+        // W1 (m_q x m) times T~^T and times T~ into the rows of the blocks (qa, qb) of Acc
+        auto add_rows = [&](int mq, int qa, int qb, double coef, const View& Wop, const View& Tside, double* Acc) {
+          const int n1 = nb[qa];
+          cta_gemm(n1, m, m, coef, Wop, Tside, 1.0, Acc + (size_t)off[qa] * m, m, sm);
+          if (qa != qb) {
+            View w2 = Wop;   // rows [n1, mq) of a dense row-major view
+            w2.b[0][0].p += (size_t)n1 * w2.b[0][0].ld;
+            w2.b[0][1] = w2.b[1][0] = w2.b[1][1] = w2.b[0][0];
+            w2.rows = w2.rs = mq - n1;
+            cta_gemm(mq - n1, m, m, coef, w2, Tside, 1.0, Acc + (size_t)off[qb] * m, m, sm);
+          }
+        };
+        // self terms: diag(e) P (T S T~^T + T^T S T~) and P (T F T~^T + T^T F T~)
+        for (int s2 = 0; s2 < 2; s2++) {
+          const View Mu = pair_view(t, s2 ? t.F : t.S, i, j, i, j);
+          double* Acc = s2 ? N : Ne;
+          for (int tr = 0; tr < 2; tr++) {
+            cta_gemm(m, m, m, 1.0, dense_view(T, m, m, m, tr), Mu, 0.0, W1, m, sm);
+            add_rows(m, ua, ub, ac, dense_view(W1, m, m, m), tr ? Ttv : transpose(Ttv), Acc);
+          }
+        }
+        // couplings: -f_ik T_(k,j) and -f_kj T_(i,k) for every k of the fragment
+        for (int kc = 0; kc < no; kc++) {
+          const int k = jb.orbs[kc];
+          for (int s2 = 0; s2 < 2; s2++) {
+            const int x = s2 ? ua : kc, y = s2 ? kc : ub;
+            const double coef = s2 ? -t.f_occ[(size_t)k * n + j] : -t.f_occ[(size_t)i * n + k];
+            if (coef == 0.0) continue;
+            const int qa = min(x, y), qb = max(x, y), trq = x > y;
+            const int q = uid[qa * 3 + qb], mq = pm[q];
+            const View Squ = pair_view(t, t.S, jb.orbs[qa], jb.orbs[qb], i, j);
+            for (int tr = 0; tr < 2; tr++) {
+              cta_gemm(mq, m, mq, 1.0, dense_view(Tp[q], mq, mq, mq, trq ^ tr), Squ, 0.0, W1, m, sm);
+              add_rows(mq, qa, qb, ac * coef, dense_view(W1, mq, m, m), tr ? Ttv : transpose(Ttv), N);
+            }
+          }
+        }
+        // dP = diag(e) (Q_i Ne_i + Q_j Ne_j) + sum_x Q_x N_x
+        cta_gemm(nv, m, nb[ua], 1.0, dense_view(t.Q[i], nv, nb[ua], nb[ua]),
+                 dense_view(Ne + (size_t)off[ua] * m, nb[ua], m, m), 0.0, Dt, m, sm);
+        if (ub != ua)
+          cta_gemm(nv, m, nb[ub], 1.0, dense_view(t.Q[j], nv, nb[ub], nb[ub]),
+                   dense_view(Ne + (size_t)off[ub] * m, nb[ub], m, m), 1.0, Dt, m, sm);
+        for (size_t idx = threadIdx.x; idx < (size_t)nv * m; idx += NT) Dt[idx] *= e_vir[idx / m];
+        __syncthreads();
+        for (int a = 0; a < no; a++)
+          cta_gemm(nv, m, nb[a], 1.0, dense_view(t.Q[jb.orbs[a]], nv, nb[a], nb[a]),
+                   dense_view(N + (size_t)off[a] * m, nb[a], m, m), 1.0, Dt, m, sm);
+        const int ni = t.n_osv[i], nj = (i == j) ? 0 : t.n_osv[j];
+        for (size_t idx = threadIdx.x; idx < (size_t)nv * m; idx += NT) {
+          const int r = (int)(idx / m), col = (int)(idx % m);
+          if (col < ni) jb.slot[ua][(size_t)r * ni + col] += Dt[idx];
+          else jb.slot[ub][(size_t)r * nj + col - ni] += Dt[idx];
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      const View P = pbasis(t, i, j);
-      const View Tv = dense_view(Tp[u], m, m, m);
-      cta_gemm(nv, m, m, 1.0, P, transpose(Tv), 0.0, Yt, m, sm);
-      cta_gemm(nv, m, m, 1.0, P, Tv, 0.0, Y, m, sm);
-      const View X = dense_view(XL, nv, nv, nv);
-      cta_gemm(nv, m, nv, 1.0, X, dense_view(Yt, nv, m, m), 0.0, Dt, m, sm);
-      cta_gemm(nv, m, nv, 1.0, transpose(X), dense_view(Y, nv, m, m), 1.0, Dt, m, sm);
-      const int ni = t.n_osv[i], nj = (i == j) ? 0 : t.n_osv[j];
-      for (size_t idx = threadIdx.x; idx < (size_t)nv * m; idx += NT) {
-        const int r = (int)(idx / m), col = (int)(idx % m);
-        if (col < ni) jb.slot[ai][(size_t)r * ni + col] += Dt[idx];
-        else jb.slot[aj][(size_t)r * nj + col - ni] += Dt[idx];
-      }
-      __syncthreads();
-    }
   }
 }
 
