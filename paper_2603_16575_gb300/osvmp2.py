@@ -441,25 +441,31 @@ class Context:
 
 
 def mbe3_energy_function():
-    """torch.autograd.Function around osvmp2_energy_grad.
+    """torch.autograd.Function around osvmp2_energy_grad / osvmp2_energy_grad_relaxed.
 
-    forward(ctx_obj, B, f_occ, e_vir, r2, r3, prec, l_osv) -> E (0-dim float64 tensor)
-    backward: dE/dB, dE/df_occ (symmetrised) and dE/de_vir from the adjoint kernels,
-    with the OSVs held fixed, each scaled by the incoming gradient.
+    forward(ctx_obj, B, f_occ, e_vir, r_occ, r2, r3, prec, l_osv, relaxed) -> E (0-dim float64 tensor)
+    backward: dE/dB, dE/df_occ (symmetrised) and dE/de_vir from the adjoint kernels, each
+    scaled by the incoming gradient; with the OSVs held fixed, or with relaxed=True (FP64
+    form) including their response to T_ii at fixed OSV counts.
     """
     import torch
 
     class _MBE3Energy(torch.autograd.Function):
         @staticmethod
-        def forward(fctx, ctx_obj, B, f_occ, e_vir, r_occ, r2, r3, prec="fp64", l_osv=1e-4):
+        def forward(fctx, ctx_obj, B, f_occ, e_vir, r_occ, r2, r3, prec="fp64", l_osv=1e-4, relaxed=False):
             ctx_obj.build_osv(f_occ, e_vir, l_osv, B=B, r_occ=r_occ)
-            E, dB, df, de, _ = ctx_obj.energy_grad(r2, r3, prec, want_dB=True)
+            if relaxed:
+                if prec != "fp64":
+                    raise ValueError("the relaxed gradient runs in the FP64 form only")
+                E, dB, df, de, _, _ = ctx_obj.energy_grad_relaxed(r2, r3, want_dB=True)
+            else:
+                E, dB, df, de, _ = ctx_obj.energy_grad(r2, r3, prec, want_dB=True)
             fctx.save_for_backward(dB, df, de)
             return torch.tensor(E, dtype=torch.float64, device=B.device)
 
         @staticmethod
         def backward(fctx, g):
             dB, df, de = fctx.saved_tensors
-            return None, g * dB, g * df, g * de, None, None, None, None, None
+            return None, g * dB, g * df, g * de, None, None, None, None, None, None
 
     return _MBE3Energy

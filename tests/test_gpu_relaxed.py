@@ -84,3 +84,21 @@ def test_relaxed_rows_at_the_gradient_workload_shape():
     assert np.abs(got - ref).max() < 1e-9 * np.abs(ref).max()
     assert np.abs(ref - frozen).max() > 1e-6 * np.abs(ref).max()
     ctx.close()
+
+
+def test_autograd_function_relaxed_backward():
+    from paper_2603_16575_gb300 import Context, osvmp2
+    s = synth.make_system(5, 36, 70, seed=31, lam=1.5)
+    ctx = Context(0)
+    B = _t(s.B_full()).requires_grad_(True)
+    f = _t(s.f_occ).requires_grad_(True)
+    e = _t(s.e_vir).requires_grad_(True)
+    Fn = osvmp2.mbe3_energy_function()
+    E = Fn.apply(ctx, B, f, e, s.r_occ, 4.5, 4.0, "fp64", 1e-3, True)
+    (2.0 * E).backward()
+    E2, dB, df, de, _, _ = ctx.energy_grad_relaxed(4.5, 4.0)
+    _, dB0, _, _, _ = ctx.energy_grad(4.5, 4.0)
+    assert float(E) == E2
+    assert torch.allclose(B.grad, 2.0 * dB) and torch.allclose(f.grad, 2.0 * df) and torch.allclose(e.grad, 2.0 * de)
+    assert not torch.allclose(dB, dB0)
+    ctx.close()
