@@ -383,7 +383,9 @@ __device__ inline dfl cta_sum_df(dfl v, float* red) {
 // FP32 pairs in place of its FP64 elements (converted on the first step).
 // Outputs in FP64: d, e, tau, and reflector k in row k to the right of the
 // diagonal (A[k][k+1+t] = v_t, v_0 = 1), as cta_tridiag_sym.
-// sm: 4 n + 64 doubles (vp, wp, vk, p as pairs; reductions) + ntw * 32 * 33 doubles of tiles.
+// sm: 4 n + 64 doubles (vp, wp, vk, p as pairs; reductions) + ntw * 16 * 33 doubles of staging
+// tiles (each 32 x 32 tile goes through them in two halves of 16 rows, so that every warp of
+// the CTA fits one).
 // refl_df: reflector k stored as (hi, lo) pairs instead of FP64 (read by k_eig_back_df).
 template <int NTH>
 __device__ inline void cta_tridiag_sym_df(double* A, int n, int lda, double* d, double* e, double* tau, double* sm,
@@ -394,7 +396,7 @@ __device__ inline void cta_tridiag_sym_df(double* A, int n, int lda, double* d, 
   dfl* vk = wp + n;                        // current reflector v_k
   dfl* p = vk + n;                         // A_k v_k, then w_k
   float* red = reinterpret_cast<float*>(p + n);   // 64 doubles of room
-  dfl* tiles = reinterpret_cast<dfl*>(sm + 4 * n + 64);   // ntw x 32 x 33 pairs
+  dfl* tiles = reinterpret_cast<dfl*>(sm + 4 * n + 64);   // ntw x 16 x 33 pairs
   dfl* gpart = reinterpret_cast<dfl*>(gpart_d);
   dfl* Ad = reinterpret_cast<dfl*>(A);     // element (r, c) of the lower triangle at Ad[r * lda + c]
   __shared__ double s_tc, s_sc;
@@ -448,7 +450,7 @@ __device__ inline void cta_tridiag_sym_df(double* A, int n, int lda, double* d, 
     const int nb = (L + 31) >> 5;
     const int ntile = nb * (nb + 1) / 2;
     if (warp < ntw) {
-      dfl* tb = tiles + (size_t)warp * 32 * 33;
+      dfl* tb = tiles + (size_t)warp * 16 * 33;
       for (int tl = warp; tl < ntile; tl += ntw) {
         int bi = 0;
         while ((bi + 1) * (bi + 2) / 2 <= tl) bi++;
@@ -457,37 +459,47 @@ __device__ inline void cta_tridiag_sym_df(double* A, int n, int lda, double* d, 
         const int c = c0 + lane;
         const bool cin = c < n;
         const dfl nvpc = cin ? df_neg(vp[c]) : dfl{0.f, 0.f}, nwpc = cin ? df_neg(wp[c]) : dfl{0.f, 0.f};
-        float csh = 0.f, csl = 0.f;   // column sum, unnormalised pair
-        for (int i0 = 0; i0 < 32; i0 += 8) {   // eight rows' loads in flight before their arithmetic
-          dfl av[8];
-#pragma unroll
-          for (int u = 0; u < 8; u++) {
-            const int r = r0 + i0 + u;
-            av[u] = (cin && r < n && r >= c) ? Ad[(size_t)r * lda + c] : dfl{0.f, 0.f};
-          }
-#pragma unroll
-          for (int u = 0; u < 8; u++) {
-            const int r = r0 + i0 + u;
-            dfl a{0.f, 0.f};
-            if (cin && r < n && r >= c) {
-              a = av[u];
-              if (k > 0) {
-                a = df_fma2(vp[r], nwpc, wp[r], nvpc, a);
-                Ad[(size_t)r * lda + c] = a;
-              }
-              df_acc(csh, csl, a, vk[r]);
-            }
-            tb[(i0 + u) * 33 + lane] = (r > c) ? a : dfl{0.f, 0.f};   // the row sums take the strictly lower part
-          }
-        }
-        __syncwarp();
-        float rsh = 0.f, rsl = 0.f;
-#pragma unroll 8
-        for (int j = 0; j < 32; j++) df_acc(rsh, rsl, tb[lane * 33 + j], vk[min(c0 + j, n - 1)]);
         dfl* gp = gpart + (size_t)tl * 64;
+        float csh = 0.f, csl = 0.f;   // column sum, unnormalised pair
+        for (int h = 0; h < 32; h += 16) {
+          for (int i0 = h; i0 < h + 16; i0 += 8) {   // eight rows' loads in flight before their arithmetic
+            dfl av[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+              const int r = r0 + i0 + u;
+              av[u] = (cin && r < n && r >= c) ? Ad[(size_t)r * lda + c] : dfl{0.f, 0.f};
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+              const int r = r0 + i0 + u;
+              dfl a{0.f, 0.f};
+              if (cin && r < n && r >= c) {
+                a = av[u];
+                if (k > 0) {
+                  a = df_fma2(vp[r], nwpc, wp[r], nvpc, a);
+                  Ad[(size_t)r * lda + c] = a;
+                }
+                df_acc(csh, csl, a, vk[r]);
+              }
+              tb[(i0 - h + u) * 33 + lane] = (r > c) ? a : dfl{0.f, 0.f};   // the row sums take the strictly lower part
+            }
+          }
+          __syncwarp();
+          // row sums of these 16 rows: lane (g, rho) sums row rho over column half g, and the
+          // two halves are added in a fixed order
+          const int rho = lane & 15, g = lane >> 4;
+          float rsh = 0.f, rsl = 0.f;
+#pragma unroll 8
+          for (int j = 16 * g; j < 16 * g + 16; j++) df_acc(rsh, rsl, tb[rho * 33 + j], vk[min(c0 + j, n - 1)]);
+          const float oh = __shfl_xor_sync(0xffffffffu, rsh, 16), ol = __shfl_xor_sync(0xffffffffu, rsl, 16);
+          if (g == 0) {
+            float sh, st;
+            two_sum_f(rsh, oh, sh, st);
+            gp[32 + h + rho] = df_norm(sh, (rsl + ol) + st);
+          }
+          __syncwarp();
+        }
         gp[lane] = df_norm(csh, csl);
-        gp[32 + lane] = df_norm(rsh, rsl);
-        __syncwarp();
       }
     }
     __syncthreads();

@@ -240,7 +240,7 @@ __device__ void eig_topk(double* A, int n, double thr, int kmax, double* V, doub
   // tridiagonal carries ~48 bits): d and e (and the Gram-Schmidt dots) as pairs in
   // the tridiagonalisation's tile room, when it holds them and the scales stay
   // well inside FP32 range.
-  const bool inv_df = dfl_tridiag && ntw >= 2 && 2 * n + k <= ntw * 32 * 33 && s_norm > 1e-12 && s_norm < 1e12;
+  const bool inv_df = dfl_tridiag && ntw >= 2 && 2 * n + k <= ntw * 16 * 33 && s_norm > 1e-12 && s_norm < 1e12;
   dfl* ddf = reinterpret_cast<dfl*>(sm + 4 * n + 64);
   dfl* edf = ddf + n;
   dfl* Vd = reinterpret_cast<dfl*>(scr + 3 * n + eig_osv_work_doubles(n));   // kept vectors, pairs [k][n]
@@ -540,11 +540,13 @@ __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double th
   }
 }
 
-// Warps of 32 x 33-double tiles in the shared memory of the top-k path's
-// symmetric tridiagonalisation (0 when fewer than two fit).
-static int eig_tile_warps(int nv, double thr) {
+// Warps of rows x 33-double staging tiles in the shared memory of the top-k path's
+// symmetric tridiagonalisation (0 when fewer than two fit): 32 rows in FP64, 16 in
+// double-float (whose sweep stages each tile in two halves).
+static int eig_tile_rows(bool dfl_tridiag) { return dfl_tridiag ? 16 : 32; }
+static int eig_tile_warps(int nv, double thr, int rows) {
   if (nv <= ZSMEM_MAX || !(thr > 0.0)) return 0;
-  const size_t cap = (size_t)224 * 1024 / sizeof(double), base = (size_t)4 * nv + 64, tile = 32 * 33;
+  const size_t cap = (size_t)224 * 1024 / sizeof(double), base = (size_t)4 * nv + 64, tile = (size_t)rows * 33;
   const int ntw = cap > base ? (int)std::min<size_t>(NT_EIG / 32, (cap - base) / tile) : 0;
   return ntw >= 2 ? ntw : 0;
 }
@@ -553,9 +555,10 @@ void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, 
                     double* scratch, int* err, bool dfl_tridiag, cudaStream_t st) {
   const int zsmem = nv <= ZSMEM_MAX;
   size_t smem = (size_t)(4 * nv + 64) * sizeof(double);
-  const int ntw = eig_tile_warps(nv, thr);
+  const int rows = eig_tile_rows(dfl_tridiag);
+  const int ntw = eig_tile_warps(nv, thr, rows);
   if (zsmem) smem += (size_t)nv * (nv + 1) * sizeof(double);
-  else if (ntw >= 2) smem += (size_t)ntw * 32 * 33 * sizeof(double);
+  else if (ntw >= 2) smem += (size_t)ntw * rows * 33 * sizeof(double);
   cudaFuncSetAttribute(k_eig_osv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_eig_osv<<<nb, NT_EIG, smem, st>>>(T, nv, thr, kmax, V, w, k, scratch, err, zsmem, ntw, dfl_tridiag ? 1 : 0);
   note_launch(1);
@@ -564,7 +567,7 @@ void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, 
 void launch_eig_back(double* T, int nb, int nv, double thr, int kmax, double* V, const int* k, double* scratch,
                      bool dfl_tridiag, cudaStream_t st) {
   if (nv <= ZSMEM_MAX || !(thr > 0.0)) return;   // the other paths form the eigenvectors in k_eig_osv
-  const int ntw = eig_tile_warps(nv, thr);
+  const int ntw = eig_tile_warps(nv, thr, eig_tile_rows(dfl_tridiag));
   dim3 grid(nb, (std::min(kmax, nv) + EB_WARPS - 1) / EB_WARPS);
   const size_t ss = eig_osv_scratch_doubles(nv, kmax);
   if (dfl_tridiag && ntw >= 2 && nv <= EB_DF_MAXN) {   // reflectors stored as pairs
