@@ -84,7 +84,8 @@ typedef struct {
   int32_t no_autotune; /* 0 (default): the first osvmp2_mbe3_energy for a given fragment count and
                           largest pair order times the candidate launch shapes of the mixed
                           fragment solve and keeps the fastest (osvmp2_get_solve_plan); 1: fixed
-                          default shape.  The energies are identical either way. */
+                          default shape (2 CTAs per SM); 2: fixed shape of 3 CTAs per SM.  The
+                          energies are identical either way. */
   int32_t mem_cap_mib; /* 0 (default): no limit.  Otherwise the device memory this ctx may hold at
                           once (its cache, pair store and temporaries), in MiB; a request beyond it
                           fails with OSVMP2_E_NOMEM as a failed cudaMalloc would.  Library extension
@@ -149,7 +150,8 @@ void osvmp2_default_opts(osvmp2_opts *opts);
  * unchanged).  Takes effect for the next call; built OSVs and pair blocks are
  * kept. */
 int osvmp2_set_opts(osvmp2_ctx *ctx, const osvmp2_opts *opts);
-/* Launch shape of the last mixed MBE(3) fragment solve: out[0] CTAs per SM, out[1] tile set
+/* Launch shape of the last mixed MBE(3) fragment solve: out[0] CTAs per SM (1-3; 3 runs the
+ * solver built for 80 registers per thread), out[1] tile set
  * of its FP32 contractions (0: 64/96-wide tiles, 1: also 80-wide), out[2] 1 if chosen by the
  * autotuner, out[3] number of tuned (fragment count, largest pair order) keys.  out: 4 ints
  * (host).  The solve and the MBE(3) sum run as one CUDA graph, replayed with updated

@@ -1148,7 +1148,7 @@ void osvmp2_default_opts(osvmp2_opts* o) {
 static bool opts_valid(const osvmp2_opts& o) {
   return o.max_iter > 0 && o.tau_s >= 0 && o.tol_update > 0 && o.tol_energy > 0 && o.mem_cap_mib >= 0 &&
          (o.osv_method == 0 || o.osv_method == 1) && o.rosv_max_rows >= 0 &&
-         (o.osv_prec == OSVMP2_FP64 || o.osv_prec == OSVMP2_MIXED) && (o.no_autotune == 0 || o.no_autotune == 1);
+         (o.osv_prec == OSVMP2_FP64 || o.osv_prec == OSVMP2_MIXED) && (o.no_autotune >= 0 && o.no_autotune <= 2);
 }
 
 int osvmp2_get_solve_plan(const osvmp2_ctx* c, int32_t* out) {
@@ -1844,7 +1844,8 @@ static int mbe3_core(osvmp2_ctx* c, osvmp2_prec prec, double* e_out, osvmp2_mbe_
     for (int u = 0; u < 3; u++) orbs_h[3 * f + u] = c->frags[f].orbs[u];
     w_h[f] = c->frags[f].weight;
   }
-  int n_cta = std::max(1, std::min(nf, 2 * c->num_sms));   // scratch sized for the largest launch
+  // scratch sized for the largest launch: the mixed solver's autotuner tries up to 3 CTAs per SM
+  int n_cta = std::max(1, std::min(nf, (prec == OSVMP2_MIXED ? 3 : 2) * c->num_sms));
   Tmp d_orbs, d_order, d_w, d_out, d_cnt, d_scr;
   TRY(tmp_alloc(c, d_orbs, orbs_h.size() * sizeof(int)));
   TRY(tmp_alloc(c, d_order, nf * sizeof(int)));
@@ -1891,7 +1892,7 @@ static int mbe3_core(osvmp2_ctx* c, osvmp2_prec prec, double* e_out, osvmp2_mbe_
       const int nc = std::max(1, std::min(nf, pl.ctas_per_sm * c->num_sms));
       launch_frag_solve_mixed(tb, (const int*)d_orbs.p, (const int*)d_order.p, nf, max_m, o, sig.tab,
                               (double*)d_scr.p, nc, (int*)d_cnt.p, (FragOut*)d_out.p, tdst,
-                              (const long long*)d_toff.p, c->err_d, st);
+                              (const long long*)d_toff.p, c->err_d, pl.ctas_per_sm, st);
     };
     // autotuner: the first call for a (fragment count, largest pair order) times
     // every candidate plan on the full solve and keeps the fastest
@@ -1899,12 +1900,13 @@ static int mbe3_core(osvmp2_ctx* c, osvmp2_prec prec, double* e_out, osvmp2_mbe_
     auto it = c->plans.find(key);
     if (it == c->plans.end()) {
       SolvePlan best;
+      if (c->opts.no_autotune == 2) best.ctas_per_sm = 3;
       if (!c->opts.no_autotune) {
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         float best_ms = 1e30f;
-        for (int cps = 1; cps <= 2; cps++)
+        for (int cps = 1; cps <= 3; cps++)
           for (int tl = 0; tl <= 1; tl++) {
             SolvePlan pl;
             pl.ctas_per_sm = cps;

@@ -231,7 +231,8 @@ struct SigmaTable {
 };
 void launch_frag_solve_mixed(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
                              SolveOpts o, const SigmaTable& sgt, double* scratch, int n_cta, int* counter,
-                             FragOut* out, double* Tstore, const long long* Toff, int* err, cudaStream_t st);
+                             FragOut* out, double* Tstore, const long long* Toff, int* err, int ctas_per_sm,
+                             cudaStream_t st);
 // Row-major tiles of U-slice products (gproj_tc.cu): out[row * ld_out + col] = A_row . B_col,
 // A and B tensor maps over (possibly different) U slice stores with K = n_vir.
 int launch_rows_tc(const float* A, long long a_rows, const float* B, long long b_rows, int n_vir, int ldv,

@@ -91,7 +91,9 @@ __device__ __forceinline__ const float* sigma_lookup(const SigmaTable& st, int l
   return (a < st.off[lo + 1] && st.hi[a] == hi) ? st.base + st.pos[a] : nullptr;
 }
 
-__global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int* __restrict__ frag_orbs,
+// MINB: resident CTAs per SM the registers are budgeted for (2: 128 registers; 3: 80, with spills)
+template <int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_frag_solve_mixed(Tables t, const int* __restrict__ frag_orbs,
                                                          const int* __restrict__ order, int n_frag, int max_m,
                                                          SolveOpts o, SigmaTable sgt, double* scratch, int* counter,
                                                          FragOut* out, double* Tstore,
@@ -321,11 +323,16 @@ __global__ void __launch_bounds__(NT, 2) k_frag_solve_mixed(Tables t, const int*
 
 void launch_frag_solve_mixed(const Tables& t, const int* frag_orbs, const int* order, int n_frag, int max_m,
                              SolveOpts o, const SigmaTable& sgt, double* scratch, int n_cta, int* counter,
-                             FragOut* out, double* Tstore, const long long* Toff, int* err, cudaStream_t st) {
+                             FragOut* out, double* Tstore, const long long* Toff, int* err, int ctas_per_sm,
+                             cudaStream_t st) {
   if (n_frag == 0) return;
   cudaMemsetAsync(counter, 0, sizeof(int), st);
-  k_frag_solve_mixed<<<n_cta, NT, 0, st>>>(t, frag_orbs, order, n_frag, max_m, o, sgt, scratch, counter, out, Tstore,
-                                           Toff, err);
+  if (ctas_per_sm >= 3)
+    k_frag_solve_mixed<3><<<n_cta, NT, 0, st>>>(t, frag_orbs, order, n_frag, max_m, o, sgt, scratch, counter, out,
+                                                Tstore, Toff, err);
+  else
+    k_frag_solve_mixed<2><<<n_cta, NT, 0, st>>>(t, frag_orbs, order, n_frag, max_m, o, sgt, scratch, counter, out,
+                                                Tstore, Toff, err);
   note_launch(1);
 }
 

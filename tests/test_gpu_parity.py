@@ -289,6 +289,25 @@ def test_mixed_autotuned_graph_replay_is_exact():
     assert energies[0] == energies[1]
 
 
+def test_mixed_launch_shapes_give_identical_energies():
+    """The mixed solver built for 2 and for 3 resident CTAs per SM (128 and 80 registers per
+    thread) and launched at 1, 2 or 3 CTAs per SM computes the same energies bit for bit."""
+    s = synth.make_system(14, 60, 120, seed=43, lam=1.2)
+    got = []
+    for no_tune in (1, 2, 0):
+        ctx = _ctx(no_autotune=no_tune)
+        _build(ctx, s, 1e-4)
+        E, _ = ctx.mbe3_energy(4.5, 3.8, "mixed")
+        _, _, ef = ctx.fragment_results()
+        plan = ctx.solve_plan()
+        if no_tune:
+            assert plan["ctas_per_sm"] == no_tune + 1 and not plan["tuned"]
+        got.append((E, ef.copy()))
+        ctx.close()
+    for E, ef in got[1:]:
+        assert E == got[0][0] and np.array_equal(ef, got[0][1])
+
+
 def test_mixed_form_large_pair_orders():
     """Pairs of order above 192 (more OSVs per orbital than the 128-orbital workload): the
     mixed preconditioner (eigen-solver scratch sized at launch) and solver against the oracle."""
