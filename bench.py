@@ -41,7 +41,8 @@ FP32_SIMT_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12    # 128 FFMA/clk/SM at the 2070
 # from one single-pass ncu capture of the bench workload
 # (profiles/traffic_k_eig_osv_mbe3_n128.md); kernels without a capture of their
 # current code report null.
-KERNEL_TRAFFIC = {"k_eig_osv": 34.05e9 + 42.26e9}   # 128-orbital workload itself (1 pass), bytes per launch
+KERNEL_TRAFFIC = {"k_eig_osv": 34.27e9 + 43.22e9,          # 128-orbital workload itself (1 pass), bytes per launch
+                  "k_frag_solve_mixed": 20.24e9 + 12.24e9}   # the autotuner's plan (2 CTAs per SM)
 
 
 def load_peaks():
