@@ -102,3 +102,18 @@ def test_autograd_function_relaxed_backward():
     assert torch.allclose(B.grad, 2.0 * dB) and torch.allclose(f.grad, 2.0 * df) and torch.allclose(e.grad, 2.0 * de)
     assert not torch.allclose(dB, dB0)
     ctx.close()
+
+
+def test_untruncated_relaxed_equals_frozen_bit_for_bit():
+    """l_osv = 0 keeps every eigenvector: nothing is discarded, the response vanishes, and the
+    relaxed outputs are the frozen ones exactly, with no gap at the cut."""
+    from paper_2603_16575_gb300 import Context
+    s = synth.make_system(5, 30, 60, seed=2, lam=1.2, f_off=3e-2)
+    ctx = Context(0)
+    n_osv = _build(ctx, s, 0.0)
+    assert list(n_osv) == [30] * 5
+    E, dB, df, de, st, gap = ctx.energy_grad_relaxed(4.5, 3.8)
+    E0, dB0, df0, de0, _ = ctx.energy_grad(4.5, 3.8)
+    assert gap == float("inf") and E == E0
+    assert torch.equal(dB, dB0) and torch.equal(df, df0) and torch.equal(de, de0)
+    ctx.close()
