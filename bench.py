@@ -364,6 +364,7 @@ def run_gpu(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": 1e3 * t_tot / args.steps,
+        "step_ms": {"best": 1e3 * min(t_steps), "median": 1e3 * statistics.median(t_steps)},
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
