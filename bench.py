@@ -165,6 +165,21 @@ def dist_env():
     return rank, world, local
 
 
+def job_rate(t_local, units_local, world, device="cpu"):
+    """Whole-job rate of independent replicas: (units of all ranks, the slowest rank's time,
+    units / time).  Every rank calls it (two all-reduces when world > 1)."""
+    t, units = float(t_local), float(units_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        uu = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+        t, units = float(tt.item()), float(uu.item())
+    return units, t, units / t
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -271,12 +286,7 @@ def run_gpu(args):
                "fp64_form_ms_per_step": 1e3 * t64, "fp64_form_fragments_per_s": n_frag / t64}
         ctx.set_opts(osv_prec=osv_prec)
         ctx.profile(reset=True)
-    t_tot = sum(t_steps)
-    if world > 1:
-        tt = torch.tensor([t_tot], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_tot = float(tt.item())
-    value = world * n_frag * args.steps / t_tot
+    _, t_tot, value = job_rate(sum(t_steps), n_frag * args.steps, world, dev)
 
     # ---- end to end: host (pinned) inputs copied in and the energy read back every step
     pin = lambda a: torch.tensor(a).pin_memory()
@@ -299,7 +309,7 @@ def run_gpu(args):
                 d_B.copy_(h_B, non_blocking=True)
         E2, _, _ = step(B_in=d_B, env_in=d_env, f_in=d_f, e_in=d_e)   # E2 is read back to the host
         e2e_t.append(time.perf_counter() - t0)
-    e2e_value = world * n_frag / statistics.median(e2e_t)
+    _, _, e2e_value = job_rate(statistics.median(e2e_t), n_frag, world, dev)
 
     # ---- roofline of the dominant kernel (largest device time in the timed region)
     gemm = MEASURED_GEMM_PEAKS
