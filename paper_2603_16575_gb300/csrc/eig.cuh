@@ -759,7 +759,9 @@ __device__ inline int cta_syev_cm(T* A, int n, int lda, T* w, T* Z, int ldz, T* 
 // to swp (l, h pairs, capacity cap_s sweeps) and its rotations (c, s pairs,
 // capacity cap_r) to rot.  Returns 0 on convergence (*n_sw sweeps recorded, d
 // holds the eigenvalues), 1 if the sweep limit was reached, 2 if a record
-// would overflow.
+// would overflow.  With partial, the overflow return also sets *n_sw to the
+// sweeps recorded so far (d, e are then those after them, so a later call
+// continues the chase).
 // Givens rotation (c, s) with c x + s z = r >= 0, -s x + c z = 0.  FP64: one
 // reciprocal square root; FP32: a correctly rounded square root and one
 // division (unbiased rounding, so the accumulated rotations stay orthogonal
@@ -796,7 +798,7 @@ __device__ __forceinline__ void chase_rotation(float x, float z, float& c, float
 
 template <class T>
 __device__ inline int tridiag_qr_record(T* __restrict__ d, T* __restrict__ e, int n, int* __restrict__ swp, int cap_s,
-                                        T* __restrict__ rot, int cap_r, int* n_sw) {
+                                        T* __restrict__ rot, int cap_r, int* n_sw, bool partial = false) {
   const T eps = sizeof(T) == 8 ? T(2.220446049250313e-16) : T(1.1920929e-07);
   const int max_sweeps = 40 * n + 100;
   int ns = 0, nr = 0;
@@ -814,7 +816,10 @@ __device__ inline int tridiag_qr_record(T* __restrict__ d, T* __restrict__ e, in
       if (fabs(e[l - 1]) <= eps * (fabs(d[l - 1]) + fabs(d[l]))) { e[l - 1] = T(0.0); break; }
       l--;
     }
-    if (ns >= cap_s || nr + (h - l) > cap_r) return 2;
+    if (ns >= cap_s || nr + (h - l) > cap_r) {
+      if (partial) *n_sw = ns;
+      return 2;
+    }
     swp[2 * ns] = l;
     swp[2 * ns + 1] = h;
     ns++;
@@ -870,6 +875,53 @@ __device__ inline void apply_qr_record_cm(T* Z, int ldz, int n, const int* swp, 
     }
   }
   __syncthreads();
+}
+
+// Full symmetric eigen-decomposition as cta_syev_cm (FP64, Z column-major), with the
+// implicit QR split as in the batched routines above: thread 0 chases the tridiagonal
+// and records its rotations into the storage of A (no longer needed once Z is formed;
+// lda == n), and the CTA applies each full record to the rows of Z, so the CTA waits
+// once per record instead of once per rotation.  Returns 0 on success, 1 otherwise.
+template <int NTH = NT>
+__device__ inline int cta_syev_cm_rec(double* A, int n, double* w, double* Z, int ldz, double* e, double* tau,
+                                      double* sm) {
+  double* v = sm;
+  double* p = sm + n;
+  double* red = sm + 4 * n;
+  __shared__ int s_rc, s_ns;
+  if (n == 1) {
+    if (threadIdx.x == 0) { w[0] = A[0]; Z[0] = 1.0; }
+    __syncthreads();
+    return 0;
+  }
+  cta_tridiag<NTH>(A, n, n, w, e, tau, v, p, red);
+  cta_form_z_cm<NTH>(A, n, n, tau, Z, ldz, v, p);
+  for (int t = threadIdx.x; t < n; t += NTH) {   // the chase runs on shared copies of d and e
+    v[t] = w[t];
+    p[t] = (t + 1 < n) ? e[t] : 0.0;
+  }
+  __syncthreads();
+  const size_t room = (size_t)n * n;                       // doubles of A
+  const int cap_s = (int)(room / 8 > 16 ? room / 8 : 16);  // sweeps: two ints (one double) each
+  int* swp = reinterpret_cast<int*>(A);
+  double* rot = A + cap_s;
+  const int cap_r = (int)((room - (size_t)cap_s) / 2);     // rotations: (c, s) pairs
+  int rc = 1;
+  for (int chunk = 0; chunk < 64; chunk++) {
+    if (threadIdx.x == 0) {
+      int ns = 0;
+      s_rc = tridiag_qr_record(v, p, n, swp, cap_s, rot, cap_r, &ns, true);
+      s_ns = ns;
+    }
+    __syncthreads();
+    apply_qr_record_cm<NTH>(Z, ldz, n, swp, s_ns, rot);   // ends with a barrier
+    const int r = s_rc;
+    __syncthreads();                                      // every thread has read s_rc
+    if (r != 2) { rc = r; break; }
+  }
+  for (int t = threadIdx.x; t < n; t += NTH) w[t] = v[t];
+  __syncthreads();
+  return rc;
 }
 
 // ---------------------------------------------------------------- top-k

@@ -95,12 +95,15 @@ __device__ inline void sign_vectors(double* V, int n, int k) {
 
 // Full decomposition path (n <= ZSMEM_MAX with Z in shared memory, or any n
 // with Z in global scratch): eigenvalues sorted descending, then selection.
+// zcm: Z column-major (eigenvector-major), for Z in global memory, where the rotations of the
+// QR sweeps then touch contiguous columns; row-major otherwise (Z in shared memory).
 __device__ void eig_full_select(double* A, int n, double thr, int kmax, double* V, double* w, int* kout,
-                                double* scr, int* err, double* Zs, int ldz, double* sm) {
+                                double* scr, int* err, double* Zs, int ldz, double* sm, bool zcm) {
   double* e = scr;
   double* tau = scr + n;
   double* ww = scr + 2 * n;
-  int rc = cta_syev<NT_EIG>(A, n, n, ww, Zs, ldz, e, tau, sm);
+  int rc = zcm ? cta_syev_cm_rec<NT_EIG>(A, n, ww, Zs, ldz, e, tau, sm)
+               : cta_syev<NT_EIG>(A, n, n, ww, Zs, ldz, e, tau, sm);
   __shared__ int s_k;
   int* perm = reinterpret_cast<int*>(sm);   // sm reused: n ints (n <= 4n doubles)
   if (threadIdx.x == 0) {
@@ -127,7 +130,7 @@ __device__ void eig_full_select(double* A, int n, double thr, int kmax, double* 
   const int k = s_k;
   for (int idx = threadIdx.x; idx < n * k; idx += NT_EIG) {
     const int t = idx / n, r = idx % n;
-    V[(size_t)t * n + r] = Zs[(size_t)r * ldz + perm[t]];
+    V[(size_t)t * n + r] = zcm ? Zs[(size_t)perm[t] * ldz + r] : Zs[(size_t)r * ldz + perm[t]];
   }
   __syncthreads();
   sign_vectors(V, n, k);
@@ -531,12 +534,12 @@ __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double th
     const int ldz = nv + 1;
     double* Zs = dyn;
     double* sm = dyn + (size_t)nv * ldz;
-    eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zs, ldz, sm);
+    eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zs, ldz, sm, false);
   } else if (thr > 0.0) {
     eig_topk(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, dyn, ntw, dfl_tridiag);
   } else {
     double* Zg = scr + 3 * nv;
-    eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zg, nv, dyn);
+    eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zg, nv, dyn, true);
   }
 }
 
