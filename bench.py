@@ -316,7 +316,7 @@ def run_gpu(args):
     peak_fp64 = gemm["fp64_tflops"]
     peak_fp32 = gemm["fp32_tflops"] or FP32_SIMT_PEAK
     peak_split = gemm["tf32_tflops"] / 10.0       # split-TF32: 10 TF32 slice products per product
-    a1_flops = projection_flops(ctx, s, n_osv) * args.steps   # SURVEY-style A1: 2 n_aux n_vir N_i per orbital
+    a1_flops = projection_flops(ctx, s, n_osv) * args.steps   # algorithmic A1: 2 n_aux n_vir N_i per orbital
     kern = {
         # phase key: (kernel, bound, peak TFLOP/s, peak source, algorithmic flops in the timed region)
         "k_eig": ("k_eig_osv", "alu",
