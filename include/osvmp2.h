@@ -297,7 +297,9 @@ int osvmp2_energy_grad(osvmp2_ctx *ctx, double r2_cut, double r3_cut, osvmp2_pre
  *   dE/dB_x += 2 (Z_x / D) B_x, dE/de_a -= 2 sum_(x,b) (Z_x T_xx / D)_ab,
  *   dE/df_xx += 2 sum (Z_x T_xx / D),  D_ab = e_a + e_b - 2 f_xx.
  * FP64 form only (the pair store of an FP64 osvmp2_mbe3_energy), exact OSVs only
- * (opts.osv_method 0): OSVMP2_E_ARG otherwise.  OSVMP2_E_NUMERIC when the FP64
+ * (opts.osv_method 0): OSVMP2_E_ARG otherwise.  T_ii and its eigenpairs are formed again
+ * in FP64 inside the call; after a mixed OSV build (opts.osv_prec) they agree with the
+ * built OSVs to that build's accuracy.  OSVMP2_E_NUMERIC when the FP64
  * eigenvalues of T_xx give another count above l_osv than the built OSVs, or no
  * positive gap at the cut.  Outputs as osvmp2_energy_grad (overwritten). */
 int osvmp2_energy_grad_relaxed(osvmp2_ctx *ctx, double r2_cut, double r3_cut, double *e_out,
