@@ -686,8 +686,9 @@ __device__ inline int cta_syev(double* A, int n, int lda, double* w, double* Z, 
 // Z = H_0 H_1 ... H_{n-3} from the reflectors left in A, stored column-major
 // (Z[r][c] at Z[c * ldz + r]); a warp per column forms the dot products along
 // contiguous memory.  y, vs: shared scratch of n elements each.
-// T = double or float.
-template <int NTH = NT, class T>
+// T = double or float.  ROWV: reflector k in row k to the right of the diagonal
+// (cta_tridiag_sym) instead of below the sub-diagonal of column k (cta_tridiag).
+template <int NTH = NT, class T, bool ROWV = false>
 __device__ inline void cta_form_z_cm(const T* A, int n, int lda, const T* tau, T* Z, int ldz, T* y, T* vs) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = NTH / 32;
@@ -697,7 +698,8 @@ __device__ inline void cta_form_z_cm(const T* A, int n, int lda, const T* tau, T
     const T tk = tau[k];
     if (tk == T(0.0)) continue;
     const int L = n - k - 1;
-    for (int r = tid; r < L; r += NTH) vs[r] = (r == 0) ? T(1.0) : A[(size_t)(k + 1 + r) * lda + k];
+    for (int r = tid; r < L; r += NTH)
+      vs[r] = (r == 0) ? T(1.0) : (ROWV ? A[(size_t)k * lda + k + 1 + r] : A[(size_t)(k + 1 + r) * lda + k]);
     __syncthreads();
     // y_c = tau * sum_r v_r Z[k+1+r][k+1+c]: column k+1+c is contiguous
     for (int c = warp; c < L; c += NW) {
@@ -881,10 +883,12 @@ __device__ inline void apply_qr_record_cm(T* Z, int ldz, int n, const int* swp, 
 // implicit QR split as in the batched routines above: thread 0 chases the tridiagonal
 // and records its rotations into the storage of A (no longer needed once Z is formed;
 // lda == n), and the CTA applies each full record to the rows of Z, so the CTA waits
-// once per record instead of once per rotation.  Returns 0 on success, 1 otherwise.
+// once per record instead of once per rotation.  With ntw >= 2 warps of tiles in sm
+// (after its 4 n + 64 doubles) the tridiagonalisation is the fused sweep cta_tridiag_sym,
+// its partial sums in gpart.  Returns 0 on success, 1 otherwise.
 template <int NTH = NT>
 __device__ inline int cta_syev_cm_rec(double* A, int n, double* w, double* Z, int ldz, double* e, double* tau,
-                                      double* sm) {
+                                      double* sm, int ntw, double* gpart) {
   double* v = sm;
   double* p = sm + n;
   double* red = sm + 4 * n;
@@ -894,8 +898,13 @@ __device__ inline int cta_syev_cm_rec(double* A, int n, double* w, double* Z, in
     __syncthreads();
     return 0;
   }
-  cta_tridiag<NTH>(A, n, n, w, e, tau, v, p, red);
-  cta_form_z_cm<NTH>(A, n, n, tau, Z, ldz, v, p);
+  if (ntw >= 2) {
+    cta_tridiag_sym<NTH>(A, n, n, w, e, tau, sm, ntw, gpart);
+    cta_form_z_cm<NTH, double, true>(A, n, n, tau, Z, ldz, v, p);
+  } else {
+    cta_tridiag<NTH>(A, n, n, w, e, tau, v, p, red);
+    cta_form_z_cm<NTH>(A, n, n, tau, Z, ldz, v, p);
+  }
   for (int t = threadIdx.x; t < n; t += NTH) {   // the chase runs on shared copies of d and e
     v[t] = w[t];
     p[t] = (t + 1 < n) ? e[t] : 0.0;

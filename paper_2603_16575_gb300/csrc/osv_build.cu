@@ -97,12 +97,16 @@ __device__ inline void sign_vectors(double* V, int n, int k) {
 // with Z in global scratch): eigenvalues sorted descending, then selection.
 // zcm: Z column-major (eigenvector-major), for Z in global memory, where the rotations of the
 // QR sweeps then touch contiguous columns; row-major otherwise (Z in shared memory).
+// ntw (zcm only): warps of tiles after the 4 n + 64 doubles of sm for the fused sweep, whose
+// partial sums go to V (written only at the end); 0 for the plain tridiagonalisation.
 __device__ void eig_full_select(double* A, int n, double thr, int kmax, double* V, double* w, int* kout,
-                                double* scr, int* err, double* Zs, int ldz, double* sm, bool zcm) {
+                                double* scr, int* err, double* Zs, int ldz, double* sm, bool zcm, int ntw = 0) {
   double* e = scr;
   double* tau = scr + n;
   double* ww = scr + 2 * n;
-  int rc = zcm ? cta_syev_cm_rec<NT_EIG>(A, n, ww, Zs, ldz, e, tau, sm)
+  const int nbt = (n - 1 + 31) / 32;
+  if ((size_t)nbt * (nbt + 1) / 2 * 64 > (size_t)kmax * n) ntw = 0;   // the partial sums must fit V
+  int rc = zcm ? cta_syev_cm_rec<NT_EIG>(A, n, ww, Zs, ldz, e, tau, sm, ntw, V)
                : cta_syev<NT_EIG>(A, n, n, ww, Zs, ldz, e, tau, sm);
   __shared__ int s_k;
   int* perm = reinterpret_cast<int*>(sm);   // sm reused: n ints (n <= 4n doubles)
@@ -539,7 +543,7 @@ __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double th
     eig_topk(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, dyn, ntw, dfl_tridiag);
   } else {
     double* Zg = scr + 3 * nv;
-    eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zg, nv, dyn, true);
+    eig_full_select(A, nv, thr, kmax, Vb, wb, kout + b, scr, err, Zg, nv, dyn, true, ntw);
   }
 }
 
@@ -548,7 +552,8 @@ __global__ void __launch_bounds__(NT_EIG) k_eig_osv(double* T, int nv, double th
 // double-float (whose sweep stages each tile in two halves).
 static int eig_tile_rows(bool dfl_tridiag) { return dfl_tridiag ? 16 : 32; }
 static int eig_tile_warps(int nv, double thr, int rows) {
-  if (nv <= ZSMEM_MAX || !(thr > 0.0)) return 0;
+  (void)thr;   // the top-k path and the full path with Z in global memory both sweep in tiles
+  if (nv <= ZSMEM_MAX) return 0;
   const size_t cap = (size_t)224 * 1024 / sizeof(double), base = (size_t)4 * nv + 64, tile = (size_t)rows * 33;
   const int ntw = cap > base ? (int)std::min<size_t>(NT_EIG / 32, (cap - base) / tile) : 0;
   return ntw >= 2 ? ntw : 0;
@@ -558,7 +563,8 @@ void launch_eig_osv(double* T, int nb, int nv, double thr, int kmax, double* V, 
                     double* scratch, int* err, bool dfl_tridiag, cudaStream_t st) {
   const int zsmem = nv <= ZSMEM_MAX;
   size_t smem = (size_t)(4 * nv + 64) * sizeof(double);
-  const int rows = eig_tile_rows(dfl_tridiag);
+  // the full path (thr <= 0) sweeps in FP64 tiles whatever dfl_tridiag says
+  const int rows = (thr > 0.0) ? eig_tile_rows(dfl_tridiag) : eig_tile_rows(false);
   const int ntw = eig_tile_warps(nv, thr, rows);
   if (zsmem) smem += (size_t)nv * (nv + 1) * sizeof(double);
   else if (ntw >= 2) smem += (size_t)ntw * rows * 33 * sizeof(double);
