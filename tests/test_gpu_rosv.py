@@ -70,3 +70,24 @@ def test_too_few_rows_is_reported():
     ctx.set_opts(rosv_max_rows=0)
     assert _build(ctx, s, 1e-4).min() > 0
     ctx.close()
+
+
+def test_chain_800_randomized_osv_build_samples_match_oracle():
+    """The 800-orbital chain (6000 virtuals, 16000 aux, B regenerated, never stored) at its full
+    size, the randomized OSV build in the mixed form as bench.py times it: orbitals 0 and 400
+    against the oracle's randomized OSVs with the same Gaussian rows (counts exact, values and
+    kept-space projectors to the split-precision T_ii's accuracy)."""
+    from paper_2603_16575_gb300 import Context
+    s = synth.workload("chain_n800", seed=0)
+    ctx = Context(0, osv_prec="mixed", osv_method="randomized")
+    n_osv = ctx.build_osv(_t(s.f_occ), _t(s.e_vir), 1e-4, env=_t(s.env), seed=s.seed, n_aux=s.n_aux,
+                          r_occ=s.r_occ)
+    assert len(n_osv) == 800 and min(n_osv) > 0
+    for i in (0, 400):
+        Qg, wg = (x.cpu().numpy() for x in ctx.get_osv(i))
+        T = oracle.semicanonical_tii(s.B_block(i), s.e_vir, s.f_occ[i, i])
+        ro = oracle.randomized_osv(T, 1e-4, lambda k, i=i: synth.gauss_row(s.seed, i, k, s.n_vir))
+        assert Qg.shape[1] == ro.Q.shape[1]
+        assert np.abs(wg - ro.omega).max() < 1e-8 * ro.omega.max()
+        assert np.abs(Qg @ Qg.T - ro.Q @ ro.Q.T).max() < 1e-6
+    ctx.close()
