@@ -117,3 +117,24 @@ def test_untruncated_relaxed_equals_frozen_bit_for_bit():
     assert gap == float("inf") and E == E0
     assert torch.equal(dB, dB0) and torch.equal(df, df0) and torch.equal(de, de0)
     ctx.close()
+
+
+def test_relaxed_failure_statuses_and_recovery():
+    """Made on the host: the call before any OSV build is E_STATE; max_iter = 1 makes the
+    fragment solve fail with E_NOCONV; the ctx then gives the gradient with the default limit."""
+    from paper_2603_16575_gb300 import Context, osvmp2
+    ctx = Context(0)
+    with pytest.raises(osvmp2.OSVMP2Error) as ei:
+        ctx.energy_grad_relaxed(4.5, 3.8)
+    assert ei.value.code == osvmp2.STATUS_CODES["E_STATE"]
+    s = synth.make_system(6, 40, 80, seed=9, lam=1.2, f_off=3e-2)
+    _build(ctx, s, 1e-4)
+    ctx.set_opts(max_iter=1)
+    with pytest.raises(osvmp2.OSVMP2Error) as ei:
+        ctx.energy_grad_relaxed(4.5, 3.8)
+    assert ei.value.code == osvmp2.STATUS_CODES["E_NOCONV"]
+    ctx.set_opts(max_iter=100)
+    E, dB, df, de, st, gap = ctx.energy_grad_relaxed(4.5, 3.8)
+    assert st["n_unconverged"] == 0 and np.isfinite(E) and gap > 0
+    assert bool(torch.isfinite(dB).all()) and bool(torch.isfinite(de).all()) and bool(torch.isfinite(df).all())
+    ctx.close()
