@@ -29,18 +29,6 @@ struct BRows {   // B_i as an n_vir x n_aux matrix
   __device__ __forceinline__ double get(int a, int P) const { return s.get(i, a, P); }
 };
 
-// P_p = [Q_i Q_j] (n_vir x m); P_ii = Q_i
-__device__ inline View pbasis(const Tables& t, int i, int j) {
-  const int nv = t.n_vir, ni = t.n_osv[i];
-  if (i == j) return dense_view(t.Q[i], nv, ni, ni);
-  const int nj = t.n_osv[j];
-  View v;
-  v.rows = nv; v.cols = ni + nj; v.rs = nv; v.cs = ni;
-  v.b[0][0] = v.b[1][0] = Blk{t.Q[i], ni, 0};
-  v.b[0][1] = v.b[1][1] = Blk{t.Q[j], nj, 0};
-  return v;
-}
-
 // A = B_a^T P_p (n_aux x m) from the stored projections B_a^T Q_x ([n_aux][n_x])
 __device__ inline View proj_view(const RelaxKJob& jb, int side, int ni, int nj, int n_aux) {
   if (jb.i == jb.j) return dense_view(jb.bt_ii, n_aux, ni, ni);
